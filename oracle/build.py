@@ -1,0 +1,29 @@
+"""Compile the oracle (plain C++, no contraction of a*b+c) into a shared library.
+
+Test infrastructure: see ``oracle/__init__.py``.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "pm_oracle.cpp")
+OUT_DIR = os.path.join(HERE, "_build")
+OUT = os.path.join(OUT_DIR, "liboracle.so")
+
+FLAGS = ["-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+         "-fno-math-errno"]
+
+
+def build(force: bool = False) -> str:
+    """Build (if stale) and return the path of the oracle library."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
+        return OUT
+    tmp = OUT + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", *FLAGS, SRC, "-o", tmp])
+    os.replace(tmp, OUT)
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force=True))

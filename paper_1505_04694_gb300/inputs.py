@@ -1,0 +1,237 @@
+"""Seeded synthetic inputs: grids, jitter, the psi-Hessian metric, batch metrics.
+
+This module holds none of the adaptation arithmetic (no edge length, quality,
+orientation test or operator); it only produces meshes and metric fields that
+both the CUDA library and the CPU oracle consume.
+
+Workloads follow the paper's synthetic benchmark (Sec. 4): a structured
+triangulation of the unit square adapted to the Hessian of
+
+    psi(x, y) = 0.1 sin(50 x) + arctan(-0.1 / (2 x - sin(5 y)))
+
+at t = 0.  The solver-driven experiments of Sec. 4 (viscous fingering,
+structural optimisation) need solvers and data that are not part of this
+library; these seeded generators stand in for them.
+
+Random numbers come from splitmix64 (Steele, Lea, Flood 2014), a published
+counter-based generator: value i of stream s is mix(s + (i + 1) * golden).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n consecutive splitmix64 outputs of stream `seed` (uint64 array)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of splitmix64."""
+    z = splitmix64(seed, n, offset)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def grid_mesh(n: int):
+    """n x n vertices on the unit square, 2 (n-1)^2 counter-clockwise triangles.
+
+    Vertex id j*n + i sits at (i/(n-1), j/(n-1)).  Square (i, j), k = j*(n-1)+i,
+    gives triangles 2k = (v_ij, v_i+1j, v_i+1j+1) and 2k+1 = (v_ij, v_i+1j+1,
+    v_ij+1): the diagonal runs bottom-left to top-right.
+    """
+    s = np.arange(n, dtype=np.float64) / float(n - 1)
+    X, Y = np.meshgrid(s, s)  # Y[j, i] = s[j]
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1).copy()
+    jj, ii = np.meshgrid(np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    v00 = (jj * n + ii).ravel()
+    v10 = v00 + 1
+    v11 = v00 + n + 1
+    v01 = v00 + n
+    tri = np.empty((2 * (n - 1) ** 2, 3), np.int32)
+    tri[0::2] = np.stack([v00, v10, v11], axis=1)
+    tri[1::2] = np.stack([v00, v11, v01], axis=1)
+    return xy, tri
+
+
+def jitter_interior(xy: np.ndarray, n: int, amp: float, seed: int) -> np.ndarray:
+    """Move every interior grid vertex by U(-amp, amp) per coordinate."""
+    xy = xy.copy()
+    u = uniform01(seed, 2 * xy.shape[0]).reshape(-1, 2)
+    j, i = np.divmod(np.arange(xy.shape[0]), n)
+    inner = (i > 0) & (i < n - 1) & (j > 0) & (j < n - 1)
+    xy[inner] += (2.0 * u[inner] - 1.0) * amp
+    return xy
+
+
+def psi_hessian(x: np.ndarray, y: np.ndarray):
+    """Analytic Hessian of psi at t = 0.
+
+    With D = sin(5y) - 2x, arctan(0.1/D) equals a piecewise constant minus
+    arctan(10 D), so the Hessian is smooth across D = 0:
+      g' = -10/(1+100 D^2),  g'' = 2000 D/(1+100 D^2)^2
+      H_xx = -250 sin(50x) + 4 g'',  H_xy = -10 cos(5y) g'',
+      H_yy = 25 cos(5y)^2 g'' - 25 sin(5y) g'.
+    """
+    D = np.sin(5.0 * y) - 2.0 * x
+    den = 1.0 + 100.0 * D * D
+    g1 = -10.0 / den
+    g2 = 2000.0 * D / (den * den)
+    c5 = np.cos(5.0 * y)
+    hxx = -250.0 * np.sin(50.0 * x) + 4.0 * g2
+    hxy = -10.0 * c5 * g2
+    hyy = 25.0 * c5 * c5 * g2 - 25.0 * np.sin(5.0 * y) * g1
+    return hxx, hxy, hyy
+
+
+def psi(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """psi(x, y, t=0) itself (used only to check psi_hessian by differences)."""
+    return 0.1 * np.sin(50.0 * x) + np.arctan(-0.1 / (2.0 * x - np.sin(5.0 * y)))
+
+
+def _abs_hessian_metric(hxx, hxy, hyy, c, hmin, hmax):
+    """M = R diag(clamp(c |lambda_i|, 1/hmax^2, 1/hmin^2)) R^T per vertex."""
+    tr = 0.5 * (hxx + hyy)
+    dif = 0.5 * (hxx - hyy)
+    rad = np.sqrt(dif * dif + hxy * hxy)
+    l1 = tr + rad
+    l2 = tr - rad
+    theta = 0.5 * np.arctan2(2.0 * hxy, hxx - hyy)  # eigenvector of l1
+    ct, st = np.cos(theta), np.sin(theta)
+    lo, hi = 1.0 / (hmax * hmax), 1.0 / (hmin * hmin)
+    a = np.clip(c * np.abs(l1), lo, hi)
+    b = np.clip(c * np.abs(l2), lo, hi)
+    m00 = a * ct * ct + b * st * st
+    m01 = (a - b) * ct * st
+    m11 = a * st * st + b * ct * ct
+    return np.stack([m00, m01, m11], axis=1)
+
+
+def estimated_elements(xy: np.ndarray, tri: np.ndarray, m: np.ndarray) -> float:
+    """N = (4/sqrt 3) * sum_K area_K * mean_i sqrt(det M_i): the number of unit
+    equilateral metric triangles that tile the domain."""
+    p = xy[tri]
+    area = 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1])
+                        - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0]))
+    sd = np.sqrt(np.maximum(m[:, 0] * m[:, 2] - m[:, 1] ** 2, 0.0))
+    return float(4.0 / math.sqrt(3.0) * np.sum(area * sd[tri].mean(axis=1)))
+
+
+def psi_metric(xy: np.ndarray, tri: np.ndarray, target_elements: float,
+               hmin: float = 1e-3, hmax: float = 0.3) -> np.ndarray:
+    """|Hessian(psi)| metric scaled (bisection on c) so that the estimated
+    element count matches target_elements; sizes clamped to [hmin, hmax]."""
+    hxx, hxy, hyy = psi_hessian(xy[:, 0], xy[:, 1])
+    lo, hi = 1e-8, 1e8
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        n = estimated_elements(xy, tri, _abs_hessian_metric(hxx, hxy, hyy, mid, hmin, hmax))
+        if n < target_elements:
+            lo = mid
+        else:
+            hi = mid
+        if hi / lo < 1.0 + 1e-10:
+            break
+    return _abs_hessian_metric(hxx, hxy, hyy, math.sqrt(lo * hi), hmin, hmax)
+
+
+def uniform_metric(nv: int, h: float) -> np.ndarray:
+    m = np.zeros((nv, 3))
+    m[:, 0] = 1.0 / (h * h)
+    m[:, 2] = 1.0 / (h * h)
+    return m
+
+
+def constant_aniso_metric(nv: int, theta: float, aspect: float, h: float) -> np.ndarray:
+    """M = R(theta) diag(1/h^2, 1/(aspect h)^2) R(theta)^T at every vertex."""
+    a = 1.0 / (h * h)
+    b = 1.0 / ((aspect * h) ** 2)
+    c, s = math.cos(theta), math.sin(theta)
+    m = np.empty((nv, 3))
+    m[:, 0] = a * c * c + b * s * s
+    m[:, 1] = (a - b) * c * s
+    m[:, 2] = a * s * s + b * c * c
+    return m
+
+
+@dataclass
+class Params:
+    """Adaptation parameters (mirrors the library's pm_params)."""
+    L_low: float = 0.4
+    L_up: float = math.sqrt(2.0)
+    q_thresh: float = 0.7
+    max_iter: int = 10
+    max_smooth_sweeps: int = 10
+    seed: int = 1
+    opt_smooth_rounds: int = 0
+    max_rounds: int = 0
+
+
+@dataclass
+class Workload:
+    name: str
+    xy: np.ndarray
+    tri: np.ndarray
+    m: np.ndarray
+    params: Params
+
+
+def small_uniform(n: int = 41, h: float = 0.02, seed: int = 1) -> Workload:
+    """Unit-square n x n grid, uniform isotropic metric I/h^2 (the small case)."""
+    xy, tri = grid_mesh(n)
+    return Workload(f"uniform grid {n}x{n}, M=I/{h}^2", xy, tri, uniform_metric(xy.shape[0], h),
+                    Params(seed=seed))
+
+
+def psi_workload(n: int, target_elements: float, jitter: bool, seed: int) -> Workload:
+    """Unit-square n x n grid (interior jitter +-10% of the spacing if asked),
+    psi-Hessian metric scaled to about `target_elements` output triangles."""
+    xy, tri = grid_mesh(n)
+    if jitter:
+        xy = jitter_interior(xy, n, 0.1 / (n - 1), seed)
+    m = psi_metric(xy, tri, target_elements)
+    tag = "jittered " if jitter else ""
+    return Workload(f"psi-Hessian {tag}grid {n}x{n} -> ~{target_elements:.3g} triangles", xy, tri,
+                    m, Params(seed=seed))
+
+
+def anisotropic_2m() -> Workload:
+    """257 x 257 jittered grid (131,072 triangles), psi metric, ~2M triangles."""
+    return psi_workload(257, 2.0e6, True, 2)
+
+
+def anisotropic_20m() -> Workload:
+    """1025 x 1025 grid (2,097,152 triangles), psi metric, ~20M triangles."""
+    return psi_workload(1025, 2.0e7, False, 3)
+
+
+def batch_workloads(count: int = 512, seed: int = 5, tmin: float = 1e3, tmax: float = 2e5):
+    """`count` unit-square grids with log-uniform initial sizes in [tmin, tmax]
+    triangles, each with its own constant anisotropic metric: rotation
+    U[0, pi), aspect log-U[1, 100], size h log-U[0.002, 0.05]."""
+    out = []
+    for i in range(count):
+        s = (seed << 32) + i
+        u = uniform01(s, 4)
+        T = math.exp(math.log(tmin) + u[0] * (math.log(tmax) - math.log(tmin)))
+        n = int(round(math.sqrt(T / 2.0))) + 1
+        theta = math.pi * u[1]
+        aspect = math.exp(u[2] * math.log(100.0))
+        h = math.exp(math.log(0.002) + u[3] * (math.log(0.05) - math.log(0.002)))
+        xy, tri = grid_mesh(n)
+        m = constant_aniso_metric(xy.shape[0], theta, aspect, h)
+        out.append(Workload(f"batch[{i}] grid {n}x{n} theta={theta:.3f} a={aspect:.2f} h={h:.4f}",
+                            xy, tri, m, Params(seed=(s & 0xFFFFFFFF))))
+    return out

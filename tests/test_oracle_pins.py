@@ -1,0 +1,593 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU needed).
+
+Each test names what it pins: closed forms of the quality functional and the
+metric length (Sec. 2.2), published hash test vectors, brute force for the
+independent set (Sec. 3.2) and for the collapse/flip rules (Sec. 2.4), the
+hand-derived uniform-grid result, round-equals-sequential (Sec. 3.2-3.3) and
+mesh invariants.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1505_04694_gb300 import inputs
+from tests import meshcheck as MC
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def ulps(a, b):
+    return abs(a - b) / math.ulp(max(abs(a), abs(b)))
+
+
+# --- hash (Sec. 3.2 priorities) ----------------------------------------------
+
+def test_fmix32_published_vectors():
+    # MurmurHash3_x86_32 of the empty input is fmix32(seed); published test
+    # vectors: seed 0 -> 0, seed 1 -> 0x514E28B7, seed 0xFFFFFFFF -> 0x81F16F39.
+    assert O.fmix32(0) == 0
+    assert O.fmix32(1) == 0x514E28B7
+    assert O.fmix32(0xFFFFFFFF) == 0x81F16F39
+
+
+def test_fmix32_no_collisions_sample():
+    vals = {O.fmix32(i * 2654435761 & 0xFFFFFFFF) for i in range(20000)}
+    assert len(vals) == 20000
+
+
+# --- metric length and quality closed forms (Sec. 2.2) ----------------------
+
+def iso(h):
+    return np.array([1.0 / h ** 2, 0.0, 1.0 / h ** 2])
+
+
+def test_edge_length_isotropic_and_symmetric():
+    h = 0.02
+    a, b = np.array([0.1, 0.2]), np.array([0.13, 0.24])
+    L = O.edge_length(a, iso(h), b, iso(h))
+    assert abs(L - 0.05 / h) <= 4 * math.ulp(L)
+    ma, mb = np.array([3.0, 0.5, 2.0]), np.array([1.0, -0.2, 4.0])
+    assert O.edge_length(a, ma, b, mb) == O.edge_length(b, mb, a, ma)  # bitwise
+
+
+def test_edge_length_anisotropic_axis():
+    # M = diag(1/h1^2, 1/h2^2): an x-edge of length d has metric length d/h1.
+    h1, h2 = 0.01, 0.3
+    m = np.array([1 / h1 ** 2, 0.0, 1 / h2 ** 2])
+    assert abs(O.edge_length(np.zeros(2), m, np.array([0.02, 0.0]), m) - 2.0) < 1e-14
+    assert abs(O.edge_length(np.zeros(2), m, np.array([0.0, 0.6]), m) - 2.0) < 1e-14
+
+
+def equilateral(h, x0=0.3, y0=0.1, rot=0.0):
+    pts = []
+    for k in range(3):
+        a = rot + 2 * math.pi * k / 3
+        pts.append([x0 + h / math.sqrt(3) * math.cos(a), y0 + h / math.sqrt(3) * math.sin(a)])
+    return np.array(pts)
+
+
+@pytest.mark.parametrize("rot", [0.0, 0.3, 1.1, 2.5])
+def test_quality_equilateral_unit_metric_is_one(rot):
+    h = 0.02
+    xy = equilateral(h, rot=rot)
+    m = np.tile(iso(h), (3, 1))
+    for ids in ([0, 1, 2], [5, 9, 7], [11, 3, 8]):
+        q = O.tri_quality(ids, xy, m)
+        assert abs(q - 1.0) < 1e-13
+
+
+def test_quality_equilateral_under_anisotropic_metric():
+    # Map an equilateral unit-metric triangle by A; metric A^-T M A^-1 keeps q = 1.
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        A = rng.normal(size=(2, 2)) + 3 * np.eye(2)
+        if np.linalg.det(A) <= 0:
+            A[:, 0] *= -1
+        xy0 = equilateral(1.0)
+        xy = xy0 @ A.T
+        Ai = np.linalg.inv(A)
+        M = Ai.T @ np.eye(2) @ Ai
+        m = np.tile([M[0, 0], M[0, 1], M[1, 1]], (3, 1))
+        assert abs(O.tri_quality([0, 1, 2], xy, m) - 1.0) < 1e-12
+
+
+def test_quality_right_isosceles_closed_form():
+    # legs a, hypotenuse a*sqrt2, unit metric: P = a(2+sqrt2), area a^2/2,
+    # q = 12 sqrt3 (a^2/2) / P^2 * F(P/3).
+    for a in (0.5, 3.0 / (2 + math.sqrt(2)), 1.3):
+        xy = np.array([[0.0, 0.0], [a, 0.0], [0.0, a]])
+        m = np.tile([1.0, 0.0, 1.0], (3, 1))
+        P = a * (2 + math.sqrt(2))
+        x = P / 3
+        s = min(x, 1 / x)
+        F = (s * (2 - s)) ** 3
+        expect = 12 * math.sqrt(3) * (a * a / 2) / P ** 2 * F
+        assert abs(O.tri_quality([0, 1, 2], xy, m) - expect) < 1e-14
+    # at unit perimeter the value is 6 sqrt3 / (2 + sqrt2)^2
+    a = 3.0 / (2 + math.sqrt(2))
+    xy = np.array([[0.0, 0.0], [a, 0.0], [0.0, a]])
+    q = O.tri_quality([0, 1, 2], xy, np.tile([1.0, 0.0, 1.0], (3, 1)))
+    assert abs(q - 6 * math.sqrt(3) / (2 + math.sqrt(2)) ** 2) < 1e-14
+
+
+def test_quality_affine_invariance():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        xy = rng.uniform(0, 1, size=(3, 2))
+        if MC.exact_orient(*xy) <= 0:
+            xy = xy[[0, 2, 1]]
+        Ms = []
+        for _k in range(3):
+            B = rng.normal(size=(2, 2))
+            Ms.append(B @ B.T + 0.5 * np.eye(2))
+        m = np.array([[M[0, 0], M[0, 1], M[1, 1]] for M in Ms])
+        A = rng.normal(size=(2, 2)) + 2 * np.eye(2)
+        if np.linalg.det(A) <= 0:
+            A[:, 1] *= -1
+        Ai = np.linalg.inv(A)
+        m2 = []
+        for M in Ms:
+            N = Ai.T @ M @ Ai
+            m2.append([N[0, 0], N[0, 1], N[1, 1]])
+        q1 = O.tri_quality([0, 1, 2], xy, m)
+        q2 = O.tri_quality([0, 1, 2], xy @ A.T, np.array(m2))
+        assert abs(q1 - q2) <= 1e-12 * abs(q1)
+
+
+def test_quality_rotation_of_storage_does_not_matter():
+    rng = np.random.default_rng(2)
+    xy = np.array([[0.0, 0.0], [1.0, 0.1], [0.3, 0.9]])
+    m = np.array([[2.0, 0.3, 1.0], [1.5, -0.1, 2.0], [1.0, 0.0, 1.0]])
+    ids = np.array([4, 9, 2])
+    q = O.tri_quality(ids, xy, m)
+    for s in (1, 2):
+        perm = [(s + i) % 3 for i in range(3)]
+        assert O.tri_quality(ids[perm], xy[perm], m[perm]) == q  # bitwise
+    del rng
+
+
+# --- gradient (quality functional derivative) --------------------------------
+
+def random_triangle(rng):
+    xy = rng.uniform(0, 1, size=(3, 2))
+    if MC.exact_orient(*xy) <= 0:
+        xy = xy[[0, 2, 1]]
+    m = []
+    for _ in range(3):
+        B = rng.normal(size=(2, 2))
+        M = B @ B.T + 0.3 * np.eye(2)
+        m.append([M[0, 0], M[0, 1], M[1, 1]])
+    return xy, np.array(m) * rng.uniform(1, 50)
+
+
+def test_gradient_central_differences():
+    rng = np.random.default_rng(3)
+    ids = np.array([7, 3, 5])
+    worst = 0.0
+    for _ in range(40):
+        xy, m = random_triangle(rng)
+        q, g = O.tri_quality_grad(ids, xy, m)
+        assert q == O.tri_quality(ids, xy, m)
+        fd = np.zeros((3, 5))
+        for v in range(3):
+            for j in range(5):
+                base = xy[v, j] if j < 2 else m[v, j - 2]
+                h = 1e-6 * max(abs(base), 1e-3)
+                xp, mp = xy.copy(), m.copy()
+                xm, mm = xy.copy(), m.copy()
+                if j < 2:
+                    xp[v, j] += h
+                    xm[v, j] -= h
+                else:
+                    mp[v, j - 2] += h
+                    mm[v, j - 2] -= h
+                fd[v, j] = (O.tri_quality(ids, xp, mp) - O.tri_quality(ids, xm, mm)) / (2 * h)
+        # compare per component class (coordinates / metric) in relative norm
+        for sl in (slice(0, 2), slice(2, 5)):
+            err = np.linalg.norm(g[:, sl] - fd[:, sl]) / max(np.linalg.norm(fd[:, sl]), 1e-300)
+            worst = max(worst, err)
+    assert worst < 1e-6
+
+
+def test_gradient_matches_autodiff():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    ids = [2, 0, 1]  # canonical rotation starts at stored slot 1
+
+    def q_torch(xy, m):
+        order = [1, 2, 0]
+        p, mm = xy[order], m[order]
+        k = (mm[0] + mm[1] + mm[2]) / 3.0
+        P = 0
+        for a, b in ((0, 1), (1, 2), (2, 0)):
+            d = p[b] - p[a]
+            P = P + torch.sqrt(k[0] * d[0] * d[0] + 2 * k[1] * d[0] * d[1] + k[2] * d[1] * d[1])
+        o = (p[1, 0] - p[0, 0]) * (p[2, 1] - p[0, 1]) - (p[1, 1] - p[0, 1]) * (p[2, 0] - p[0, 0])
+        AM = torch.sqrt(k[0] * k[2] - k[1] * k[1]) * 0.5 * o
+        x = P / 3.0
+        s = torch.where(x <= 1.0, x, 1.0 / x)
+        F = (s * (2.0 - s)) ** 3
+        return 12.0 * math.sqrt(3.0) * AM / (P * P) * F
+
+    for _ in range(40):
+        xy, m = random_triangle(rng)
+        q, g = O.tri_quality_grad(np.array(ids), xy, m)
+        txy = torch.tensor(xy, dtype=torch.float64, requires_grad=True)
+        tm = torch.tensor(m, dtype=torch.float64, requires_grad=True)
+        tq = q_torch(txy, tm)
+        tq.backward()
+        ref = np.concatenate([txy.grad.numpy(), tm.grad.numpy()], axis=1)
+        assert abs(float(tq.detach()) - q) <= 1e-13 * abs(q)
+        assert np.linalg.norm(g - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+# --- independent set (Sec. 3.2) -----------------------------------------------
+
+def test_independent_set_brute_force():
+    w = inputs.psi_workload(9, 300, True, 7)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    nv = w.xy.shape[0]
+    NN, _ = MC.adjacency([tuple(t) for t in w.tri], nv)
+    rng = np.random.default_rng(5)
+    for trial in range(30):
+        cand = (rng.uniform(size=nv) < rng.uniform(0.2, 1.0)).astype(np.uint8)
+        seed, r = int(rng.integers(0, 2 ** 32)), int(rng.integers(0, 1000))
+        S = om.independent_set(cand, seed, r)
+        pr = [O.prio(v, seed, r) for v in range(nv)]
+        for v in range(nv):
+            local_max = bool(cand[v]) and all(not cand[u] or pr[u] < pr[v] for u in NN[v])
+            assert bool(S[v]) == local_max
+            if S[v]:
+                assert not any(S[u] for u in NN[v])  # independence
+        if cand.any():
+            assert S.any()  # the global maximum candidate is always selected
+
+
+# --- small uniform case: hand-derived result ---------------------------------
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = v.strip()
+    return vals
+
+
+def test_small_uniform_exact_result():
+    g = read_golden("small_uniform_counts.txt")
+    w = inputs.small_uniform()
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    st = om.adapt(O.make_params())
+    xy, tri, m = om.get_mesh()
+    assert xy.shape[0] == int(g["vertices"])
+    assert tri.shape[0] == int(g["triangles"])
+    assert st["splits"] == int(g["splits"])
+    assert st["collapses"] == int(g["collapses"]) and st["flips"] == int(g["flips"])
+    assert st["moves"] == int(g["moves"]) and st["converged"] == 1
+    ok, why = MC.unit_square_ok(xy, tri)
+    assert ok, why
+    assert MC.fast_conformity(tri, xy.shape[0])[0]
+
+
+# --- refinement templates (Sec. 2.4.2) ---------------------------------------
+
+def _single_triangle_refine(xy, m, L_up):
+    om = O.OracleMesh(xy, np.array([[0, 1, 2]])).set_metric(m)
+    om.refine(O.make_params(L_low=1e-9, L_up=L_up, max_rounds=1))
+    return om.get_mesh()
+
+
+def test_refine_three_splits_gives_four_equal_children():
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.25, 0.75]])
+    m = np.tile([1.0, 0.0, 1.0], (3, 1))
+    oxy, tri, om_ = _single_triangle_refine(xy, m, 0.5)
+    assert tri.shape[0] == 4 and oxy.shape[0] == 6
+    p = oxy[tri]
+    area = 0.5 * ((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1])
+                  - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0]))
+    assert np.all(area == 0.375 / 4)  # dyadic coordinates: exact
+    mids = {tuple(r) for r in oxy[3:]}
+    assert mids == {(0.5, 0.0), (0.625, 0.375), (0.125, 0.375)}
+
+
+def test_refine_one_and_two_splits():
+    # anisotropic metric makes only x-extended edges long
+    m = np.tile([100.0, 0.0, 0.01], (3, 1))
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    oxy, tri, _ = _single_triangle_refine(xy, m, 5.0)  # edges with |dx| = 1 exceed
+    # edges (0,1) and (1,2) have |dx| = 1 -> two splits -> three children
+    assert tri.shape[0] == 3 and oxy.shape[0] == 5
+    assert MC.valid_triangulation(oxy, [tuple(t) for t in tri])[0]
+    m2 = np.tile([100.0, 0.0, 0.01], (3, 1))
+    xy2 = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0]])
+    oxy2, tri2, _ = _single_triangle_refine(xy2, m2, 5.0)  # only (0,1),(2,0) have |dx|=1
+    assert tri2.shape[0] == 3
+    m3 = np.tile([1.0, 0.0, 100.0], (3, 1))
+    oxy3, tri3, _ = _single_triangle_refine(xy2, m3, 5.0)  # only (1,2) has |dy| = 1 ... and (2,0)
+    assert tri3.shape[0] == 3
+    xy4 = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 0.05]])
+    oxy4, tri4, _ = _single_triangle_refine(xy4, m3, 5.0)  # no |dy| = 1 edge
+    assert tri4.shape[0] == 1
+    xy5 = np.array([[0.0, 0.0], [0.05, 0.0], [0.05, 1.0]])
+    oxy5, tri5, _ = _single_triangle_refine(xy5, m3, 5.0)  # (1,2),(2,0) long
+    assert tri5.shape[0] == 3
+    xy6 = np.array([[0.0, 0.0], [0.05, 0.5], [0.0, 1.0]])
+    oxy6, tri6, _ = _single_triangle_refine(xy6, m3, 7.5)  # only (2,0) has |dy| = 1
+    assert tri6.shape[0] == 2 and oxy6.shape[0] == 4
+
+
+# --- brute force for the collapse and flip rules (Sec. 2.4.1, 2.4.3) ---------
+
+def tiny_meshes():
+    out = []
+    for n, seed in ((5, 11), (6, 12), (6, 13), (7, 14)):
+        xy, tri = inputs.grid_mesh(n)
+        xy = inputs.jitter_interior(xy, n, 0.3 / (n - 1), seed)
+        rng = np.random.default_rng(seed)
+        m = []
+        for _ in range(xy.shape[0]):
+            th = rng.uniform(0, math.pi)
+            h1 = (1.0 / (n - 1)) * rng.uniform(1.0, 4.0)
+            h2 = h1 * rng.uniform(1.0, 3.0)
+            c, s = math.cos(th), math.sin(th)
+            a, b = 1 / h1 ** 2, 1 / h2 ** 2
+            m.append([a * c * c + b * s * s, (a - b) * c * s, a * s * s + b * c * c])
+        out.append((xy, tri, np.array(m)))
+    return out
+
+
+def brute_collapse_valid(xy, tris, corner, v, w, L_up, elen):
+    NN, NE = MC.adjacency(tris, xy.shape[0])
+    bedges = MC.boundary_edges(tris)
+    bverts = {a for e in bedges for a in e}
+    is_bedge = (v, w) in bedges or (w, v) in bedges
+    if corner[v]:
+        return False
+    if v in bverts and not is_bedge:
+        return False
+    new = []
+    for t in tris:
+        if v in t and w in t:
+            continue
+        new.append(tuple(w if a == v else a for a in t))
+    ok, _ = MC.valid_triangulation(xy, new)
+    if not ok:
+        return False
+    if MC.total_area_exact(xy, new) != MC.total_area_exact(xy, tris):
+        return False
+    nb = MC.boundary_edges(new)
+    for a, b in nb:
+        if not MC.on_square_side(xy[a], xy[b]):
+            return False
+    for x in NN[v]:
+        if x != w and x not in NN[w] and elen(w, x) > L_up:
+            return False
+    return True
+
+
+def test_collapse_rule_brute_force():
+    checked = 0
+    for xy, tri, m in tiny_meshes():
+        om = O.OracleMesh(xy, tri).set_metric(m)
+        tris = [tuple(int(a) for a in t) for t in tri]
+        raw = om.get_raw()
+        corner = (raw["vflag"] & 2) > 0
+        NN, _ = MC.adjacency(tris, xy.shape[0])
+        bedges = MC.boundary_edges(tris)
+        bverts = {a for e in bedges for a in e}
+        p = O.make_params(L_low=1.0, L_up=2.5)
+
+        def elen(a, b):
+            return O.edge_length(xy[a], m[a], xy[b], m[b])
+
+        for v in range(xy.shape[0]):
+            cands = []
+            for w in sorted(NN[v]):
+                if v in bverts and not ((v, w) in bedges or (w, v) in bedges):
+                    continue
+                L = elen(v, w)
+                if L < p.L_low:
+                    cands.append((L, w))
+            cands.sort()
+            expect = -1
+            if not corner[v]:
+                for L, w in cands:
+                    if brute_collapse_valid(xy, tris, corner, v, w, p.L_up, elen):
+                        expect = w
+                        break
+            assert om.coarsen_target(v, p) == expect, (v, cands)
+            checked += len(cands)
+    assert checked > 50
+
+
+def test_flip_rule_brute_force():
+    n_flip = 0
+    for xy, tri, m in tiny_meshes():
+        om = O.OracleMesh(xy, tri).set_metric(m)
+        tris = [tuple(int(a) for a in t) for t in tri]
+        NN, NE = MC.adjacency(tris, xy.shape[0])
+        p = O.make_params(q_thresh=1.0)
+
+        def q_of(t):
+            return O.tri_quality(np.array(t), xy[list(t)], m[list(t)])
+
+        for v in range(xy.shape[0]):
+            best, bw = None, -1
+            for w in sorted(NN[v]):
+                K1 = [t for t in tris if any(t[i] == v and t[(i + 1) % 3] == w for i in range(3))]
+                K2 = [t for t in tris if any(t[i] == w and t[(i + 1) % 3] == v for i in range(3))]
+                if not K1 or not K2:
+                    continue
+                c = [a for a in K1[0] if a not in (v, w)][0]
+                d = [a for a in K2[0] if a not in (v, w)][0]
+                if c in NN[d]:
+                    continue
+                T1, T2 = (v, d, c), (d, w, c)
+                if not (MC.exact_orient(xy[v], xy[d], xy[c]) > 0
+                        and MC.exact_orient(xy[d], xy[w], xy[c]) > 0):
+                    continue
+                qold = min(q_of(K1[0]), q_of(K2[0]))
+                if not qold < p.q_thresh:
+                    continue
+                gain = min(q_of(T1), q_of(T2)) - qold
+                if gain > 0 and (best is None or gain > best):
+                    best, bw = gain, w
+            got, c, d = om.swap_target(v, p)
+            assert got == bw, v
+            n_flip += got >= 0
+    assert n_flip > 20
+
+
+# --- round-equals-sequential and invariants ---------------------------------
+
+@pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (25, 8000, 22), (33, 20000, 2)])
+def test_round_equals_sequential_and_invariants(n, T, seed):
+    w = inputs.psi_workload(n, T, True, seed)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    om.set_check_sequential(True)
+    st = om.adapt(O.make_params(seed=seed))
+    assert not om.seq_failed()
+    assert om.check() == 0
+    xy, tri, m = om.get_mesh()
+    ok, why = MC.unit_square_ok(xy, tri)
+    assert ok, why
+    assert MC.fast_conformity(tri, xy.shape[0])[0]
+    assert st["collapses"] > 0 and st["flips"] > 0 and st["splits"] > 0 and st["moves"] > 0
+
+
+def test_operators_keep_invariants_round_by_round():
+    w = inputs.psi_workload(21, 6000, True, 9)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    om.set_check_sequential(True)
+    for op in ("refine", "coarsen", "swap", "refine", "coarsen", "swap", "smooth"):
+        for _ in range(3):
+            getattr(om, op)(O.make_params(seed=9, max_rounds=2))
+            assert om.check() == 0, op
+    assert not om.seq_failed()
+
+
+# --- smoothing (Sec. 2.4.4) ---------------------------------------------------
+
+def hex_patch(offset):
+    """Centre vertex 0 with a regular hexagon ring 1..6 (radius 1)."""
+    ring = [[math.cos(k * math.pi / 3), math.sin(k * math.pi / 3)] for k in range(6)]
+    xy = np.array([[offset[0], offset[1]]] + ring)
+    tri = np.array([[0, 1 + k, 1 + (k + 1) % 6] for k in range(6)])
+    return xy, tri
+
+
+def test_laplacian_smoothing_moves_to_centroid_uniform_metric():
+    xy, tri = hex_patch((0.21, -0.13))
+    m = np.tile([1.0, 0.0, 1.0], (7, 1))
+    om = O.OracleMesh(xy, tri).set_metric(m)
+    q_before = om.quality_elems().min()
+    st = om.smooth(O.make_params(q_thresh=1.01, max_smooth_sweeps=1))
+    raw = om.get_raw()
+    assert st["moves"] == 1
+    assert np.abs(raw["xy"][0]).max() < 1e-15  # centroid of the ring is the origin
+    np.testing.assert_array_equal(raw["m"][0], [1.0, 0.0, 1.0])
+    assert om.quality_elems().min() > q_before
+
+
+def test_laplacian_smoothing_metric_weighted_target():
+    # Ring metric is uniform (A); the centre carries metric B.  With every edge
+    # metric W = (A + B)/2 identical, the weighted mean is the plain centroid.
+    xy, tri = hex_patch((0.1, 0.05))
+    m = np.tile([2.0, 0.5, 3.0], (7, 1))
+    m[0] = [1.0, -0.2, 1.5]
+    om = O.OracleMesh(xy, tri).set_metric(m)
+    om.smooth(O.make_params(q_thresh=1.01, max_smooth_sweeps=1))
+    raw = om.get_raw()
+    if raw["xy"][0].any():
+        assert np.abs(raw["xy"][0]).max() < 1e-14
+
+
+def test_smoothing_never_lowers_ball_min_quality():
+    w = inputs.psi_workload(25, 8000, True, 4)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    p = O.make_params(seed=4)
+    om.refine(p)
+    om.swap(p)
+    q0 = om.quality_elems()
+    st = om.smooth(p)
+    q1 = om.quality_elems()
+    assert st["moves"] > 0
+    assert np.nanmin(q1) >= np.nanmin(q0)
+    assert om.check() == 0
+
+
+def test_opt_smoothing_increases_quality_sum():
+    w = inputs.psi_workload(25, 8000, True, 6)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    p = O.make_params(seed=6, opt_smooth_rounds=20)
+    om.refine(p)
+    s0 = om.quality(grad=False)
+    qmin0 = np.nanmin(om.quality_elems())
+    st = om.opt_smooth(p)
+    assert st["moves"] > 0
+    assert om.quality(grad=False) > s0
+    assert np.nanmin(om.quality_elems()) >= qmin0
+    assert om.check() == 0
+
+
+# --- mesh-level gradient -------------------------------------------------------
+
+def test_mesh_gradient_central_differences():
+    w = inputs.psi_workload(9, 300, True, 8)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    qs, dxy, dm = om.quality()
+    rng = np.random.default_rng(8)
+    for v in rng.choice(w.xy.shape[0], 10, replace=False):
+        for j in range(5):
+            xy, m = w.xy.copy(), w.m.copy()
+            # step relative to the local scale: the shortest incident edge for
+            # coordinates, the metric's largest diagonal entry for metric entries
+            nbr = np.unique(w.tri[(w.tri == v).any(axis=1)])
+            nbr = nbr[nbr != v]
+            lmin = np.min(np.hypot(*(w.xy[nbr] - w.xy[v]).T))
+            h = 1e-6 * (lmin if j < 2 else max(m[v, 0], m[v, 2]))
+            vals = []
+            for sgn in (1, -1):
+                xy2, m2 = xy.copy(), m.copy()
+                if j < 2:
+                    xy2[v, j] += sgn * h
+                else:
+                    m2[v, j - 2] += sgn * h
+                o2 = O.OracleMesh(xy2, w.tri).set_metric(m2)
+                vals.append(o2.quality(grad=False))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = dxy[v, j] if j < 2 else dm[v, j - 2]
+            assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-6)
+
+
+# --- input generator -----------------------------------------------------------
+
+def test_psi_hessian_matches_differences():
+    rng = np.random.default_rng(9)
+    x = rng.uniform(0, 1, 400)
+    y = rng.uniform(0, 1, 400)
+    D = np.sin(5 * y) - 2 * x
+    keep = np.abs(D) > 0.05
+    x, y = x[keep], y[keep]
+    h = 1e-4
+    hxx, hxy, hyy = inputs.psi_hessian(x, y)
+    f = inputs.psi
+    fxx = (f(x + h, y) - 2 * f(x, y) + f(x - h, y)) / h ** 2
+    fyy = (f(x, y + h) - 2 * f(x, y) + f(x, y - h)) / h ** 2
+    fxy = (f(x + h, y + h) - f(x + h, y - h) - f(x - h, y + h) + f(x - h, y - h)) / (4 * h * h)
+    for a, b in ((hxx, fxx), (hxy, fxy), (hyy, fyy)):
+        assert np.all(np.abs(a - b) <= 1e-3 * (1 + np.abs(a)))
+
+
+def test_psi_metric_hits_target_estimate():
+    w = inputs.psi_workload(65, 1.0e5, True, 2)
+    n = inputs.estimated_elements(w.xy, w.tri, w.m)
+    assert abs(n / 1.0e5 - 1) < 1e-6
+    det = w.m[:, 0] * w.m[:, 2] - w.m[:, 1] ** 2
+    assert (w.m[:, 0] > 0).all() and (det > 0).all()
