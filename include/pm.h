@@ -1,0 +1,196 @@
+/*
+ * pm.h - C interface of the GB300 library for round-based independent-set
+ * 2D anisotropic mesh adaptation.
+ *
+ * The method is that of Rokos, Gorman, Jensen and Kelly, "Thread Parallelism
+ * for Highly Irregular Computation in Anisotropic Mesh Adaptation":
+ *   - Algorithm 1 (Sec. 2.3): repeat {coarsen; swap; refine} until no change
+ *     or the iteration limit, then smooth;
+ *   - the four kernels of Sec. 2.4 (edge collapse, edge split with refinement
+ *     templates, edge flip, quality-constrained vertex smoothing), each swept
+ *     until nothing changes (propagation, Sec. 2.4.5);
+ *   - rounds of independent sets of the vertex graph (Sec. 3.2), worklists
+ *     built by atomic fetch-and-add (Sec. 3.4) and a deferred update that
+ *     commits adjacency changes after each set (Sec. 3.3).
+ * Inputs follow the problem statement of Sec. 2.3: a triangulation M and a
+ * node-wise metric tensor field S.
+ *
+ * Conventions shared by every entry point:
+ *   - All floating point is IEEE binary64.  Vertex coordinates are interleaved
+ *     (x0, y0, x1, y1, ...).  The metric of a vertex is the symmetric positive
+ *     definite 2x2 tensor [[m00, m01], [m01, m11]], stored as (m00, m01, m11).
+ *     Triangles are int32 vertex-id triples in counter-clockwise order.
+ *   - Plain pointers are HOST memory and are only read or written during the
+ *     call; the library keeps no pointer to them.  Entry points ending in _dev
+ *     take DEVICE pointers on the mesh's device, used in stream order on the
+ *     mesh's stream (the call returns after the stream has been synchronised
+ *     unless stated otherwise).
+ *   - The library owns all device state of a mesh (released by
+ *     pm_mesh_destroy).  A handle is not thread-safe; different handles may be
+ *     used from different threads.
+ *   - Every call returns a pm_status.  Invalid arguments are rejected before
+ *     any device work.  Errors detected on the device (capacity, timeout)
+ *     come back through a status word; pm_last_error() gives a message.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pm_mesh pm_mesh;
+
+typedef enum {
+  PM_OK = 0,
+  PM_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter */
+  PM_ERR_INVALID_MESH = 2,  /* ids out of range, inverted or overlapping
+                               elements, non-manifold vertex, isolated vertex */
+  PM_ERR_OOM = 3,           /* device allocation failed */
+  PM_ERR_CAPACITY = 4,      /* a fixed capacity was exceeded */
+  PM_ERR_CUDA = 5,          /* CUDA runtime error */
+  PM_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+} pm_status;
+
+/* Adaptation parameters.
+ *   L_low, L_up      metric edge-length bounds: edges shorter than L_low are
+ *                    collapsed (Sec. 2.4.1), longer than L_up split (2.4.2);
+ *                    0 < L_low < L_up.
+ *   q_thresh         quality below which an element's edges may be flipped
+ *                    (2.4.3) and its vertices smoothed (2.4.4); >= 0.
+ *   max_iter         iteration limit of Algorithm 1 (>= 0).
+ *   max_smooth_sweeps  limit of Laplacian smoothing sweeps (>= 0).
+ *   seed             seed of the independent-set priorities.
+ *   opt_smooth_rounds  rounds of optimisation-based smoothing run after the
+ *                    Laplacian sweeps (0 = none).
+ *   max_rounds       cap on the rounds of one operator call (0 = none). */
+typedef struct {
+  double L_low, L_up, q_thresh;
+  int32_t max_iter, max_smooth_sweeps;
+  uint32_t seed;
+  int32_t opt_smooth_rounds;
+  int32_t max_rounds;
+} pm_params;
+
+/* Counters of one call: rounds executed (every round that formed a
+ * non-empty candidate set), operations applied, whether Algorithm 1 stopped
+ * because an iteration changed nothing, and wall time in milliseconds
+ * (host clock around the call, device synchronised). */
+typedef struct {
+  int64_t rounds, collapses, splits, flips, moves;
+  int32_t converged;
+  double ms;
+} pm_stats;
+
+/* Create a mesh on CUDA device `device` from host arrays.
+ *   xy[2*nv], tri[3*ne]; corner[nv] (nullable): 1 marks a vertex that must
+ *   never move or disappear; when null, corners are the boundary vertices
+ *   whose two boundary edges are not collinear.
+ *   cap_factor >= 1: initial slot capacity as a multiple of nv and ne (the
+ *   mesh grows beyond it by itself when refinement needs room).
+ * The metric starts as the identity; set it with pm_set_metric.
+ * Builds the adjacency (Sec. 3.1: NN vertex-vertex and NE vertex-element
+ * lists, kept as sorted sets) and checks the mesh: PM_ERR_INVALID_MESH when a
+ * triangle is not counter-clockwise, an edge is used twice in the same
+ * direction, a vertex is not manifold, or a vertex is not used. */
+pm_status pm_mesh_create(const double* xy, int32_t nv, const int32_t* tri, int32_t ne,
+                         const uint8_t* corner, int32_t cap_factor, int device,
+                         pm_mesh** out);
+
+/* Same as pm_mesh_create with device input arrays (read on `stream`, a
+ * cudaStream_t or null for a new stream of the library's own). */
+pm_status pm_mesh_create_dev(const double* xy, int32_t nv, const int32_t* tri, int32_t ne,
+                             const uint8_t* corner, int32_t cap_factor, void* stream,
+                             pm_mesh** out);
+
+pm_status pm_mesh_destroy(pm_mesh* mesh);
+
+/* Use `stream` (a cudaStream_t on the mesh's device) for all later work. */
+pm_status pm_set_stream(pm_mesh* mesh, void* stream);
+
+/* Set the node-wise metric (Sec. 2.1): m[3*nv] = (m00, m01, m11) per vertex
+ * in the mesh's current vertex numbering.  PM_ERR_INVALID_ARG unless every
+ * entry is finite and m00 > 0, m00*m11 - m01^2 > 0. */
+pm_status pm_set_metric(pm_mesh* mesh, const double* m);
+pm_status pm_set_metric_dev(pm_mesh* mesh, const double* m);
+
+/* The operators (Sec. 2.4), each run in rounds of independent sets until no
+ * candidate is left.  They do not renumber: removed vertices and elements
+ * keep their slots until pm_adapt renumbers or pm_get_mesh compacts a copy.
+ *   pm_coarsen  collapse every edge shorter than L_low where valid (2.4.1);
+ *   pm_refine   split every edge longer than L_up, templates per element;
+ *   pm_swap     flip edges whose two elements' minimum quality improves;
+ *   pm_smooth   quality-constrained Laplacian smoothing, then
+ *               opt_smooth_rounds rounds of optimisation-based smoothing;
+ *   pm_adapt    Algorithm 1 (Sec. 2.3) followed by smoothing; renumbers
+ *               after every iteration and at the end.
+ * `stats` may be null. */
+pm_status pm_coarsen(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
+pm_status pm_refine(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
+pm_status pm_swap(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
+pm_status pm_smooth(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
+pm_status pm_adapt(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
+
+/* Optimisation-based smoothing only (Sec. 2.4.4, gradient form):
+ * params->opt_smooth_rounds rounds of independent sets of interior vertices. */
+pm_status pm_opt_smooth(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
+
+/* Adapt n meshes together (each with its own parameters and seed): every
+ * round of every operator is one launch per kernel over all meshes'
+ * worklists.  Results are identical to n separate pm_adapt calls.
+ * stats[n] may be null.  All meshes must live on the same device. */
+pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params,
+                         pm_stats* stats);
+
+/* Copy out the mesh, compacted (live vertices and elements in ascending slot
+ * order) with every triangle rotated so its smallest vertex id comes first.
+ * Two-call protocol: with null arrays only *nv and *ne are written.
+ * xy[2*nv], tri[3*ne], m[3*nv] may each be null. */
+pm_status pm_get_mesh(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
+                      double* m);
+pm_status pm_get_mesh_dev(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
+                          double* m);
+
+/* Raw slot state without compaction (for round-by-round comparisons):
+ * *nv, *ne = slots in use; xy[2*nv], m[3*nv], tri[3*ne], valive[nv],
+ * talive[ne], vflag[nv] (bit0 boundary, bit1 corner).  Null arrays: sizes
+ * only. */
+pm_status pm_get_raw(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, double* m,
+                     int32_t* tri, uint8_t* valive, uint8_t* talive, uint8_t* vflag);
+
+/* Sorted adjacency rows of vertex slot v (Sec. 3.1): nn[cap], ne[cap];
+ * *nnlen, *nelen receive the full row lengths. */
+pm_status pm_adjacency(pm_mesh* mesh, int32_t v, int32_t* nn, int32_t* nnlen, int32_t* ne,
+                       int32_t* nelen, int32_t cap);
+
+/* Element quality functional (Sec. 2.2, Vasilevskii et al.) and its gradient
+ * over the live elements of the mesh.  *q_sum = sum of qualities; dxy[2*nv]
+ * and dm[3*nv] (nullable) receive d(q_sum)/d(x,y) and d(q_sum)/d(m00,m01,m11)
+ * per vertex slot (zero for dead slots), each the sum over the vertex's
+ * elements in ascending element id. */
+pm_status pm_quality(pm_mesh* mesh, double* q_sum, double* dxy, double* dm);
+
+/* The same functional on plain device arrays (no mesh handle), for use under
+ * automatic differentiation: xy[2*nv], m[3*nv], tri[3*ne] on the current
+ * device.  q_sum (1 double), dxy[2*nv], dm[3*nv] are device outputs; dxy and
+ * dm may be null for the forward value only.  Runs on `stream`
+ * (cudaStream_t, null = legacy default stream) and returns without
+ * synchronising.  Temporary device memory is allocated and released in the
+ * call.  Gradient rows: each vertex sums its elements in ascending id. */
+pm_status pm_quality_arrays_dev(const double* xy, const double* m, int32_t nv,
+                                const int32_t* tri, int32_t ne, double* q_sum, double* dxy,
+                                double* dm, void* stream);
+
+const char* pm_status_string(pm_status s);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PM_H */

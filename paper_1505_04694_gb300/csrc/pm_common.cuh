@@ -1,0 +1,324 @@
+// Shared device-side definitions of the GB300 mesh-adaptation library.
+//
+// Arithmetic follows the readings of the paper used throughout the library:
+// FP64, no contraction of a*b+c (compiled with -fmad=false), every expression
+// evaluated in the order written, IEEE-correct division and square root.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pm.h"
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Storage layout (structure of arrays; all meshes of a batch share the arrays,
+// each mesh owns the slot ranges [vbase, vbase + vcap) and [ebase, ebase + ecap)).
+// Ids stored in EN / NN / NE are LOCAL to the mesh (slot - base).
+// ---------------------------------------------------------------------------
+
+enum : uint8_t { VF_ALIVE = 1, VF_BND = 2, VF_CORNER = 4 };
+
+// Per-mesh table (device copy); arrays of length nmesh.
+struct MeshTab {
+  int* vbase;
+  int* vcap;
+  int* ebase;
+  int* ecap;
+  int* nv;      // used vertex slots (alive + dead) of each mesh
+  int* ne;      // used element slots
+  uint32_t* seed;
+  uint32_t* r;  // round counter of the current call
+  int* had;     // 1 when the mesh formed candidates this round
+  int* active;  // mesh takes part in the current phase
+  unsigned long long* ops;       // operations applied in the current call
+  unsigned long long* iter_ops;  // operations of the current outer iteration
+  double* L_low;                 // per-mesh parameters
+  double* L_up;
+  double* q_thresh;
+};
+
+struct Store {
+  int nmesh;
+  int W;          // row capacity of NN and NE
+  int vslots;     // total vertex slots (sum of vcap)
+  int eslots;     // total element slots
+  double2* xy;
+  double4* M;     // (m00, m01, m11, 0)
+  uint8_t* vflag;
+  int4* EN;       // (v0, v1, v2, alive)
+  int* NN;        // vslots * W
+  int* NNlen;
+  int* NE;
+  int* NElen;
+  MeshTab tab;
+};
+
+// Status words written by kernels (device).
+struct DevStatus {
+  int err;       // pm_status set by a kernel (first writer wins)
+  int overflow;  // an adjacency row would exceed W
+  int maxdeg;    // largest row length seen by the last adjacency build
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void set_err(DevStatus* st, int code) {
+  atomicCAS(&st->err, 0, code);
+}
+
+// Mesh of a global vertex slot (binary search over the sorted bases).
+__device__ __forceinline__ int mesh_of_vslot(const Store& S, int slot) {
+  if (S.nmesh == 1) return 0;
+  int lo = 0, hi = S.nmesh - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(S.tab.vbase + mid) <= slot) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int mesh_of_eslot(const Store& S, int slot) {
+  if (S.nmesh == 1) return 0;
+  int lo = 0, hi = S.nmesh - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(S.tab.ebase + mid) <= slot) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Warp-aggregated append (the GPU form of the atomic-capture worklist of
+// Sec. 3.4): one atomic per warp reserves room for every lane with pred set.
+// All 32 lanes of the warp must call it.
+__device__ __forceinline__ void warp_append(bool pred, int val, int* list, int* count) {
+  unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m == 0) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
+// Append once per round: the stamp array holds the tag of the last round in
+// which the slot was appended.
+__device__ __forceinline__ bool stamp_first(int* stamp, int slot, int tag) {
+  return atomicExch(stamp + slot, tag) != tag;
+}
+
+__device__ __forceinline__ bool row_has(const int* row, int len, int val) {
+  for (int k = 0; k < len; ++k) {
+    int x = row[k];
+    if (x == val) return true;
+    if (x > val) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int row_find(const int* row, int len, int val) {
+  for (int k = 0; k < len; ++k) {
+    int x = row[k];
+    if (x == val) return k;
+    if (x > val) return -1;
+  }
+  return -1;
+}
+
+// Insert into a sorted small buffer without duplicates; returns false when
+// the buffer is full.
+__device__ __forceinline__ bool sorted_insert(int* buf, int& n, int cap, int val) {
+  int k = n;
+  while (k > 0 && buf[k - 1] > val) --k;
+  if (k > 0 && buf[k - 1] == val) return true;
+  if (n >= cap) return false;
+  for (int j = n; j > k; --j) buf[j] = buf[j - 1];
+  buf[k] = val;
+  ++n;
+  return true;
+}
+
+__device__ __forceinline__ void sorted_erase(int* buf, int& n, int val) {
+  int k = 0;
+  while (k < n && buf[k] < val) ++k;
+  if (k < n && buf[k] == val) {
+    for (int j = k; j < n - 1; ++j) buf[j] = buf[j + 1];
+    --n;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic (Sec. 2.2).
+// ---------------------------------------------------------------------------
+
+struct VD {
+  double x, y, m00, m01, m11;
+};
+
+__device__ __forceinline__ VD load_vd(const Store& S, int slot) {
+  double2 p = S.xy[slot];
+  double4 m = S.M[slot];
+  return VD{p.x, p.y, m.x, m.y, m.z};
+}
+
+// Metric length of edge (a,b) under the mean of the end-point metrics.
+__device__ __forceinline__ double metric_len(const VD& a, const VD& b) {
+  double e00 = 0.5 * (a.m00 + b.m00);
+  double e01 = 0.5 * (a.m01 + b.m01);
+  double e11 = 0.5 * (a.m11 + b.m11);
+  double dx = b.x - a.x;
+  double dy = b.y - a.y;
+  double L2 = ((e00 * dx) * dx + ((2.0 * e01) * dx) * dy) + (e11 * dy) * dy;
+  return sqrt(L2);
+}
+
+__device__ __forceinline__ double orient3(const VD& p, const VD& q, const VD& r) {
+  return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);
+}
+
+// Rotate (i0,i1,i2) so that the smallest id comes first (cyclic order kept).
+__device__ __forceinline__ void canon(int& i0, int& i1, int& i2, VD& a, VD& b, VD& c) {
+  if (i1 < i0 && i1 < i2) {
+    int t = i0; i0 = i1; i1 = i2; i2 = t;
+    VD u = a; a = b; b = c; c = u;
+  } else if (i2 < i0 && i2 < i1) {
+    int t = i2; i2 = i1; i1 = i0; i0 = t;
+    VD u = c; c = b; b = a; a = u;
+  }
+}
+
+__device__ __forceinline__ double orient_c(int i0, int i1, int i2, VD a, VD b, VD c) {
+  canon(i0, i1, i2, a, b, c);
+  return orient3(a, b, c);
+}
+
+constexpr double QC = 12.0 * 1.7320508075688772;  // 12 sqrt(3)
+
+__device__ __forceinline__ double len_under(double k00, double k01, double k11, const VD& p,
+                                            const VD& q) {
+  double dx = q.x - p.x;
+  double dy = q.y - p.y;
+  double L2 = ((k00 * dx) * dx + ((2.0 * k01) * dx) * dy) + (k11 * dy) * dy;
+  return sqrt(L2);
+}
+
+// Vasilevskii-Lipnikov quality in the element-mean metric, canonical rotation.
+__device__ __forceinline__ double quality_c(int i0, int i1, int i2, VD a, VD b, VD c) {
+  canon(i0, i1, i2, a, b, c);
+  double k00 = ((a.m00 + b.m00) + c.m00) / 3.0;
+  double k01 = ((a.m01 + b.m01) + c.m01) / 3.0;
+  double k11 = ((a.m11 + b.m11) + c.m11) / 3.0;
+  double l0 = len_under(k00, k01, k11, a, b);
+  double l1 = len_under(k00, k01, k11, b, c);
+  double l2 = len_under(k00, k01, k11, c, a);
+  double P = (l0 + l1) + l2;
+  double area = 0.5 * orient3(a, b, c);
+  double AM = sqrt(k00 * k11 - k01 * k01) * area;
+  double xx = P / 3.0;
+  double s = (xx <= 1.0) ? xx : 1.0 / xx;
+  double f = s * (2.0 - s);
+  double F = (f * f) * f;
+  return ((QC * AM) / (P * P)) * F;
+}
+
+// Reverse-mode derivative of quality_c; g[k][0..4] = dq/d(x,y,m00,m01,m11) of
+// the k-th vertex in the caller's order.  Same operation order as the
+// definition of the derivative used by the optimisation-based smoother.
+__device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, VD b, VD c,
+                                                 double g[3][5]) {
+  int s = 0;
+  if (i1 < i0 && i1 < i2) s = 1;
+  else if (i2 < i0 && i2 < i1) s = 2;
+  canon(i0, i1, i2, a, b, c);
+  double k00 = ((a.m00 + b.m00) + c.m00) / 3.0;
+  double k01 = ((a.m01 + b.m01) + c.m01) / 3.0;
+  double k11 = ((a.m11 + b.m11) + c.m11) / 3.0;
+  double dx[3] = {b.x - a.x, c.x - b.x, a.x - c.x};
+  double dy[3] = {b.y - a.y, c.y - b.y, a.y - c.y};
+  double l[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    double L2 = ((k00 * dx[e]) * dx[e] + ((2.0 * k01) * dx[e]) * dy[e]) + (k11 * dy[e]) * dy[e];
+    l[e] = sqrt(L2);
+  }
+  double P = (l[0] + l[1]) + l[2];
+  double area = 0.5 * orient3(a, b, c);
+  double sd = sqrt(k00 * k11 - k01 * k01);
+  double AM = sd * area;
+  double xx = P / 3.0;
+  bool left = (xx <= 1.0);
+  double sv = left ? xx : 1.0 / xx;
+  double f = sv * (2.0 - sv);
+  double F = (f * f) * f;
+  double t = (QC * AM) / (P * P);
+  double q = t * F;
+  double gF = t;
+  double gt = F;
+  double gAM = (gt * QC) / (P * P);
+  double gP = -((2.0 * t) / P) * gt;
+  double gf = (3.0 * (f * f)) * gF;
+  double gs = (2.0 - 2.0 * sv) * gf;
+  double gxx = left ? gs : -(gs / (xx * xx));
+  gP = gP + gxx / 3.0;
+  double gsd = area * gAM;
+  double garea = sd * gAM;
+  double gdet = gsd / (2.0 * sd);
+  double gk00 = k11 * gdet;
+  double gk11 = k00 * gdet;
+  double gk01 = -(2.0 * k01) * gdet;
+  double go = 0.5 * garea;
+  double gdx[3], gdy[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    double gL2 = gP / (2.0 * l[e]);
+    gk00 = gk00 + (dx[e] * dx[e]) * gL2;
+    gk01 = gk01 + (2.0 * (dx[e] * dy[e])) * gL2;
+    gk11 = gk11 + (dy[e] * dy[e]) * gL2;
+    gdx[e] = ((2.0 * k00) * dx[e] + (2.0 * k01) * dy[e]) * gL2;
+    gdy[e] = ((2.0 * k01) * dx[e] + (2.0 * k11) * dy[e]) * gL2;
+  }
+  double cg[3][5];
+  cg[0][0] = (go * (b.y - c.y) - gdx[0]) + gdx[2];
+  cg[1][0] = (go * (c.y - a.y) + gdx[0]) - gdx[1];
+  cg[2][0] = (go * (a.y - b.y) + gdx[1]) - gdx[2];
+  cg[0][1] = (go * (c.x - b.x) - gdy[0]) + gdy[2];
+  cg[1][1] = (go * (a.x - c.x) + gdy[0]) - gdy[1];
+  cg[2][1] = (go * (b.x - a.x) + gdy[1]) - gdy[2];
+  double m0 = gk00 / 3.0, m1 = gk01 / 3.0, m2 = gk11 / 3.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    cg[k][2] = m0;
+    cg[k][3] = m1;
+    cg[k][4] = m2;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int dst = (s + k) % 3;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) g[dst][j] = cg[k][j];
+  }
+  return q;
+}
+
+// Hash priority for the independent sets (Sec. 3.2): MurmurHash3 fmix32 of
+// (local id xor per-round seed).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ uint32_t prio(uint32_t v, uint32_t seed, uint32_t r) {
+  uint32_t sr = seed + 0x9E3779B9u * r;
+  return fmix32(v ^ sr);
+}
+
+}  // namespace pm

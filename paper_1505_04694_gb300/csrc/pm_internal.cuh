@@ -1,0 +1,116 @@
+// Host-side structures of the library (one translation unit per subsystem
+// shares these declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "pm_common.cuh"
+
+namespace pm {
+
+constexpr int MAXW = 64;          // largest supported adjacency row
+constexpr int BLOCK = 128;        // threads per block of the round kernels
+
+struct ScanWork {
+  unsigned long long* state = nullptr;  // one word per tile
+  int* ticket = nullptr;
+  unsigned epoch = 0;
+  int tiles_cap = 0;
+};
+
+int scan_tiles(int n);
+void scan_exclusive(const int* in, int* out, int n, ScanWork& w, DevStatus* st, cudaStream_t s);
+
+// Per-round worklists and marks (slot-indexed scratch, sized with the store).
+struct Work {
+  int* D[2] = {nullptr, nullptr};  // dirty / pending lists (ping-pong)
+  int* C = nullptr;                // candidates
+  int* Sl = nullptr;               // independent set
+  int* A = nullptr;                // vertices whose rows change (commit owners)
+  int* P = nullptr;                // next-sweep list (smoothing)
+  int* target = nullptr;           // collapse target (local id) per vertex
+  int4* opA = nullptr;             // flip record (w, c, d, K1) per vertex
+  int* opK2 = nullptr;
+  double2* mvxy = nullptr;         // smoothing move per vertex
+  double4* mvM = nullptr;
+  int* dmark = nullptr;            // per-round stamps
+  int* amark = nullptr;
+  int* cmark = nullptr;
+  int* smark = nullptr;
+  int* pmark = nullptr;
+  int* vcnt = nullptr;             // per-vertex counts (refine / renumber), vslots + 1
+  int* vscan = nullptr;            // vslots + 1
+  unsigned long long* vmask = nullptr;  // refine: marked NN entries
+  int* ecnt = nullptr;             // per-element counts, eslots + 1
+  int* escan = nullptr;
+  int4* emid = nullptr;            // refine: midpoint ids per element edge
+  int* counts = nullptr;           // device counters (see CountIdx)
+};
+
+enum CountIdx { CN_D0 = 0, CN_D1 = 1, CN_C = 2, CN_S = 3, CN_A = 4, CN_P = 5, CN_NUM = 8 };
+
+// Everything the library keeps on the device for a set of meshes.
+struct MeshSet {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nmesh = 0;
+  // host mirror of the per-mesh table
+  std::vector<int> vbase, vcap, ebase, ecap, nv, ne;
+  std::vector<uint32_t> seed;
+  std::vector<double> L_low, L_up, q_thresh;
+  Store S{};          // device arrays (S.tab points into tabmem)
+  Store B{};          // second buffer set for renumbering
+  Work w{};
+  ScanWork scan{};
+  DevStatus* st = nullptr;     // device
+  DevStatus* hst = nullptr;    // pinned host
+  int* hcounts = nullptr;      // pinned host copy of w.counts
+  void* tabmem = nullptr;      // device block holding MeshTab arrays
+  int tag = 0;                 // per-round stamp value
+  int num_sms = 152;
+  std::vector<void*> allocs;   // device allocations owned by the set
+};
+
+// ---- mesh storage (pm_mesh.cu) ----
+cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap,
+                      int W);
+void set_free(MeshSet& m);
+cudaError_t upload_tab(MeshSet& m);
+cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap, int W);
+int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev);
+int renumber(MeshSet& m);
+int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
+                int* ne_out);
+int sync_status(MeshSet& m);
+int validate_mesh(MeshSet& m);
+cudaError_t refresh_sizes(MeshSet& m);
+
+// ---- operators (pm_ops.cu) ----
+int op_coarsen(MeshSet& m, int max_rounds);
+int op_swap(MeshSet& m, int max_rounds);
+int op_refine(MeshSet& m, int max_rounds);
+int op_smooth(MeshSet& m, int max_sweeps, int max_rounds);
+int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds);
+void zero_ops(MeshSet& m);
+cudaError_t fetch_ops(MeshSet& m, std::vector<unsigned long long>& ops);
+
+// ---- quality (pm_quality.cu) ----
+int quality_mesh(MeshSet& m, double* qsum_host, double* dxy_host, double* dm_host);
+int quality_arrays(const double* xy, const double* mt, int nv, const int* tri, int ne,
+                   double* qsum, double* dxy, double* dm, cudaStream_t s);
+
+// ---- errors (pm_capi.cu) ----
+void set_last_error(const std::string& msg);
+
+inline int grid_for(const MeshSet& m, long long n, int per_sm = 8) {
+  long long want = (n + BLOCK - 1) / BLOCK;
+  long long cap = (long long)m.num_sms * per_sm;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+}  // namespace pm

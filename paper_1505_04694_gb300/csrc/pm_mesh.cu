@@ -1,0 +1,662 @@
+// Mesh storage: allocation, growth, adjacency construction, validation,
+// renumbering and compacted output.
+//
+// Adjacency (Sec. 3.1, "adjacency list of a vertex"): every vertex slot owns
+// two fixed-capacity rows of W int32 entries, NN (neighbour vertices) and NE
+// (incident elements), each kept sorted.  Rows are rebuilt from the element
+// list here; between rebuilds the operators keep them current through the
+// deferred-update commit (pm_ops.cu).
+#include <algorithm>
+#include <cstring>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(MeshSet& m, T** p, size_t count, bool zero) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMallocAsync((void**)p, bytes, m.stream);
+  if (e != cudaSuccess) return e;
+  m.allocs.push_back(*p);
+  if (zero) e = cudaMemsetAsync(*p, 0, bytes, m.stream);
+  return e;
+}
+
+__device__ __forceinline__ bool vslot_used(const Store& S, int slot, int& mi) {
+  mi = mesh_of_vslot(S, slot);
+  return slot - S.tab.vbase[mi] < S.tab.nv[mi];
+}
+
+__device__ __forceinline__ bool eslot_used(const Store& S, int slot, int& mi) {
+  mi = mesh_of_eslot(S, slot);
+  return slot - S.tab.ebase[mi] < S.tab.ne[mi];
+}
+
+// ---- relayout (growth) ------------------------------------------------------
+
+__global__ void k_relayout_v(Store A, Store B) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!vslot_used(A, s, mi)) continue;
+    int ns = B.tab.vbase[mi] + (s - A.tab.vbase[mi]);
+    B.xy[ns] = A.xy[s];
+    B.M[ns] = A.M[s];
+    B.vflag[ns] = A.vflag[s];
+    int wn = A.W < B.W ? A.W : B.W;
+    int a = A.NNlen[s], b = A.NElen[s];
+    B.NNlen[ns] = a;
+    B.NElen[ns] = b;
+    for (int k = 0; k < wn; ++k) {
+      B.NN[(size_t)ns * B.W + k] = A.NN[(size_t)s * A.W + k];
+      B.NE[(size_t)ns * B.W + k] = A.NE[(size_t)s * A.W + k];
+    }
+  }
+}
+
+__global__ void k_relayout_e(Store A, Store B) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.eslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!eslot_used(A, s, mi)) continue;
+    int ns = B.tab.ebase[mi] + (s - A.tab.ebase[mi]);
+    B.EN[ns] = A.EN[s];
+  }
+}
+
+// ---- adjacency build ----------------------------------------------------------
+
+__global__ void k_zero_nelen(Store S) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+    S.NElen[s] = 0;
+  }
+}
+
+__global__ void k_fill_ne(Store S, DevStatus* st) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!eslot_used(S, s, mi)) continue;
+    int4 e = S.EN[s];
+    if (!e.w) continue;
+    int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi];
+    int K = s - eb;
+    int vs[3] = {e.x, e.y, e.z};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      int slot = vb + vs[i];
+      int pos = atomicAdd(S.NElen + slot, 1);
+      if (pos < S.W) S.NE[(size_t)slot * S.W + pos] = K;
+      else atomicExch(&st->overflow, 1);
+    }
+  }
+}
+
+// Sort the NE row, derive the NN row (sorted union of the other vertices of
+// the incident elements), check manifoldness, optionally derive the boundary
+// flag (a vertex is on the boundary when it has one more neighbour than
+// incident elements).
+__global__ void k_finish_rows(Store S, int derive, DevStatus* st) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!vslot_used(S, s, mi)) continue;
+    uint8_t f = S.vflag[s];
+    if (!(f & VF_ALIVE)) {
+      S.NNlen[s] = 0;
+      S.NElen[s] = 0;
+      continue;
+    }
+    int nel = S.NElen[s];
+    if (nel > S.W) {
+      atomicExch(&st->overflow, 1);
+      atomicMax(&st->maxdeg, nel);
+      continue;
+    }
+    int* ne = S.NE + (size_t)s * S.W;
+    int buf[MAXW];
+    for (int k = 0; k < nel; ++k) buf[k] = ne[k];
+    for (int k = 1; k < nel; ++k) {  // insertion sort
+      int x = buf[k];
+      int j = k - 1;
+      while (j >= 0 && buf[j] > x) {
+        buf[j + 1] = buf[j];
+        --j;
+      }
+      buf[j + 1] = x;
+    }
+    for (int k = 0; k < nel; ++k) ne[k] = buf[k];
+    int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi];
+    int lv = s - vb;
+    int nnb[MAXW];
+    int nn = 0;
+    int nxt[MAXW];
+    int nnx = 0;
+    bool ok = true;
+    for (int k = 0; k < nel; ++k) {
+      int4 e = S.EN[eb + buf[k]];
+      int i = (e.x == lv) ? 0 : (e.y == lv) ? 1 : 2;
+      int vv[3] = {e.x, e.y, e.z};
+      int a = vv[(i + 1) % 3], b = vv[(i + 2) % 3];
+      if (!sorted_insert(nnb, nn, MAXW, a) || !sorted_insert(nnb, nn, MAXW, b)) ok = false;
+      // the outgoing directed edge lv->a must be unique (no overlapping elements)
+      int before = nnx;
+      if (!sorted_insert(nxt, nnx, MAXW, a)) ok = false;
+      if (nnx == before && derive) set_err(st, PM_ERR_INVALID_MESH);
+    }
+    if (!ok || nn > S.W) {
+      atomicExch(&st->overflow, 1);
+      atomicMax(&st->maxdeg, nn);
+      continue;
+    }
+    atomicMax(&st->maxdeg, nn);
+    int* row = S.NN + (size_t)s * S.W;
+    for (int k = 0; k < nn; ++k) row[k] = nnb[k];
+    S.NNlen[s] = nn;
+    if (derive) {
+      int d = nn - nel;
+      if (nel == 0 || (d != 0 && d != 1)) set_err(st, PM_ERR_INVALID_MESH);
+      S.vflag[s] = (uint8_t)((f & ~VF_BND) | (d == 1 ? VF_BND : 0));
+    }
+  }
+}
+
+__device__ __forceinline__ int edge_elements(const Store& S, int slot, int eb, int lw) {
+  const int* ne = S.NE + (size_t)slot * S.W;
+  int nel = S.NElen[slot];
+  int c = 0;
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[eb + ne[k]];
+    if (e.x == lw || e.y == lw || e.z == lw) ++c;
+  }
+  return c;
+}
+
+// Corners: boundary vertices whose two boundary neighbours are not collinear
+// with them (or the caller's flags).
+__global__ void k_corners(Store S, const uint8_t* corner) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!vslot_used(S, s, mi)) continue;
+    uint8_t f = S.vflag[s];
+    if (!(f & VF_ALIVE)) continue;
+    int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi];
+    bool c = false;
+    if (corner) {
+      c = corner[s - vb] != 0;
+    } else if (f & VF_BND) {
+      const int* nn = S.NN + (size_t)s * S.W;
+      int nnl = S.NNlen[s];
+      int bn[2];
+      int k2 = 0;
+      for (int k = 0; k < nnl; ++k) {
+        if (edge_elements(S, s, eb, nn[k]) == 1 && k2 < 2) bn[k2++] = nn[k];
+      }
+      if (k2 < 2) {
+        c = true;
+      } else {
+        int lo = bn[0] < bn[1] ? bn[0] : bn[1];
+        int hi = bn[0] < bn[1] ? bn[1] : bn[0];
+        c = orient3(load_vd(S, vb + lo), load_vd(S, s), load_vd(S, vb + hi)) != 0.0;
+      }
+    }
+    S.vflag[s] = (uint8_t)((f & ~VF_CORNER) | (c ? VF_CORNER : 0));
+  }
+}
+
+// Ids in range, distinct, and every element counter-clockwise (canonical).
+__global__ void k_validate_elems(Store S, DevStatus* st) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!eslot_used(S, s, mi)) continue;
+    int4 e = S.EN[s];
+    if (!e.w) continue;
+    int nv = S.tab.nv[mi], vb = S.tab.vbase[mi];
+    if (e.x < 0 || e.y < 0 || e.z < 0 || e.x >= nv || e.y >= nv || e.z >= nv || e.x == e.y ||
+        e.y == e.z || e.x == e.z) {
+      set_err(st, PM_ERR_INVALID_MESH);
+      continue;
+    }
+    if (!(orient_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
+                   load_vd(S, vb + e.z)) > 0.0))
+      set_err(st, PM_ERR_INVALID_MESH);
+  }
+}
+
+// ---- renumbering -----------------------------------------------------------
+
+__global__ void k_flags_v(Store S, int* cnt) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    cnt[s] = (vslot_used(S, s, mi) && (S.vflag[s] & VF_ALIVE)) ? 1 : 0;
+  }
+}
+
+__global__ void k_flags_e(Store S, int* cnt) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    cnt[s] = (eslot_used(S, s, mi) && S.EN[s].w) ? 1 : 0;
+  }
+}
+
+// Per-mesh live counts from the scans: n_i = scan[base_i + used_i] - scan[base_i].
+__global__ void k_mesh_totals(Store S, const int* vscan, const int* escan, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nmesh) return;
+  int vb = S.tab.vbase[i], eb = S.tab.ebase[i];
+  out[2 * i] = vscan[vb + S.tab.nv[i]] - vscan[vb];
+  out[2 * i + 1] = escan[eb + S.tab.ne[i]] - escan[eb];
+}
+
+__global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!vslot_used(A, s, mi)) continue;
+    if (!(A.vflag[s] & VF_ALIVE)) continue;
+    int vb = A.tab.vbase[mi], eb = A.tab.ebase[mi];
+    int v0 = vscan[vb], e0 = escan[eb];
+    int ns = vb + (vscan[s] - v0);
+    B.xy[ns] = A.xy[s];
+    B.M[ns] = A.M[s];
+    B.vflag[ns] = A.vflag[s];
+    int a = A.NNlen[s], b = A.NElen[s];
+    const int* nn = A.NN + (size_t)s * A.W;
+    const int* ne = A.NE + (size_t)s * A.W;
+    int* nn2 = B.NN + (size_t)ns * B.W;
+    int* ne2 = B.NE + (size_t)ns * B.W;
+    for (int k = 0; k < a; ++k) nn2[k] = vscan[vb + nn[k]] - v0;
+    for (int k = 0; k < b; ++k) ne2[k] = escan[eb + ne[k]] - e0;
+    B.NNlen[ns] = a;
+    B.NElen[ns] = b;
+  }
+}
+
+__global__ void k_renum_e(Store A, Store B, const int* vscan, const int* escan) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.eslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!eslot_used(A, s, mi)) continue;
+    int4 e = A.EN[s];
+    if (!e.w) continue;
+    int vb = A.tab.vbase[mi], eb = A.tab.ebase[mi];
+    int v0 = vscan[vb];
+    int ns = eb + (escan[s] - escan[eb]);
+    B.EN[ns] = make_int4(vscan[vb + e.x] - v0, vscan[vb + e.y] - v0, vscan[vb + e.z] - v0, 1);
+  }
+}
+
+// Compacted output of one mesh (canonical rotation of every triangle).
+__global__ void k_out_v(Store S, int mesh, const int* vscan, double* xy, double* mt) {
+  int vb = S.tab.vbase[mesh], nv = S.tab.nv[mesh];
+  int v0 = vscan[vb];
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nv; l += gridDim.x * blockDim.x) {
+    int s = vb + l;
+    if (!(S.vflag[s] & VF_ALIVE)) continue;
+    int o = vscan[s] - v0;
+    double2 p = S.xy[s];
+    double4 m = S.M[s];
+    if (xy) {
+      xy[2 * o] = p.x;
+      xy[2 * o + 1] = p.y;
+    }
+    if (mt) {
+      mt[3 * o] = m.x;
+      mt[3 * o + 1] = m.y;
+      mt[3 * o + 2] = m.z;
+    }
+  }
+}
+
+__global__ void k_out_e(Store S, int mesh, const int* vscan, const int* escan, int32_t* tri) {
+  int vb = S.tab.vbase[mesh], eb = S.tab.ebase[mesh], ne = S.tab.ne[mesh];
+  int v0 = vscan[vb], e0 = escan[eb];
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < ne; l += gridDim.x * blockDim.x) {
+    int s = eb + l;
+    int4 e = S.EN[s];
+    if (!e.w) continue;
+    int o = escan[s] - e0;
+    int a = vscan[vb + e.x] - v0, b = vscan[vb + e.y] - v0, c = vscan[vb + e.z] - v0;
+    if (b < a && b < c) {
+      int t = a; a = b; b = c; c = t;
+    } else if (c < a && c < b) {
+      int t = c; c = b; b = a; a = t;
+    }
+    tri[3 * o] = a;
+    tri[3 * o + 1] = b;
+    tri[3 * o + 2] = c;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+cudaError_t upload_tab(MeshSet& m) {
+  int n = m.nmesh;
+  std::vector<int> ints(6 * n);
+  for (int i = 0; i < n; ++i) {
+    ints[i] = m.vbase[i];
+    ints[n + i] = m.vcap[i];
+    ints[2 * n + i] = m.ebase[i];
+    ints[3 * n + i] = m.ecap[i];
+    ints[4 * n + i] = m.nv[i];
+    ints[5 * n + i] = m.ne[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(m.S.tab.vbase, ints.data(), ints.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, m.stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(m.S.tab.seed, m.seed.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                      m.stream);
+  if (e != cudaSuccess) return e;
+  std::vector<double> dbl(3 * n);
+  for (int i = 0; i < n; ++i) {
+    dbl[i] = m.L_low[i];
+    dbl[n + i] = m.L_up[i];
+    dbl[2 * n + i] = m.q_thresh[i];
+  }
+  e = cudaMemcpyAsync(m.S.tab.L_low, dbl.data(), dbl.size() * sizeof(double),
+                      cudaMemcpyHostToDevice, m.stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(m.stream);  // host vectors go out of scope
+}
+
+// Read back the per-mesh used-slot counts (nv, ne) into the host mirror.
+cudaError_t refresh_sizes(MeshSet& m) {
+  std::vector<int> t(2 * m.nmesh);
+  cudaError_t e = cudaMemcpyAsync(t.data(), m.S.tab.nv, 2 * m.nmesh * sizeof(int),
+                                  cudaMemcpyDeviceToHost, m.stream);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(m.stream);
+  for (int i = 0; i < m.nmesh; ++i) {
+    m.nv[i] = t[i];
+    m.ne[i] = t[m.nmesh + i];
+  }
+  return e;
+}
+
+static cudaError_t alloc_store(MeshSet& m, Store& S, bool zero) {
+  cudaError_t e;
+  size_t V = S.vslots, E = S.eslots, W = S.W;
+  if ((e = dalloc(m, &S.xy, V, zero))) return e;
+  if ((e = dalloc(m, &S.M, V, zero))) return e;
+  if ((e = dalloc(m, &S.vflag, V, true))) return e;
+  if ((e = dalloc(m, &S.EN, E, zero))) return e;
+  if ((e = dalloc(m, &S.NN, V * W, false))) return e;
+  if ((e = dalloc(m, &S.NNlen, V, true))) return e;
+  if ((e = dalloc(m, &S.NE, V * W, false))) return e;
+  if ((e = dalloc(m, &S.NElen, V, true))) return e;
+  return cudaSuccess;
+}
+
+cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap,
+                      int W) {
+  int n = m.nmesh;
+  m.vcap = vcap;
+  m.ecap = ecap;
+  m.vbase.assign(n, 0);
+  m.ebase.assign(n, 0);
+  long long vs = 0, es = 0;
+  for (int i = 0; i < n; ++i) {
+    m.vbase[i] = (int)vs;
+    m.ebase[i] = (int)es;
+    vs += vcap[i];
+    es += ecap[i];
+  }
+  if (vs >= (1LL << 31) - 4 || es >= (1LL << 31) - 4 || vs * (long long)W >= (1LL << 40))
+    return cudaErrorMemoryAllocation;
+  cudaError_t e;
+  Store& S = m.S;
+  S.nmesh = n;
+  S.W = W;
+  S.vslots = (int)vs;
+  S.eslots = (int)es;
+  if ((e = alloc_store(m, S, true))) return e;
+  m.B = S;
+  if ((e = alloc_store(m, m.B, false))) return e;
+  // table
+  size_t tab_bytes = (size_t)n * (6 * sizeof(int) + 2 * sizeof(uint32_t) + 2 * sizeof(int) +
+                                  2 * sizeof(unsigned long long) + 3 * sizeof(double)) + 64;
+  char* t = nullptr;
+  if ((e = dalloc(m, &t, tab_bytes, true))) return e;
+  m.tabmem = t;
+  MeshTab& T = S.tab;
+  // doubles and 64-bit counters first (alignment)
+  T.L_low = (double*)t; t += n * sizeof(double);
+  T.L_up = (double*)t; t += n * sizeof(double);
+  T.q_thresh = (double*)t; t += n * sizeof(double);
+  T.ops = (unsigned long long*)t; t += n * sizeof(unsigned long long);
+  T.iter_ops = (unsigned long long*)t; t += n * sizeof(unsigned long long);
+  T.vbase = (int*)t; t += n * sizeof(int);
+  T.vcap = (int*)t; t += n * sizeof(int);
+  T.ebase = (int*)t; t += n * sizeof(int);
+  T.ecap = (int*)t; t += n * sizeof(int);
+  T.nv = (int*)t; t += n * sizeof(int);
+  T.ne = (int*)t; t += n * sizeof(int);
+  T.seed = (uint32_t*)t; t += n * sizeof(uint32_t);
+  T.r = (uint32_t*)t; t += n * sizeof(uint32_t);
+  T.had = (int*)t; t += n * sizeof(int);
+  T.active = (int*)t; t += n * sizeof(int);
+  m.B.tab = T;
+  // work
+  Work& w = m.w;
+  if ((e = dalloc(m, &w.D[0], vs, false))) return e;
+  if ((e = dalloc(m, &w.D[1], vs, false))) return e;
+  if ((e = dalloc(m, &w.C, vs, false))) return e;
+  if ((e = dalloc(m, &w.Sl, vs, false))) return e;
+  if ((e = dalloc(m, &w.A, vs, false))) return e;
+  if ((e = dalloc(m, &w.P, vs, false))) return e;
+  if ((e = dalloc(m, &w.target, vs, false))) return e;
+  if ((e = dalloc(m, &w.opA, vs, false))) return e;
+  if ((e = dalloc(m, &w.opK2, vs, false))) return e;
+  if ((e = dalloc(m, &w.mvxy, vs, false))) return e;
+  if ((e = dalloc(m, &w.mvM, vs, false))) return e;
+  if ((e = dalloc(m, &w.dmark, vs, true))) return e;
+  if ((e = dalloc(m, &w.amark, vs, true))) return e;
+  if ((e = dalloc(m, &w.cmark, vs, true))) return e;
+  if ((e = dalloc(m, &w.smark, vs, true))) return e;
+  if ((e = dalloc(m, &w.pmark, vs, true))) return e;
+  if ((e = dalloc(m, &w.vcnt, vs + 1, false))) return e;
+  if ((e = dalloc(m, &w.vscan, vs + 1, false))) return e;
+  if ((e = dalloc(m, &w.vmask, vs, false))) return e;
+  if ((e = dalloc(m, &w.ecnt, es + 1, false))) return e;
+  if ((e = dalloc(m, &w.escan, es + 1, false))) return e;
+  if ((e = dalloc(m, &w.emid, es, false))) return e;
+  if ((e = dalloc(m, &w.counts, CN_NUM + 2 * n + 8, true))) return e;
+  int tiles = scan_tiles((int)std::max(vs, es) + 1);
+  if ((e = dalloc(m, &m.scan.state, tiles, true))) return e;
+  if ((e = dalloc(m, &m.scan.ticket, 1, true))) return e;
+  m.scan.tiles_cap = tiles;
+  if (!m.st) {
+    if ((e = cudaMalloc(&m.st, sizeof(DevStatus)))) return e;
+    if ((e = cudaMemsetAsync(m.st, 0, sizeof(DevStatus), m.stream))) return e;
+    if ((e = cudaMallocHost(&m.hst, sizeof(DevStatus)))) return e;
+    if ((e = cudaMallocHost(&m.hcounts, (CN_NUM + 2 * std::max(n, 1024) + 8) * sizeof(int))))
+      return e;
+  }
+  return cudaSuccess;
+}
+
+void set_free(MeshSet& m) {
+  for (void* p : m.allocs) cudaFreeAsync(p, m.stream);
+  m.allocs.clear();
+}
+
+// Move the meshes into new regions of capacity vcap/ecap and row width W.
+cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap, int W) {
+  MeshSet n2;
+  n2.device = m.device;
+  n2.stream = m.stream;
+  n2.nmesh = m.nmesh;
+  n2.nv = m.nv;
+  n2.ne = m.ne;
+  n2.seed = m.seed;
+  n2.L_low = m.L_low;
+  n2.L_up = m.L_up;
+  n2.q_thresh = m.q_thresh;
+  n2.st = m.st;
+  n2.hst = m.hst;
+  n2.hcounts = m.hcounts;
+  n2.num_sms = m.num_sms;
+  cudaError_t e = set_alloc(n2, vcap, ecap, W);
+  if (e != cudaSuccess) {
+    set_free(n2);
+    return e;
+  }
+  if ((e = upload_tab(n2))) {
+    set_free(n2);
+    return e;
+  }
+  // carry the per-call round counters and op counts
+  int nm = m.nmesh;
+  cudaMemcpyAsync(n2.S.tab.r, m.S.tab.r, nm * sizeof(uint32_t), cudaMemcpyDeviceToDevice, m.stream);
+  cudaMemcpyAsync(n2.S.tab.active, m.S.tab.active, nm * sizeof(int), cudaMemcpyDeviceToDevice,
+                  m.stream);
+  cudaMemcpyAsync(n2.S.tab.ops, m.S.tab.ops, 2 * nm * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToDevice, m.stream);
+  k_relayout_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, n2.S);
+  k_relayout_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, n2.S);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  set_free(m);
+  m.vbase = n2.vbase;
+  m.vcap = n2.vcap;
+  m.ebase = n2.ebase;
+  m.ecap = n2.ecap;
+  m.S = n2.S;
+  m.B = n2.B;
+  m.w = n2.w;
+  m.scan = n2.scan;
+  m.tabmem = n2.tabmem;
+  m.allocs = n2.allocs;
+  n2.allocs.clear();
+  m.tag = 0;  // fresh stamp arrays
+  return cudaSuccess;
+}
+
+// Widen the adjacency rows to W (contents are rebuilt by the caller); every
+// other array, worklist and stamp keeps its place.
+cudaError_t grow_rows(MeshSet& m, int W) {
+  int* ptrs[4] = {m.S.NN, m.S.NE, m.B.NN, m.B.NE};
+  for (int* p : ptrs) {
+    cudaFreeAsync(p, m.stream);
+    m.allocs.erase(std::remove(m.allocs.begin(), m.allocs.end(), (void*)p), m.allocs.end());
+  }
+  size_t n = (size_t)m.S.vslots * W;
+  cudaError_t e;
+  if ((e = dalloc(m, &m.S.NN, n, false))) return e;
+  if ((e = dalloc(m, &m.S.NE, n, false))) return e;
+  if ((e = dalloc(m, &m.B.NN, n, false))) return e;
+  if ((e = dalloc(m, &m.B.NE, n, false))) return e;
+  m.S.W = W;
+  m.B.W = W;
+  return cudaSuccess;
+}
+
+int sync_status(MeshSet& m) {
+  cudaError_t e = cudaMemcpyAsync(m.hst, m.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, m.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m.stream);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("CUDA: ") + cudaGetErrorString(e));
+    return PM_ERR_CUDA;
+  }
+  return m.hst->err;
+}
+
+// Build NN and NE from the element list for every mesh of the set.  With
+// `derive_flags` (creation) also derive boundary and corner flags and check
+// manifoldness.  Grows W (rebuilding) when a row does not fit.
+int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) {
+  for (;;) {
+    cudaMemsetAsync(&m.st->overflow, 0, 2 * sizeof(int), m.stream);
+    k_zero_nelen<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S);
+    k_fill_ne<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, m.st);
+    k_finish_rows<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, derive_flags ? 1 : 0,
+                                                                  m.st);
+    int err = sync_status(m);
+    if (err) return err;
+    if (!m.hst->overflow) break;
+    int need = std::max(m.hst->maxdeg, m.S.W + 1);
+    int W = m.S.W;
+    while (W < need) W *= 2;
+    if (W > MAXW) {
+      set_last_error("adjacency row longer than the supported maximum of 64 entries");
+      return PM_ERR_CAPACITY;
+    }
+    cudaError_t e = grow_rows(m, W);
+    if (e != cudaSuccess) {
+      set_last_error(std::string("growing adjacency rows: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;
+    }
+  }
+  if (derive_flags) {
+    k_corners<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, corner_dev);
+    return sync_status(m);
+  }
+  return PM_OK;
+}
+
+int validate_mesh(MeshSet& m) {
+  k_validate_elems<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, m.st);
+  return sync_status(m);
+}
+
+// Stable compaction of every mesh (live vertices and elements in ascending
+// slot order), adjacency remapped (rows stay sorted: the map is monotone).
+int renumber(MeshSet& m) {
+  Work& w = m.w;
+  k_flags_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, w.vcnt);
+  k_flags_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, w.ecnt);
+  scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
+  scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
+  int* tot = w.counts + CN_NUM;
+  k_mesh_totals<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, w.escan, tot);
+  // the second buffer's flags must read "dead" beyond the new counts
+  cudaMemsetAsync(m.B.vflag, 0, m.S.vslots, m.stream);
+  k_renum_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, m.B, w.vscan, w.escan);
+  k_renum_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, m.B, w.vscan, w.escan);
+  cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
+  int err = sync_status(m);
+  if (err) return err;
+  for (int i = 0; i < m.nmesh; ++i) {
+    m.nv[i] = m.hcounts[2 * i];
+    m.ne[i] = m.hcounts[2 * i + 1];
+  }
+  std::swap(m.S.xy, m.B.xy);
+  std::swap(m.S.M, m.B.M);
+  std::swap(m.S.vflag, m.B.vflag);
+  std::swap(m.S.EN, m.B.EN);
+  std::swap(m.S.NN, m.B.NN);
+  std::swap(m.S.NNlen, m.B.NNlen);
+  std::swap(m.S.NE, m.B.NE);
+  std::swap(m.S.NElen, m.B.NElen);
+  std::vector<int> t(2 * m.nmesh);
+  for (int i = 0; i < m.nmesh; ++i) {
+    t[i] = m.nv[i];
+    t[m.nmesh + i] = m.ne[i];
+  }
+  cudaMemcpyAsync(m.S.tab.nv, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, m.stream);
+  return sync_status(m);
+}
+
+// Compacted, canonically rotated copy of mesh `mesh` into device buffers
+// (each may be null).  Writes the live counts.
+int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
+                int* ne_out) {
+  Work& w = m.w;
+  k_flags_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, w.vcnt);
+  k_flags_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, w.ecnt);
+  scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
+  scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
+  int* tot = w.counts + CN_NUM;
+  k_mesh_totals<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, w.escan, tot);
+  if (xy || mt)
+    k_out_v<<<grid_for(m, m.nv[mesh]), BLOCK, 0, m.stream>>>(m.S, mesh, w.vscan, xy, mt);
+  if (tri)
+    k_out_e<<<grid_for(m, m.ne[mesh]), BLOCK, 0, m.stream>>>(m.S, mesh, w.vscan, w.escan, tri);
+  cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
+  int err = sync_status(m);
+  if (err) return err;
+  *nv_out = m.hcounts[2 * mesh];
+  *ne_out = m.hcounts[2 * mesh + 1];
+  return PM_OK;
+}
+
+}  // namespace pm

@@ -1,0 +1,1177 @@
+// The adaptation operators (Sec. 2.4) run in rounds of independent sets
+// (Sec. 3.2).  One round of coarsening, swapping or smoothing is:
+//
+//   evaluate  every dirty vertex decides its operation on the current mesh and
+//             joins the candidate list (warp-aggregated atomic append, the
+//             worklist scheme of Sec. 3.4);
+//   select    candidates that beat every candidate neighbour by hash priority
+//             form the independent set S; the others stay dirty;
+//   apply     each member of S rewrites only its own ball (disjoint between
+//             members) and records which vertices' adjacency changes;
+//   commit    the deferred update of Sec. 3.3: after the whole set has been
+//             applied, every affected vertex rebuilds its own NN/NE rows from
+//             the operations of its S neighbours, so exactly one thread writes
+//             each list.
+//
+// Every kernel walks its list with a grid-stride loop over a count that lives
+// in device memory, so a round needs no host round trip until the candidate
+// count is read to decide termination.
+#include <algorithm>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+
+namespace {
+
+// ---- shared device helpers ---------------------------------------------------
+
+struct MeshCtx {
+  int mi, vb, eb;
+};
+
+__device__ __forceinline__ MeshCtx ctx_of(const Store& S, int slot) {
+  MeshCtx c;
+  c.mi = mesh_of_vslot(S, slot);
+  c.vb = S.tab.vbase[c.mi];
+  c.eb = S.tab.ebase[c.mi];
+  return c;
+}
+
+__device__ __forceinline__ const int* nn_row(const Store& S, int slot) {
+  return S.NN + (size_t)slot * S.W;
+}
+__device__ __forceinline__ const int* ne_row(const Store& S, int slot) {
+  return S.NE + (size_t)slot * S.W;
+}
+
+__device__ __forceinline__ int warp_max(int x) { return __reduce_max_sync(0xffffffffu, x); }
+
+// Per-mesh operation counter, aggregated over the lanes of a warp that share a
+// mesh (all lanes must call).
+__device__ __forceinline__ void count_op(const Store& S, bool pred, int mi) {
+  unsigned act = __ballot_sync(0xffffffffu, pred);
+  if (!act) return;
+  unsigned grp = __match_any_sync(0xffffffffu, pred ? mi : -1);
+  int lane = threadIdx.x & 31;
+  if (pred && (__ffs(grp) - 1) == lane) atomicAdd(S.tab.ops + mi, (unsigned long long)__popc(grp));
+}
+
+// Advance the per-mesh round counter of every mesh that formed candidates in
+// the round whose set was just selected (run by one block before the apply).
+__device__ __forceinline__ void advance_rounds(const Store& S) {
+  if (blockIdx.x != 0) return;
+  for (int i = threadIdx.x; i < S.nmesh; i += blockDim.x) {
+    if (S.tab.had[i]) {
+      S.tab.r[i] += 1;
+      S.tab.had[i] = 0;
+    }
+  }
+}
+
+__device__ __forceinline__ int count_elems_with(const Store& S, const int* ne, int nel, int eb,
+                                                int lw) {
+  int c = 0;
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[eb + ne[k]];
+    if (e.x == lw || e.y == lw || e.z == lw) ++c;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double elem_quality(const Store& S, int vb, int4 e) {
+  return quality_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
+                   load_vd(S, vb + e.z));
+}
+
+// ---- worklist initialisation ---------------------------------------------------
+
+// mode 0: every live vertex of an active mesh; mode 1: live interior vertices.
+__global__ void k_init_list(Store S, int mode, int* list, int* count) {
+  for (int i0 = blockIdx.x * blockDim.x; i0 < S.vslots; i0 += gridDim.x * blockDim.x) {
+    int s = i0 + threadIdx.x;
+    bool take = false;
+    if (s < S.vslots) {
+      int mi = mesh_of_vslot(S, s);
+      if (s - S.tab.vbase[mi] < S.tab.nv[mi] && S.tab.active[mi]) {
+        uint8_t f = S.vflag[s];
+        take = (f & VF_ALIVE) && (mode == 0 || !(f & VF_BND));
+      }
+    }
+    warp_append(take, s, list, count);
+  }
+}
+
+// ---- independent set (Sec. 3.2) -------------------------------------------------
+// v joins S when prio(v) exceeds the priority of every neighbour that is a
+// candidate of the same round.  Losers go to `keep` (still dirty / pending).
+__global__ void k_select(Store S, const int* C, const int* nCp, const int* cmark, int* smark,
+                         int tag, int* Sl, int* nS, int* keep, int* nkeep, int* kmark) {
+  const int n = *nCp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool win = false, lose = false;
+    int v = 0;
+    if (i < n) {
+      v = C[i];
+      MeshCtx c = ctx_of(S, v);
+      uint32_t seed = S.tab.seed[c.mi], r = S.tab.r[c.mi];
+      uint32_t pv = prio((uint32_t)(v - c.vb), seed, r);
+      const int* nn = nn_row(S, v);
+      int nnl = S.NNlen[v];
+      win = true;
+      for (int k = 0; k < nnl; ++k) {
+        int u = nn[k];
+        if (cmark[c.vb + u] == tag && prio((uint32_t)u, seed, r) > pv) {
+          win = false;
+          break;
+        }
+      }
+      if (win) smark[v] = tag;
+      else if (keep) lose = stamp_first(kmark, v, tag);
+    }
+    warp_append(win, v, Sl, nS);
+    if (keep) warp_append(lose, v, keep, nkeep);
+  }
+}
+
+// ---- coarsening (Sec. 2.4.1) ---------------------------------------------------
+
+struct CoarsenCtx {
+  const Store* S;
+  MeshCtx c;
+  int v, lv;
+  const int* nn;
+  int nnl;
+  const int* ne;
+  int nel;
+  VD dv;
+  bool bnd;
+};
+
+// Validity of collapsing v onto local neighbour u: link condition, all
+// remaining ball elements counter-clockwise, no new edge longer than L_up.
+__device__ bool collapse_valid(const CoarsenCtx& x, int u, double L_up) {
+  const Store& S = *x.S;
+  bool bedge = count_elems_with(S, x.ne, x.nel, x.c.eb, u) == 1;
+  if (x.bnd && !bedge) return false;
+  int ws = x.c.vb + u;
+  const int* nnw = nn_row(S, ws);
+  int nnwl = S.NNlen[ws];
+  int common = 0;
+  {
+    int a = 0, b = 0;
+    while (a < x.nnl && b < nnwl) {
+      int p = x.nn[a], q = nnw[b];
+      if (p == q) {
+        ++common;
+        ++a;
+        ++b;
+      } else if (p < q) {
+        ++a;
+      } else {
+        ++b;
+      }
+    }
+  }
+  if (common != (bedge ? 1 : 2)) return false;
+  VD dw = load_vd(S, ws);
+  for (int k = 0; k < x.nel; ++k) {
+    int4 e = S.EN[x.c.eb + x.ne[k]];
+    if (e.x == u || e.y == u || e.z == u) continue;
+    int i0 = e.x, i1 = e.y, i2 = e.z;
+    VD d0 = (i0 == x.lv) ? dw : load_vd(S, x.c.vb + i0);
+    VD d1 = (i1 == x.lv) ? dw : load_vd(S, x.c.vb + i1);
+    VD d2 = (i2 == x.lv) ? dw : load_vd(S, x.c.vb + i2);
+    if (i0 == x.lv) i0 = u;
+    if (i1 == x.lv) i1 = u;
+    if (i2 == x.lv) i2 = u;
+    if (!(orient_c(i0, i1, i2, d0, d1, d2) > 0.0)) return false;
+  }
+  for (int k = 0; k < x.nnl; ++k) {
+    int y = x.nn[k];
+    if (y == u || row_has(nnw, nnwl, y)) continue;
+    if (metric_len(dw, load_vd(S, x.c.vb + y)) > L_up) return false;
+  }
+  return true;
+}
+
+// Target of v (local id) or -1: the first neighbour, by (metric length, id),
+// shorter than L_low whose collapse is valid.
+__device__ int coarsen_target(const Store& S, int v, MeshCtx c) {
+  uint8_t f = S.vflag[v];
+  if (!(f & VF_ALIVE) || (f & VF_CORNER)) return -1;
+  CoarsenCtx x;
+  x.S = &S;
+  x.c = c;
+  x.v = v;
+  x.lv = v - c.vb;
+  x.nn = nn_row(S, v);
+  x.nnl = S.NNlen[v];
+  x.ne = ne_row(S, v);
+  x.nel = S.NElen[v];
+  x.dv = load_vd(S, v);
+  x.bnd = (f & VF_BND) != 0;
+  const double L_low = S.tab.L_low[c.mi], L_up = S.tab.L_up[c.mi];
+  double cl[MAXW];
+  int cw[MAXW];
+  int nc = 0;
+  for (int k = 0; k < x.nnl; ++k) {
+    int u = x.nn[k];
+    if (x.bnd && count_elems_with(S, x.ne, x.nel, c.eb, u) != 1) continue;
+    double L = metric_len(x.dv, load_vd(S, c.vb + u));
+    if (!(L < L_low)) continue;
+    int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
+    while (j > 0 && cl[j - 1] > L) {
+      cl[j] = cl[j - 1];
+      cw[j] = cw[j - 1];
+      --j;
+    }
+    cl[j] = L;
+    cw[j] = u;
+    ++nc;
+  }
+  for (int j = 0; j < nc; ++j)
+    if (collapse_valid(x, cw[j], L_up)) return cw[j];
+  return -1;
+}
+
+__global__ void k_coarsen_eval(Store S, const int* D, const int* nDp, int* target, int* C,
+                               int* nC, int* cmark, int tag) {
+  const int n = *nDp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int v = 0, t = -1;
+    if (i < n) {
+      v = D[i];
+      MeshCtx c = ctx_of(S, v);
+      t = coarsen_target(S, v, c);
+      target[v] = t;
+      if (t >= 0) {
+        cmark[v] = tag;
+        S.tab.had[c.mi] = 1;
+      }
+    }
+    warp_append(t >= 0, v, C, nC);
+  }
+}
+
+// Apply the collapses of S: elements containing edge (v, w) die, the other
+// ball elements take w in v's place (slot and orientation kept), v dies.
+// Neighbours of v are affected (rows change) and dirty for the next round.
+__global__ void k_coarsen_apply(Store S, const int* Sl, const int* nSp, const int* target,
+                                int* A, int* nA, int* amark, int* Dn, int* nDn, int* dmark,
+                                int tag) {
+  advance_rounds(S);
+  const int n = *nSp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool ok = i < n;
+    int v = 0, nnl = 0, mi = 0, vb = 0;
+    const int* nn = nullptr;
+    if (ok) {
+      v = Sl[i];
+      MeshCtx c = ctx_of(S, v);
+      mi = c.mi;
+      vb = c.vb;
+      int lv = v - c.vb;
+      int w = target[v];
+      const int* ne = ne_row(S, v);
+      int nel = S.NElen[v];
+      for (int k = 0; k < nel; ++k) {
+        int4* pe = S.EN + c.eb + ne[k];
+        int4 e = *pe;
+        if (e.x == w || e.y == w || e.z == w) {
+          e.w = 0;
+        } else {
+          if (e.x == lv) e.x = w;
+          if (e.y == lv) e.y = w;
+          if (e.z == lv) e.z = w;
+        }
+        *pe = e;
+      }
+      S.vflag[v] = (uint8_t)(S.vflag[v] & ~VF_ALIVE);
+      nn = nn_row(S, v);
+      nnl = S.NNlen[v];
+    }
+    count_op(S, ok, mi);
+    int kmax = warp_max(nnl);
+    for (int k = 0; k < kmax; ++k) {
+      bool has = ok && k < nnl;
+      int s = has ? vb + nn[k] : 0;
+      bool fa = has && stamp_first(amark, s, tag);
+      warp_append(fa, s, A, nA);
+      bool fd = has && stamp_first(dmark, s, tag);
+      warp_append(fd, s, Dn, nDn);
+    }
+  }
+}
+
+// Deferred-update commit of a coarsening round for affected vertex u:
+//   NN(u) <- (NN(u) minus collapsed neighbours) + their targets, and when u is
+//            the target of x: + NN(x) minus u;
+//   NE(u) <- live elements of NE(u) + (when u is the target of x) NE(x).
+__global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const int* target,
+                                 const int* smark, int tag, DevStatus* st) {
+  const int n = *nAp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int u = A[i];
+    MeshCtx c = ctx_of(S, u);
+    int lu = u - c.vb;
+    const int* nn = nn_row(S, u);
+    const int* ne = ne_row(S, u);
+    int nnl = S.NNlen[u], nel = S.NElen[u];
+    int nb[MAXW], eb[MAXW];
+    int nn2 = 0, ne2 = 0;
+    bool ok = true;
+    for (int k = 0; k < nel; ++k) {
+      int K = ne[k];
+      if (S.EN[c.eb + K].w) ok &= sorted_insert(eb, ne2, MAXW, K);
+    }
+    for (int k = 0; k < nnl; ++k) {
+      int x = nn[k];
+      int xs = c.vb + x;
+      if (smark[xs] != tag) {
+        ok &= sorted_insert(nb, nn2, MAXW, x);
+        continue;
+      }
+      int t = target[xs];
+      if (t != lu) {
+        ok &= sorted_insert(nb, nn2, MAXW, t);
+        continue;
+      }
+      const int* nnx = nn_row(S, xs);
+      int nnxl = S.NNlen[xs];
+      for (int j = 0; j < nnxl; ++j)
+        if (nnx[j] != lu) ok &= sorted_insert(nb, nn2, MAXW, nnx[j]);
+      const int* nex = ne_row(S, xs);
+      int nexl = S.NElen[xs];
+      for (int j = 0; j < nexl; ++j) {
+        int K = nex[j];
+        if (S.EN[c.eb + K].w) ok &= sorted_insert(eb, ne2, MAXW, K);
+      }
+    }
+    if (!ok || nn2 > S.W || ne2 > S.W) {
+      atomicExch(&st->overflow, 1);
+      atomicMax(&st->maxdeg, max(nn2, ne2));
+      continue;
+    }
+    int* wn = S.NN + (size_t)u * S.W;
+    int* we = S.NE + (size_t)u * S.W;
+    for (int k = 0; k < nn2; ++k) wn[k] = nb[k];
+    for (int k = 0; k < ne2; ++k) we[k] = eb[k];
+    S.NNlen[u] = nn2;
+    S.NElen[u] = ne2;
+  }
+}
+
+// ---- swapping (Sec. 2.4.3) ------------------------------------------------------
+
+// Best flip of v: over interior edges (v,w) with elements K1=(v,w,c) and
+// K2=(w,v,d), min quality below q_thresh, flip not duplicating edge (c,d) and
+// keeping (v,d,c), (d,w,c) counter-clockwise; the largest strictly positive
+// gain in minimum quality wins, ties to the smallest w.
+__device__ bool swap_eval(const Store& S, int v, MeshCtx c, int4& op, int& opK2) {
+  uint8_t f = S.vflag[v];
+  if (!(f & VF_ALIVE)) return false;
+  const double qt = S.tab.q_thresh[c.mi];
+  int lv = v - c.vb;
+  const int* ne = ne_row(S, v);
+  int nel = S.NElen[v];
+  int nxt[MAXW], prv[MAXW];
+  double q[MAXW];
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[c.eb + ne[k]];
+    int i = (e.x == lv) ? 0 : (e.y == lv) ? 1 : 2;
+    int a = (i == 0) ? e.y : (i == 1) ? e.z : e.x;  // after v
+    int b = (i == 0) ? e.z : (i == 1) ? e.x : e.y;  // before v
+    nxt[k] = a;
+    prv[k] = b;
+    q[k] = elem_quality(S, c.vb, e);
+  }
+  bool found = false;
+  double best = 0.0;
+  int bw = 0;
+  VD dv = load_vd(S, v);
+  for (int k1 = 0; k1 < nel; ++k1) {
+    int w = nxt[k1];
+    int cc = prv[k1];
+    int k2 = -1;
+    for (int k = 0; k < nel; ++k)
+      if (prv[k] == w) {
+        k2 = k;
+        break;
+      }
+    if (k2 < 0) continue;  // boundary edge
+    int d = nxt[k2];
+    double qold = (q[k1] < q[k2]) ? q[k1] : q[k2];
+    if (!(qold < qt)) continue;
+    if (row_has(nn_row(S, c.vb + d), S.NNlen[c.vb + d], cc)) continue;
+    VD dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc), dd = load_vd(S, c.vb + d);
+    if (!(orient_c(lv, d, cc, dv, dd, dc) > 0.0)) continue;
+    if (!(orient_c(d, w, cc, dd, dw, dc) > 0.0)) continue;
+    double n1 = quality_c(lv, d, cc, dv, dd, dc);
+    double n2 = quality_c(d, w, cc, dd, dw, dc);
+    double qnew = (n1 < n2) ? n1 : n2;
+    double gain = qnew - qold;
+    if (!(gain > 0.0)) continue;
+    if (!found || gain > best || (gain == best && w < bw)) {
+      found = true;
+      best = gain;
+      bw = w;
+      op = make_int4(w, cc, d, ne[k1]);
+      opK2 = ne[k2];
+    }
+  }
+  return found;
+}
+
+__global__ void k_swap_eval(Store S, const int* D, const int* nDp, int4* opA, int* opK2, int* C,
+                            int* nC, int* cmark, int tag) {
+  const int n = *nDp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int v = 0;
+    bool cand = false;
+    if (i < n) {
+      v = D[i];
+      MeshCtx c = ctx_of(S, v);
+      int4 op;
+      int k2;
+      cand = swap_eval(S, v, c, op, k2);
+      if (cand) {
+        opA[v] = op;
+        opK2[v] = k2;
+        cmark[v] = tag;
+        S.tab.had[c.mi] = 1;
+      }
+    }
+    warp_append(cand, v, C, nC);
+  }
+}
+
+__global__ void k_swap_apply(Store S, const int* Sl, const int* nSp, const int4* opA,
+                             const int* opK2, int* A, int* nA, int* amark, int* Dn, int* nDn,
+                             int* dmark, int tag) {
+  advance_rounds(S);
+  const int n = *nSp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool ok = i < n;
+    int mi = 0;
+    int t[4] = {0, 0, 0, 0};
+    if (ok) {
+      int v = Sl[i];
+      MeshCtx c = ctx_of(S, v);
+      mi = c.mi;
+      int lv = v - c.vb;
+      int4 op = opA[v];
+      int K2 = opK2[v];
+      S.EN[c.eb + op.w] = make_int4(lv, op.z, op.y, 1);  // K1 = (v, d, c)
+      S.EN[c.eb + K2] = make_int4(op.z, op.x, op.y, 1);  // K2 = (d, w, c)
+      t[0] = v;
+      t[1] = c.vb + op.x;
+      t[2] = c.vb + op.y;
+      t[3] = c.vb + op.z;
+    }
+    count_op(S, ok, mi);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bool fa = ok && stamp_first(amark, t[k], tag);
+      warp_append(fa, t[k], A, nA);
+      bool fd = ok && stamp_first(dmark, t[k], tag);
+      warp_append(fd, t[k], Dn, nDn);
+    }
+  }
+}
+
+// Deferred-update commit of a swap round for affected vertex u, from the
+// flips of u itself and of its S neighbours (records w, c, d, K1, K2):
+//   u == v: NN -w, NE -K2;  u == w: NN -v, NE -K1;
+//   u == c: NN +d, NE +K2;  u == d: NN +c, NE +K1.
+__global__ void k_swap_commit(Store S, const int* A, const int* nAp, const int4* opA,
+                              const int* opK2, const int* smark, int tag, DevStatus* st) {
+  const int n = *nAp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int u = A[i];
+    MeshCtx c = ctx_of(S, u);
+    int lu = u - c.vb;
+    int* nn = S.NN + (size_t)u * S.W;
+    int* ne = S.NE + (size_t)u * S.W;
+    int nnl = S.NNlen[u], nel = S.NElen[u];
+    int nb[MAXW], eb[MAXW];
+    for (int k = 0; k < nnl; ++k) nb[k] = nn[k];
+    for (int k = 0; k < nel; ++k) eb[k] = ne[k];
+    int nn2 = nnl, ne2 = nel;
+    bool ok = true;
+    for (int k = -1; k < nnl; ++k) {
+      int x = (k < 0) ? lu : nn[k];
+      int xs = c.vb + x;
+      if (smark[xs] != tag) continue;
+      int4 op = opA[xs];
+      int K2 = opK2[xs];
+      if (x == lu) {
+        sorted_erase(nb, nn2, op.x);
+        sorted_erase(eb, ne2, K2);
+      }
+      if (op.x == lu) {
+        sorted_erase(nb, nn2, x);
+        sorted_erase(eb, ne2, op.w);
+      }
+      if (op.y == lu) {
+        ok &= sorted_insert(nb, nn2, MAXW, op.z);
+        ok &= sorted_insert(eb, ne2, MAXW, K2);
+      }
+      if (op.z == lu) {
+        ok &= sorted_insert(nb, nn2, MAXW, op.y);
+        ok &= sorted_insert(eb, ne2, MAXW, op.w);
+      }
+    }
+    if (!ok || nn2 > S.W || ne2 > S.W) {
+      atomicExch(&st->overflow, 1);
+      atomicMax(&st->maxdeg, max(nn2, ne2));
+      continue;
+    }
+    for (int k = 0; k < nn2; ++k) nn[k] = nb[k];
+    for (int k = 0; k < ne2; ++k) ne[k] = eb[k];
+    S.NNlen[u] = nn2;
+    S.NElen[u] = ne2;
+  }
+}
+
+// ---- smoothing (Sec. 2.4.4) -------------------------------------------------------
+
+__device__ __forceinline__ double ball_min_quality(const Store& S, MeshCtx c, const int* ne,
+                                                   int nel, double* qsum) {
+  double qmin = 0.0, sum = 0.0;
+  for (int k = 0; k < nel; ++k) {
+    double q = elem_quality(S, c.vb, S.EN[c.eb + ne[k]]);
+    if (k == 0 || q < qmin) qmin = q;
+    sum = sum + q;
+  }
+  if (qsum) *qsum = sum;
+  return qmin;
+}
+
+// Locate (X, Y) in v's ball (v at its current place) and interpolate the
+// metric barycentrically there.
+__device__ bool interpolate_in_ball(const Store& S, MeshCtx c, const int* ne, int nel, double X,
+                                    double Y, double4& Mout) {
+  VD px{X, Y, 0.0, 0.0, 0.0};
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[c.eb + ne[k]];
+    int i0 = e.x, i1 = e.y, i2 = e.z;
+    VD a = load_vd(S, c.vb + i0), b = load_vd(S, c.vb + i1), d = load_vd(S, c.vb + i2);
+    canon(i0, i1, i2, a, b, d);
+    double o = orient3(a, b, d);
+    double l0 = orient3(px, b, d) / o;
+    double l1 = orient3(a, px, d) / o;
+    double l2 = orient3(a, b, px) / o;
+    if (l0 >= 0.0 && l1 >= 0.0 && l2 >= 0.0) {
+      Mout.x = (l0 * a.m00 + l1 * b.m00) + l2 * d.m00;
+      Mout.y = (l0 * a.m01 + l1 * b.m01) + l2 * d.m01;
+      Mout.z = (l0 * a.m11 + l1 * b.m11) + l2 * d.m11;
+      Mout.w = 0.0;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Ball with v moved to (X, Y, M): all counter-clockwise?  min and sum of q.
+__device__ bool ball_after_move(const Store& S, MeshCtx c, int lv, const int* ne, int nel,
+                                double X, double Y, double4 Mv, double& qmin, double& qsum) {
+  VD nvd{X, Y, Mv.x, Mv.y, Mv.z};
+  qmin = 0.0;
+  qsum = 0.0;
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[c.eb + ne[k]];
+    VD a = (e.x == lv) ? nvd : load_vd(S, c.vb + e.x);
+    VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
+    VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
+    if (!(orient_c(e.x, e.y, e.z, a, b, d) > 0.0)) return false;
+    double q = quality_c(e.x, e.y, e.z, a, b, d);
+    if (k == 0 || q < qmin) qmin = q;
+    qsum = qsum + q;
+  }
+  return true;
+}
+
+// Quality-constrained Laplacian move of v: metric-weighted neighbour mean,
+// metric interpolated at the target, kept when the ball stays valid and its
+// minimum quality strictly increases.
+__device__ bool smooth_eval(const Store& S, int v, MeshCtx c, double2& X, double4& Mv) {
+  uint8_t f = S.vflag[v];
+  if (!(f & VF_ALIVE) || (f & VF_BND)) return false;
+  const int* ne = ne_row(S, v);
+  int nel = S.NElen[v];
+  double qold = ball_min_quality(S, c, ne, nel, nullptr);
+  if (!(qold < S.tab.q_thresh[c.mi])) return false;
+  const int* nn = nn_row(S, v);
+  int nnl = S.NNlen[v];
+  double4 mv = S.M[v];
+  double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
+  for (int k = 0; k < nnl; ++k) {
+    int js = c.vb + nn[k];
+    double2 pj = S.xy[js];
+    double4 mj = S.M[js];
+    double w00 = 0.5 * (mv.x + mj.x);
+    double w01 = 0.5 * (mv.y + mj.y);
+    double w11 = 0.5 * (mv.z + mj.z);
+    a00 = a00 + w00;
+    a01 = a01 + w01;
+    a11 = a11 + w11;
+    b0 = b0 + (w00 * pj.x + w01 * pj.y);
+    b1 = b1 + (w01 * pj.x + w11 * pj.y);
+  }
+  double det = a00 * a11 - a01 * a01;
+  if (!(det > 0.0)) return false;
+  double x = (a11 * b0 - a01 * b1) / det;
+  double y = (a00 * b1 - a01 * b0) / det;
+  double4 Mn;
+  if (!interpolate_in_ball(S, c, ne, nel, x, y, Mn)) return false;
+  double qmin, qsum;
+  if (!ball_after_move(S, c, v - c.vb, ne, nel, x, y, Mn, qmin, qsum)) return false;
+  if (!(qmin > qold)) return false;
+  X = make_double2(x, y);
+  Mv = Mn;
+  return true;
+}
+
+__global__ void k_smooth_eval(Store S, const int* D, const int* nDp, double2* mvxy, double4* mvM,
+                              int* C, int* nC, int* cmark, int tag) {
+  const int n = *nDp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int v = 0;
+    bool cand = false;
+    if (i < n) {
+      v = D[i];
+      MeshCtx c = ctx_of(S, v);
+      double2 X;
+      double4 Mv;
+      cand = smooth_eval(S, v, c, X, Mv);
+      if (cand) {
+        mvxy[v] = X;
+        mvM[v] = Mv;
+        cmark[v] = tag;
+        S.tab.had[c.mi] = 1;
+      }
+    }
+    warp_append(cand, v, C, nC);
+  }
+}
+
+// Move the members of S; live interior neighbours become pending for the next
+// sweep (stamp pmark with the sweep tag).
+__global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const double2* mvxy,
+                               const double4* mvM, int* P, int* nP, int* pmark, int ptag) {
+  advance_rounds(S);
+  const int n = *nSp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool ok = i < n;
+    int mi = 0, vb = 0, nnl = 0;
+    const int* nn = nullptr;
+    if (ok) {
+      int v = Sl[i];
+      MeshCtx c = ctx_of(S, v);
+      mi = c.mi;
+      vb = c.vb;
+      S.xy[v] = mvxy[v];
+      S.M[v] = mvM[v];
+      nn = nn_row(S, v);
+      nnl = S.NNlen[v];
+    }
+    count_op(S, ok, mi);
+    int kmax = warp_max(nnl);
+    for (int k = 0; k < kmax; ++k) {
+      bool has = ok && k < nnl;
+      int s = has ? vb + nn[k] : 0;
+      bool take = false;
+      if (has) {
+        uint8_t f = S.vflag[s];
+        take = (f & VF_ALIVE) && !(f & VF_BND) && stamp_first(pmark, s, ptag);
+      }
+      warp_append(take, s, P, nP);
+    }
+  }
+}
+
+// Optimisation-based smoothing of one member of S (gradient ascent of the
+// ball's quality sum in v's coordinates, metric fixed; step 0.1 * shortest
+// incident edge / |g|, halved up to five times; kept when every element stays
+// counter-clockwise, the minimum quality does not drop and the sum rises).
+__device__ bool opt_eval(const Store& S, int v, MeshCtx c, double2& Xo, double4& Mo) {
+  uint8_t f = S.vflag[v];
+  if (!(f & VF_ALIVE) || (f & VF_BND)) return false;
+  int lv = v - c.vb;
+  const int* ne = ne_row(S, v);
+  int nel = S.NElen[v];
+  double gx = 0.0, gy = 0.0;
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[c.eb + ne[k]];
+    double g[3][5];
+    quality_grad_c(e.x, e.y, e.z, load_vd(S, c.vb + e.x), load_vd(S, c.vb + e.y),
+                   load_vd(S, c.vb + e.z), g);
+    int i = (e.x == lv) ? 0 : (e.y == lv) ? 1 : 2;
+    gx = gx + g[i][0];
+    gy = gy + g[i][1];
+  }
+  double gn = sqrt(gx * gx + gy * gy);
+  if (!(gn > 0.0)) return false;
+  const int* nn = nn_row(S, v);
+  int nnl = S.NNlen[v];
+  double2 pv = S.xy[v];
+  double lmin = 0.0;
+  for (int k = 0; k < nnl; ++k) {
+    double2 pj = S.xy[c.vb + nn[k]];
+    double dx = pj.x - pv.x;
+    double dy = pj.y - pv.y;
+    double l = sqrt(dx * dx + dy * dy);
+    if (k == 0 || l < lmin) lmin = l;
+  }
+  double qsum_old;
+  double qmin_old = ball_min_quality(S, c, ne, nel, &qsum_old);
+  double alpha = (0.1 * lmin) / gn;
+  for (int k = 0; k < 6; ++k) {
+    double X = pv.x + alpha * gx;
+    double Y = pv.y + alpha * gy;
+    double4 Mn;
+    if (interpolate_in_ball(S, c, ne, nel, X, Y, Mn)) {
+      double qmin, qsum;
+      if (ball_after_move(S, c, lv, ne, nel, X, Y, Mn, qmin, qsum) && qmin >= qmin_old &&
+          qsum > qsum_old) {
+        Xo = make_double2(X, Y);
+        Mo = Mn;
+        return true;
+      }
+    }
+    alpha = alpha * 0.5;
+  }
+  return false;
+}
+
+// Evaluate and apply in one pass: members of S are pairwise non-adjacent, so
+// no member reads a vertex another member moves.
+__global__ void k_opt_apply(Store S, const int* Sl, const int* nSp) {
+  advance_rounds(S);
+  const int n = *nSp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool moved = false;
+    int mi = 0;
+    if (i < n) {
+      int v = Sl[i];
+      MeshCtx c = ctx_of(S, v);
+      mi = c.mi;
+      double2 X;
+      double4 Mv;
+      moved = opt_eval(S, v, c, X, Mv);
+      if (moved) {
+        S.xy[v] = X;
+        S.M[v] = Mv;
+      }
+    }
+    count_op(S, moved, mi);
+  }
+}
+
+// Every listed vertex is a candidate of this round.
+__global__ void k_stamp_list(Store S, const int* L, const int* nLp, int* cmark, int tag) {
+  const int n = *nLp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int v = L[i];
+    cmark[v] = tag;
+    S.tab.had[mesh_of_vslot(S, v)] = 1;
+  }
+}
+
+// ---- refinement (Sec. 2.4.2) -----------------------------------------------------
+
+// Mark edges (a, b), a < b, longer than L_up: bit k of vmask[a] for NN entry k.
+__global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+    int mi = mesh_of_vslot(S, s);
+    int vb = S.tab.vbase[mi];
+    unsigned long long m = 0;
+    if (s - vb < S.tab.nv[mi] && S.tab.active[mi] && (S.vflag[s] & VF_ALIVE)) {
+      int la = s - vb;
+      const int* nn = nn_row(S, s);
+      int nnl = S.NNlen[s];
+      VD da = load_vd(S, s);
+      const double L_up = S.tab.L_up[mi];
+      for (int k = 0; k < nnl; ++k) {
+        int b = nn[k];
+        if (b <= la) continue;
+        if (metric_len(da, load_vd(S, vb + b)) > L_up) m |= 1ull << k;
+      }
+    }
+    mask[s] = m;
+    cnt[s] = __popcll(m);
+  }
+}
+
+// Per-mesh number of new vertices (edges to split).
+__global__ void k_refine_newcount(Store S, const int* vscan, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nmesh) return;
+  int vb = S.tab.vbase[i];
+  out[i] = vscan[vb + S.tab.nv[i]] - vscan[vb];
+}
+
+// A mesh that splits edges counts the round and its splits.
+__global__ void k_refine_vtotals(Store S, const int* vscan) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nmesh) return;
+  int vb = S.tab.vbase[i];
+  int t = vscan[vb + S.tab.nv[i]] - vscan[vb];
+  if (t > 0) {
+    S.tab.r[i] += 1;
+    S.tab.ops[i] += (unsigned long long)t;
+  }
+}
+
+__device__ __forceinline__ int mid_id(const Store& S, int vb, int nv, const int* vscan,
+                                      const unsigned long long* mask, int p, int q) {
+  int a = p < q ? p : q, b = p < q ? q : p;
+  unsigned long long m = mask[vb + a];
+  if (!m) return -1;
+  int k = row_find(nn_row(S, vb + a), S.NNlen[vb + a], b);
+  if (k < 0 || !((m >> k) & 1ull)) return -1;
+  int rank = __popcll(m & ((1ull << k) - 1ull));
+  return nv + (vscan[vb + a] - vscan[vb]) + rank;
+}
+
+__global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long long* mask) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+    unsigned long long m = mask[s];
+    if (!m) continue;
+    int mi = mesh_of_vslot(S, s);
+    int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi], nv = S.tab.nv[mi];
+    const int* nn = nn_row(S, s);
+    const int* ne = ne_row(S, s);
+    int nel = S.NElen[s];
+    int base = nv + (vscan[s] - vscan[vb]);
+    int rank = 0;
+    VD da = load_vd(S, s);
+    while (m) {
+      int k = __ffsll((long long)m) - 1;
+      m &= m - 1;
+      int b = nn[k];
+      VD db = load_vd(S, vb + b);
+      int slot = vb + base + rank;
+      ++rank;
+      S.xy[slot] = make_double2(0.5 * (da.x + db.x), 0.5 * (da.y + db.y));
+      S.M[slot] = make_double4(0.5 * (da.m00 + db.m00), 0.5 * (da.m01 + db.m01),
+                               0.5 * (da.m11 + db.m11), 0.0);
+      bool bedge = count_elems_with(S, ne, nel, eb, b) == 1;
+      S.vflag[slot] = (uint8_t)(VF_ALIVE | (bedge ? VF_BND : 0));
+    }
+  }
+}
+
+// Children per live element (1..4) and the midpoint ids of its edges.
+__global__ void k_refine_count(Store S, const int* vscan, const unsigned long long* mask,
+                               int* ecnt, int4* emid) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+    int mi = mesh_of_eslot(S, s);
+    int eb = S.tab.ebase[mi];
+    int extra = 0;
+    if (s - eb < S.tab.ne[mi] && S.tab.active[mi]) {
+      int4 e = S.EN[s];
+      if (e.w) {
+        int vb = S.tab.vbase[mi], nv = S.tab.nv[mi];
+        int m0 = mid_id(S, vb, nv, vscan, mask, e.x, e.y);
+        int m1 = mid_id(S, vb, nv, vscan, mask, e.y, e.z);
+        int m2 = mid_id(S, vb, nv, vscan, mask, e.z, e.x);
+        extra = (m0 >= 0) + (m1 >= 0) + (m2 >= 0);
+        emid[s] = make_int4(m0, m1, m2, extra);
+      }
+    }
+    ecnt[s] = extra;
+  }
+}
+
+// Templates: one split -> (a,m,o),(m,b,o); two splits -> (m0,u1,m1) plus the
+// trapezoid (u0,m0,m1,u2) cut along its metric-shorter diagonal; three
+// splits -> four children.  The first child keeps the parent's slot, the rest
+// take ne + scan(extra children) in parent order.
+__global__ void k_refine_split(Store S, const int* escan, const int4* emid) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+    int mi = mesh_of_eslot(S, s);
+    int eb = S.tab.ebase[mi];
+    if (!(s - eb < S.tab.ne[mi]) || !S.tab.active[mi]) continue;
+    int4 e = S.EN[s];
+    if (!e.w) continue;
+    int4 md = emid[s];
+    if (md.w == 0) continue;
+    int vb = S.tab.vbase[mi];
+    int nslot = eb + S.tab.ne[mi] + (escan[s] - escan[eb]);
+    int t[3] = {e.x, e.y, e.z};
+    int mm[3] = {md.x, md.y, md.z};
+    if (md.w == 1) {
+      int i = (mm[0] >= 0) ? 0 : (mm[1] >= 0) ? 1 : 2;
+      int a = t[i], b = t[(i + 1) % 3], o = t[(i + 2) % 3], m = mm[i];
+      S.EN[s] = make_int4(a, m, o, 1);
+      S.EN[nslot] = make_int4(m, b, o, 1);
+    } else if (md.w == 2) {
+      int j = (mm[0] < 0) ? 0 : (mm[1] < 0) ? 1 : 2;
+      int q = (j + 1) % 3;
+      int u0 = t[q], u1 = t[(q + 1) % 3], u2 = t[(q + 2) % 3];
+      int m0 = mm[q], m1 = mm[(q + 1) % 3];
+      S.EN[s] = make_int4(m0, u1, m1, 1);
+      double d1 = metric_len(load_vd(S, vb + u0), load_vd(S, vb + m1));
+      double d2 = metric_len(load_vd(S, vb + m0), load_vd(S, vb + u2));
+      if (d1 <= d2) {
+        S.EN[nslot] = make_int4(u0, m0, m1, 1);
+        S.EN[nslot + 1] = make_int4(u0, m1, u2, 1);
+      } else {
+        S.EN[nslot] = make_int4(u0, m0, u2, 1);
+        S.EN[nslot + 1] = make_int4(m0, m1, u2, 1);
+      }
+    } else {
+      S.EN[s] = make_int4(t[0], mm[0], mm[2], 1);
+      S.EN[nslot] = make_int4(mm[0], t[1], mm[1], 1);
+      S.EN[nslot + 1] = make_int4(mm[2], mm[1], t[2], 1);
+      S.EN[nslot + 2] = make_int4(mm[0], mm[1], mm[2], 1);
+    }
+  }
+}
+
+__global__ void k_refine_sizes(Store S, const int* vscan, const int* escan) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nmesh) return;
+  int vb = S.tab.vbase[i], eb = S.tab.ebase[i];
+  int nv = S.tab.nv[i], ne = S.tab.ne[i];
+  S.tab.nv[i] = nv + (vscan[vb + nv] - vscan[vb]);
+  S.tab.ne[i] = ne + (escan[eb + ne] - escan[eb]);
+}
+
+// ---- host helpers --------------------------------------------------------------
+
+struct RoundIO {
+  int nC;
+  int overflow;
+  int err;
+};
+
+RoundIO read_round(MeshSet& m) {
+  cudaMemcpyAsync(m.hcounts, m.w.counts, CN_NUM * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
+  cudaMemcpyAsync(m.hst, m.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, m.stream);
+  cudaError_t e = cudaStreamSynchronize(m.stream);
+  RoundIO io;
+  io.nC = m.hcounts[CN_C];
+  io.overflow = m.hst->overflow;
+  io.err = (e != cudaSuccess) ? PM_ERR_CUDA : m.hst->err;
+  if (e != cudaSuccess) set_last_error(std::string("CUDA: ") + cudaGetErrorString(e));
+  return io;
+}
+
+void zero_counts(MeshSet& m, int first, int num) {
+  cudaMemsetAsync(m.w.counts + first, 0, num * sizeof(int), m.stream);
+}
+
+int after_round(MeshSet& m, const RoundIO& io) {
+  if (io.err) return io.err;
+  if (io.overflow) return rebuild_adjacency(m, false, nullptr);
+  return PM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Operator loops (host)
+// ---------------------------------------------------------------------------
+
+void zero_ops(MeshSet& m) {
+  cudaMemsetAsync(m.S.tab.ops, 0, m.nmesh * sizeof(unsigned long long), m.stream);
+}
+
+cudaError_t fetch_ops(MeshSet& m, std::vector<unsigned long long>& ops) {
+  ops.resize(m.nmesh);
+  cudaError_t e = cudaMemcpyAsync(ops.data(), m.S.tab.ops, m.nmesh * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, m.stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(m.stream);
+}
+
+// Rounds of collapses until no dirty vertex has a valid collapse.
+int op_coarsen(MeshSet& m, int max_rounds) {
+  Work& w = m.w;
+  const int gv = grid_for(m, m.S.vslots);
+  zero_counts(m, 0, CN_NUM);
+  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 0, w.D[0], w.counts + CN_D0);
+  int cur = 0;
+  for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
+    int tag = ++m.tag;
+    int nxt = 1 - cur;
+    zero_counts(m, CN_C, 3);
+    zero_counts(m, nxt, 1);
+    k_coarsen_eval<<<gv, BLOCK, 0, m.stream>>>(m.S, w.D[cur], w.counts + cur, w.target, w.C,
+                                               w.counts + CN_C, w.cmark, tag);
+    k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
+                                         w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
+    k_coarsen_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S, w.target, w.A,
+                                                w.counts + CN_A, w.amark, w.D[nxt],
+                                                w.counts + nxt, w.dmark, tag);
+    k_coarsen_commit<<<gv, BLOCK, 0, m.stream>>>(m.S, w.A, w.counts + CN_A, w.target, w.smark, tag,
+                                                 m.st);
+    RoundIO io = read_round(m);
+    if (io.nC == 0) break;
+    int err = after_round(m, io);
+    if (err) return err;
+    cur = nxt;
+  }
+  return PM_OK;
+}
+
+// Rounds of flips until no dirty vertex has an improving flip.
+int op_swap(MeshSet& m, int max_rounds) {
+  Work& w = m.w;
+  const int gv = grid_for(m, m.S.vslots);
+  zero_counts(m, 0, CN_NUM);
+  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 0, w.D[0], w.counts + CN_D0);
+  int cur = 0;
+  for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
+    int tag = ++m.tag;
+    int nxt = 1 - cur;
+    zero_counts(m, CN_C, 3);
+    zero_counts(m, nxt, 1);
+    k_swap_eval<<<gv, BLOCK, 0, m.stream>>>(m.S, w.D[cur], w.counts + cur, w.opA, w.opK2, w.C,
+                                            w.counts + CN_C, w.cmark, tag);
+    k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
+                                         w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
+    k_swap_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S, w.opA, w.opK2, w.A,
+                                             w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt,
+                                             w.dmark, tag);
+    k_swap_commit<<<gv, BLOCK, 0, m.stream>>>(m.S, w.A, w.counts + CN_A, w.opA, w.opK2, w.smark,
+                                              tag, m.st);
+    RoundIO io = read_round(m);
+    if (io.nC == 0) break;
+    int err = after_round(m, io);
+    if (err) return err;
+    cur = nxt;
+  }
+  return PM_OK;
+}
+
+// Rounds of splits until no edge is longer than L_up.  Capacity is checked
+// (and grown) before any new vertex or element is written.
+int op_refine(MeshSet& m, int max_rounds) {
+  Work& w = m.w;
+  for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
+    const int gv = grid_for(m, m.S.vslots);
+    const int ge = grid_for(m, m.S.eslots);
+    k_refine_mark<<<gv, BLOCK, 0, m.stream>>>(m.S, w.vcnt, w.vmask);
+    scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
+    int* tot = w.counts + CN_NUM;
+    std::vector<int> newv(m.nmesh);
+    k_refine_newcount<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, tot);
+    cudaMemcpyAsync(m.hcounts + CN_NUM, tot, m.nmesh * sizeof(int), cudaMemcpyDeviceToHost,
+                    m.stream);
+    {
+      int err = sync_status(m);
+      if (err) return err;
+    }
+    for (int i = 0; i < m.nmesh; ++i) newv[i] = m.hcounts[CN_NUM + i];
+    long long total = 0;
+    bool need_grow = false;
+    std::vector<int> vcap = m.vcap, ecap = m.ecap;
+    for (int i = 0; i < m.nmesh; ++i) {
+      total += newv[i];
+      long long vneed = (long long)m.nv[i] + newv[i];
+      long long eneed = (long long)m.ne[i] + 2LL * newv[i];
+      if (vneed > m.vcap[i]) {
+        vcap[i] = (int)std::min<long long>(std::max<long long>(2LL * m.vcap[i], vneed + vneed / 2),
+                                           (1LL << 30));
+        need_grow = true;
+      }
+      if (eneed > m.ecap[i]) {
+        ecap[i] = (int)std::min<long long>(std::max<long long>(2LL * m.ecap[i], eneed + eneed / 2),
+                                           (1LL << 30));
+        need_grow = true;
+      }
+    }
+    if (total == 0) break;
+    if (need_grow) {
+      cudaError_t e = grow(m, vcap, ecap, m.S.W);
+      if (e != cudaSuccess) {
+        set_last_error(std::string("growing mesh storage: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;
+      }
+      --nr;  // redo this round on the new layout
+      continue;
+    }
+    k_refine_vtotals<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan);
+    k_refine_newverts<<<gv, BLOCK, 0, m.stream>>>(m.S, w.vscan, w.vmask);
+    k_refine_count<<<ge, BLOCK, 0, m.stream>>>(m.S, w.vscan, w.vmask, w.ecnt, w.emid);
+    scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
+    k_refine_split<<<ge, BLOCK, 0, m.stream>>>(m.S, w.escan, w.emid);
+    k_refine_sizes<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, w.escan);
+    cudaError_t e = refresh_sizes(m);
+    if (e != cudaSuccess) return PM_ERR_CUDA;
+    int err = rebuild_adjacency(m, false, nullptr);
+    if (err) return err;
+  }
+  return PM_OK;
+}
+
+// Laplacian sweeps, each a sequence of rounds over the sweep's pending set.
+int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
+  Work& w = m.w;
+  const int gv = grid_for(m, m.S.vslots);
+  zero_counts(m, 0, CN_NUM);
+  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 1, w.D[0], w.counts + CN_D0);
+  long long nr = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int ptag = ++m.tag;  // stamp of the next sweep's pending list
+    zero_counts(m, CN_P, 1);
+    int cur = 0;
+    bool moved = false;
+    while (max_rounds == 0 || nr < max_rounds) {
+      int tag = ++m.tag;
+      int nxt = 1 - cur;
+      zero_counts(m, CN_C, 2);
+      zero_counts(m, nxt, 1);
+      k_smooth_eval<<<gv, BLOCK, 0, m.stream>>>(m.S, w.D[cur], w.counts + cur, w.mvxy, w.mvM, w.C,
+                                                w.counts + CN_C, w.cmark, tag);
+      k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
+                                           w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt,
+                                           w.dmark);
+      k_smooth_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S, w.mvxy, w.mvM, w.P,
+                                                 w.counts + CN_P, w.pmark, ptag);
+      RoundIO io = read_round(m);
+      if (io.err) return io.err;
+      if (io.nC == 0) break;
+      ++nr;
+      moved = true;
+      cur = nxt;
+    }
+    if (!moved) break;
+    // the next sweep's pending list becomes the current list
+    std::swap(w.D[0], w.P);
+    cudaMemcpyAsync(w.counts + CN_D0, w.counts + CN_P, sizeof(int), cudaMemcpyDeviceToDevice,
+                    m.stream);
+  }
+  return PM_OK;
+}
+
+// Rounds of optimisation-based smoothing over all interior vertices.
+int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds) {
+  Work& w = m.w;
+  const int gv = grid_for(m, m.S.vslots);
+  zero_counts(m, 0, CN_NUM);
+  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 1, w.C, w.counts + CN_C);
+  for (int it = 0; it < nrounds && (max_rounds == 0 || it < max_rounds); ++it) {
+    int tag = ++m.tag;
+    zero_counts(m, CN_S, 1);
+    k_stamp_list<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, tag);
+    k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
+                                         w.counts + CN_S, nullptr, nullptr, nullptr);
+    k_opt_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S);
+  }
+  return sync_status(m);
+}
+
+}  // namespace pm

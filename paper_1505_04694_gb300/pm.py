@@ -1,0 +1,320 @@
+"""Python binding of the C interface in include/pm.h (argument marshalling only).
+
+Every step of the adaptation runs in the CUDA library
+``paper_1505_04694_gb300/_build/libpm.so``; this module never computes
+anything itself.  Importing it raises ImportError when the library has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``).
+
+Host arrays are numpy; device arrays are torch CUDA tensors (their
+``data_ptr()`` is passed to the ``*_dev`` entry points).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpm.so")
+
+PM_OK = 0
+STATUS_NAMES = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_INVALID_MESH", 3: "PM_ERR_OOM",
+                4: "PM_ERR_CAPACITY", 5: "PM_ERR_CUDA", 6: "PM_ERR_TIMEOUT"}
+
+# Every function declared in include/pm.h.
+EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_stream",
+           "pm_set_metric", "pm_set_metric_dev", "pm_coarsen", "pm_refine", "pm_swap",
+           "pm_smooth", "pm_adapt", "pm_opt_smooth", "pm_adapt_batch", "pm_get_mesh",
+           "pm_get_mesh_dev", "pm_get_raw", "pm_adjacency", "pm_quality",
+           "pm_quality_arrays_dev", "pm_status_string", "pm_last_error"]
+
+
+class PmParams(C.Structure):
+    _fields_ = [("L_low", C.c_double), ("L_up", C.c_double), ("q_thresh", C.c_double),
+                ("max_iter", C.c_int32), ("max_smooth_sweeps", C.c_int32),
+                ("seed", C.c_uint32), ("opt_smooth_rounds", C.c_int32),
+                ("max_rounds", C.c_int32)]
+
+
+class PmStats(C.Structure):
+    _fields_ = [("rounds", C.c_int64), ("collapses", C.c_int64), ("splits", C.c_int64),
+                ("flips", C.c_int64), ("moves", C.c_int64), ("converged", C.c_int32),
+                ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PmError(RuntimeError):
+    def __init__(self, status, where, msg=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {msg}".strip())
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing")
+    try:  # let torch's CUDA runtime satisfy libcudart when it is installed
+        import torch  # noqa: F401
+    except Exception:
+        pass
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip, up = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
+    mp = C.POINTER(C.c_void_p)
+    sig = {
+        "pm_mesh_create": [dp, C.c_int32, ip, C.c_int32, up, C.c_int32, C.c_int, mp],
+        "pm_mesh_create_dev": [vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, vp, mp],
+        "pm_mesh_destroy": [vp],
+        "pm_set_stream": [vp, vp],
+        "pm_set_metric": [vp, dp],
+        "pm_set_metric_dev": [vp, vp],
+        "pm_coarsen": [vp, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_refine": [vp, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_swap": [vp, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_smooth": [vp, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_adapt": [vp, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_opt_smooth": [vp, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_adapt_batch": [mp, C.c_int32, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_get_mesh": [vp, ip, ip, dp, ip, dp],
+        "pm_get_mesh_dev": [vp, ip, ip, vp, vp, vp],
+        "pm_get_raw": [vp, ip, ip, dp, dp, ip, up, up, up],
+        "pm_adjacency": [vp, C.c_int32, ip, ip, ip, ip, C.c_int32],
+        "pm_quality": [vp, dp, dp, dp],
+        "pm_quality_arrays_dev": [vp, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.pm_status_string.argtypes = [C.c_int]
+    L.pm_status_string.restype = C.c_char_p
+    L.pm_last_error.argtypes = []
+    L.pm_last_error.restype = C.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(status, where):
+    if status != PM_OK:
+        raise PmError(status, where, lib.pm_last_error().decode())
+
+
+def _d(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _u(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+@dataclass
+class Params:
+    """pm_params (same defaults as the paper-derived workloads)."""
+    L_low: float = 0.4
+    L_up: float = 2.0 ** 0.5
+    q_thresh: float = 0.7
+    max_iter: int = 10
+    max_smooth_sweeps: int = 10
+    seed: int = 1
+    opt_smooth_rounds: int = 0
+    max_rounds: int = 0
+
+    def c(self) -> PmParams:
+        return PmParams(self.L_low, self.L_up, self.q_thresh, self.max_iter,
+                        self.max_smooth_sweeps, self.seed & 0xFFFFFFFF, self.opt_smooth_rounds,
+                        self.max_rounds)
+
+
+def as_params(p) -> PmParams:
+    if isinstance(p, PmParams):
+        return p
+    if isinstance(p, Params):
+        return p.c()
+    return Params(**{k: getattr(p, k) for k in Params.__dataclass_fields__}).c()
+
+
+class Mesh:
+    """A mesh on the GPU (pm_mesh handle)."""
+
+    def __init__(self, handle):
+        self.h = C.c_void_p(handle)
+
+    # -- creation ------------------------------------------------------------
+    @classmethod
+    def from_host(cls, xy, tri, corner=None, cap_factor=2, device=0):
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        cp = None
+        if corner is not None:
+            corner = np.ascontiguousarray(corner, dtype=np.uint8)
+            cp = _u(corner)
+        out = C.c_void_p()
+        _check(lib.pm_mesh_create(_d(xy), xy.shape[0], _i(tri), tri.shape[0], cp, cap_factor,
+                                  device, C.byref(out)), "pm_mesh_create")
+        return cls(out.value)
+
+    @classmethod
+    def from_device(cls, xy, tri, corner=None, cap_factor=2, stream=None):
+        """xy: (nv,2) float64 CUDA tensor; tri: (ne,3) int32 CUDA tensor."""
+        out = C.c_void_p()
+        _check(lib.pm_mesh_create_dev(C.c_void_p(xy.data_ptr()), xy.shape[0],
+                                      C.c_void_p(tri.data_ptr()), tri.shape[0],
+                                      C.c_void_p(corner.data_ptr()) if corner is not None else None,
+                                      cap_factor, C.c_void_p(stream), C.byref(out)),
+               "pm_mesh_create_dev")
+        return cls(out.value)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            lib.pm_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        _check(lib.pm_set_stream(self.h, C.c_void_p(stream)), "pm_set_stream")
+
+    # -- metric --------------------------------------------------------------
+    def set_metric(self, m):
+        m = np.ascontiguousarray(m, dtype=np.float64).reshape(-1, 3)
+        _check(lib.pm_set_metric(self.h, _d(m)), "pm_set_metric")
+        return self
+
+    def set_metric_dev(self, m):
+        _check(lib.pm_set_metric_dev(self.h, C.c_void_p(m.data_ptr())), "pm_set_metric_dev")
+        return self
+
+    # -- operators -------------------------------------------------------------
+    def _op(self, fn, name, params):
+        st = PmStats()
+        p = as_params(params)
+        _check(fn(self.h, C.byref(p), C.byref(st)), name)
+        return st.as_dict()
+
+    def coarsen(self, params):
+        return self._op(lib.pm_coarsen, "pm_coarsen", params)
+
+    def refine(self, params):
+        return self._op(lib.pm_refine, "pm_refine", params)
+
+    def swap(self, params):
+        return self._op(lib.pm_swap, "pm_swap", params)
+
+    def smooth(self, params):
+        return self._op(lib.pm_smooth, "pm_smooth", params)
+
+    def opt_smooth(self, params):
+        return self._op(lib.pm_opt_smooth, "pm_opt_smooth", params)
+
+    def adapt(self, params):
+        return self._op(lib.pm_adapt, "pm_adapt", params)
+
+    # -- output --------------------------------------------------------------
+    def sizes(self):
+        nv = np.zeros(1, np.int32)
+        ne = np.zeros(1, np.int32)
+        _check(lib.pm_get_mesh(self.h, _i(nv), _i(ne), None, None, None), "pm_get_mesh")
+        return int(nv[0]), int(ne[0])
+
+    def get_mesh(self):
+        nv, ne = self.sizes()
+        xy = np.zeros((nv, 2))
+        tri = np.zeros((ne, 3), np.int32)
+        m = np.zeros((nv, 3))
+        a = np.zeros(1, np.int32)
+        b = np.zeros(1, np.int32)
+        _check(lib.pm_get_mesh(self.h, _i(a), _i(b), _d(xy), _i(tri), _d(m)), "pm_get_mesh")
+        return xy, tri, m
+
+    def get_mesh_dev(self, xy, tri, m):
+        """Write the compacted mesh into preallocated CUDA tensors; returns (nv, ne)."""
+        a = np.zeros(1, np.int32)
+        b = np.zeros(1, np.int32)
+        _check(lib.pm_get_mesh_dev(self.h, _i(a), _i(b),
+                                   C.c_void_p(xy.data_ptr()) if xy is not None else None,
+                                   C.c_void_p(tri.data_ptr()) if tri is not None else None,
+                                   C.c_void_p(m.data_ptr()) if m is not None else None),
+               "pm_get_mesh_dev")
+        return int(a[0]), int(b[0])
+
+    def get_raw(self):
+        a = np.zeros(1, np.int32)
+        b = np.zeros(1, np.int32)
+        _check(lib.pm_get_raw(self.h, _i(a), _i(b), None, None, None, None, None, None),
+               "pm_get_raw")
+        n, e = int(a[0]), int(b[0])
+        xy = np.zeros((n, 2))
+        m = np.zeros((n, 3))
+        tri = np.zeros((e, 3), np.int32)
+        va = np.zeros(n, np.uint8)
+        ta = np.zeros(e, np.uint8)
+        vf = np.zeros(n, np.uint8)
+        _check(lib.pm_get_raw(self.h, _i(a), _i(b), _d(xy), _d(m), _i(tri), _u(va), _u(ta),
+                              _u(vf)), "pm_get_raw")
+        return dict(xy=xy, m=m, tri=tri, valive=va, talive=ta, vflag=vf)
+
+    def adjacency(self, v, cap=256):
+        nn = np.zeros(cap, np.int32)
+        ne = np.zeros(cap, np.int32)
+        a = np.zeros(1, np.int32)
+        b = np.zeros(1, np.int32)
+        _check(lib.pm_adjacency(self.h, v, _i(nn), _i(a), _i(ne), _i(b), cap), "pm_adjacency")
+        return nn[: a[0]].copy(), ne[: b[0]].copy()
+
+    def quality(self, grad=True):
+        nv = self.get_raw_sizes()[0]
+        qs = np.zeros(1)
+        if not grad:
+            _check(lib.pm_quality(self.h, _d(qs), None, None), "pm_quality")
+            return float(qs[0])
+        dxy = np.zeros((nv, 2))
+        dm = np.zeros((nv, 3))
+        _check(lib.pm_quality(self.h, _d(qs), _d(dxy), _d(dm)), "pm_quality")
+        return float(qs[0]), dxy, dm
+
+    def get_raw_sizes(self):
+        a = np.zeros(1, np.int32)
+        b = np.zeros(1, np.int32)
+        _check(lib.pm_get_raw(self.h, _i(a), _i(b), None, None, None, None, None, None),
+               "pm_get_raw")
+        return int(a[0]), int(b[0])
+
+
+def adapt_batch(meshes, params):
+    """pm_adapt_batch over a list of Mesh objects; params: one or one per mesh."""
+    n = len(meshes)
+    if not isinstance(params, (list, tuple)):
+        params = [params] * n
+    arr = (PmParams * n)(*[as_params(p) for p in params])
+    hs = (C.c_void_p * n)(*[m.h.value for m in meshes])
+    st = (PmStats * n)()
+    _check(lib.pm_adapt_batch(hs, n, arr, st), "pm_adapt_batch")
+    return [s.as_dict() for s in st]
+
+
+def quality_arrays_dev(xy, m, tri, qsum, dxy=None, dm=None, stream=0):
+    """pm_quality_arrays_dev on CUDA tensors (stream-ordered, no sync)."""
+    _check(lib.pm_quality_arrays_dev(C.c_void_p(xy.data_ptr()), C.c_void_p(m.data_ptr()),
+                                     xy.shape[0], C.c_void_p(tri.data_ptr()), tri.shape[0],
+                                     C.c_void_p(qsum.data_ptr()),
+                                     C.c_void_p(dxy.data_ptr()) if dxy is not None else None,
+                                     C.c_void_p(dm.data_ptr()) if dm is not None else None,
+                                     C.c_void_p(stream)), "pm_quality_arrays_dev")

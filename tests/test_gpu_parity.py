@@ -1,0 +1,204 @@
+"""GPU (CUDA library through the C interface) against the CPU oracle.
+
+Topology and coordinates must match bit for bit (Sec. 3.2-3.3 round
+semantics, FP64 without contraction on both sides); the quality sum and
+gradient to a relative 1e-12 (different summation order of the mesh total).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1505_04694_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+pm = pytest.importorskip("paper_1505_04694_gb300.pm")
+
+
+def bits(a):
+    return np.ascontiguousarray(a).view(np.uint64)
+
+
+def assert_same_mesh(g, o, what=""):
+    gxy, gtri, gm = g
+    oxy, otri, om = o
+    assert gtri.shape == otri.shape and gxy.shape == oxy.shape, (what, gtri.shape, otri.shape)
+    bad = np.nonzero((gtri != otri).any(axis=1))[0]
+    assert bad.size == 0, f"{what}: {bad.size} triangles differ, first {bad[:5]}"
+    bx = np.nonzero((bits(gxy) != bits(oxy)).any(axis=1))[0]
+    assert bx.size == 0, f"{what}: {bx.size} vertices differ in coordinates, first {bx[:5]}"
+    bm = np.nonzero((bits(gm) != bits(om)).any(axis=1))[0]
+    assert bm.size == 0, f"{what}: {bm.size} vertices differ in metric, first {bm[:5]}"
+
+
+def assert_same_raw(g, o, what=""):
+    for k in ("valive", "talive", "vflag", "tri"):
+        assert np.array_equal(g[k], o[k]), f"{what}: raw {k} differs"
+    alive = g["valive"] > 0
+    assert np.array_equal(bits(g["xy"][alive]), bits(o["xy"][alive])), f"{what}: xy"
+    assert np.array_equal(bits(g["m"][alive]), bits(o["m"][alive])), f"{what}: metric"
+
+
+def assert_same_adjacency(gm, om, raw):
+    for v in np.nonzero(raw["valive"])[0]:
+        a = gm.adjacency(int(v))
+        b = om.adjacency(int(v))
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), f"row of vertex {v}"
+
+
+def both(w, seed):
+    g = pm.Mesh.from_host(w.xy, w.tri, device=0)
+    g.set_metric(w.m)
+    o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    return g, o
+
+
+def gp(seed, **kw):
+    return pm.Params(seed=seed, **kw)
+
+
+def op(seed, **kw):
+    return O.make_params(seed=seed, **kw)
+
+
+STAT_KEYS = ("rounds", "collapses", "splits", "flips", "moves", "converged")
+
+
+def test_small_uniform_adapt_bit_exact():
+    w = inputs.small_uniform()
+    g, o = both(w, 1)
+    sg = g.adapt(gp(1))
+    so = o.adapt(op(1))
+    assert_same_mesh(g.get_mesh(), o.get_mesh(), "small uniform")
+    for k in STAT_KEYS:
+        assert sg[k] == so[k], k
+    assert g.sizes() == (3281, 6400)
+
+
+@pytest.mark.parametrize("n,T,seed", [(9, 400, 5), (17, 3000, 21), (25, 8000, 22), (33, 20000, 2),
+                                      (65, 100000, 2)])
+def test_psi_adapt_bit_exact(n, T, seed):
+    w = inputs.psi_workload(n, T, True, seed)
+    g, o = both(w, seed)
+    sg = g.adapt(gp(seed))
+    so = o.adapt(op(seed))
+    assert_same_mesh(g.get_mesh(), o.get_mesh(), f"psi {n}")
+    for k in STAT_KEYS:
+        assert sg[k] == so[k], (k, sg[k], so[k])
+
+
+@pytest.mark.parametrize("opname", ["coarsen", "swap", "refine", "smooth", "opt_smooth"])
+def test_single_operator_raw_state_and_rows(opname):
+    w = inputs.psi_workload(21, 6000, True, 9)
+    g, o = both(w, 9)
+    # bring the mesh into a state where every operator has work
+    for name in ("refine", "coarsen"):
+        getattr(g, name)(gp(9))
+        getattr(o, name)(op(9))
+    kw = dict(opt_smooth_rounds=5) if opname == "opt_smooth" else {}
+    sg = getattr(g, opname)(gp(9, **kw))
+    so = getattr(o, opname)(op(9, **kw))
+    for k in STAT_KEYS:
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    rg, ro = g.get_raw(), o.get_raw()
+    assert_same_raw(rg, ro, opname)
+    assert_same_adjacency(g, o, rg)
+
+
+def test_round_by_round():
+    w = inputs.psi_workload(25, 8000, True, 12)
+    g, o = both(w, 12)
+    for opname in ("refine", "coarsen", "swap", "smooth"):
+        for _ in range(4):
+            sg = getattr(g, opname)(gp(12, max_rounds=1))
+            so = getattr(o, opname)(op(12, max_rounds=1))
+            assert sg["rounds"] == so["rounds"]
+            rg, ro = g.get_raw(), o.get_raw()
+            assert_same_raw(rg, ro, opname)
+        assert_same_adjacency(g, o, rg)
+
+
+def test_quality_and_gradient_against_oracle():
+    w = inputs.psi_workload(33, 20000, True, 3)
+    g, o = both(w, 3)
+    g.refine(gp(3))
+    o.refine(op(3))
+    qg, dg, mg = g.quality()
+    qo, do, mo = o.quality()
+    assert abs(qg - qo) <= 1e-12 * abs(qo)
+    # the per-vertex sums use the same order on both sides
+    assert np.array_equal(bits(dg), bits(do))
+    assert np.array_equal(bits(mg), bits(mo))
+
+
+def test_quality_arrays_and_autograd():
+    torch = pytest.importorskip("torch")
+    from paper_1505_04694_gb300.autograd import quality
+
+    w = inputs.psi_workload(17, 3000, True, 4)
+    o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    qo, do, mo = o.quality()
+    dev = torch.device("cuda:0")
+    xy = torch.tensor(w.xy, dtype=torch.float64, device=dev, requires_grad=True)
+    m = torch.tensor(w.m, dtype=torch.float64, device=dev, requires_grad=True)
+    tri = torch.tensor(w.tri, dtype=torch.int32, device=dev)
+    q = quality(xy, m, tri)
+    q.backward()
+    assert abs(float(q) - qo) <= 1e-12 * abs(qo)
+    gx = xy.grad.cpu().numpy()
+    gm = m.grad.cpu().numpy()
+    assert np.linalg.norm(gx - do) <= 1e-12 * np.linalg.norm(do)
+    assert np.linalg.norm(gm - mo) <= 1e-12 * np.linalg.norm(mo)
+
+
+def test_autograd_gradcheck_small():
+    torch = pytest.importorskip("torch")
+    from paper_1505_04694_gb300.autograd import QualityFunction
+
+    xy0, tri0 = inputs.grid_mesh(3)  # 8 triangles
+    xy0 = inputs.jitter_interior(xy0, 3, 0.1, 7)
+    m0 = inputs.uniform_metric(xy0.shape[0], 0.4)
+    dev = torch.device("cuda:0")
+    xy = torch.tensor(xy0, dtype=torch.float64, device=dev, requires_grad=True)
+    m = torch.tensor(m0, dtype=torch.float64, device=dev, requires_grad=True)
+    tri = torch.tensor(tri0, dtype=torch.int32, device=dev)
+    assert torch.autograd.gradcheck(lambda a, b: QualityFunction.apply(a, b, tri), (xy, m),
+                                    eps=1e-7, atol=1e-7, rtol=1e-6)
+
+
+def test_batch_equals_single_runs():
+    ws = [inputs.psi_workload(n, T, True, s) for n, T, s in ((9, 400, 31), (17, 3000, 32),
+                                                             (13, 1500, 33))]
+    ws.append(inputs.small_uniform())
+    meshes = []
+    params = []
+    for i, w in enumerate(ws):
+        g = pm.Mesh.from_host(w.xy, w.tri, device=0)
+        g.set_metric(w.m)
+        meshes.append(g)
+        params.append(gp(w.params.seed))
+    stats = pm.adapt_batch(meshes, params)
+    for w, g, st in zip(ws, meshes, stats):
+        o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+        so = o.adapt(op(w.params.seed))
+        assert_same_mesh(g.get_mesh(), o.get_mesh(), w.name)
+        for k in STAT_KEYS:
+            assert st[k] == so[k], (w.name, k, st[k], so[k])
+
+
+def test_rejects_invalid_input():
+    xy, tri = inputs.grid_mesh(5)
+    bad = tri.copy()
+    bad[3] = bad[3][[0, 2, 1]]  # clockwise element
+    with pytest.raises(pm.PmError) as e:
+        pm.Mesh.from_host(xy, bad, device=0)
+    assert e.value.status == 2
+    g = pm.Mesh.from_host(xy, tri, device=0)
+    m = inputs.uniform_metric(xy.shape[0], 0.1)
+    m[4, 2] = -1.0
+    with pytest.raises(pm.PmError) as e:
+        g.set_metric(m)
+    assert e.value.status == 1
+    with pytest.raises(pm.PmError) as e:
+        g.adapt(pm.Params(L_low=2.0, L_up=1.0))
+    assert e.value.status == 1
