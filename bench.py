@@ -1,0 +1,309 @@
+"""Benchmark: adapted elements/s of the full 2D adaptation loop on GB300.
+
+One step = one pass of the whole path on the psi-Hessian anisotropic
+workload (257 x 257 jittered grid, 131,072 triangles, metric scaled to about
+2M output triangles; the synthetic benchmark of Sec. 4 at t = 0):
+  mesh ingest + adjacency build (pm_mesh_create_dev), metric upload
+  (pm_set_metric_dev), Algorithm 1 with every operator round, smoothing and
+  renumbering (pm_adapt), compacted output (pm_get_mesh_dev).
+Inputs are resident in HBM when a step's timer starts; the L2 is flushed
+(256 MiB write) between steps, outside the timed region.  value = output
+triangles of all steps of all ranks / max over ranks of the summed step time.
+
+--impl reference times the CPU oracle (sequential C++, one core) on a bounded
+sample of the same workload family; see the `cpu_baseline` key.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Adapted elements/s, full 2D adapt loop, 1 GB300; batched vs one-mesh-per-launch"
+WORKLOAD = "psi-Hessian anisotropic adaptation, 257x257 jittered grid (131,072 triangles) -> ~2.1M triangles"
+# bounded CPU sample of the same workload family (about 10-20 s of oracle work)
+SAMPLE = dict(n=181, target=1.0e6, seed=2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roofline-kernel", default=None)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="device-resident steps only (no e2e pass, no CPU baseline)")
+    return ap.parse_args()
+
+
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if n > 1 else "gloo")
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                mx.append(float(s[2]))
+                for name, val in zip(names, s[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline_run(samples=1):
+    """Oracle (sequential C++) on the bounded sample; returns elements/s etc."""
+    from oracle import oracle as O
+    from paper_1505_04694_gb300 import inputs
+
+    w = inputs.psi_workload(SAMPLE["n"], SAMPLE["target"], True, SAMPLE["seed"])
+    vals = []
+    for _ in range(samples):
+        om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+        t = time.perf_counter()
+        om.adapt(O.make_params(seed=SAMPLE["seed"]))
+        _, tri, _ = om.get_mesh()
+        dt = time.perf_counter() - t
+        vals.append((tri.shape[0], dt))
+    return vals
+
+
+def sample_desc():
+    return (f"oracle (sequential C++, -O2 -ffp-contract=off) full adapt loop on the same workload "
+            f"family at {SAMPLE['n']}x{SAMPLE['n']} jittered grid, target {SAMPLE['target']:.0e} "
+            f"triangles; value = output triangles / wall time")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline_run(1)
+    res = cpu_baseline_run(args.steps)
+    tri = sum(r[0] for r in res)
+    secs = sum(r[1] for r in res)
+    v = tri / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{SAMPLE}"},
+        "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": sample_desc()},
+        "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1505_04694_gb300 import inputs, pm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    w = inputs.anisotropic_2m()
+    params = pm.Params(seed=w.params.seed)
+    xy_d = torch.tensor(w.xy, dtype=torch.float64, device=dev)
+    tri_d = torch.tensor(w.tri, dtype=torch.int32, device=dev)
+    m_d = torch.tensor(w.m, dtype=torch.float64, device=dev)
+    cap_out = 4_000_000
+    oxy = torch.empty((cap_out, 2), dtype=torch.float64, device=dev)
+    otri = torch.empty((cap_out, 3), dtype=torch.int32, device=dev)
+    om_ = torch.empty((cap_out, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        g = pm.Mesh.from_device(xy_d, tri_d, cap_factor=2, stream=sp)
+        g.set_metric_dev(m_d)
+        g.adapt(params)
+        nv, ne = g.get_mesh_dev(oxy, otri, om_)
+        g.close()
+        return ne
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    launches0 = pm.kernel_launches()
+    kname = args.roofline_kernel or "k_swap_eval"
+    pm.profile_enable(kname)
+    total_ms = 0.0
+    tris = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tris += step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+    barrier()
+    launches = pm.kernel_launches() - launches0
+    kms, klaunch = pm.profile_read()
+    pm.profile_enable(None)
+    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    n_local = torch.tensor([float(tris)], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n_local, op=dist.ReduceOp.SUM)
+    t_max = float(t_local.item())
+    value = float(n_local.item()) / (t_max / 1e3)
+
+    # end to end through the public C interface with host buffers
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "elements/s",
+                              "ms_per_step": t_max / args.steps, "gpu_launches": launches}))
+        return
+    pin_xy = torch.from_numpy(w.xy.copy()).pin_memory()
+    pin_tri = torch.from_numpy(w.tri.astype(np.int32)).pin_memory()
+    pin_m = torch.from_numpy(w.m.copy()).pin_memory()
+    h_xy, h_tri, h_m = pin_xy.numpy(), pin_tri.numpy(), pin_m.numpy()
+    e2e_s = 0.0
+    d2h = 0
+    e2e_tris = 0
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        g = pm.Mesh.from_host(h_xy, h_tri, cap_factor=2, device=local)
+        g.set_metric(h_m)
+        g.adapt(params)
+        oxyh, otrih, omh = g.get_mesh()
+        g.close()
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            e2e_s += dt
+            e2e_tris += otrih.shape[0]
+            d2h = oxyh.nbytes + otrih.nbytes + omh.nbytes
+    h2d = h_xy.nbytes + h_tri.nbytes + h_m.nbytes
+
+    peaks, how = measured_peaks()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "elements/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "output_triangles_per_step": tris // max(args.steps, 1),
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_tris / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "how": "pm_mesh_create + pm_set_metric + pm_adapt + pm_get_mesh on pinned host "
+                       "buffers, wall clock per step"},
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / max(args.steps, 1),
+        "roofline": {"kernel": kname, "kernel_ms_total": kms, "kernel_launches": klaunch,
+                     "kernel_share_of_step_time": kms / total_ms if total_ms else None,
+                     "peak_source": how},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = cpu_baseline_run(1)
+        tri_c, secs = res[0]
+        line["cpu_baseline"] = {"value": tri_c / secs, "unit": "elements/s", "cores": 1,
+                                "kind": "oracle", "sample": sample_desc(),
+                                "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -184,6 +184,18 @@ pm_status pm_quality_arrays_dev(const double* xy, const double* m, int32_t nv,
                                 const int32_t* tri, int32_t ne, double* q_sum, double* dxy,
                                 double* dm, void* stream);
 
+/* Measurement support (not part of the method).
+ * pm_kernel_launches: number of CUDA kernels this library has launched in
+ * the process so far.
+ * pm_profile_enable: while `kernel_substring` is non-empty, every launch of a
+ * library kernel whose name contains it is bracketed by CUDA events on the
+ * stream it runs on; enabling (or disabling with null/"") clears earlier
+ * records.  pm_profile_read waits for the recorded launches and returns their
+ * summed device time and count. */
+uint64_t pm_kernel_launches(void);
+pm_status pm_profile_enable(const char* kernel_substring);
+pm_status pm_profile_read(double* total_ms, int64_t* launches);
+
 const char* pm_status_string(pm_status s);
 
 /* Message of the last error on the calling thread ("" if none). */

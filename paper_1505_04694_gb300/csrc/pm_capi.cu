@@ -142,7 +142,7 @@ pm_status create_common(const double* xy, int nv, const int32_t* tri, int ne,
   if (!s) {
     const int32_t* t = host ? tri_dev : tri;
     const uint8_t* c = host ? corner_dev : corner;
-    k_ingest<<<grid_for(m, std::max(nv, ne)), BLOCK, 0, m.stream>>>(m.S, t, ne, nv);
+    PM_LAUNCH(k_ingest, grid_for(m, std::max(nv, ne)), BLOCK, 0, m.stream, m.S, t, ne, nv);
     int err = validate_mesh(m);
     if (err) s = (pm_status)err;
     if (s == PM_ERR_INVALID_MESH)
@@ -489,14 +489,14 @@ static pm_status set_metric_impl(pm_mesh* h, const double* M, bool host) {
     if (e) return cuda_status(e, "uploading metric");
     src = tmp;
   } else {
-    k_metric_check<<<grid_for(m, nv), BLOCK, 0, m.stream>>>(src, nv, m.st);
+    PM_LAUNCH(k_metric_check, grid_for(m, nv), BLOCK, 0, m.stream, src, nv, m.st);
     int err = sync_status(m);
     if (err) {
       cudaMemsetAsync(m.st, 0, sizeof(DevStatus), m.stream);
       return fail((pm_status)err, "metric must be finite and symmetric positive definite");
     }
   }
-  k_metric_set<<<grid_for(m, nv), BLOCK, 0, m.stream>>>(m.S, src, nv);
+  PM_LAUNCH(k_metric_set, grid_for(m, nv), BLOCK, 0, m.stream, m.S, src, nv);
   if (tmp) cudaFreeAsync(tmp, m.stream);
   return (pm_status)sync_status(m);
 }

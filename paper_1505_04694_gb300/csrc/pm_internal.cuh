@@ -106,6 +106,26 @@ int quality_arrays(const double* xy, const double* mt, int nv, const int* tri, i
 // ---- errors (pm_capi.cu) ----
 void set_last_error(const std::string& msg);
 
+// ---- launches (pm_prof.cu) ----
+// Every kernel of the library is launched through PM_LAUNCH: it counts the
+// launch and, while profiling is on for a matching kernel name, brackets it
+// with CUDA events on its own stream.
+extern unsigned long long g_launches;
+extern bool g_prof_on;
+int prof_begin(const char* name, cudaStream_t s);
+void prof_end(int slot, cudaStream_t s);
+
+template <class K, class... A>
+inline void launch(const char* name, K kern, dim3 g, dim3 b, size_t sh, cudaStream_t s,
+                   A... args) {
+  __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED);
+  int slot = g_prof_on ? prof_begin(name, s) : -1;
+  kern<<<g, b, sh, s>>>(args...);
+  if (slot >= 0) prof_end(slot, s);
+}
+
+#define PM_LAUNCH(k, g, b, sh, s, ...) ::pm::launch(#k, k, g, b, sh, s, __VA_ARGS__)
+
 inline int grid_for(const MeshSet& m, long long n, int per_sm = 8) {
   long long want = (n + BLOCK - 1) / BLOCK;
   long long cap = (long long)m.num_sms * per_sm;

@@ -511,8 +511,8 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
                   m.stream);
   cudaMemcpyAsync(n2.S.tab.ops, m.S.tab.ops, 2 * nm * sizeof(unsigned long long),
                   cudaMemcpyDeviceToDevice, m.stream);
-  k_relayout_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, n2.S);
-  k_relayout_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, n2.S);
+  PM_LAUNCH(k_relayout_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, n2.S);
+  PM_LAUNCH(k_relayout_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, n2.S);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   set_free(m);
@@ -566,9 +566,9 @@ int sync_status(MeshSet& m) {
 int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) {
   for (;;) {
     cudaMemsetAsync(&m.st->overflow, 0, 2 * sizeof(int), m.stream);
-    k_zero_nelen<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S);
-    k_fill_ne<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, m.st);
-    k_finish_rows<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, derive_flags ? 1 : 0,
+    PM_LAUNCH(k_zero_nelen, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S);
+    PM_LAUNCH(k_fill_ne, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, m.st);
+    PM_LAUNCH(k_finish_rows, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, derive_flags ? 1 : 0,
                                                                   m.st);
     int err = sync_status(m);
     if (err) return err;
@@ -587,14 +587,14 @@ int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) 
     }
   }
   if (derive_flags) {
-    k_corners<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, corner_dev);
+    PM_LAUNCH(k_corners, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, corner_dev);
     return sync_status(m);
   }
   return PM_OK;
 }
 
 int validate_mesh(MeshSet& m) {
-  k_validate_elems<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, m.st);
+  PM_LAUNCH(k_validate_elems, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, m.st);
   return sync_status(m);
 }
 
@@ -602,16 +602,16 @@ int validate_mesh(MeshSet& m) {
 // slot order), adjacency remapped (rows stay sorted: the map is monotone).
 int renumber(MeshSet& m) {
   Work& w = m.w;
-  k_flags_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, w.vcnt);
-  k_flags_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, w.ecnt);
+  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, w.vcnt);
+  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, w.ecnt);
   scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
   scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
-  k_mesh_totals<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, w.escan, tot);
+  PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
   // the second buffer's flags must read "dead" beyond the new counts
   cudaMemsetAsync(m.B.vflag, 0, m.S.vslots, m.stream);
-  k_renum_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, m.B, w.vscan, w.escan);
-  k_renum_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, m.B, w.vscan, w.escan);
+  PM_LAUNCH(k_renum_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
+  PM_LAUNCH(k_renum_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
   cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   int err = sync_status(m);
   if (err) return err;
@@ -641,16 +641,16 @@ int renumber(MeshSet& m) {
 int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
                 int* ne_out) {
   Work& w = m.w;
-  k_flags_v<<<grid_for(m, m.S.vslots), BLOCK, 0, m.stream>>>(m.S, w.vcnt);
-  k_flags_e<<<grid_for(m, m.S.eslots), BLOCK, 0, m.stream>>>(m.S, w.ecnt);
+  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, w.vcnt);
+  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, w.ecnt);
   scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
   scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
-  k_mesh_totals<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, w.escan, tot);
+  PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
   if (xy || mt)
-    k_out_v<<<grid_for(m, m.nv[mesh]), BLOCK, 0, m.stream>>>(m.S, mesh, w.vscan, xy, mt);
+    PM_LAUNCH(k_out_v, grid_for(m, m.nv[mesh]), BLOCK, 0, m.stream, m.S, mesh, w.vscan, xy, mt);
   if (tri)
-    k_out_e<<<grid_for(m, m.ne[mesh]), BLOCK, 0, m.stream>>>(m.S, mesh, w.vscan, w.escan, tri);
+    PM_LAUNCH(k_out_e, grid_for(m, m.ne[mesh]), BLOCK, 0, m.stream, m.S, mesh, w.vscan, w.escan, tri);
   cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   int err = sync_status(m);
   if (err) return err;

@@ -1001,21 +1001,21 @@ int op_coarsen(MeshSet& m, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
   zero_counts(m, 0, CN_NUM);
-  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 0, w.D[0], w.counts + CN_D0);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0);
   int cur = 0;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
     int tag = ++m.tag;
     int nxt = 1 - cur;
     zero_counts(m, CN_C, 3);
     zero_counts(m, nxt, 1);
-    k_coarsen_eval<<<gv, BLOCK, 0, m.stream>>>(m.S, w.D[cur], w.counts + cur, w.target, w.C,
+    PM_LAUNCH(k_coarsen_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.target, w.C,
                                                w.counts + CN_C, w.cmark, tag);
-    k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
+    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
                                          w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
-    k_coarsen_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S, w.target, w.A,
+    PM_LAUNCH(k_coarsen_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.target, w.A,
                                                 w.counts + CN_A, w.amark, w.D[nxt],
                                                 w.counts + nxt, w.dmark, tag);
-    k_coarsen_commit<<<gv, BLOCK, 0, m.stream>>>(m.S, w.A, w.counts + CN_A, w.target, w.smark, tag,
+    PM_LAUNCH(k_coarsen_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target, w.smark, tag,
                                                  m.st);
     RoundIO io = read_round(m);
     if (io.nC == 0) break;
@@ -1031,21 +1031,21 @@ int op_swap(MeshSet& m, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
   zero_counts(m, 0, CN_NUM);
-  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 0, w.D[0], w.counts + CN_D0);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0);
   int cur = 0;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
     int tag = ++m.tag;
     int nxt = 1 - cur;
     zero_counts(m, CN_C, 3);
     zero_counts(m, nxt, 1);
-    k_swap_eval<<<gv, BLOCK, 0, m.stream>>>(m.S, w.D[cur], w.counts + cur, w.opA, w.opK2, w.C,
+    PM_LAUNCH(k_swap_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.opA, w.opK2, w.C,
                                             w.counts + CN_C, w.cmark, tag);
-    k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
+    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
                                          w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
-    k_swap_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S, w.opA, w.opK2, w.A,
+    PM_LAUNCH(k_swap_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.opA, w.opK2, w.A,
                                              w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt,
                                              w.dmark, tag);
-    k_swap_commit<<<gv, BLOCK, 0, m.stream>>>(m.S, w.A, w.counts + CN_A, w.opA, w.opK2, w.smark,
+    PM_LAUNCH(k_swap_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2, w.smark,
                                               tag, m.st);
     RoundIO io = read_round(m);
     if (io.nC == 0) break;
@@ -1063,11 +1063,11 @@ int op_refine(MeshSet& m, int max_rounds) {
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
     const int gv = grid_for(m, m.S.vslots);
     const int ge = grid_for(m, m.S.eslots);
-    k_refine_mark<<<gv, BLOCK, 0, m.stream>>>(m.S, w.vcnt, w.vmask);
+    PM_LAUNCH(k_refine_mark, gv, BLOCK, 0, m.stream, m.S, w.vcnt, w.vmask);
     scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
     int* tot = w.counts + CN_NUM;
     std::vector<int> newv(m.nmesh);
-    k_refine_newcount<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, tot);
+    PM_LAUNCH(k_refine_newcount, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, tot);
     cudaMemcpyAsync(m.hcounts + CN_NUM, tot, m.nmesh * sizeof(int), cudaMemcpyDeviceToHost,
                     m.stream);
     {
@@ -1103,12 +1103,12 @@ int op_refine(MeshSet& m, int max_rounds) {
       --nr;  // redo this round on the new layout
       continue;
     }
-    k_refine_vtotals<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan);
-    k_refine_newverts<<<gv, BLOCK, 0, m.stream>>>(m.S, w.vscan, w.vmask);
-    k_refine_count<<<ge, BLOCK, 0, m.stream>>>(m.S, w.vscan, w.vmask, w.ecnt, w.emid);
+    PM_LAUNCH(k_refine_vtotals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan);
+    PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask);
+    PM_LAUNCH(k_refine_count, ge, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid);
     scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
-    k_refine_split<<<ge, BLOCK, 0, m.stream>>>(m.S, w.escan, w.emid);
-    k_refine_sizes<<<(m.nmesh + 127) / 128, 128, 0, m.stream>>>(m.S, w.vscan, w.escan);
+    PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid);
+    PM_LAUNCH(k_refine_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan);
     cudaError_t e = refresh_sizes(m);
     if (e != cudaSuccess) return PM_ERR_CUDA;
     int err = rebuild_adjacency(m, false, nullptr);
@@ -1122,7 +1122,7 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
   zero_counts(m, 0, CN_NUM);
-  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 1, w.D[0], w.counts + CN_D0);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0);
   long long nr = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int ptag = ++m.tag;  // stamp of the next sweep's pending list
@@ -1134,12 +1134,12 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
       int nxt = 1 - cur;
       zero_counts(m, CN_C, 2);
       zero_counts(m, nxt, 1);
-      k_smooth_eval<<<gv, BLOCK, 0, m.stream>>>(m.S, w.D[cur], w.counts + cur, w.mvxy, w.mvM, w.C,
+      PM_LAUNCH(k_smooth_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.mvxy, w.mvM, w.C,
                                                 w.counts + CN_C, w.cmark, tag);
-      k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
+      PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
                                            w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt,
                                            w.dmark);
-      k_smooth_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S, w.mvxy, w.mvM, w.P,
+      PM_LAUNCH(k_smooth_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.mvxy, w.mvM, w.P,
                                                  w.counts + CN_P, w.pmark, ptag);
       RoundIO io = read_round(m);
       if (io.err) return io.err;
@@ -1162,14 +1162,14 @@ int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
   zero_counts(m, 0, CN_NUM);
-  k_init_list<<<gv, BLOCK, 0, m.stream>>>(m.S, 1, w.C, w.counts + CN_C);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.C, w.counts + CN_C);
   for (int it = 0; it < nrounds && (max_rounds == 0 || it < max_rounds); ++it) {
     int tag = ++m.tag;
     zero_counts(m, CN_S, 1);
-    k_stamp_list<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, tag);
-    k_select<<<gv, BLOCK, 0, m.stream>>>(m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
+    PM_LAUNCH(k_stamp_list, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, tag);
+    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
                                          w.counts + CN_S, nullptr, nullptr, nullptr);
-    k_opt_apply<<<gv, BLOCK, 0, m.stream>>>(m.S, w.Sl, w.counts + CN_S);
+    PM_LAUNCH(k_opt_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S);
   }
   return sync_status(m);
 }

@@ -177,8 +177,8 @@ __global__ void k_sum_stage2(const double* part, int n, double* out) {
 }
 
 void dsum(const double* x, int n, double* part, double* out, cudaStream_t s) {
-  k_sum_stage1<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, n, part);
-  k_sum_stage2<<<1, RED_BLOCKS, 0, s>>>(part, RED_BLOCKS, out);
+  PM_LAUNCH(k_sum_stage1, RED_BLOCKS, RED_THREADS, 0, s, x, n, part);
+  PM_LAUNCH(k_sum_stage2, 1, RED_BLOCKS, 0, s, part, RED_BLOCKS, out);
 }
 
 int gridn(long long n) {
@@ -207,9 +207,9 @@ int quality_mesh(MeshSet& m, double* qsum_host, double* dxy_host, double* dm_hos
     status = PM_ERR_OOM;
   } else {
     out = part + RED_BLOCKS;
-    k_elem_qgrad_store<<<gridn(ne), 128, 0, s>>>(m.S, 0, qel, eg);
+    PM_LAUNCH(k_elem_qgrad_store, gridn(ne), 128, 0, s, m.S, 0, qel, eg);
     dsum(qel, ne, part, out, s);
-    if (grad) k_vgather_store<<<gridn(nv), 128, 0, s>>>(m.S, 0, eg, dxy, dm);
+    if (grad) PM_LAUNCH(k_vgather_store, gridn(nv), 128, 0, s, m.S, 0, eg, dxy, dm);
     cudaMemcpyAsync(qsum_host, out, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (dxy_host) cudaMemcpyAsync(dxy_host, dxy, nv * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (dm_host) cudaMemcpyAsync(dm_host, dm, nv * 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -239,12 +239,12 @@ int quality_arrays(const double* xy, const double* mt, int nv, const int* tri, i
     set_last_error(std::string("quality workspace: ") + cudaGetErrorString(e));
     status = PM_ERR_OOM;
   } else {
-    k_elem_qgrad_arr<<<gridn(ne), 128, 0, s>>>(xy, mt, tri, ne, qel, eg);
+    PM_LAUNCH(k_elem_qgrad_arr, gridn(ne), 128, 0, s, xy, mt, tri, ne, qel, eg);
     dsum(qel, ne, part, qsum, s);
     if (grad) {
       int* fill = cnt + (nv + 1);
       cudaMemsetAsync(cnt, 0, (nv + 1) * sizeof(int) * 2, s);
-      k_corner_count<<<gridn(ne), 128, 0, s>>>(tri, ne, cnt);
+      PM_LAUNCH(k_corner_count, gridn(ne), 128, 0, s, tri, ne, cnt);
       ScanWork sw;
       cudaMallocAsync(&sw.state, (size_t)scan_tiles(nv + 1) * sizeof(unsigned long long), s);
       cudaMallocAsync(&sw.ticket, sizeof(int), s);
@@ -253,8 +253,8 @@ int quality_arrays(const double* xy, const double* mt, int nv, const int* tri, i
       cudaMallocAsync(&st, sizeof(DevStatus), s);
       cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
       scan_exclusive(cnt, off, nv, sw, st, s);
-      k_corner_fill<<<gridn(ne), 128, 0, s>>>(tri, ne, off, fill, col);
-      k_vgather_arr<<<gridn(nv), 128, 0, s>>>(off, col, eg, nv, dxy, dm);
+      PM_LAUNCH(k_corner_fill, gridn(ne), 128, 0, s, tri, ne, off, fill, col);
+      PM_LAUNCH(k_vgather_arr, gridn(nv), 128, 0, s, off, col, eg, nv, dxy, dm);
       cudaFreeAsync(sw.state, s);
       cudaFreeAsync(sw.ticket, s);
       cudaFreeAsync(st, s);

@@ -135,7 +135,7 @@ void scan_exclusive(const int* in, int* out, int n, ScanWork& w, DevStatus* st, 
   cudaMemsetAsync(w.ticket, 0, sizeof(int), s);
   w.epoch = (w.epoch + 1) & 0x3FFFFFFFu;
   if (w.epoch == 0) w.epoch = 1;
-  k_scan<<<tiles, SCAN_THREADS, 0, s>>>(in, out, n, w.state, w.ticket, w.epoch, st);
+  PM_LAUNCH(k_scan, tiles, SCAN_THREADS, 0, s, in, out, n, w.state, w.ticket, w.epoch, st);
 }
 
 }  // namespace pm

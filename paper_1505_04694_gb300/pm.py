@@ -28,7 +28,8 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_set_metric", "pm_set_metric_dev", "pm_coarsen", "pm_refine", "pm_swap",
            "pm_smooth", "pm_adapt", "pm_opt_smooth", "pm_adapt_batch", "pm_get_mesh",
            "pm_get_mesh_dev", "pm_get_raw", "pm_adjacency", "pm_quality",
-           "pm_quality_arrays_dev", "pm_status_string", "pm_last_error"]
+           "pm_quality_arrays_dev", "pm_status_string", "pm_last_error", "pm_kernel_launches",
+           "pm_profile_enable", "pm_profile_read"]
 
 
 class PmParams(C.Structure):
@@ -88,6 +89,12 @@ def _load():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = C.c_int
+    L.pm_kernel_launches.argtypes = []
+    L.pm_kernel_launches.restype = C.c_uint64
+    L.pm_profile_enable.argtypes = [C.c_char_p]
+    L.pm_profile_enable.restype = C.c_int
+    L.pm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.pm_profile_read.restype = C.c_int
     L.pm_status_string.argtypes = [C.c_int]
     L.pm_status_string.restype = C.c_char_p
     L.pm_last_error.argtypes = []
@@ -318,3 +325,22 @@ def quality_arrays_dev(xy, m, tri, qsum, dxy=None, dm=None, stream=0):
                                      C.c_void_p(dxy.data_ptr()) if dxy is not None else None,
                                      C.c_void_p(dm.data_ptr()) if dm is not None else None,
                                      C.c_void_p(stream)), "pm_quality_arrays_dev")
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib.pm_kernel_launches())
+
+
+def profile_enable(kernel_substring):
+    """Time every launch of library kernels whose name contains the string."""
+    _check(lib.pm_profile_enable(kernel_substring.encode() if kernel_substring else None),
+           "pm_profile_enable")
+
+
+def profile_read():
+    """(total device milliseconds, launches) of the profiled kernels."""
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(lib.pm_profile_read(C.byref(ms), C.byref(n)), "pm_profile_read")
+    return float(ms.value), int(n.value)
