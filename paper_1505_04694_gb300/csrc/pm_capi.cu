@@ -156,6 +156,7 @@ pm_status create_common(const double* xy, int nv, const int32_t* tri, int ne,
           set_last_error("invalid mesh: overlapping elements, non-manifold or unused vertex");
       }
     }
+    if (!s) s = (pm_status)refresh_quality(m);
   }
   if (tri_dev) cudaFreeAsync(tri_dev, m.stream);
   if (corner_dev) cudaFreeAsync(corner_dev, m.stream);
@@ -191,6 +192,8 @@ pm_status begin_call(MeshSet& m, const pm_params* P, int stride) {
   cudaMemsetAsync(m.S.tab.active, 0xFF, m.nmesh * sizeof(int), m.stream);
   cudaMemsetAsync(m.st, 0, sizeof(DevStatus), m.stream);
   zero_ops(m);
+  // evaluations from earlier calls may predate a new metric or parameters
+  m.lo_coarsen = m.lo_swap = m.lo_refine = m.tag;
   return PM_OK;
 }
 
@@ -353,6 +356,7 @@ pm_status copy_region(MeshSet& dst, int di, MeshSet& src, int si, cudaStream_t s
   if (!e) e = cp(dst.S.NNlen + vd, src.S.NNlen + vs, nv * sizeof(int));
   if (!e) e = cp(dst.S.NElen + vd, src.S.NElen + vs, nv * sizeof(int));
   if (!e) e = cp(dst.S.EN + ed, src.S.EN + es, ne * sizeof(int4));
+  if (!e) e = cp(dst.S.qK + ed, src.S.qK + es, ne * sizeof(double));
   if (dst.S.W == src.S.W) {
     if (!e) e = cp(dst.S.NN + vd * dst.S.W, src.S.NN + vs * src.S.W, (size_t)nv * src.S.W * 4);
     if (!e) e = cp(dst.S.NE + vd * dst.S.W, src.S.NE + vs * src.S.W, (size_t)nv * src.S.W * 4);
@@ -498,7 +502,7 @@ static pm_status set_metric_impl(pm_mesh* h, const double* M, bool host) {
   }
   PM_LAUNCH(k_metric_set, grid_for(m, nv), BLOCK, 0, m.stream, m.S, src, nv);
   if (tmp) cudaFreeAsync(tmp, m.stream);
-  return (pm_status)sync_status(m);
+  return (pm_status)refresh_quality(m);
 }
 
 pm_status pm_set_metric(pm_mesh* h, const double* M) { return set_metric_impl(h, M, true); }

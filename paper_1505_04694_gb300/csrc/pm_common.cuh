@@ -37,6 +37,7 @@ struct MeshTab {
   double* L_low;                 // per-mesh parameters
   double* L_up;
   double* q_thresh;
+  double4* band;                 // (L_low_lo^2, L_low_hi^2, L_up_lo^2, L_up_hi^2)
 };
 
 struct Store {
@@ -48,10 +49,21 @@ struct Store {
   double4* M;     // (m00, m01, m11, 0)
   uint8_t* vflag;
   int4* EN;       // (v0, v1, v2, alive)
+  double* qK;     // quality of every live element (kept current by all operators)
   int* NN;        // vslots * W
   int* NNlen;
   int* NE;
   int* NElen;
+  // Change stamps: touch[v] is the (odd) round stamp of the last change of
+  // v's rows or position; evc/evs/evm/evr are the (even) round tags of v's
+  // last collapse / flip / smoothing / split evaluation.  An evaluation whose
+  // inputs (v, its rows, its neighbours' rows and positions) carry no newer
+  // stamp would give the same answer again.
+  int* touch;
+  int* evc;
+  int* evs;
+  int* evm;
+  int* evr;
   MeshTab tab;
 };
 
@@ -177,6 +189,30 @@ __device__ __forceinline__ double metric_len(const VD& a, const VD& b) {
   return sqrt(L2);
 }
 
+// Squared metric length (the radicand of metric_len, same operations).
+__device__ __forceinline__ double metric_len2(const VD& a, const VD& b) {
+  double e00 = 0.5 * (a.m00 + b.m00);
+  double e01 = 0.5 * (a.m01 + b.m01);
+  double e11 = 0.5 * (a.m11 + b.m11);
+  double dx = b.x - a.x;
+  double dy = b.y - a.y;
+  return ((e00 * dx) * dx + ((2.0 * e01) * dx) * dy) + (e11 * dy) * dy;
+}
+
+// sqrt(L2) > t and sqrt(L2) < t decided exactly without the square root
+// outside a band of relative width 1e-9 around t: lo2 <= (t(1-1e-9))^2 and
+// hi2 >= (t(1+1e-9))^2, far wider than the rounding of sqrt or of the squares.
+__device__ __forceinline__ bool len_gt(double L2, double lo2, double hi2, double t) {
+  if (L2 > hi2) return true;
+  if (L2 < lo2) return false;
+  return sqrt(L2) > t;
+}
+__device__ __forceinline__ bool len_lt(double L2, double lo2, double hi2, double t) {
+  if (L2 < lo2) return true;
+  if (L2 > hi2) return false;
+  return sqrt(L2) < t;
+}
+
 __device__ __forceinline__ double orient3(const VD& p, const VD& q, const VD& r) {
   return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);
 }
@@ -198,6 +234,7 @@ __device__ __forceinline__ double orient_c(int i0, int i1, int i2, VD a, VD b, V
 }
 
 constexpr double QC = 12.0 * 1.7320508075688772;  // 12 sqrt(3)
+constexpr double THIRD = 1.0 / 3.0;                 // mean of three terms = sum * THIRD
 
 __device__ __forceinline__ double len_under(double k00, double k01, double k11, const VD& p,
                                             const VD& q) {
@@ -210,16 +247,16 @@ __device__ __forceinline__ double len_under(double k00, double k01, double k11, 
 // Vasilevskii-Lipnikov quality in the element-mean metric, canonical rotation.
 __device__ __forceinline__ double quality_c(int i0, int i1, int i2, VD a, VD b, VD c) {
   canon(i0, i1, i2, a, b, c);
-  double k00 = ((a.m00 + b.m00) + c.m00) / 3.0;
-  double k01 = ((a.m01 + b.m01) + c.m01) / 3.0;
-  double k11 = ((a.m11 + b.m11) + c.m11) / 3.0;
+  double k00 = ((a.m00 + b.m00) + c.m00) * THIRD;
+  double k01 = ((a.m01 + b.m01) + c.m01) * THIRD;
+  double k11 = ((a.m11 + b.m11) + c.m11) * THIRD;
   double l0 = len_under(k00, k01, k11, a, b);
   double l1 = len_under(k00, k01, k11, b, c);
   double l2 = len_under(k00, k01, k11, c, a);
   double P = (l0 + l1) + l2;
   double area = 0.5 * orient3(a, b, c);
   double AM = sqrt(k00 * k11 - k01 * k01) * area;
-  double xx = P / 3.0;
+  double xx = P * THIRD;
   double s = (xx <= 1.0) ? xx : 1.0 / xx;
   double f = s * (2.0 - s);
   double F = (f * f) * f;
@@ -235,9 +272,9 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   if (i1 < i0 && i1 < i2) s = 1;
   else if (i2 < i0 && i2 < i1) s = 2;
   canon(i0, i1, i2, a, b, c);
-  double k00 = ((a.m00 + b.m00) + c.m00) / 3.0;
-  double k01 = ((a.m01 + b.m01) + c.m01) / 3.0;
-  double k11 = ((a.m11 + b.m11) + c.m11) / 3.0;
+  double k00 = ((a.m00 + b.m00) + c.m00) * THIRD;
+  double k01 = ((a.m01 + b.m01) + c.m01) * THIRD;
+  double k11 = ((a.m11 + b.m11) + c.m11) * THIRD;
   double dx[3] = {b.x - a.x, c.x - b.x, a.x - c.x};
   double dy[3] = {b.y - a.y, c.y - b.y, a.y - c.y};
   double l[3];
@@ -250,7 +287,7 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   double area = 0.5 * orient3(a, b, c);
   double sd = sqrt(k00 * k11 - k01 * k01);
   double AM = sd * area;
-  double xx = P / 3.0;
+  double xx = P * THIRD;
   bool left = (xx <= 1.0);
   double sv = left ? xx : 1.0 / xx;
   double f = sv * (2.0 - sv);
@@ -264,7 +301,7 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   double gf = (3.0 * (f * f)) * gF;
   double gs = (2.0 - 2.0 * sv) * gf;
   double gxx = left ? gs : -(gs / (xx * xx));
-  gP = gP + gxx / 3.0;
+  gP = gP + gxx * THIRD;
   double gsd = area * gAM;
   double garea = sd * gAM;
   double gdet = gsd / (2.0 * sd);
@@ -289,7 +326,7 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   cg[0][1] = (go * (c.x - b.x) - gdy[0]) + gdy[2];
   cg[1][1] = (go * (a.x - c.x) + gdy[0]) - gdy[1];
   cg[2][1] = (go * (b.x - a.x) + gdy[1]) - gdy[2];
-  double m0 = gk00 / 3.0, m1 = gk01 / 3.0, m2 = gk11 / 3.0;
+  double m0 = gk00 * THIRD, m1 = gk01 * THIRD, m2 = gk11 * THIRD;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     cg[k][2] = m0;

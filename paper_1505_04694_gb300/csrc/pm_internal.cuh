@@ -47,10 +47,15 @@ struct Work {
   int* ecnt = nullptr;             // per-element counts, eslots + 1
   int* escan = nullptr;
   int4* emid = nullptr;            // refine: midpoint ids per element edge
+  int* E = nullptr;                // vertices evaluated in full this round
+  int2* items = nullptr;           // flip candidates (vertex, edge slots) of this round
+  double* gains = nullptr;         // gain of each (vertex, ball-element slot), vslots * W
   int* counts = nullptr;           // device counters (see CountIdx)
 };
 
-enum CountIdx { CN_D0 = 0, CN_D1 = 1, CN_C = 2, CN_S = 3, CN_A = 4, CN_P = 5, CN_NUM = 8 };
+enum CountIdx {
+  CN_D0 = 0, CN_D1 = 1, CN_C = 2, CN_S = 3, CN_A = 4, CN_P = 5, CN_E = 6, CN_I = 7, CN_NUM = 8
+};
 
 // Everything the library keeps on the device for a set of meshes.
 struct MeshSet {
@@ -70,7 +75,9 @@ struct MeshSet {
   DevStatus* hst = nullptr;    // pinned host
   int* hcounts = nullptr;      // pinned host copy of w.counts
   void* tabmem = nullptr;      // device block holding MeshTab arrays
-  int tag = 0;                 // per-round stamp value
+  int tag = 0;                 // per-round tag (even); the round's change stamp is tag + 1
+  // evaluations with tags at or below these are stale for that operator
+  int lo_coarsen = 0, lo_swap = 0, lo_refine = 0;
   int num_sms = 152;
   std::vector<void*> allocs;   // device allocations owned by the set
 };
@@ -87,6 +94,7 @@ int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int*
                 int* ne_out);
 int sync_status(MeshSet& m);
 int validate_mesh(MeshSet& m);
+int refresh_quality(MeshSet& m);
 cudaError_t refresh_sizes(MeshSet& m);
 
 // ---- operators (pm_ops.cu) ----

@@ -45,6 +45,11 @@ __global__ void k_relayout_v(Store A, Store B) {
     B.xy[ns] = A.xy[s];
     B.M[ns] = A.M[s];
     B.vflag[ns] = A.vflag[s];
+    B.touch[ns] = A.touch[s];
+    B.evc[ns] = A.evc[s];
+    B.evs[ns] = A.evs[s];
+    B.evm[ns] = A.evm[s];
+    B.evr[ns] = A.evr[s];
     int wn = A.W < B.W ? A.W : B.W;
     int a = A.NNlen[s], b = A.NElen[s];
     B.NNlen[ns] = a;
@@ -62,6 +67,7 @@ __global__ void k_relayout_e(Store A, Store B) {
     if (!eslot_used(A, s, mi)) continue;
     int ns = B.tab.ebase[mi] + (s - A.tab.ebase[mi]);
     B.EN[ns] = A.EN[s];
+    B.qK[ns] = A.qK[s];
   }
 }
 
@@ -222,6 +228,19 @@ __global__ void k_validate_elems(Store S, DevStatus* st) {
   }
 }
 
+// Quality of every live element into the cache.
+__global__ void k_qcache_all(Store S) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!eslot_used(S, s, mi)) continue;
+    int4 e = S.EN[s];
+    if (!e.w) continue;
+    int vb = S.tab.vbase[mi];
+    S.qK[s] = quality_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
+                        load_vd(S, vb + e.z));
+  }
+}
+
 // ---- renumbering -----------------------------------------------------------
 
 __global__ void k_flags_v(Store S, int* cnt) {
@@ -258,6 +277,11 @@ __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) 
     B.xy[ns] = A.xy[s];
     B.M[ns] = A.M[s];
     B.vflag[ns] = A.vflag[s];
+    B.touch[ns] = A.touch[s];
+    B.evc[ns] = A.evc[s];
+    B.evs[ns] = A.evs[s];
+    B.evm[ns] = A.evm[s];
+    B.evr[ns] = A.evr[s];
     int a = A.NNlen[s], b = A.NElen[s];
     const int* nn = A.NN + (size_t)s * A.W;
     const int* ne = A.NE + (size_t)s * A.W;
@@ -280,6 +304,7 @@ __global__ void k_renum_e(Store A, Store B, const int* vscan, const int* escan) 
     int v0 = vscan[vb];
     int ns = eb + (escan[s] - escan[eb]);
     B.EN[ns] = make_int4(vscan[vb + e.x] - v0, vscan[vb + e.y] - v0, vscan[vb + e.z] - v0, 1);
+    B.qK[ns] = A.qK[s];
   }
 }
 
@@ -355,6 +380,16 @@ cudaError_t upload_tab(MeshSet& m) {
   e = cudaMemcpyAsync(m.S.tab.L_low, dbl.data(), dbl.size() * sizeof(double),
                       cudaMemcpyHostToDevice, m.stream);
   if (e != cudaSuccess) return e;
+  std::vector<double4> band(n);
+  for (int i = 0; i < n; ++i) {
+    double a = m.L_low[i], b = m.L_up[i];
+    double alo = a * (1.0 - 1e-9), ahi = a * (1.0 + 1e-9);
+    double blo = b * (1.0 - 1e-9), bhi = b * (1.0 + 1e-9);
+    band[i] = make_double4(alo * alo, ahi * ahi, blo * blo, bhi * bhi);
+  }
+  e = cudaMemcpyAsync(m.S.tab.band, band.data(), n * sizeof(double4), cudaMemcpyHostToDevice,
+                      m.stream);
+  if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(m.stream);  // host vectors go out of scope
 }
 
@@ -379,10 +414,16 @@ static cudaError_t alloc_store(MeshSet& m, Store& S, bool zero) {
   if ((e = dalloc(m, &S.M, V, zero))) return e;
   if ((e = dalloc(m, &S.vflag, V, true))) return e;
   if ((e = dalloc(m, &S.EN, E, zero))) return e;
+  if ((e = dalloc(m, &S.qK, E, zero))) return e;
   if ((e = dalloc(m, &S.NN, V * W, false))) return e;
   if ((e = dalloc(m, &S.NNlen, V, true))) return e;
   if ((e = dalloc(m, &S.NE, V * W, false))) return e;
   if ((e = dalloc(m, &S.NElen, V, true))) return e;
+  if ((e = dalloc(m, &S.touch, V, true))) return e;
+  if ((e = dalloc(m, &S.evc, V, true))) return e;
+  if ((e = dalloc(m, &S.evs, V, true))) return e;
+  if ((e = dalloc(m, &S.evm, V, true))) return e;
+  if ((e = dalloc(m, &S.evr, V, true))) return e;
   return cudaSuccess;
 }
 
@@ -413,12 +454,14 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   if ((e = alloc_store(m, m.B, false))) return e;
   // table
   size_t tab_bytes = (size_t)n * (6 * sizeof(int) + 2 * sizeof(uint32_t) + 2 * sizeof(int) +
-                                  2 * sizeof(unsigned long long) + 3 * sizeof(double)) + 64;
+                                  2 * sizeof(unsigned long long) + 3 * sizeof(double) +
+                                  sizeof(double4)) + 64;
   char* t = nullptr;
   if ((e = dalloc(m, &t, tab_bytes, true))) return e;
   m.tabmem = t;
   MeshTab& T = S.tab;
-  // doubles and 64-bit counters first (alignment)
+  // 32-byte, then 8-byte aligned members first
+  T.band = (double4*)t; t += n * sizeof(double4);
   T.L_low = (double*)t; t += n * sizeof(double);
   T.L_up = (double*)t; t += n * sizeof(double);
   T.q_thresh = (double*)t; t += n * sizeof(double);
@@ -459,6 +502,10 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   if ((e = dalloc(m, &w.ecnt, es + 1, false))) return e;
   if ((e = dalloc(m, &w.escan, es + 1, false))) return e;
   if ((e = dalloc(m, &w.emid, es, false))) return e;
+  if ((e = dalloc(m, &w.E, vs, false))) return e;
+  // each interior edge gives at most two items and a planar mesh has < 3V edges
+  if ((e = dalloc(m, &w.items, (size_t)vs * 6 + 64, false))) return e;
+  if ((e = dalloc(m, &w.gains, (size_t)vs * W, false))) return e;
   if ((e = dalloc(m, &w.counts, CN_NUM + 2 * n + 8, true))) return e;
   int tiles = scan_tiles((int)std::max(vs, es) + 1);
   if ((e = dalloc(m, &m.scan.state, tiles, true))) return e;
@@ -527,7 +574,9 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
   m.tabmem = n2.tabmem;
   m.allocs = n2.allocs;
   n2.allocs.clear();
-  m.tag = 0;  // fresh stamp arrays
+  // per-round stamp arrays start at zero, below every later tag; scratch that
+  // held evaluation results is fresh, so earlier evaluations are stale
+  m.lo_coarsen = m.lo_swap = m.lo_refine = m.tag;
   return cudaSuccess;
 }
 
@@ -547,7 +596,9 @@ cudaError_t grow_rows(MeshSet& m, int W) {
   if ((e = dalloc(m, &m.B.NE, n, false))) return e;
   m.S.W = W;
   m.B.W = W;
-  return cudaSuccess;
+  cudaFreeAsync(m.w.gains, m.stream);
+  m.allocs.erase(std::remove(m.allocs.begin(), m.allocs.end(), (void*)m.w.gains), m.allocs.end());
+  return dalloc(m, &m.w.gains, n, false);
 }
 
 int sync_status(MeshSet& m) {
@@ -593,6 +644,11 @@ int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) 
   return PM_OK;
 }
 
+int refresh_quality(MeshSet& m) {
+  PM_LAUNCH(k_qcache_all, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S);
+  return sync_status(m);
+}
+
 int validate_mesh(MeshSet& m) {
   PM_LAUNCH(k_validate_elems, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, m.st);
   return sync_status(m);
@@ -623,10 +679,16 @@ int renumber(MeshSet& m) {
   std::swap(m.S.M, m.B.M);
   std::swap(m.S.vflag, m.B.vflag);
   std::swap(m.S.EN, m.B.EN);
+  std::swap(m.S.qK, m.B.qK);
   std::swap(m.S.NN, m.B.NN);
   std::swap(m.S.NNlen, m.B.NNlen);
   std::swap(m.S.NE, m.B.NE);
   std::swap(m.S.NElen, m.B.NElen);
+  std::swap(m.S.touch, m.B.touch);
+  std::swap(m.S.evc, m.B.evc);
+  std::swap(m.S.evs, m.B.evs);
+  std::swap(m.S.evm, m.B.evm);
+  std::swap(m.S.evr, m.B.evr);
   std::vector<int> t(2 * m.nmesh);
   for (int i = 0; i < m.nmesh; ++i) {
     t[i] = m.nv[i];

@@ -84,18 +84,46 @@ __device__ __forceinline__ double elem_quality(const Store& S, int vb, int4 e) {
                    load_vd(S, vb + e.z));
 }
 
+// Refresh the cached quality of the live elements of v's ball.
+__device__ __forceinline__ void refresh_ball_quality(const Store& S, int vb, int eb, const int* ne,
+                                                     int nel) {
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[eb + ne[k]];
+    if (e.w) S.qK[eb + ne[k]] = elem_quality(S, vb, e);
+  }
+}
+
+// Inputs of v's evaluation unchanged since tag `et`?  Evaluations read v's
+// rows, the elements and vertices of its ball and the rows and positions of
+// its neighbours; every change to those stamps v or a neighbour.  Only
+// evaluations newer than `lo` count.
+__device__ __forceinline__ bool unchanged(const Store& S, int v, int vb, int et, int lo) {
+  if (et <= lo) return false;
+  if (S.touch[v] > et) return false;
+  const int* nn = S.NN + (size_t)v * S.W;
+  int nnl = S.NNlen[v];
+  for (int k = 0; k < nnl; ++k)
+    if (S.touch[vb + nn[k]] > et) return false;
+  return true;
+}
+
 // ---- worklist initialisation ---------------------------------------------------
 
 // mode 0: every live vertex of an active mesh; mode 1: live interior vertices.
-__global__ void k_init_list(Store S, int mode, int* list, int* count) {
+// With `ev`, vertices whose last evaluation (newer than `lo`) found nothing
+// and whose inputs are unchanged since are left out: they would find
+// nothing again.
+__global__ void k_init_list(Store S, int mode, int* list, int* count, const int* ev, int lo) {
   for (int i0 = blockIdx.x * blockDim.x; i0 < S.vslots; i0 += gridDim.x * blockDim.x) {
     int s = i0 + threadIdx.x;
     bool take = false;
     if (s < S.vslots) {
       int mi = mesh_of_vslot(S, s);
-      if (s - S.tab.vbase[mi] < S.tab.nv[mi] && S.tab.active[mi]) {
+      int vb = S.tab.vbase[mi];
+      if (s - vb < S.tab.nv[mi] && S.tab.active[mi]) {
         uint8_t f = S.vflag[s];
         take = (f & VF_ALIVE) && (mode == 0 || !(f & VF_BND));
+        if (take && ev) take = !unchanged(S, s, vb, ev[s], lo);
       }
     }
     warp_append(take, s, list, count);
@@ -137,6 +165,9 @@ __global__ void k_select(Store S, const int* C, const int* nCp, const int* cmark
 
 // ---- coarsening (Sec. 2.4.1) ---------------------------------------------------
 
+struct CoarsenCtx;
+__device__ __forceinline__ double S_L_up(const CoarsenCtx& x);
+
 struct CoarsenCtx {
   const Store* S;
   MeshCtx c;
@@ -149,9 +180,12 @@ struct CoarsenCtx {
   bool bnd;
 };
 
+__device__ __forceinline__ double S_L_up(const CoarsenCtx& x) { return x.S->tab.L_up[x.c.mi]; }
+
 // Validity of collapsing v onto local neighbour u: link condition, all
 // remaining ball elements counter-clockwise, no new edge longer than L_up.
-__device__ bool collapse_valid(const CoarsenCtx& x, int u, double L_up) {
+__device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band) {
+  const double L_up = S_L_up(x);
   const Store& S = *x.S;
   bool bedge = count_elems_with(S, x.ne, x.nel, x.c.eb, u) == 1;
   if (x.bnd && !bedge) return false;
@@ -191,7 +225,7 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double L_up) {
   for (int k = 0; k < x.nnl; ++k) {
     int y = x.nn[k];
     if (y == u || row_has(nnw, nnwl, y)) continue;
-    if (metric_len(dw, load_vd(S, x.c.vb + y)) > L_up) return false;
+    if (len_gt(metric_len2(dw, load_vd(S, x.c.vb + y)), band.z, band.w, L_up)) return false;
   }
   return true;
 }
@@ -212,15 +246,17 @@ __device__ int coarsen_target(const Store& S, int v, MeshCtx c) {
   x.nel = S.NElen[v];
   x.dv = load_vd(S, v);
   x.bnd = (f & VF_BND) != 0;
-  const double L_low = S.tab.L_low[c.mi], L_up = S.tab.L_up[c.mi];
+  const double L_low = S.tab.L_low[c.mi];
+  const double4 band = S.tab.band[c.mi];
   double cl[MAXW];
   int cw[MAXW];
   int nc = 0;
   for (int k = 0; k < x.nnl; ++k) {
     int u = x.nn[k];
     if (x.bnd && count_elems_with(S, x.ne, x.nel, c.eb, u) != 1) continue;
-    double L = metric_len(x.dv, load_vd(S, c.vb + u));
-    if (!(L < L_low)) continue;
+    double L2 = metric_len2(x.dv, load_vd(S, c.vb + u));
+    if (!len_lt(L2, band.x, band.y, L_low)) continue;
+    double L = sqrt(L2);
     int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
     while (j > 0 && cl[j - 1] > L) {
       cl[j] = cl[j - 1];
@@ -232,12 +268,12 @@ __device__ int coarsen_target(const Store& S, int v, MeshCtx c) {
     ++nc;
   }
   for (int j = 0; j < nc; ++j)
-    if (collapse_valid(x, cw[j], L_up)) return cw[j];
+    if (collapse_valid(x, cw[j], band)) return cw[j];
   return -1;
 }
 
 __global__ void k_coarsen_eval(Store S, const int* D, const int* nDp, int* target, int* C,
-                               int* nC, int* cmark, int tag) {
+                               int* nC, int* cmark, int tag, int pass0) {
   const int n = *nDp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -245,8 +281,13 @@ __global__ void k_coarsen_eval(Store S, const int* D, const int* nDp, int* targe
     if (i < n) {
       v = D[i];
       MeshCtx c = ctx_of(S, v);
-      t = coarsen_target(S, v, c);
-      target[v] = t;
+      if (unchanged(S, v, c.vb, S.evc[v], pass0)) {
+        t = target[v];
+      } else {
+        t = coarsen_target(S, v, c);
+        target[v] = t;
+        S.evc[v] = tag;
+      }
       if (t >= 0) {
         cmark[v] = tag;
         S.tab.had[c.mi] = 1;
@@ -287,6 +328,7 @@ __global__ void k_coarsen_apply(Store S, const int* Sl, const int* nSp, const in
           if (e.x == lv) e.x = w;
           if (e.y == lv) e.y = w;
           if (e.z == lv) e.z = w;
+          S.qK[c.eb + ne[k]] = elem_quality(S, c.vb, e);
         }
         *pe = e;
       }
@@ -316,6 +358,7 @@ __global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const in
   const int n = *nAp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int u = A[i];
+    S.touch[u] = tag + 1;
     MeshCtx c = ctx_of(S, u);
     int lu = u - c.vb;
     const int* nn = nn_row(S, u);
@@ -367,86 +410,167 @@ __global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const in
 
 // ---- swapping (Sec. 2.4.3) ------------------------------------------------------
 
-// Best flip of v: over interior edges (v,w) with elements K1=(v,w,c) and
-// K2=(w,v,d), min quality below q_thresh, flip not duplicating edge (c,d) and
-// keeping (v,d,c), (d,w,c) counter-clockwise; the largest strictly positive
-// gain in minimum quality wins, ties to the smallest w.
-__device__ bool swap_eval(const Store& S, int v, MeshCtx c, int4& op, int& opK2) {
-  uint8_t f = S.vflag[v];
-  if (!(f & VF_ALIVE)) return false;
-  const double qt = S.tab.q_thresh[c.mi];
-  int lv = v - c.vb;
-  const int* ne = ne_row(S, v);
-  int nel = S.NElen[v];
-  int nxt[MAXW], prv[MAXW];
-  double q[MAXW];
-  for (int k = 0; k < nel; ++k) {
-    int4 e = S.EN[c.eb + ne[k]];
-    int i = (e.x == lv) ? 0 : (e.y == lv) ? 1 : 2;
-    int a = (i == 0) ? e.y : (i == 1) ? e.z : e.x;  // after v
-    int b = (i == 0) ? e.z : (i == 1) ? e.x : e.y;  // before v
-    nxt[k] = a;
-    prv[k] = b;
-    q[k] = elem_quality(S, c.vb, e);
-  }
-  bool found = false;
-  double best = 0.0;
-  int bw = 0;
-  VD dv = load_vd(S, v);
-  for (int k1 = 0; k1 < nel; ++k1) {
-    int w = nxt[k1];
-    int cc = prv[k1];
-    int k2 = -1;
-    for (int k = 0; k < nel; ++k)
-      if (prv[k] == w) {
-        k2 = k;
-        break;
-      }
-    if (k2 < 0) continue;  // boundary edge
-    int d = nxt[k2];
-    double qold = (q[k1] < q[k2]) ? q[k1] : q[k2];
-    if (!(qold < qt)) continue;
-    if (row_has(nn_row(S, c.vb + d), S.NNlen[c.vb + d], cc)) continue;
-    VD dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc), dd = load_vd(S, c.vb + d);
-    if (!(orient_c(lv, d, cc, dv, dd, dc) > 0.0)) continue;
-    if (!(orient_c(d, w, cc, dd, dw, dc) > 0.0)) continue;
-    double n1 = quality_c(lv, d, cc, dv, dd, dc);
-    double n2 = quality_c(d, w, cc, dd, dw, dc);
-    double qnew = (n1 < n2) ? n1 : n2;
-    double gain = qnew - qold;
-    if (!(gain > 0.0)) continue;
-    if (!found || gain > best || (gain == best && w < bw)) {
-      found = true;
-      best = gain;
-      bw = w;
-      op = make_int4(w, cc, d, ne[k1]);
-      opK2 = ne[k2];
-    }
-  }
-  return found;
-}
-
-__global__ void k_swap_eval(Store S, const int* D, const int* nDp, int4* opA, int* opK2, int* C,
-                            int* nC, int* cmark, int tag) {
+// Flip evaluation in three passes so that the FP64 work runs on full warps.
+// Pass 1 (per dirty vertex): reuse an unchanged earlier result, or list the
+// vertex's interior edges whose two elements' cached minimum quality is below
+// q_thresh and whose flip would not duplicate an edge.
+__global__ void k_swap_scan(Store S, const int* D, const int* nDp, const int4* opA, int* C,
+                            int* nC, int* cmark, int tag, int pass0, int* E, int* nE,
+                            int2* items, int* nI, int icap, double* gains, DevStatus* st) {
   const int n = *nDp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
-    int v = 0;
-    bool cand = false;
+    int v = 0, nel = 0;
+    bool reuse_cand = false, eval = false;
+    MeshCtx c{0, 0, 0};
+    const int* ne = nullptr;
     if (i < n) {
       v = D[i];
-      MeshCtx c = ctx_of(S, v);
-      int4 op;
-      int k2;
-      cand = swap_eval(S, v, c, op, k2);
-      if (cand) {
-        opA[v] = op;
-        opK2[v] = k2;
-        cmark[v] = tag;
-        S.tab.had[c.mi] = 1;
+      c = ctx_of(S, v);
+      if (unchanged(S, v, c.vb, S.evs[v], pass0)) {
+        reuse_cand = opA[v].x >= 0;
+        if (reuse_cand) {
+          cmark[v] = tag;
+          S.tab.had[c.mi] = 1;
+        }
+      } else if (S.vflag[v] & VF_ALIVE) {
+        eval = true;
+        S.evs[v] = tag;
+        ne = ne_row(S, v);
+        nel = S.NElen[v];
       }
     }
-    warp_append(cand, v, C, nC);
+    warp_append(reuse_cand, v, C, nC);
+    warp_append(eval, v, E, nE);
+    const int lv = v - c.vb;
+    const double qt = eval ? S.tab.q_thresh[c.mi] : 0.0;
+    int kmax = warp_max(nel);
+    for (int k1 = 0; k1 < kmax; ++k1) {
+      bool emit = false;
+      int k2 = -1;
+      if (eval && k1 < nel) {
+        gains[(size_t)v * S.W + k1] = -1.0;
+        int4 e = S.EN[c.eb + ne[k1]];
+        int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;   // after v
+        int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;  // before v
+        for (int k = 0; k < nel; ++k) {
+          int4 f = S.EN[c.eb + ne[k]];
+          int pv = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
+          if (pv == w) {
+            k2 = k;
+            break;
+          }
+        }
+        if (k2 >= 0) {
+          double q1 = S.qK[c.eb + ne[k1]], q2 = S.qK[c.eb + ne[k2]];
+          double qold = (q1 < q2) ? q1 : q2;
+          if (qold < qt) {
+            int4 f = S.EN[c.eb + ne[k2]];
+            int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+            emit = !row_has(nn_row(S, c.vb + d), S.NNlen[c.vb + d], cc);
+          }
+        }
+      }
+      unsigned m = __ballot_sync(0xffffffffu, emit);
+      if (m) {
+        int lane = threadIdx.x & 31, leader = __ffs(m) - 1, base = 0;
+        if (lane == leader) base = atomicAdd(nI, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        int pos = base + __popc(m & ((1u << lane) - 1u));
+        if (emit) {
+          if (pos < icap) items[pos] = make_int2(v, k1 | (k2 << 8));
+          else set_err(st, PM_ERR_CAPACITY);
+        }
+      }
+    }
+  }
+}
+
+// Pass 2 (per listed edge, dense FP64): both flipped elements counter-
+// clockwise and their minimum quality above the old minimum -> the gain.
+__global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* gains) {
+  const int n = *nIp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int2 it = items[i];
+    int v = it.x, k1 = it.y & 0xFF, k2 = it.y >> 8;
+    MeshCtx c = ctx_of(S, v);
+    int lv = v - c.vb;
+    const int* ne = ne_row(S, v);
+    int K1 = ne[k1], K2 = ne[k2];
+    int4 e = S.EN[c.eb + K1];
+    int4 f = S.EN[c.eb + K2];
+    int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
+    int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;
+    int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+    double q1 = S.qK[c.eb + K1], q2 = S.qK[c.eb + K2];
+    double qold = (q1 < q2) ? q1 : q2;
+    VD dv = load_vd(S, v), dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc),
+       dd = load_vd(S, c.vb + d);
+    double gain = -1.0;
+    if (orient_c(lv, d, cc, dv, dd, dc) > 0.0 && orient_c(d, w, cc, dd, dw, dc) > 0.0) {
+      // gain = min(n1, n2) - qold > 0 exactly when both exceed qold
+      double n1 = quality_c(lv, d, cc, dv, dd, dc);
+      if (n1 > qold) {
+        double n2 = quality_c(d, w, cc, dd, dw, dc);
+        if (n2 > qold) gain = ((n1 < n2) ? n1 : n2) - qold;
+      }
+    }
+    gains[(size_t)v * S.W + k1] = gain;
+  }
+}
+
+// Pass 3 (per evaluated vertex): largest strictly positive gain, ties to the
+// smallest w; the flip record (w, c, d, K1, K2) of the winner.
+__global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double* gains,
+                            int4* opA, int* opK2, int* C, int* nC, int* cmark, int tag) {
+  const int n = *nEp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int v = 0;
+    bool found = false;
+    if (i < n) {
+      v = E[i];
+      MeshCtx c = ctx_of(S, v);
+      int lv = v - c.vb;
+      const int* ne = ne_row(S, v);
+      int nel = S.NElen[v];
+      double best = 0.0;
+      int bw = 0, bk = -1;
+      for (int k = 0; k < nel; ++k) {
+        double g = gains[(size_t)v * S.W + k];
+        if (!(g > 0.0)) continue;
+        int4 e = S.EN[c.eb + ne[k]];
+        int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
+        if (!found || g > best || (g == best && w < bw)) {
+          found = true;
+          best = g;
+          bw = w;
+          bk = k;
+        }
+      }
+      if (found) {
+        int4 e = S.EN[c.eb + ne[bk]];
+        int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;
+        int k2 = -1;
+        for (int k = 0; k < nel; ++k) {
+          int4 f = S.EN[c.eb + ne[k]];
+          int pv = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
+          if (pv == bw) {
+            k2 = k;
+            break;
+          }
+        }
+        int4 f = S.EN[c.eb + ne[k2]];
+        int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+        opA[v] = make_int4(bw, cc, d, ne[bk]);
+        opK2[v] = ne[k2];
+        cmark[v] = tag;
+        S.tab.had[c.mi] = 1;
+      } else {
+        opA[v].x = -1;
+      }
+    }
+    warp_append(found, v, C, nC);
   }
 }
 
@@ -467,8 +591,12 @@ __global__ void k_swap_apply(Store S, const int* Sl, const int* nSp, const int4*
       int lv = v - c.vb;
       int4 op = opA[v];
       int K2 = opK2[v];
-      S.EN[c.eb + op.w] = make_int4(lv, op.z, op.y, 1);  // K1 = (v, d, c)
-      S.EN[c.eb + K2] = make_int4(op.z, op.x, op.y, 1);  // K2 = (d, w, c)
+      int4 t1 = make_int4(lv, op.z, op.y, 1);  // K1 = (v, d, c)
+      int4 t2 = make_int4(op.z, op.x, op.y, 1);  // K2 = (d, w, c)
+      S.EN[c.eb + op.w] = t1;
+      S.EN[c.eb + K2] = t2;
+      S.qK[c.eb + op.w] = elem_quality(S, c.vb, t1);
+      S.qK[c.eb + K2] = elem_quality(S, c.vb, t2);
       t[0] = v;
       t[1] = c.vb + op.x;
       t[2] = c.vb + op.y;
@@ -494,6 +622,7 @@ __global__ void k_swap_commit(Store S, const int* A, const int* nAp, const int4*
   const int n = *nAp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int u = A[i];
+    S.touch[u] = tag + 1;
     MeshCtx c = ctx_of(S, u);
     int lu = u - c.vb;
     int* nn = S.NN + (size_t)u * S.W;
@@ -545,7 +674,7 @@ __device__ __forceinline__ double ball_min_quality(const Store& S, MeshCtx c, co
                                                    int nel, double* qsum) {
   double qmin = 0.0, sum = 0.0;
   for (int k = 0; k < nel; ++k) {
-    double q = elem_quality(S, c.vb, S.EN[c.eb + ne[k]]);
+    double q = S.qK[c.eb + ne[k]];
     if (k == 0 || q < qmin) qmin = q;
     sum = sum + q;
   }
@@ -579,8 +708,11 @@ __device__ bool interpolate_in_ball(const Store& S, MeshCtx c, const int* ne, in
 }
 
 // Ball with v moved to (X, Y, M): all counter-clockwise?  min and sum of q.
+// With `floor` set, gives up (false) as soon as a quality is at or below
+// *floor (strict) or below it (non-strict): the caller would reject the move.
 __device__ bool ball_after_move(const Store& S, MeshCtx c, int lv, const int* ne, int nel,
-                                double X, double Y, double4 Mv, double& qmin, double& qsum) {
+                                double X, double Y, double4 Mv, double& qmin, double& qsum,
+                                const double* floor = nullptr, bool strict = true) {
   VD nvd{X, Y, Mv.x, Mv.y, Mv.z};
   qmin = 0.0;
   qsum = 0.0;
@@ -590,7 +722,14 @@ __device__ bool ball_after_move(const Store& S, MeshCtx c, int lv, const int* ne
     VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
     VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
     if (!(orient_c(e.x, e.y, e.z, a, b, d) > 0.0)) return false;
+  }
+  for (int k = 0; k < nel; ++k) {
+    int4 e = S.EN[c.eb + ne[k]];
+    VD a = (e.x == lv) ? nvd : load_vd(S, c.vb + e.x);
+    VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
+    VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
     double q = quality_c(e.x, e.y, e.z, a, b, d);
+    if (floor && (strict ? !(q > *floor) : (q < *floor))) return false;
     if (k == 0 || q < qmin) qmin = q;
     qsum = qsum + q;
   }
@@ -631,31 +770,69 @@ __device__ bool smooth_eval(const Store& S, int v, MeshCtx c, double2& X, double
   double4 Mn;
   if (!interpolate_in_ball(S, c, ne, nel, x, y, Mn)) return false;
   double qmin, qsum;
-  if (!ball_after_move(S, c, v - c.vb, ne, nel, x, y, Mn, qmin, qsum)) return false;
+  if (!ball_after_move(S, c, v - c.vb, ne, nel, x, y, Mn, qmin, qsum, &qold, true)) return false;
   if (!(qmin > qold)) return false;
   X = make_double2(x, y);
   Mv = Mn;
   return true;
 }
 
-__global__ void k_smooth_eval(Store S, const int* D, const int* nDp, double2* mvxy, double4* mvM,
-                              int* C, int* nC, int* cmark, int tag) {
+// Smoothing evaluation in two passes.  Pass 1 (per pending vertex): reuse an
+// unchanged earlier result, drop vertices whose ball is already good enough
+// (cached qualities), list the rest for the full move evaluation.
+__global__ void k_smooth_scan(Store S, const int* D, const int* nDp, double4* mvM, int* C,
+                              int* nC, int* cmark, int tag, int pass0, int* E, int* nE) {
   const int n = *nDp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int v = 0;
+    bool reuse_cand = false, eval = false;
+    if (i < n) {
+      v = D[i];
+      MeshCtx c = ctx_of(S, v);
+      if (unchanged(S, v, c.vb, S.evm[v], pass0)) {
+        reuse_cand = mvM[v].w != 0.0;
+        if (reuse_cand) {
+          cmark[v] = tag;
+          S.tab.had[c.mi] = 1;
+        }
+      } else {
+        S.evm[v] = tag;
+        uint8_t f = S.vflag[v];
+        if ((f & VF_ALIVE) && !(f & VF_BND)) {
+          double qold = ball_min_quality(S, c, ne_row(S, v), S.NElen[v], nullptr);
+          eval = qold < S.tab.q_thresh[c.mi];
+        }
+        if (!eval) mvM[v].w = 0.0;
+      }
+    }
+    warp_append(reuse_cand, v, C, nC);
+    warp_append(eval, v, E, nE);
+  }
+}
+
+// Pass 2 (per listed vertex, dense FP64): the full quality-constrained move.
+__global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mvxy, double4* mvM,
+                              int* C, int* nC, int* cmark, int tag) {
+  const int n = *nEp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
     int v = 0;
     bool cand = false;
     if (i < n) {
-      v = D[i];
+      v = E[i];
       MeshCtx c = ctx_of(S, v);
       double2 X;
       double4 Mv;
       cand = smooth_eval(S, v, c, X, Mv);
       if (cand) {
+        Mv.w = 1.0;  // marks a stored move
         mvxy[v] = X;
         mvM[v] = Mv;
         cmark[v] = tag;
         S.tab.had[c.mi] = 1;
+      } else {
+        mvM[v].w = 0.0;
       }
     }
     warp_append(cand, v, C, nC);
@@ -665,7 +842,8 @@ __global__ void k_smooth_eval(Store S, const int* D, const int* nDp, double2* mv
 // Move the members of S; live interior neighbours become pending for the next
 // sweep (stamp pmark with the sweep tag).
 __global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const double2* mvxy,
-                               const double4* mvM, int* P, int* nP, int* pmark, int ptag) {
+                               const double4* mvM, int* P, int* nP, int* pmark, int ptag,
+                               int stamp) {
   advance_rounds(S);
   const int n = *nSp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
@@ -679,7 +857,11 @@ __global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const dou
       mi = c.mi;
       vb = c.vb;
       S.xy[v] = mvxy[v];
-      S.M[v] = mvM[v];
+      double4 mv = mvM[v];
+      mv.w = 0.0;
+      S.M[v] = mv;
+      S.touch[v] = stamp;
+      refresh_ball_quality(S, c.vb, c.eb, ne_row(S, v), S.NElen[v]);
       nn = nn_row(S, v);
       nnl = S.NNlen[v];
     }
@@ -740,8 +922,8 @@ __device__ bool opt_eval(const Store& S, int v, MeshCtx c, double2& Xo, double4&
     double4 Mn;
     if (interpolate_in_ball(S, c, ne, nel, X, Y, Mn)) {
       double qmin, qsum;
-      if (ball_after_move(S, c, lv, ne, nel, X, Y, Mn, qmin, qsum) && qmin >= qmin_old &&
-          qsum > qsum_old) {
+      if (ball_after_move(S, c, lv, ne, nel, X, Y, Mn, qmin, qsum, &qmin_old, false) &&
+          qmin >= qmin_old && qsum > qsum_old) {
         Xo = make_double2(X, Y);
         Mo = Mn;
         return true;
@@ -754,7 +936,7 @@ __device__ bool opt_eval(const Store& S, int v, MeshCtx c, double2& Xo, double4&
 
 // Evaluate and apply in one pass: members of S are pairwise non-adjacent, so
 // no member reads a vertex another member moves.
-__global__ void k_opt_apply(Store S, const int* Sl, const int* nSp) {
+__global__ void k_opt_apply(Store S, const int* Sl, const int* nSp, int stamp) {
   advance_rounds(S);
   const int n = *nSp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
@@ -771,6 +953,8 @@ __global__ void k_opt_apply(Store S, const int* Sl, const int* nSp) {
       if (moved) {
         S.xy[v] = X;
         S.M[v] = Mv;
+        S.touch[v] = stamp;
+        refresh_ball_quality(S, c.vb, c.eb, ne_row(S, v), S.NElen[v]);
       }
     }
     count_op(S, moved, mi);
@@ -790,21 +974,31 @@ __global__ void k_stamp_list(Store S, const int* L, const int* nLp, int* cmark, 
 // ---- refinement (Sec. 2.4.2) -----------------------------------------------------
 
 // Mark edges (a, b), a < b, longer than L_up: bit k of vmask[a] for NN entry k.
-__global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask) {
+// A vertex unchanged since it was marked earlier in this pass keeps its mask;
+// one unchanged since the end of an earlier complete pass has none.
+__global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int tag, int pass0,
+                              int lo) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
     int mi = mesh_of_vslot(S, s);
     int vb = S.tab.vbase[mi];
     unsigned long long m = 0;
-    if (s - vb < S.tab.nv[mi] && S.tab.active[mi] && (S.vflag[s] & VF_ALIVE)) {
+    bool live = s - vb < S.tab.nv[mi] && S.tab.active[mi] && (S.vflag[s] & VF_ALIVE);
+    if (live && unchanged(S, s, vb, S.evr[s], pass0)) {
+      m = mask[s];
+    } else if (live && unchanged(S, s, vb, S.evr[s], lo)) {
+      m = 0;
+    } else if (live) {
+      S.evr[s] = tag;
       int la = s - vb;
       const int* nn = nn_row(S, s);
       int nnl = S.NNlen[s];
       VD da = load_vd(S, s);
       const double L_up = S.tab.L_up[mi];
+      const double4 band = S.tab.band[mi];
       for (int k = 0; k < nnl; ++k) {
         int b = nn[k];
         if (b <= la) continue;
-        if (metric_len(da, load_vd(S, vb + b)) > L_up) m |= 1ull << k;
+        if (len_gt(metric_len2(da, load_vd(S, vb + b)), band.z, band.w, L_up)) m |= 1ull << k;
       }
     }
     mask[s] = m;
@@ -843,7 +1037,8 @@ __device__ __forceinline__ int mid_id(const Store& S, int vb, int nv, const int*
   return nv + (vscan[vb + a] - vscan[vb]) + rank;
 }
 
-__global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long long* mask) {
+__global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long long* mask,
+                                  int stamp) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
     unsigned long long m = mask[s];
     if (!m) continue;
@@ -867,6 +1062,8 @@ __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long
                                0.5 * (da.m11 + db.m11), 0.0);
       bool bedge = count_elems_with(S, ne, nel, eb, b) == 1;
       S.vflag[slot] = (uint8_t)(VF_ALIVE | (bedge ? VF_BND : 0));
+      S.touch[slot] = stamp;
+      S.evc[slot] = S.evs[slot] = S.evm[slot] = S.evr[slot] = 0;
     }
   }
 }
@@ -897,7 +1094,7 @@ __global__ void k_refine_count(Store S, const int* vscan, const unsigned long lo
 // trapezoid (u0,m0,m1,u2) cut along its metric-shorter diagonal; three
 // splits -> four children.  The first child keeps the parent's slot, the rest
 // take ne + scan(extra children) in parent order.
-__global__ void k_refine_split(Store S, const int* escan, const int4* emid) {
+__global__ void k_refine_split(Store S, const int* escan, const int4* emid, int stamp) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
     int mi = mesh_of_eslot(S, s);
     int eb = S.tab.ebase[mi];
@@ -908,33 +1105,42 @@ __global__ void k_refine_split(Store S, const int* escan, const int4* emid) {
     if (md.w == 0) continue;
     int vb = S.tab.vbase[mi];
     int nslot = eb + S.tab.ne[mi] + (escan[s] - escan[eb]);
+    auto put = [&](int slot, int a, int b, int c) {
+      S.EN[slot] = make_int4(a, b, c, 1);
+      S.qK[slot] = quality_c(a, b, c, load_vd(S, vb + a), load_vd(S, vb + b), load_vd(S, vb + c));
+    };
     int t[3] = {e.x, e.y, e.z};
     int mm[3] = {md.x, md.y, md.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      S.touch[vb + t[k]] = stamp;
+      if (mm[k] >= 0) S.touch[vb + mm[k]] = stamp;
+    }
     if (md.w == 1) {
       int i = (mm[0] >= 0) ? 0 : (mm[1] >= 0) ? 1 : 2;
       int a = t[i], b = t[(i + 1) % 3], o = t[(i + 2) % 3], m = mm[i];
-      S.EN[s] = make_int4(a, m, o, 1);
-      S.EN[nslot] = make_int4(m, b, o, 1);
+      put(s, a, m, o);
+      put(nslot, m, b, o);
     } else if (md.w == 2) {
       int j = (mm[0] < 0) ? 0 : (mm[1] < 0) ? 1 : 2;
       int q = (j + 1) % 3;
       int u0 = t[q], u1 = t[(q + 1) % 3], u2 = t[(q + 2) % 3];
       int m0 = mm[q], m1 = mm[(q + 1) % 3];
-      S.EN[s] = make_int4(m0, u1, m1, 1);
+      put(s, m0, u1, m1);
       double d1 = metric_len(load_vd(S, vb + u0), load_vd(S, vb + m1));
       double d2 = metric_len(load_vd(S, vb + m0), load_vd(S, vb + u2));
       if (d1 <= d2) {
-        S.EN[nslot] = make_int4(u0, m0, m1, 1);
-        S.EN[nslot + 1] = make_int4(u0, m1, u2, 1);
+        put(nslot, u0, m0, m1);
+        put(nslot + 1, u0, m1, u2);
       } else {
-        S.EN[nslot] = make_int4(u0, m0, u2, 1);
-        S.EN[nslot + 1] = make_int4(m0, m1, u2, 1);
+        put(nslot, u0, m0, u2);
+        put(nslot + 1, m0, m1, u2);
       }
     } else {
-      S.EN[s] = make_int4(t[0], mm[0], mm[2], 1);
-      S.EN[nslot] = make_int4(mm[0], t[1], mm[1], 1);
-      S.EN[nslot + 1] = make_int4(mm[2], mm[1], t[2], 1);
-      S.EN[nslot + 2] = make_int4(mm[0], mm[1], mm[2], 1);
+      put(s, t[0], mm[0], mm[2]);
+      put(nslot, mm[0], t[1], mm[1]);
+      put(nslot + 1, mm[2], mm[1], t[2]);
+      put(nslot + 2, mm[0], mm[1], mm[2]);
     }
   }
 }
@@ -996,33 +1202,42 @@ cudaError_t fetch_ops(MeshSet& m, std::vector<unsigned long long>& ops) {
   return cudaStreamSynchronize(m.stream);
 }
 
-// Rounds of collapses until no dirty vertex has a valid collapse.
+// Rounds of collapses until no dirty vertex has a valid collapse.  The first
+// round's list leaves out vertices whose last collapse evaluation found
+// nothing and whose inputs have not changed since.
 int op_coarsen(MeshSet& m, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
+  const int pass0 = m.tag;
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evc,
+            m.lo_coarsen);
   int cur = 0;
+  bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
-    int tag = ++m.tag;
+    int tag = (m.tag += 2);
     int nxt = 1 - cur;
     zero_counts(m, CN_C, 3);
     zero_counts(m, nxt, 1);
-    PM_LAUNCH(k_coarsen_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.target, w.C,
-                                               w.counts + CN_C, w.cmark, tag);
-    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
-                                         w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
+    PM_LAUNCH(k_coarsen_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.target,
+              w.C, w.counts + CN_C, w.cmark, tag, pass0);
+    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
+              w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
     PM_LAUNCH(k_coarsen_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.target, w.A,
-                                                w.counts + CN_A, w.amark, w.D[nxt],
-                                                w.counts + nxt, w.dmark, tag);
-    PM_LAUNCH(k_coarsen_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target, w.smark, tag,
-                                                 m.st);
+              w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt, w.dmark, tag);
+    PM_LAUNCH(k_coarsen_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target,
+              w.smark, tag, m.st);
     RoundIO io = read_round(m);
-    if (io.nC == 0) break;
+    if (io.err) return io.err;
+    if (io.nC == 0) {
+      complete = true;
+      break;
+    }
     int err = after_round(m, io);
     if (err) return err;
     cur = nxt;
   }
+  if (!complete) m.lo_coarsen = m.tag;  // some vertex may still have a collapse
   return PM_OK;
 }
 
@@ -1030,29 +1245,42 @@ int op_coarsen(MeshSet& m, int max_rounds) {
 int op_swap(MeshSet& m, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
+  const int pass0 = m.tag;
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evs,
+            m.lo_swap);
   int cur = 0;
+  bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
-    int tag = ++m.tag;
+    int tag = (m.tag += 2);
     int nxt = 1 - cur;
     zero_counts(m, CN_C, 3);
     zero_counts(m, nxt, 1);
-    PM_LAUNCH(k_swap_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.opA, w.opK2, w.C,
-                                            w.counts + CN_C, w.cmark, tag);
-    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
-                                         w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
-    PM_LAUNCH(k_swap_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.opA, w.opK2, w.A,
-                                             w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt,
-                                             w.dmark, tag);
-    PM_LAUNCH(k_swap_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2, w.smark,
-                                              tag, m.st);
+    zero_counts(m, CN_E, 2);
+    PM_LAUNCH(k_swap_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.opA, w.C,
+              w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E, w.items,
+              w.counts + CN_I, m.S.vslots * 6 + 64, w.gains, m.st);
+    PM_LAUNCH(k_swap_edge, grid_for(m, 6LL * m.S.vslots, 16), BLOCK, 0, m.stream, m.S, w.items,
+              w.counts + CN_I, w.gains);
+    PM_LAUNCH(k_swap_pick, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
+              w.opK2, w.C, w.counts + CN_C, w.cmark, tag);
+    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
+              w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
+    PM_LAUNCH(k_swap_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.opA, w.opK2,
+              w.A, w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt, w.dmark, tag);
+    PM_LAUNCH(k_swap_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2,
+              w.smark, tag, m.st);
     RoundIO io = read_round(m);
-    if (io.nC == 0) break;
+    if (io.err) return io.err;
+    if (io.nC == 0) {
+      complete = true;
+      break;
+    }
     int err = after_round(m, io);
     if (err) return err;
     cur = nxt;
   }
+  if (!complete) m.lo_swap = m.tag;
   return PM_OK;
 }
 
@@ -1060,10 +1288,15 @@ int op_swap(MeshSet& m, int max_rounds) {
 // (and grown) before any new vertex or element is written.
 int op_refine(MeshSet& m, int max_rounds) {
   Work& w = m.w;
+  int pass0 = m.tag;
+  bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
     const int gv = grid_for(m, m.S.vslots);
     const int ge = grid_for(m, m.S.eslots);
-    PM_LAUNCH(k_refine_mark, gv, BLOCK, 0, m.stream, m.S, w.vcnt, w.vmask);
+    int tag = (m.tag += 2);
+    if (m.lo_refine > pass0) pass0 = m.lo_refine;  // storage was regrown
+    PM_LAUNCH(k_refine_mark, gv, BLOCK, 0, m.stream, m.S, w.vcnt, w.vmask, tag, pass0,
+              m.lo_refine);
     scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
     int* tot = w.counts + CN_NUM;
     std::vector<int> newv(m.nmesh);
@@ -1093,7 +1326,10 @@ int op_refine(MeshSet& m, int max_rounds) {
         need_grow = true;
       }
     }
-    if (total == 0) break;
+    if (total == 0) {
+      complete = true;
+      break;
+    }
     if (need_grow) {
       cudaError_t e = grow(m, vcap, ecap, m.S.W);
       if (e != cudaSuccess) {
@@ -1103,17 +1339,19 @@ int op_refine(MeshSet& m, int max_rounds) {
       --nr;  // redo this round on the new layout
       continue;
     }
+    const int stamp = tag + 1;
     PM_LAUNCH(k_refine_vtotals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan);
-    PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask);
+    PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, stamp);
     PM_LAUNCH(k_refine_count, ge, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid);
     scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
-    PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid);
+    PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid, stamp);
     PM_LAUNCH(k_refine_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan);
     cudaError_t e = refresh_sizes(m);
     if (e != cudaSuccess) return PM_ERR_CUDA;
     int err = rebuild_adjacency(m, false, nullptr);
     if (err) return err;
   }
+  if (!complete) m.lo_refine = m.tag;
   return PM_OK;
 }
 
@@ -1121,26 +1359,29 @@ int op_refine(MeshSet& m, int max_rounds) {
 int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
+  const int pass0 = m.tag;
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0, nullptr, 0);
   long long nr = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    int ptag = ++m.tag;  // stamp of the next sweep's pending list
+    int ptag = (m.tag += 2);  // stamp of the next sweep's pending list
     zero_counts(m, CN_P, 1);
     int cur = 0;
     bool moved = false;
     while (max_rounds == 0 || nr < max_rounds) {
-      int tag = ++m.tag;
+      int tag = (m.tag += 2);
       int nxt = 1 - cur;
       zero_counts(m, CN_C, 2);
       zero_counts(m, nxt, 1);
-      PM_LAUNCH(k_smooth_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.mvxy, w.mvM, w.C,
-                                                w.counts + CN_C, w.cmark, tag);
-      PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
-                                           w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt,
-                                           w.dmark);
-      PM_LAUNCH(k_smooth_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.mvxy, w.mvM, w.P,
-                                                 w.counts + CN_P, w.pmark, ptag);
+      zero_counts(m, CN_E, 1);
+      PM_LAUNCH(k_smooth_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.mvM, w.C,
+                w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E);
+      PM_LAUNCH(k_smooth_eval, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.mvxy, w.mvM,
+                w.C, w.counts + CN_C, w.cmark, tag);
+      PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark,
+                tag, w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
+      PM_LAUNCH(k_smooth_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.mvxy,
+                w.mvM, w.P, w.counts + CN_P, w.pmark, ptag, tag + 1);
       RoundIO io = read_round(m);
       if (io.err) return io.err;
       if (io.nC == 0) break;
@@ -1162,14 +1403,14 @@ int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vslots);
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.C, w.counts + CN_C);
+  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.C, w.counts + CN_C, nullptr, 0);
   for (int it = 0; it < nrounds && (max_rounds == 0 || it < max_rounds); ++it) {
-    int tag = ++m.tag;
+    int tag = (m.tag += 2);
     zero_counts(m, CN_S, 1);
     PM_LAUNCH(k_stamp_list, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, tag);
-    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag, w.Sl,
-                                         w.counts + CN_S, nullptr, nullptr, nullptr);
-    PM_LAUNCH(k_opt_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S);
+    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
+              w.Sl, w.counts + CN_S, nullptr, nullptr, nullptr);
+    PM_LAUNCH(k_opt_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, tag + 1);
   }
   return sync_status(m);
 }

@@ -195,13 +195,15 @@ def small_uniform(n: int = 41, h: float = 0.02, seed: int = 1) -> Workload:
                     Params(seed=seed))
 
 
-def psi_workload(n: int, target_elements: float, jitter: bool, seed: int) -> Workload:
+def psi_workload(n: int, target_elements: float, jitter: bool, seed: int,
+                 hmin: float = 1e-3, hmax: float = 0.3) -> Workload:
     """Unit-square n x n grid (interior jitter +-10% of the spacing if asked),
-    psi-Hessian metric scaled to about `target_elements` output triangles."""
+    psi-Hessian metric with sizes clamped to [hmin, hmax], scaled to about
+    `target_elements` output triangles."""
     xy, tri = grid_mesh(n)
     if jitter:
         xy = jitter_interior(xy, n, 0.1 / (n - 1), seed)
-    m = psi_metric(xy, tri, target_elements)
+    m = psi_metric(xy, tri, target_elements, hmin, hmax)
     tag = "jittered " if jitter else ""
     return Workload(f"psi-Hessian {tag}grid {n}x{n} -> ~{target_elements:.3g} triangles", xy, tri,
                     m, Params(seed=seed))
@@ -213,8 +215,20 @@ def anisotropic_2m() -> Workload:
 
 
 def anisotropic_20m() -> Workload:
-    """1025 x 1025 grid (2,097,152 triangles), psi metric, ~20M triangles."""
-    return psi_workload(1025, 2.0e7, False, 3)
+    """1025 x 1025 grid (2,097,152 triangles), the same psi metric scaled to
+    ~20M triangles.  With sizes clamped at h >= 1e-3 at most
+    (4/sqrt 3)/h^2 ~ 2.3M unit triangles fit the unit square, so the size
+    bounds of the 2M case are scaled by sqrt(2M/20M) to keep the same field
+    reachable at ten times the element count."""
+    f = math.sqrt(2.0e6 / 2.0e7)
+    return psi_workload(1025, 2.0e7, False, 3, hmin=1e-3 * f, hmax=0.3 * f)
+
+
+def paper_550k() -> Workload:
+    """The paper's own benchmark size (Sec. 4): ~200 x 200 isotropic initial
+    grid (201 x 201 vertices here) adapted with a requirement of ~550k
+    elements; sizes in [1e-3, 0.3], jittered interior."""
+    return psi_workload(201, 5.5e5, True, 4)
 
 
 def batch_workloads(count: int = 512, seed: int = 5, tmin: float = 1e3, tmax: float = 2e5):

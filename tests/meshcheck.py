@@ -90,10 +90,20 @@ def unit_square_ok(xy, tris, tol=1e-12):
         return False, "inverted element"
     if abs(area.sum() - 1.0) > tol:
         return False, f"area {area.sum()!r}"
-    tl = [tuple(int(v) for v in t) for t in tris]
-    for a, b in boundary_edges(tl):
-        if not on_square_side(xy[a], xy[b]):
-            return False, f"boundary edge off the square {a}-{b}"
+    t = np.asarray(tris, dtype=np.int64)
+    nv = xy.shape[0]
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    key = e[:, 0] * nv + e[:, 1]
+    rkey = e[:, 1] * nv + e[:, 0]
+    bnd = e[~np.isin(key, rkey)]
+    pa, pb = xy[bnd[:, 0]], xy[bnd[:, 1]]
+    side = np.zeros(bnd.shape[0], bool)
+    for k in (0, 1):
+        for val in (0.0, 1.0):
+            side |= (pa[:, k] == val) & (pb[:, k] == val)
+    if not side.all():
+        i = int(np.nonzero(~side)[0][0])
+        return False, f"boundary edge off the square {bnd[i]}"
     corners = {(0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (1.0, 1.0)}
     have = {(float(x), float(y)) for x, y in xy}
     if not corners <= have:

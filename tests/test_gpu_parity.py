@@ -202,3 +202,49 @@ def test_rejects_invalid_input():
     with pytest.raises(pm.PmError) as e:
         g.adapt(pm.Params(L_low=2.0, L_up=1.0))
     assert e.value.status == 1
+
+
+# --- full-size workloads ------------------------------------------------------------
+
+@pytest.mark.slow
+def test_anisotropic_2m_full_adapt_bit_exact():
+    """The benchmark workload at full size (2.1M output triangles)."""
+    w = inputs.anisotropic_2m()
+    g, o = both(w, w.params.seed)
+    sg = g.adapt(gp(w.params.seed))
+    so = o.adapt(op(w.params.seed))
+    gm = g.get_mesh()
+    assert_same_mesh(gm, o.get_mesh(), "anisotropic 2M")
+    for k in STAT_KEYS:
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    assert gm[1].shape[0] > 2_000_000
+
+
+@pytest.mark.slow
+def test_anisotropic_20m_first_rounds_bit_exact_and_invariants():
+    """The large workload (1025^2 grid, ~20M output triangles): the first
+    rounds of every operator, started from the seeded input on both sides, are
+    compared slot by slot; the complete GPU adaptation is checked through
+    properties that hold at any size (conformity, orientation, area, boundary)."""
+    from tests import meshcheck as MC
+
+    w = inputs.anisotropic_20m()
+    seed = w.params.seed
+    g, o = both(w, seed)
+    for name, rounds in (("refine", 1), ("coarsen", 2), ("swap", 2), ("smooth", 2)):
+        sg = getattr(g, name)(gp(seed, max_rounds=rounds))
+        so = getattr(o, name)(op(seed, max_rounds=rounds))
+        for k in STAT_KEYS:
+            assert sg[k] == so[k], (name, k, sg[k], so[k])
+        assert_same_raw(g.get_raw(), o.get_raw(), name)
+    del o
+    g2 = pm.Mesh.from_host(w.xy, w.tri, device=0)
+    g2.set_metric(w.m)
+    st = g2.adapt(gp(seed))
+    xy, tri, m = g2.get_mesh()
+    assert tri.shape[0] > 15_000_000, tri.shape
+    ok, why = MC.fast_conformity(tri, xy.shape[0])
+    assert ok, why
+    ok, why = MC.unit_square_ok(xy, tri, tol=1e-9)
+    assert ok, why
+    assert st["collapses"] > 0 and st["flips"] > 0 and st["splits"] > 0
