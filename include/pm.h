@@ -196,6 +196,23 @@ uint64_t pm_kernel_launches(void);
 pm_status pm_profile_enable(const char* kernel_substring);
 pm_status pm_profile_read(double* total_ms, int64_t* launches);
 
+/* pm_quality_arrays_dev for callers that cannot allocate device memory
+ * during the call (a framework that has already reserved the device memory
+ * for its own allocator, a latency-bound loop, or a program that allows no
+ * allocation after start-up).  The paper has no counterpart: this is a
+ * service of this library.  Same arguments, results and stream behaviour as
+ * pm_quality_arrays_dev, but every temporary lives in one fixed array
+ * (about 9.6 MB) compiled into the library, which each GPU that loads the
+ * library keeps until the process exits; the call allocates and frees
+ * nothing.  Limits: ne <= 65536 elements and nv <= 65536 vertices, else
+ * PM_ERR_CAPACITY.  The first call on a device looks up the array's device
+ * address (with that device current), so make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race, so order them on one stream or synchronise in between. */
+pm_status pm_quality_arrays_noalloc_dev(const double* xy, const double* m, int32_t nv,
+                                        const int32_t* tri, int32_t ne, double* q_sum,
+                                        double* dxy, double* dm, void* stream);
+
 const char* pm_status_string(pm_status s);
 
 /* Message of the last error on the calling thread ("" if none). */

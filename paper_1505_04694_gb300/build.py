@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpm.so")
-SOURCES = ["pm_scan.cu", "pm_mesh.cu", "pm_ops.cu", "pm_quality.cu", "pm_capi.cu", "pm_prof.cu"]
+SOURCES = ["pm_scan.cu", "pm_mesh.cu", "pm_ops.cu", "pm_quality.cu", "pm_capi.cu", "pm_prof.cu", "pm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr",

@@ -29,7 +29,7 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_smooth", "pm_adapt", "pm_opt_smooth", "pm_adapt_batch", "pm_get_mesh",
            "pm_get_mesh_dev", "pm_get_raw", "pm_adjacency", "pm_quality",
            "pm_quality_arrays_dev", "pm_status_string", "pm_last_error", "pm_kernel_launches",
-           "pm_profile_enable", "pm_profile_read"]
+           "pm_profile_enable", "pm_profile_read", "pm_quality_arrays_noalloc_dev"]
 
 
 class PmParams(C.Structure):
@@ -84,6 +84,7 @@ def _load():
         "pm_adjacency": [vp, C.c_int32, ip, ip, ip, ip, C.c_int32],
         "pm_quality": [vp, dp, dp, dp],
         "pm_quality_arrays_dev": [vp, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, vp],
+        "pm_quality_arrays_noalloc_dev": [vp, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -344,3 +345,14 @@ def profile_read():
     n = C.c_int64()
     _check(lib.pm_profile_read(C.byref(ms), C.byref(n)), "pm_profile_read")
     return float(ms.value), int(n.value)
+
+
+def quality_arrays_noalloc_dev(xy, m, tri, qsum, dxy=None, dm=None, stream=0):
+    """pm_quality_arrays_noalloc_dev: as quality_arrays_dev, allocating nothing
+    (at most 65536 elements and 65536 vertices)."""
+    _check(lib.pm_quality_arrays_noalloc_dev(
+        C.c_void_p(xy.data_ptr()), C.c_void_p(m.data_ptr()), xy.shape[0],
+        C.c_void_p(tri.data_ptr()), tri.shape[0], C.c_void_p(qsum.data_ptr()),
+        C.c_void_p(dxy.data_ptr()) if dxy is not None else None,
+        C.c_void_p(dm.data_ptr()) if dm is not None else None, C.c_void_p(stream)),
+        "pm_quality_arrays_noalloc_dev")
