@@ -542,11 +542,15 @@ bool interpolate_in_ball(const OMesh& m, int v, double X, double Y, Move& mv) {
     int ids[3] = {t[0], t[1], t[2]};
     VD d[3] = {m.vd(t[0]), m.vd(t[1]), m.vd(t[2])};
     canon(ids, d);
+    // X lies in the closed element when all three sub-triangles (X replacing
+    // one vertex) are counter-clockwise or flat; its barycentric
+    // coordinates are then the sub-triangle orientations over the element's
     double o = orient3(d[0], d[1], d[2]);
-    double l0 = orient3(px, d[1], d[2]) / o;
-    double l1 = orient3(d[0], px, d[2]) / o;
-    double l2 = orient3(d[0], d[1], px) / o;
-    if (l0 >= 0.0 && l1 >= 0.0 && l2 >= 0.0) {
+    double s0 = orient3(px, d[1], d[2]);
+    double s1 = orient3(d[0], px, d[2]);
+    double s2 = orient3(d[0], d[1], px);
+    if (s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0) {
+      double l0 = s0 / o, l1 = s1 / o, l2 = s2 / o;
       mv.x = X;
       mv.y = Y;
       mv.m00 = (l0 * d[0].m00 + l1 * d[1].m00) + l2 * d[2].m00;

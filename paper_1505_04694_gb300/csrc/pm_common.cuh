@@ -45,6 +45,8 @@ struct Store {
   int W;          // row capacity of NN and NE
   int vslots;     // total vertex slots (sum of vcap)
   int eslots;     // total element slots
+  int vused;      // every slot in use lies below these bounds
+  int eused;
   double2* xy;
   double4* M;     // (m00, m01, m11, 0)
   uint8_t* vflag;

@@ -87,6 +87,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
                       int W);
 void set_free(MeshSet& m);
 cudaError_t upload_tab(MeshSet& m);
+void set_used(MeshSet& m);
 cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap, int W);
 int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev);
 int renumber(MeshSet& m);

@@ -38,7 +38,7 @@ __device__ __forceinline__ bool eslot_used(const Store& S, int slot, int& mi) {
 // ---- relayout (growth) ------------------------------------------------------
 
 __global__ void k_relayout_v(Store A, Store B) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!vslot_used(A, s, mi)) continue;
     int ns = B.tab.vbase[mi] + (s - A.tab.vbase[mi]);
@@ -62,7 +62,7 @@ __global__ void k_relayout_v(Store A, Store B) {
 }
 
 __global__ void k_relayout_e(Store A, Store B) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.eused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!eslot_used(A, s, mi)) continue;
     int ns = B.tab.ebase[mi] + (s - A.tab.ebase[mi]);
@@ -74,13 +74,13 @@ __global__ void k_relayout_e(Store A, Store B) {
 // ---- adjacency build ----------------------------------------------------------
 
 __global__ void k_zero_nelen(Store S) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     S.NElen[s] = 0;
   }
 }
 
 __global__ void k_fill_ne(Store S, DevStatus* st) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!eslot_used(S, s, mi)) continue;
     int4 e = S.EN[s];
@@ -103,7 +103,7 @@ __global__ void k_fill_ne(Store S, DevStatus* st) {
 // flag (a vertex is on the boundary when it has one more neighbour than
 // incident elements).
 __global__ void k_finish_rows(Store S, int derive, DevStatus* st) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!vslot_used(S, s, mi)) continue;
     uint8_t f = S.vflag[s];
@@ -180,7 +180,7 @@ __device__ __forceinline__ int edge_elements(const Store& S, int slot, int eb, i
 // Corners: boundary vertices whose two boundary neighbours are not collinear
 // with them (or the caller's flags).
 __global__ void k_corners(Store S, const uint8_t* corner) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!vslot_used(S, s, mi)) continue;
     uint8_t f = S.vflag[s];
@@ -211,7 +211,7 @@ __global__ void k_corners(Store S, const uint8_t* corner) {
 
 // Ids in range, distinct, and every element counter-clockwise (canonical).
 __global__ void k_validate_elems(Store S, DevStatus* st) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!eslot_used(S, s, mi)) continue;
     int4 e = S.EN[s];
@@ -230,7 +230,7 @@ __global__ void k_validate_elems(Store S, DevStatus* st) {
 
 // Quality of every live element into the cache.
 __global__ void k_qcache_all(Store S) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!eslot_used(S, s, mi)) continue;
     int4 e = S.EN[s];
@@ -244,14 +244,14 @@ __global__ void k_qcache_all(Store S) {
 // ---- renumbering -----------------------------------------------------------
 
 __global__ void k_flags_v(Store S, int* cnt) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     int mi;
     cnt[s] = (vslot_used(S, s, mi) && (S.vflag[s] & VF_ALIVE)) ? 1 : 0;
   }
 }
 
 __global__ void k_flags_e(Store S, int* cnt) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
     int mi;
     cnt[s] = (eslot_used(S, s, mi) && S.EN[s].w) ? 1 : 0;
   }
@@ -267,7 +267,7 @@ __global__ void k_mesh_totals(Store S, const int* vscan, const int* escan, int* 
 }
 
 __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!vslot_used(A, s, mi)) continue;
     if (!(A.vflag[s] & VF_ALIVE)) continue;
@@ -295,7 +295,7 @@ __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) 
 }
 
 __global__ void k_renum_e(Store A, Store B, const int* vscan, const int* escan) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.eused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!eslot_used(A, s, mi)) continue;
     int4 e = A.EN[s];
@@ -354,8 +354,18 @@ __global__ void k_out_e(Store S, int mesh, const int* vscan, const int* escan, i
 
 // ---------------------------------------------------------------------------
 
+// Bounds below which every used slot lies (from the host mirror).
+void set_used(MeshSet& m) {
+  int last = m.nmesh - 1;
+  m.S.vused = m.vbase[last] + m.nv[last];
+  m.S.eused = m.ebase[last] + m.ne[last];
+  m.B.vused = m.S.vused;
+  m.B.eused = m.S.eused;
+}
+
 cudaError_t upload_tab(MeshSet& m) {
   int n = m.nmesh;
+  set_used(m);
   std::vector<int> ints(6 * n);
   for (int i = 0; i < n; ++i) {
     ints[i] = m.vbase[i];
@@ -404,6 +414,7 @@ cudaError_t refresh_sizes(MeshSet& m) {
     m.nv[i] = t[i];
     m.ne[i] = t[m.nmesh + i];
   }
+  set_used(m);
   return e;
 }
 
@@ -558,8 +569,8 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
                   m.stream);
   cudaMemcpyAsync(n2.S.tab.ops, m.S.tab.ops, 2 * nm * sizeof(unsigned long long),
                   cudaMemcpyDeviceToDevice, m.stream);
-  PM_LAUNCH(k_relayout_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, n2.S);
-  PM_LAUNCH(k_relayout_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, n2.S);
+  PM_LAUNCH(k_relayout_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, n2.S);
+  PM_LAUNCH(k_relayout_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, n2.S);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   set_free(m);
@@ -617,9 +628,9 @@ int sync_status(MeshSet& m) {
 int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) {
   for (;;) {
     cudaMemsetAsync(&m.st->overflow, 0, 2 * sizeof(int), m.stream);
-    PM_LAUNCH(k_zero_nelen, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S);
-    PM_LAUNCH(k_fill_ne, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, m.st);
-    PM_LAUNCH(k_finish_rows, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, derive_flags ? 1 : 0,
+    PM_LAUNCH(k_zero_nelen, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S);
+    PM_LAUNCH(k_fill_ne, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.st);
+    PM_LAUNCH(k_finish_rows, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, derive_flags ? 1 : 0,
                                                                   m.st);
     int err = sync_status(m);
     if (err) return err;
@@ -638,19 +649,19 @@ int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) 
     }
   }
   if (derive_flags) {
-    PM_LAUNCH(k_corners, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, corner_dev);
+    PM_LAUNCH(k_corners, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, corner_dev);
     return sync_status(m);
   }
   return PM_OK;
 }
 
 int refresh_quality(MeshSet& m) {
-  PM_LAUNCH(k_qcache_all, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S);
+  PM_LAUNCH(k_qcache_all, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S);
   return sync_status(m);
 }
 
 int validate_mesh(MeshSet& m) {
-  PM_LAUNCH(k_validate_elems, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, m.st);
+  PM_LAUNCH(k_validate_elems, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.st);
   return sync_status(m);
 }
 
@@ -658,16 +669,16 @@ int validate_mesh(MeshSet& m) {
 // slot order), adjacency remapped (rows stay sorted: the map is monotone).
 int renumber(MeshSet& m) {
   Work& w = m.w;
-  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, w.vcnt);
-  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, w.ecnt);
-  scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
-  scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
+  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, w.vcnt);
+  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, w.ecnt);
+  scan_exclusive(w.vcnt, w.vscan, m.S.vused, m.scan, m.st, m.stream);
+  scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
   PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
   // the second buffer's flags must read "dead" beyond the new counts
   cudaMemsetAsync(m.B.vflag, 0, m.S.vslots, m.stream);
-  PM_LAUNCH(k_renum_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
-  PM_LAUNCH(k_renum_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
+  PM_LAUNCH(k_renum_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
+  PM_LAUNCH(k_renum_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
   cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   int err = sync_status(m);
   if (err) return err;
@@ -689,6 +700,7 @@ int renumber(MeshSet& m) {
   std::swap(m.S.evs, m.B.evs);
   std::swap(m.S.evm, m.B.evm);
   std::swap(m.S.evr, m.B.evr);
+  set_used(m);
   std::vector<int> t(2 * m.nmesh);
   for (int i = 0; i < m.nmesh; ++i) {
     t[i] = m.nv[i];
@@ -703,10 +715,10 @@ int renumber(MeshSet& m) {
 int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
                 int* ne_out) {
   Work& w = m.w;
-  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, m.S, w.vcnt);
-  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, m.S, w.ecnt);
-  scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
-  scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
+  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, w.vcnt);
+  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, w.ecnt);
+  scan_exclusive(w.vcnt, w.vscan, m.S.vused, m.scan, m.st, m.stream);
+  scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
   PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
   if (xy || mt)

@@ -114,10 +114,10 @@ __device__ __forceinline__ bool unchanged(const Store& S, int v, int vb, int et,
 // and whose inputs are unchanged since are left out: they would find
 // nothing again.
 __global__ void k_init_list(Store S, int mode, int* list, int* count, const int* ev, int lo) {
-  for (int i0 = blockIdx.x * blockDim.x; i0 < S.vslots; i0 += gridDim.x * blockDim.x) {
+  for (int i0 = blockIdx.x * blockDim.x; i0 < S.vused; i0 += gridDim.x * blockDim.x) {
     int s = i0 + threadIdx.x;
     bool take = false;
-    if (s < S.vslots) {
+    if (s < S.vused) {
       int mi = mesh_of_vslot(S, s);
       int vb = S.tab.vbase[mi];
       if (s - vb < S.tab.nv[mi] && S.tab.active[mi]) {
@@ -682,101 +682,6 @@ __device__ __forceinline__ double ball_min_quality(const Store& S, MeshCtx c, co
   return qmin;
 }
 
-// Locate (X, Y) in v's ball (v at its current place) and interpolate the
-// metric barycentrically there.
-__device__ bool interpolate_in_ball(const Store& S, MeshCtx c, const int* ne, int nel, double X,
-                                    double Y, double4& Mout) {
-  VD px{X, Y, 0.0, 0.0, 0.0};
-  for (int k = 0; k < nel; ++k) {
-    int4 e = S.EN[c.eb + ne[k]];
-    int i0 = e.x, i1 = e.y, i2 = e.z;
-    VD a = load_vd(S, c.vb + i0), b = load_vd(S, c.vb + i1), d = load_vd(S, c.vb + i2);
-    canon(i0, i1, i2, a, b, d);
-    double o = orient3(a, b, d);
-    double l0 = orient3(px, b, d) / o;
-    double l1 = orient3(a, px, d) / o;
-    double l2 = orient3(a, b, px) / o;
-    if (l0 >= 0.0 && l1 >= 0.0 && l2 >= 0.0) {
-      Mout.x = (l0 * a.m00 + l1 * b.m00) + l2 * d.m00;
-      Mout.y = (l0 * a.m01 + l1 * b.m01) + l2 * d.m01;
-      Mout.z = (l0 * a.m11 + l1 * b.m11) + l2 * d.m11;
-      Mout.w = 0.0;
-      return true;
-    }
-  }
-  return false;
-}
-
-// Ball with v moved to (X, Y, M): all counter-clockwise?  min and sum of q.
-// With `floor` set, gives up (false) as soon as a quality is at or below
-// *floor (strict) or below it (non-strict): the caller would reject the move.
-__device__ bool ball_after_move(const Store& S, MeshCtx c, int lv, const int* ne, int nel,
-                                double X, double Y, double4 Mv, double& qmin, double& qsum,
-                                const double* floor = nullptr, bool strict = true) {
-  VD nvd{X, Y, Mv.x, Mv.y, Mv.z};
-  qmin = 0.0;
-  qsum = 0.0;
-  for (int k = 0; k < nel; ++k) {
-    int4 e = S.EN[c.eb + ne[k]];
-    VD a = (e.x == lv) ? nvd : load_vd(S, c.vb + e.x);
-    VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
-    VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
-    if (!(orient_c(e.x, e.y, e.z, a, b, d) > 0.0)) return false;
-  }
-  for (int k = 0; k < nel; ++k) {
-    int4 e = S.EN[c.eb + ne[k]];
-    VD a = (e.x == lv) ? nvd : load_vd(S, c.vb + e.x);
-    VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
-    VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
-    double q = quality_c(e.x, e.y, e.z, a, b, d);
-    if (floor && (strict ? !(q > *floor) : (q < *floor))) return false;
-    if (k == 0 || q < qmin) qmin = q;
-    qsum = qsum + q;
-  }
-  return true;
-}
-
-// Quality-constrained Laplacian move of v: metric-weighted neighbour mean,
-// metric interpolated at the target, kept when the ball stays valid and its
-// minimum quality strictly increases.
-__device__ bool smooth_eval(const Store& S, int v, MeshCtx c, double2& X, double4& Mv) {
-  uint8_t f = S.vflag[v];
-  if (!(f & VF_ALIVE) || (f & VF_BND)) return false;
-  const int* ne = ne_row(S, v);
-  int nel = S.NElen[v];
-  double qold = ball_min_quality(S, c, ne, nel, nullptr);
-  if (!(qold < S.tab.q_thresh[c.mi])) return false;
-  const int* nn = nn_row(S, v);
-  int nnl = S.NNlen[v];
-  double4 mv = S.M[v];
-  double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
-  for (int k = 0; k < nnl; ++k) {
-    int js = c.vb + nn[k];
-    double2 pj = S.xy[js];
-    double4 mj = S.M[js];
-    double w00 = 0.5 * (mv.x + mj.x);
-    double w01 = 0.5 * (mv.y + mj.y);
-    double w11 = 0.5 * (mv.z + mj.z);
-    a00 = a00 + w00;
-    a01 = a01 + w01;
-    a11 = a11 + w11;
-    b0 = b0 + (w00 * pj.x + w01 * pj.y);
-    b1 = b1 + (w01 * pj.x + w11 * pj.y);
-  }
-  double det = a00 * a11 - a01 * a01;
-  if (!(det > 0.0)) return false;
-  double x = (a11 * b0 - a01 * b1) / det;
-  double y = (a00 * b1 - a01 * b0) / det;
-  double4 Mn;
-  if (!interpolate_in_ball(S, c, ne, nel, x, y, Mn)) return false;
-  double qmin, qsum;
-  if (!ball_after_move(S, c, v - c.vb, ne, nel, x, y, Mn, qmin, qsum, &qold, true)) return false;
-  if (!(qmin > qold)) return false;
-  X = make_double2(x, y);
-  Mv = Mn;
-  return true;
-}
-
 // Smoothing evaluation in two passes.  Pass 1 (per pending vertex): reuse an
 // unchanged earlier result, drop vertices whose ball is already good enough
 // (cached qualities), list the rest for the full move evaluation.
@@ -811,39 +716,225 @@ __global__ void k_smooth_scan(Store S, const int* D, const int* nDp, double4* mv
   }
 }
 
-// Pass 2 (per listed vertex, dense FP64): the full quality-constrained move.
+// ---- tile-parallel evaluation: 8 lanes per vertex, one ball element each ----
+// Sums keep the ascending order of the definition (every lane accumulates the
+// lanes' terms in order through shuffles); minima and all-of votes do not
+// depend on order.  All lanes of a tile end with the same result.
+
+constexpr int TW = 8;
+
+struct Tile {
+  int tl;          // lane within the tile
+  unsigned mask;   // the tile's lanes in the warp
+  int shift;       // bit offset of the tile in a warp ballot
+};
+
+__device__ __forceinline__ Tile tile_of() {
+  int lane = threadIdx.x & 31;
+  Tile t;
+  t.tl = lane & (TW - 1);
+  t.shift = lane & ~(TW - 1);
+  t.mask = 0xFFu << t.shift;
+  return t;
+}
+
+__device__ __forceinline__ double tshfl(const Tile& t, double x, int src) {
+  return __shfl_sync(t.mask, x, src, TW);
+}
+
+__device__ __forceinline__ double tmin(const Tile& t, double x) {
+#pragma unroll
+  for (int o = TW / 2; o > 0; o >>= 1) {
+    double y = __shfl_xor_sync(t.mask, x, o, TW);
+    x = (y < x) ? y : x;
+  }
+  return x;
+}
+
+__device__ __forceinline__ bool tall(const Tile& t, bool p) {
+  return ((__ballot_sync(t.mask, !p) >> t.shift) & 0xFFu) == 0u;
+}
+
+// Minimum cached quality of v's ball (and, if asked, its sum in ascending
+// element order).
+__device__ double tile_ball_quality(const Tile& t, const Store& S, MeshCtx c, const int* ne,
+                                    int nel, double* qsum) {
+  double qmin = 1e300, sum = 0.0;
+  for (int base = 0; base < nel; base += TW) {
+    int k = base + t.tl;
+    double q = (k < nel) ? S.qK[c.eb + ne[k]] : 1e300;
+    qmin = (q < qmin) ? q : qmin;
+    if (qsum) {
+      int cnt = min(TW, nel - base);
+      for (int j = 0; j < cnt; ++j) sum = sum + tshfl(t, q, j);
+    }
+  }
+  if (qsum) *qsum = sum;
+  return tmin(t, qmin);
+}
+
+// First ball element (ascending id) that contains X, with v at its current
+// place: its barycentric metric interpolation.
+__device__ bool tile_interpolate(const Tile& t, const Store& S, MeshCtx c, const int* ne, int nel,
+                                 double X, double Y, double4& Mout) {
+  VD px{X, Y, 0.0, 0.0, 0.0};
+  for (int base = 0; base < nel; base += TW) {
+    int k = base + t.tl;
+    bool inside = false;
+    VD a{}, b{}, d{};
+    double o = 1.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (k < nel) {
+      int4 e = S.EN[c.eb + ne[k]];
+      int i0 = e.x, i1 = e.y, i2 = e.z;
+      a = load_vd(S, c.vb + i0);
+      b = load_vd(S, c.vb + i1);
+      d = load_vd(S, c.vb + i2);
+      canon(i0, i1, i2, a, b, d);
+      o = orient3(a, b, d);
+      s0 = orient3(px, b, d);
+      s1 = orient3(a, px, d);
+      s2 = orient3(a, b, px);
+      inside = s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0;
+    }
+    unsigned bal = (__ballot_sync(t.mask, inside) >> t.shift) & 0xFFu;
+    if (bal) {
+      int src = __ffs(bal) - 1;
+      double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+      if (t.tl == src) {
+        double l0 = s0 / o, l1 = s1 / o, l2 = s2 / o;
+        m0 = (l0 * a.m00 + l1 * b.m00) + l2 * d.m00;
+        m1 = (l0 * a.m01 + l1 * b.m01) + l2 * d.m01;
+        m2 = (l0 * a.m11 + l1 * b.m11) + l2 * d.m11;
+      }
+      Mout = make_double4(tshfl(t, m0, src), tshfl(t, m1, src), tshfl(t, m2, src), 0.0);
+      return true;
+    }
+  }
+  return false;
+}
+
+// Ball with v moved to (X, Y, Mv): every element counter-clockwise, and every
+// quality above *floor (strict) or at least *floor (non-strict).  Writes each
+// element's new quality to qout[k] and returns the ascending-order sum.
+__device__ bool tile_ball_after_move(const Tile& t, const Store& S, MeshCtx c, int lv,
+                                     const int* ne, int nel, double X, double Y, double4 Mv,
+                                     double floor, bool strict, double* qout, double* qsum) {
+  VD nvd{X, Y, Mv.x, Mv.y, Mv.z};
+  bool ok = true;
+  double sum = 0.0;
+  for (int base = 0; base < nel; base += TW) {
+    int k = base + t.tl;
+    double q = 0.0;
+    if (k < nel) {
+      int4 e = S.EN[c.eb + ne[k]];
+      VD a = (e.x == lv) ? nvd : load_vd(S, c.vb + e.x);
+      VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
+      VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
+      if (orient_c(e.x, e.y, e.z, a, b, d) > 0.0) {
+        q = quality_c(e.x, e.y, e.z, a, b, d);
+        if (strict ? !(q > floor) : (q < floor)) ok = false;
+        if (qout) qout[k] = q;
+      } else {
+        ok = false;
+      }
+    }
+    if (qsum) {
+      int cnt = min(TW, nel - base);
+      for (int j = 0; j < cnt; ++j) sum = sum + tshfl(t, q, j);
+    }
+  }
+  if (qsum) *qsum = sum;
+  return tall(t, ok);
+}
+
+// Quality-constrained Laplacian move of v: metric-weighted neighbour mean,
+// metric interpolated at the target, kept when the ball stays valid and its
+// minimum quality strictly increases.
+__device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c, double2& Xo,
+                                 double4& Mo, double* qout) {
+  uint8_t f = S.vflag[v];
+  if (!(f & VF_ALIVE) || (f & VF_BND)) return false;
+  const int* ne = ne_row(S, v);
+  int nel = S.NElen[v];
+  double qold = tile_ball_quality(t, S, c, ne, nel, nullptr);
+  if (!(qold < S.tab.q_thresh[c.mi])) return false;
+  const int* nn = nn_row(S, v);
+  int nnl = S.NNlen[v];
+  double4 mv = S.M[v];
+  double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
+  for (int base = 0; base < nnl; base += TW) {
+    int k = base + t.tl;
+    double w00 = 0.0, w01 = 0.0, w11 = 0.0, t0 = 0.0, t1 = 0.0;
+    if (k < nnl) {
+      int js = c.vb + nn[k];
+      double2 pj = S.xy[js];
+      double4 mj = S.M[js];
+      w00 = 0.5 * (mv.x + mj.x);
+      w01 = 0.5 * (mv.y + mj.y);
+      w11 = 0.5 * (mv.z + mj.z);
+      t0 = w00 * pj.x + w01 * pj.y;
+      t1 = w01 * pj.x + w11 * pj.y;
+    }
+    int cnt = min(TW, nnl - base);
+    for (int j = 0; j < cnt; ++j) {
+      a00 = a00 + tshfl(t, w00, j);
+      a01 = a01 + tshfl(t, w01, j);
+      a11 = a11 + tshfl(t, w11, j);
+      b0 = b0 + tshfl(t, t0, j);
+      b1 = b1 + tshfl(t, t1, j);
+    }
+  }
+  double det = a00 * a11 - a01 * a01;
+  if (!(det > 0.0)) return false;
+  double x = (a11 * b0 - a01 * b1) / det;
+  double y = (a00 * b1 - a01 * b0) / det;
+  double4 Mn;
+  if (!tile_interpolate(t, S, c, ne, nel, x, y, Mn)) return false;
+  if (!tile_ball_after_move(t, S, c, v - c.vb, ne, nel, x, y, Mn, qold, true, qout, nullptr))
+    return false;
+  Xo = make_double2(x, y);
+  Mo = Mn;
+  return true;
+}
+
+// Pass 2 (one 8-lane tile per listed vertex): the full quality-constrained move.
 __global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mvxy, double4* mvM,
-                              int* C, int* nC, int* cmark, int tag) {
+                              double* qball, int* C, int* nC, int* cmark, int tag) {
   const int n = *nEp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  const Tile t = tile_of();
+  const int tiles_per_block = blockDim.x / TW;
+  for (int j0 = blockIdx.x * tiles_per_block; j0 < n; j0 += gridDim.x * tiles_per_block) {
+    int j = j0 + threadIdx.x / TW;
     int v = 0;
     bool cand = false;
-    if (i < n) {
-      v = E[i];
+    if (j < n) {
+      v = E[j];
       MeshCtx c = ctx_of(S, v);
       double2 X;
       double4 Mv;
-      cand = smooth_eval(S, v, c, X, Mv);
-      if (cand) {
-        Mv.w = 1.0;  // marks a stored move
-        mvxy[v] = X;
-        mvM[v] = Mv;
-        cmark[v] = tag;
-        S.tab.had[c.mi] = 1;
-      } else {
-        mvM[v].w = 0.0;
+      // the new ball qualities of an accepted move are kept for the apply
+      cand = tile_smooth_eval(t, S, v, c, X, Mv, qball + (size_t)v * S.W);
+      if (t.tl == 0) {
+        if (cand) {
+          Mv.w = 1.0;  // marks a stored move
+          mvxy[v] = X;
+          mvM[v] = Mv;
+          cmark[v] = tag;
+          S.tab.had[c.mi] = 1;
+        } else {
+          mvM[v].w = 0.0;
+        }
       }
     }
-    warp_append(cand, v, C, nC);
+    warp_append(cand && t.tl == 0, v, C, nC);
   }
 }
 
 // Move the members of S; live interior neighbours become pending for the next
 // sweep (stamp pmark with the sweep tag).
 __global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const double2* mvxy,
-                               const double4* mvM, int* P, int* nP, int* pmark, int ptag,
-                               int stamp) {
+                               const double4* mvM, const double* qball, int* P, int* nP,
+                               int* pmark, int ptag, int stamp) {
   advance_rounds(S);
   const int n = *nSp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
@@ -861,7 +952,9 @@ __global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const dou
       mv.w = 0.0;
       S.M[v] = mv;
       S.touch[v] = stamp;
-      refresh_ball_quality(S, c.vb, c.eb, ne_row(S, v), S.NElen[v]);
+      const int* ne = ne_row(S, v);
+      int nel = S.NElen[v];
+      for (int k = 0; k < nel; ++k) S.qK[c.eb + ne[k]] = qball[(size_t)v * S.W + k];
       nn = nn_row(S, v);
       nnl = S.NNlen[v];
     }
@@ -883,47 +976,59 @@ __global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const dou
 // Optimisation-based smoothing of one member of S (gradient ascent of the
 // ball's quality sum in v's coordinates, metric fixed; step 0.1 * shortest
 // incident edge / |g|, halved up to five times; kept when every element stays
-// counter-clockwise, the minimum quality does not drop and the sum rises).
-__device__ bool opt_eval(const Store& S, int v, MeshCtx c, double2& Xo, double4& Mo) {
+// counter-clockwise, the minimum quality does not drop and the sum rises),
+// evaluated by an 8-lane tile.
+__device__ bool tile_opt_eval(const Tile& t, const Store& S, int v, MeshCtx c, double2& Xo,
+                              double4& Mo, double* qout) {
   uint8_t f = S.vflag[v];
   if (!(f & VF_ALIVE) || (f & VF_BND)) return false;
   int lv = v - c.vb;
   const int* ne = ne_row(S, v);
   int nel = S.NElen[v];
   double gx = 0.0, gy = 0.0;
-  for (int k = 0; k < nel; ++k) {
-    int4 e = S.EN[c.eb + ne[k]];
-    double g[3][5];
-    quality_grad_c(e.x, e.y, e.z, load_vd(S, c.vb + e.x), load_vd(S, c.vb + e.y),
-                   load_vd(S, c.vb + e.z), g);
-    int i = (e.x == lv) ? 0 : (e.y == lv) ? 1 : 2;
-    gx = gx + g[i][0];
-    gy = gy + g[i][1];
+  for (int base = 0; base < nel; base += TW) {
+    int k = base + t.tl;
+    double gxk = 0.0, gyk = 0.0;
+    if (k < nel) {
+      int4 e = S.EN[c.eb + ne[k]];
+      double g[3][5];
+      quality_grad_c(e.x, e.y, e.z, load_vd(S, c.vb + e.x), load_vd(S, c.vb + e.y),
+                     load_vd(S, c.vb + e.z), g);
+      int i = (e.x == lv) ? 0 : (e.y == lv) ? 1 : 2;
+      gxk = g[i][0];
+      gyk = g[i][1];
+    }
+    int cnt = min(TW, nel - base);
+    for (int j = 0; j < cnt; ++j) {
+      gx = gx + tshfl(t, gxk, j);
+      gy = gy + tshfl(t, gyk, j);
+    }
   }
   double gn = sqrt(gx * gx + gy * gy);
   if (!(gn > 0.0)) return false;
   const int* nn = nn_row(S, v);
   int nnl = S.NNlen[v];
   double2 pv = S.xy[v];
-  double lmin = 0.0;
-  for (int k = 0; k < nnl; ++k) {
+  double lmin = 1e300;
+  for (int k = t.tl; k < nnl; k += TW) {
     double2 pj = S.xy[c.vb + nn[k]];
     double dx = pj.x - pv.x;
     double dy = pj.y - pv.y;
     double l = sqrt(dx * dx + dy * dy);
-    if (k == 0 || l < lmin) lmin = l;
+    lmin = (l < lmin) ? l : lmin;
   }
+  lmin = tmin(t, lmin);
   double qsum_old;
-  double qmin_old = ball_min_quality(S, c, ne, nel, &qsum_old);
+  double qmin_old = tile_ball_quality(t, S, c, ne, nel, &qsum_old);
   double alpha = (0.1 * lmin) / gn;
   for (int k = 0; k < 6; ++k) {
     double X = pv.x + alpha * gx;
     double Y = pv.y + alpha * gy;
     double4 Mn;
-    if (interpolate_in_ball(S, c, ne, nel, X, Y, Mn)) {
-      double qmin, qsum;
-      if (ball_after_move(S, c, lv, ne, nel, X, Y, Mn, qmin, qsum, &qmin_old, false) &&
-          qmin >= qmin_old && qsum > qsum_old) {
+    if (tile_interpolate(t, S, c, ne, nel, X, Y, Mn)) {
+      double qsum;
+      if (tile_ball_after_move(t, S, c, lv, ne, nel, X, Y, Mn, qmin_old, false, qout, &qsum) &&
+          qsum > qsum_old) {
         Xo = make_double2(X, Y);
         Mo = Mn;
         return true;
@@ -934,30 +1039,36 @@ __device__ bool opt_eval(const Store& S, int v, MeshCtx c, double2& Xo, double4&
   return false;
 }
 
-// Evaluate and apply in one pass: members of S are pairwise non-adjacent, so
-// no member reads a vertex another member moves.
-__global__ void k_opt_apply(Store S, const int* Sl, const int* nSp, int stamp) {
+// Evaluate and apply in one pass (one tile per member of S): members are
+// pairwise non-adjacent, so no member reads a vertex another member moves.
+__global__ void k_opt_apply(Store S, const int* Sl, const int* nSp, double* qball, int stamp) {
   advance_rounds(S);
   const int n = *nSp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  const Tile t = tile_of();
+  const int tiles_per_block = blockDim.x / TW;
+  for (int j0 = blockIdx.x * tiles_per_block; j0 < n; j0 += gridDim.x * tiles_per_block) {
+    int j = j0 + threadIdx.x / TW;
     bool moved = false;
     int mi = 0;
-    if (i < n) {
-      int v = Sl[i];
+    if (j < n) {
+      int v = Sl[j];
       MeshCtx c = ctx_of(S, v);
       mi = c.mi;
+      double* qb = qball + (size_t)v * S.W;
       double2 X;
       double4 Mv;
-      moved = opt_eval(S, v, c, X, Mv);
-      if (moved) {
+      moved = tile_opt_eval(t, S, v, c, X, Mv, qb);
+      __syncwarp(t.mask);
+      if (moved && t.tl == 0) {
         S.xy[v] = X;
         S.M[v] = Mv;
         S.touch[v] = stamp;
-        refresh_ball_quality(S, c.vb, c.eb, ne_row(S, v), S.NElen[v]);
+        const int* ne = ne_row(S, v);
+        int nel = S.NElen[v];
+        for (int k = 0; k < nel; ++k) S.qK[c.eb + ne[k]] = qb[k];
       }
     }
-    count_op(S, moved, mi);
+    count_op(S, moved && t.tl == 0, mi);
   }
 }
 
@@ -978,7 +1089,7 @@ __global__ void k_stamp_list(Store S, const int* L, const int* nLp, int* cmark, 
 // one unchanged since the end of an earlier complete pass has none.
 __global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int tag, int pass0,
                               int lo) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     int mi = mesh_of_vslot(S, s);
     int vb = S.tab.vbase[mi];
     unsigned long long m = 0;
@@ -1039,7 +1150,7 @@ __device__ __forceinline__ int mid_id(const Store& S, int vb, int nv, const int*
 
 __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long long* mask,
                                   int stamp) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     unsigned long long m = mask[s];
     if (!m) continue;
     int mi = mesh_of_vslot(S, s);
@@ -1071,7 +1182,7 @@ __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long
 // Children per live element (1..4) and the midpoint ids of its edges.
 __global__ void k_refine_count(Store S, const int* vscan, const unsigned long long* mask,
                                int* ecnt, int4* emid) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
     int mi = mesh_of_eslot(S, s);
     int eb = S.tab.ebase[mi];
     int extra = 0;
@@ -1095,7 +1206,7 @@ __global__ void k_refine_count(Store S, const int* vscan, const unsigned long lo
 // splits -> four children.  The first child keeps the parent's slot, the rest
 // take ne + scan(extra children) in parent order.
 __global__ void k_refine_split(Store S, const int* escan, const int4* emid, int stamp) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eslots; s += gridDim.x * blockDim.x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
     int mi = mesh_of_eslot(S, s);
     int eb = S.tab.ebase[mi];
     if (!(s - eb < S.tab.ne[mi]) || !S.tab.active[mi]) continue;
@@ -1207,7 +1318,7 @@ cudaError_t fetch_ops(MeshSet& m, std::vector<unsigned long long>& ops) {
 // nothing and whose inputs have not changed since.
 int op_coarsen(MeshSet& m, int max_rounds) {
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vslots);
+  const int gv = grid_for(m, m.S.vused);
   const int pass0 = m.tag;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evc,
@@ -1244,7 +1355,7 @@ int op_coarsen(MeshSet& m, int max_rounds) {
 // Rounds of flips until no dirty vertex has an improving flip.
 int op_swap(MeshSet& m, int max_rounds) {
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vslots);
+  const int gv = grid_for(m, m.S.vused);
   const int pass0 = m.tag;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evs,
@@ -1291,13 +1402,13 @@ int op_refine(MeshSet& m, int max_rounds) {
   int pass0 = m.tag;
   bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
-    const int gv = grid_for(m, m.S.vslots);
-    const int ge = grid_for(m, m.S.eslots);
+    const int gv = grid_for(m, m.S.vused);
+    const int ge = grid_for(m, m.S.eused);
     int tag = (m.tag += 2);
     if (m.lo_refine > pass0) pass0 = m.lo_refine;  // storage was regrown
     PM_LAUNCH(k_refine_mark, gv, BLOCK, 0, m.stream, m.S, w.vcnt, w.vmask, tag, pass0,
               m.lo_refine);
-    scan_exclusive(w.vcnt, w.vscan, m.S.vslots, m.scan, m.st, m.stream);
+    scan_exclusive(w.vcnt, w.vscan, m.S.vused, m.scan, m.st, m.stream);
     int* tot = w.counts + CN_NUM;
     std::vector<int> newv(m.nmesh);
     PM_LAUNCH(k_refine_newcount, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, tot);
@@ -1343,7 +1454,7 @@ int op_refine(MeshSet& m, int max_rounds) {
     PM_LAUNCH(k_refine_vtotals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan);
     PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, stamp);
     PM_LAUNCH(k_refine_count, ge, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid);
-    scan_exclusive(w.ecnt, w.escan, m.S.eslots, m.scan, m.st, m.stream);
+    scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
     PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid, stamp);
     PM_LAUNCH(k_refine_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan);
     cudaError_t e = refresh_sizes(m);
@@ -1358,7 +1469,7 @@ int op_refine(MeshSet& m, int max_rounds) {
 // Laplacian sweeps, each a sequence of rounds over the sweep's pending set.
 int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vslots);
+  const int gv = grid_for(m, m.S.vused);
   const int pass0 = m.tag;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0, nullptr, 0);
@@ -1376,12 +1487,12 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
       zero_counts(m, CN_E, 1);
       PM_LAUNCH(k_smooth_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.mvM, w.C,
                 w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E);
-      PM_LAUNCH(k_smooth_eval, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.mvxy, w.mvM,
-                w.C, w.counts + CN_C, w.cmark, tag);
+      PM_LAUNCH(k_smooth_eval, grid_for(m, (long long)m.S.vused * TW), BLOCK, 0, m.stream, m.S,
+                w.E, w.counts + CN_E, w.mvxy, w.mvM, w.gains, w.C, w.counts + CN_C, w.cmark, tag);
       PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark,
                 tag, w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
       PM_LAUNCH(k_smooth_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.mvxy,
-                w.mvM, w.P, w.counts + CN_P, w.pmark, ptag, tag + 1);
+                w.mvM, w.gains, w.P, w.counts + CN_P, w.pmark, ptag, tag + 1);
       RoundIO io = read_round(m);
       if (io.err) return io.err;
       if (io.nC == 0) break;
@@ -1401,7 +1512,7 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
 // Rounds of optimisation-based smoothing over all interior vertices.
 int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds) {
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vslots);
+  const int gv = grid_for(m, m.S.vused);
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.C, w.counts + CN_C, nullptr, 0);
   for (int it = 0; it < nrounds && (max_rounds == 0 || it < max_rounds); ++it) {
@@ -1410,7 +1521,8 @@ int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds) {
     PM_LAUNCH(k_stamp_list, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, tag);
     PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
               w.Sl, w.counts + CN_S, nullptr, nullptr, nullptr);
-    PM_LAUNCH(k_opt_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, tag + 1);
+    PM_LAUNCH(k_opt_apply, grid_for(m, (long long)m.S.vused * TW), BLOCK, 0, m.stream, m.S, w.Sl,
+              w.counts + CN_S, w.gains, tag + 1);
   }
   return sync_status(m);
 }
