@@ -115,6 +115,47 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+# The dominant kernel of a step and its roofline.  Smoothing evaluation is
+# bound by the FP64 pipe (DRAM under 2% in ncu), so its ceiling is the FP64
+# issue rate: ncu reports 304 FP64 results per cycle for the whole GPU
+# (sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained; 2 per SM
+# on 152 SMs) at the 2070 MHz maximum SM clock.  Work = FP64 operations
+# (+ - * / sqrt, one each) along the paths the kernel took, counted by the
+# kernel while profiled.
+ROOFLINE_KERNEL = "k_smooth_eval"
+FP64_RESULTS_PER_CYCLE = 304
+
+
+def roofline(kname, kms, klaunch, kwork, total_ms, peaks, how):
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = FP64_RESULTS_PER_CYCLE * mhz * 1e6 / 1e9  # G FP64 ops/s
+    out = {"kernel": kname, "bound": "alu", "unit": "GFLOP/s (FP64 ops)",
+           "peak": peak, "peak_source": f"derived: {FP64_RESULTS_PER_CYCLE} FP64 results/cycle x "
+                                        f"{mhz:.0f} MHz (sm_max_mhz {how})",
+           "achieved": None, "frac": None, "traffic": traffic_of(kname),
+           "kernel_ms_per_step_share": (kms / total_ms) if total_ms else None,
+           "launches": klaunch, "kernel_ms": kms, "fp64_ops": kwork}
+    if kms > 0 and kwork > 0:
+        ach = kwork / (kms / 1e3) / 1e9
+        out["achieved"] = ach
+        out["frac"] = ach / peak
+    return out
+
+
+def traffic_of(kname):
+    """DRAM bytes per launch of the kernel from the committed ncu summary
+    (profiles/traffic.txt: one "kernel bytes_per_launch" pair per line)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                parts = line.split("#", 1)[0].split()
+                if len(parts) >= 2 and parts[0] == kname:
+                    return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline_run(samples=1):
     """Oracle (sequential C++) on the bounded sample; returns elements/s etc."""
     from oracle import oracle as O
@@ -205,7 +246,7 @@ def main():
         step()
     barrier()
     launches0 = pm.kernel_launches()
-    kname = args.roofline_kernel or "k_swap_eval"
+    kname = args.roofline_kernel or ROOFLINE_KERNEL
     pm.profile_enable(kname)
     total_ms = 0.0
     tris = 0
@@ -222,7 +263,7 @@ def main():
             total_ms += e0.elapsed_time(e1)
     barrier()
     launches = pm.kernel_launches() - launches0
-    kms, klaunch = pm.profile_read()
+    kms, klaunch, kwork = pm.profile_read()
     pm.profile_enable(None)
     t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     n_local = torch.tensor([float(tris)], dtype=torch.float64, device=dev)
@@ -287,9 +328,7 @@ def main():
                        "buffers, wall clock per step"},
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / max(args.steps, 1),
-        "roofline": {"kernel": kname, "kernel_ms_total": kms, "kernel_launches": klaunch,
-                     "kernel_share_of_step_time": kms / total_ms if total_ms else None,
-                     "peak_source": how},
+        "roofline": roofline(kname, kms, klaunch, kwork, total_ms, peaks, how),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = cpu_baseline_run(1)

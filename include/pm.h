@@ -191,10 +191,12 @@ pm_status pm_quality_arrays_dev(const double* xy, const double* m, int32_t nv,
  * library kernel whose name contains it is bracketed by CUDA events on the
  * stream it runs on; enabling (or disabling with null/"") clears earlier
  * records.  pm_profile_read waits for the recorded launches and returns their
- * summed device time and count. */
+ * summed device time and count, and (work, nullable) the algorithmic work the
+ * profiled kernel counted: FP64 operations (+ - * / sqrt, one each) along
+ * the paths its threads took, for kernels that count (k_smooth_eval), else 0. */
 uint64_t pm_kernel_launches(void);
 pm_status pm_profile_enable(const char* kernel_substring);
-pm_status pm_profile_read(double* total_ms, int64_t* launches);
+pm_status pm_profile_read(double* total_ms, int64_t* launches, double* work);
 
 /* pm_quality_arrays_dev for callers that cannot allocate device memory
  * during the call (a framework that has already reserved the device memory

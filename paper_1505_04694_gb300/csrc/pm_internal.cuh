@@ -123,6 +123,9 @@ extern unsigned long long g_launches;
 extern bool g_prof_on;
 int prof_begin(const char* name, cudaStream_t s);
 void prof_end(int slot, cudaStream_t s);
+// Device counter of algorithmic work (FP64 operations) for the kernel being
+// profiled, or null when `name` is not being profiled.
+unsigned long long* prof_work(const char* name);
 
 template <class K, class... A>
 inline void launch(const char* name, K kern, dim3 g, dim3 b, size_t sh, cudaStream_t s,

@@ -776,9 +776,10 @@ __device__ double tile_ball_quality(const Tile& t, const Store& S, MeshCtx c, co
 // First ball element (ascending id) that contains X, with v at its current
 // place: its barycentric metric interpolation.
 __device__ bool tile_interpolate(const Tile& t, const Store& S, MeshCtx c, const int* ne, int nel,
-                                 double X, double Y, double4& Mout) {
+                                 double X, double Y, double4& Mout, int* tested = nullptr) {
   VD px{X, Y, 0.0, 0.0, 0.0};
   for (int base = 0; base < nel; base += TW) {
+    if (tested) *tested += min(TW, nel - base);
     int k = base + t.tl;
     bool inside = false;
     VD a{}, b{}, d{};
@@ -850,8 +851,13 @@ __device__ bool tile_ball_after_move(const Tile& t, const Store& S, MeshCtx c, i
 // Quality-constrained Laplacian move of v: metric-weighted neighbour mean,
 // metric interpolated at the target, kept when the ball stays valid and its
 // minimum quality strictly increases.
+// `ops` receives the FP64 operations (+ - * / sqrt) of the path taken: 17 per
+// neighbour (Laplacian), 11 (solve), 28 per element tested in the location
+// (four orientations), 18 (barycentrics and metric) and 77 per element of the
+// ball check (orientation 7 + quality 70).
 __device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c, double2& Xo,
-                                 double4& Mo, double* qout) {
+                                 double4& Mo, double* qout, int& ops) {
+  ops = 0;
   uint8_t f = S.vflag[v];
   if (!(f & VF_ALIVE) || (f & VF_BND)) return false;
   const int* ne = ne_row(S, v);
@@ -884,12 +890,18 @@ __device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c
       b1 = b1 + tshfl(t, t1, j);
     }
   }
+  ops = 17 * nnl + 3;
   double det = a00 * a11 - a01 * a01;
   if (!(det > 0.0)) return false;
   double x = (a11 * b0 - a01 * b1) / det;
   double y = (a00 * b1 - a01 * b0) / det;
+  ops += 8;
   double4 Mn;
-  if (!tile_interpolate(t, S, c, ne, nel, x, y, Mn)) return false;
+  int tested = 0;
+  bool found = tile_interpolate(t, S, c, ne, nel, x, y, Mn, &tested);
+  ops += 28 * tested;
+  if (!found) return false;
+  ops += 18 + 77 * nel;
   if (!tile_ball_after_move(t, S, c, v - c.vb, ne, nel, x, y, Mn, qold, true, qout, nullptr))
     return false;
   Xo = make_double2(x, y);
@@ -899,13 +911,14 @@ __device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c
 
 // Pass 2 (one 8-lane tile per listed vertex): the full quality-constrained move.
 __global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mvxy, double4* mvM,
-                              double* qball, int* C, int* nC, int* cmark, int tag) {
+                              double* qball, int* C, int* nC, int* cmark, int tag,
+                              unsigned long long* work) {
   const int n = *nEp;
   const Tile t = tile_of();
   const int tiles_per_block = blockDim.x / TW;
   for (int j0 = blockIdx.x * tiles_per_block; j0 < n; j0 += gridDim.x * tiles_per_block) {
     int j = j0 + threadIdx.x / TW;
-    int v = 0;
+    int v = 0, ops = 0;
     bool cand = false;
     if (j < n) {
       v = E[j];
@@ -913,7 +926,7 @@ __global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mv
       double2 X;
       double4 Mv;
       // the new ball qualities of an accepted move are kept for the apply
-      cand = tile_smooth_eval(t, S, v, c, X, Mv, qball + (size_t)v * S.W);
+      cand = tile_smooth_eval(t, S, v, c, X, Mv, qball + (size_t)v * S.W, ops);
       if (t.tl == 0) {
         if (cand) {
           Mv.w = 1.0;  // marks a stored move
@@ -927,6 +940,10 @@ __global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mv
       }
     }
     warp_append(cand && t.tl == 0, v, C, nC);
+    if (work) {  // measurement only: one atomic per warp
+      unsigned tot = __reduce_add_sync(0xffffffffu, t.tl == 0 ? (unsigned)ops : 0u);
+      if ((threadIdx.x & 31) == 0 && tot) atomicAdd(work, (unsigned long long)tot);
+    }
   }
 }
 
@@ -1488,7 +1505,8 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
       PM_LAUNCH(k_smooth_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.mvM, w.C,
                 w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E);
       PM_LAUNCH(k_smooth_eval, grid_for(m, (long long)m.S.vused * TW), BLOCK, 0, m.stream, m.S,
-                w.E, w.counts + CN_E, w.mvxy, w.mvM, w.gains, w.C, w.counts + CN_C, w.cmark, tag);
+                w.E, w.counts + CN_E, w.mvxy, w.mvM, w.gains, w.C, w.counts + CN_C, w.cmark, tag,
+                prof_work("k_smooth_eval"));
       PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark,
                 tag, w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
       PM_LAUNCH(k_smooth_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.mvxy,

@@ -19,6 +19,7 @@ struct ProfEvent {
 
 std::mutex g_mu;
 std::string g_filter;
+unsigned long long* g_work = nullptr;  // device counter of the profiled kernel's work
 std::vector<ProfEvent> g_pool;
 size_t g_used = 0;
 
@@ -35,6 +36,12 @@ int prof_begin(const char* name, cudaStream_t s) {
   int slot = (int)g_used++;
   cudaEventRecord(g_pool[slot].a, s);
   return slot;
+}
+
+unsigned long long* prof_work(const char* name) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_prof_on || g_filter.empty() || !std::strstr(name, g_filter.c_str())) return nullptr;
+  return g_work;
 }
 
 void prof_end(int slot, cudaStream_t s) {
@@ -59,12 +66,23 @@ pm_status pm_profile_enable(const char* kernel_substring) {
   } else {
     g_prof_on = true;
     g_filter = kernel_substring;
+    if (!g_work && cudaMalloc(&g_work, sizeof(unsigned long long)) != cudaSuccess) {
+      g_work = nullptr;
+      return PM_ERR_CUDA;
+    }
+    if (cudaMemset(g_work, 0, sizeof(unsigned long long)) != cudaSuccess) return PM_ERR_CUDA;
   }
   return PM_OK;
 }
 
-pm_status pm_profile_read(double* total_ms, int64_t* launches) {
+pm_status pm_profile_read(double* total_ms, int64_t* launches, double* work) {
   if (!total_ms || !launches) return PM_ERR_INVALID_ARG;
+  if (work) {
+    unsigned long long wv = 0;
+    if (g_work && cudaMemcpy(&wv, g_work, sizeof(wv), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PM_ERR_CUDA;
+    *work = (double)wv;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   double t = 0.0;
   for (size_t i = 0; i < g_used; ++i) {

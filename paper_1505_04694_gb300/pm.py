@@ -94,7 +94,8 @@ def _load():
     L.pm_kernel_launches.restype = C.c_uint64
     L.pm_profile_enable.argtypes = [C.c_char_p]
     L.pm_profile_enable.restype = C.c_int
-    L.pm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.pm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_double)]
     L.pm_profile_read.restype = C.c_int
     L.pm_status_string.argtypes = [C.c_int]
     L.pm_status_string.restype = C.c_char_p
@@ -340,11 +341,12 @@ def profile_enable(kernel_substring):
 
 
 def profile_read():
-    """(total device milliseconds, launches) of the profiled kernels."""
+    """(total device ms, launches, counted FP64 operations) of the profiled kernels."""
     ms = C.c_double()
     n = C.c_int64()
-    _check(lib.pm_profile_read(C.byref(ms), C.byref(n)), "pm_profile_read")
-    return float(ms.value), int(n.value)
+    wk = C.c_double()
+    _check(lib.pm_profile_read(C.byref(ms), C.byref(n), C.byref(wk)), "pm_profile_read")
+    return float(ms.value), int(n.value), float(wk.value)
 
 
 def quality_arrays_noalloc_dev(xy, m, tri, qsum, dxy=None, dm=None, stream=0):
