@@ -41,6 +41,11 @@ def parse():
     ap.add_argument("--roofline-kernel", default=None)
     ap.add_argument("--kernel-only", action="store_true",
                     help="device-resident steps only (no e2e pass, no CPU baseline)")
+    ap.add_argument("--workload", default="psi2m",
+                    choices=["psi2m", "psi20m", "paper550k", "batch", "grad"],
+                    help="psi2m (default, the headline line); psi20m / paper550k: other "
+                         "single-mesh sizes; batch: 512 meshes batched vs one mesh per "
+                         "launch; grad: quality forward+backward and optimisation smoothing")
     return ap.parse_args()
 
 
@@ -156,6 +161,161 @@ def traffic_of(kname):
     return None
 
 
+def timed(fn, dev):
+    import torch
+
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize(dev)
+    return r, time.perf_counter() - t
+
+
+def run_batch(args, rank, world, local):
+    """512 independent meshes: one pm_adapt_batch (every round one launch per
+    kernel over all meshes) against 512 pm_adapt calls, same GPU, same inputs.
+    Meshes are created from device-resident inputs inside each timed step;
+    over N ranks the meshes are split by size with no collective."""
+    import torch
+
+    from paper_1505_04694_gb300 import inputs, pm, shard
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ws = inputs.batch_workloads()
+    parts = shard.partition([w.tri.shape[0] for w in ws], world)
+    mine = [ws[i] for i in parts[rank]]
+    dev_in = [(torch.tensor(w.xy, device=dev), torch.tensor(w.tri, dtype=torch.int32, device=dev),
+               torch.tensor(w.m, device=dev)) for w in mine]
+    params = [pm.Params(seed=w.params.seed) for w in mine]
+    sp = torch.cuda.current_stream(dev).cuda_stream
+
+    def make():
+        ms = []
+        for (xy, tri, m) in dev_in:
+            g = pm.Mesh.from_device(xy, tri, cap_factor=2, stream=sp)
+            g.set_metric_dev(m)
+            ms.append(g)
+        return ms
+
+    def finish(ms):
+        n = sum(g.sizes()[1] for g in ms)
+        for g in ms:
+            g.close()
+        return n
+
+    def run(batched):
+        ms, t_make = timed(make, dev)
+        if batched:
+            _, t_adapt = timed(lambda: pm.adapt_batch(ms, params), dev)
+        else:
+            _, t_adapt = timed(lambda: [g.adapt(p) for g, p in zip(ms, params)], dev)
+        n, t_out = timed(lambda: finish(ms), dev)
+        return n, t_make, t_adapt, t_out
+
+    for _ in range(args.warmup):
+        run(True)
+        run(False)
+    acc = {True: [0, 0.0, 0.0, 0.0], False: [0, 0.0, 0.0, 0.0]}
+    for _ in range(args.steps):
+        for b in (True, False):
+            r = run(b)
+            for k in range(4):
+                acc[b][k] += r[k]
+    vals = []
+    for b in (True, False):
+        n, tm, ta, to = acc[b]
+        vals += [float(n), tm + ta + to, ta]
+    if world > 1:
+        import torch.distributed as dist
+
+        v = torch.tensor(vals, dtype=torch.float64, device=dev)
+        cnt = torch.tensor([vals[0], vals[3]], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+        vals = v.tolist()
+        vals[0], vals[3] = cnt.tolist()
+    nb, tb, tab, ns, ts, tas = vals
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": nb / tb, "unit": "elements/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tb / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {len(ws)} unit-square meshes, log-uniform sizes "
+                                   "1k-200k triangles, constant anisotropic metrics",
+                       "output_triangles_per_step": nb / args.steps,
+                       "timing": "wall clock with device synchronisation; a step creates every "
+                                 "mesh from device-resident inputs, adapts, reads the sizes"},
+            "one_mesh_per_launch": {"value": ns / ts, "unit": "elements/s",
+                                    "ms_per_step": 1e3 * ts / args.steps},
+            "adapt_phase": {"batched_elements_per_s": nb / tab,
+                            "one_mesh_per_launch_elements_per_s": ns / tas,
+                            "batched_ms": 1e3 * tab / args.steps,
+                            "one_mesh_per_launch_ms": 1e3 * tas / args.steps,
+                            "speedup": (nb / tab) / (ns / tas)},
+        }), flush=True)
+
+
+def run_grad(args, rank, world, local):
+    """The ~1M-vertex adapted mesh of the 2M workload: quality forward +
+    hand-written backward through torch.autograd (elements/s), and 20 rounds
+    of optimisation-based smoothing on independent sets."""
+    import torch
+
+    from paper_1505_04694_gb300 import inputs, pm
+    from paper_1505_04694_gb300.autograd import quality
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = inputs.anisotropic_2m()
+    g = pm.Mesh.from_host(w.xy, w.tri, device=local)
+    g.set_metric(w.m)
+    g.adapt(pm.Params(seed=w.params.seed))
+    xy0, tri0, m0 = g.get_mesh()
+    g.close()
+    xy = torch.tensor(xy0, device=dev, requires_grad=True)
+    m = torch.tensor(m0, device=dev, requires_grad=True)
+    tri = torch.tensor(tri0, dtype=torch.int32, device=dev)
+
+    def fwd_bwd():
+        xy.grad = None
+        m.grad = None
+        q = quality(xy, m, tri)
+        q.backward()
+        return q
+
+    for _ in range(max(args.warmup, 1)):
+        fwd_bwd()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fwd_bwd()
+    e1.record(stream)
+    e1.synchronize()
+    ms_fb = e0.elapsed_time(e1) / args.steps
+    opt_ms = []
+    for _ in range(args.steps):
+        h = pm.Mesh.from_host(xy0, tri0, device=local)
+        h.set_metric(m0)
+        st, dt = timed(lambda: h.opt_smooth(pm.Params(seed=4, opt_smooth_rounds=20)), dev)
+        opt_ms.append(1e3 * dt)
+        h.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "quality functional forward+backward elements/s", "value":
+            tri0.shape[0] / (ms_fb / 1e3), "unit": "elements/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"adapted psi mesh, {xy0.shape[0]} vertices, "
+                                   f"{tri0.shape[0]} triangles"},
+            "opt_smooth_20_rounds_ms": sorted(opt_ms)[len(opt_ms) // 2],
+            "opt_smooth_moves": st["moves"],
+        }), flush=True)
+
+
 def cpu_baseline_run(samples=1):
     """Oracle (sequential C++) on the bounded sample; returns elements/s etc."""
     from oracle import oracle as O
@@ -207,6 +367,12 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
+        return
+    if args.workload == "grad":
+        run_grad(args, rank, world, local)
+        return
     import numpy as np
     import torch
 
@@ -216,12 +382,14 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
-    w = inputs.anisotropic_2m()
+    w = {"psi2m": inputs.anisotropic_2m, "psi20m": inputs.anisotropic_20m,
+         "paper550k": inputs.paper_550k}[args.workload]()
+    workload_name = WORKLOAD if args.workload == "psi2m" else w.name
     params = pm.Params(seed=w.params.seed)
     xy_d = torch.tensor(w.xy, dtype=torch.float64, device=dev)
     tri_d = torch.tensor(w.tri, dtype=torch.int32, device=dev)
     m_d = torch.tensor(w.m, dtype=torch.float64, device=dev)
-    cap_out = 4_000_000
+    cap_out = 40_000_000 if args.workload == "psi20m" else 4_000_000
     oxy = torch.empty((cap_out, 2), dtype=torch.float64, device=dev)
     otri = torch.empty((cap_out, 3), dtype=torch.int32, device=dev)
     om_ = torch.empty((cap_out, 3), dtype=torch.float64, device=dev)
@@ -318,7 +486,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "output_triangles_per_step": tris // max(args.steps, 1),
+        "config": {"workload": workload_name, "output_triangles_per_step": tris // max(args.steps, 1),
                    "l2": "flushed between steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "clocks": clk.summary(),

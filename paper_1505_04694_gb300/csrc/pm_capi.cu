@@ -162,10 +162,7 @@ pm_status create_common(const double* xy, int nv, const int32_t* tri, int ne,
   if (corner_dev) cudaFreeAsync(corner_dev, m.stream);
   if (s) {
     set_free(m);
-    cudaStreamSynchronize(m.stream);
-    if (m.st) cudaFree(m.st);
-    if (m.hst) cudaFreeHost(m.hst);
-    if (m.hcounts) cudaFreeHost(m.hcounts);
+    set_release(m);
     if (own_stream) cudaStreamDestroy(m.stream);
     delete h;
     return s;
@@ -447,10 +444,7 @@ pm_status pm_mesh_destroy(pm_mesh* h) {
   MeshSet& m = h->set;
   DeviceGuard g(m.device);
   set_free(m);
-  cudaStreamSynchronize(m.stream);
-  if (m.st) cudaFree(m.st);
-  if (m.hst) cudaFreeHost(m.hst);
-  if (m.hcounts) cudaFreeHost(m.hcounts);
+  set_release(m);
   if (m.own_stream) cudaStreamDestroy(m.stream);
   delete h;
   return PM_OK;
@@ -598,10 +592,7 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params, p
   if (!st) st = (pm_status)sync_status(b);
   if (!st && stats) st = fill_stats(b, cs, t0, stats, n);
   set_free(b);
-  cudaStreamSynchronize(b.stream);
-  if (b.hcounts && b.hcounts != m0.hcounts) cudaFreeHost(b.hcounts);
-  if (b.hst && b.hst != m0.hst) cudaFreeHost(b.hst);
-  if (b.st && b.st != m0.st) cudaFree(b.st);
+  set_release(b);
   return st;
 }
 

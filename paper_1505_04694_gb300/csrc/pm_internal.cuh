@@ -74,6 +74,8 @@ struct MeshSet {
   DevStatus* st = nullptr;     // device
   DevStatus* hst = nullptr;    // pinned host
   int* hcounts = nullptr;      // pinned host copy of w.counts
+  void* pinned = nullptr;      // slot of the process-wide pinned arena (hst, hcounts)
+  bool pinned_own = false;     // slot too small: a private pinned allocation
   void* tabmem = nullptr;      // device block holding MeshTab arrays
   int tag = 0;                 // per-round tag (even); the round's change stamp is tag + 1
   // evaluations with tags at or below these are stale for that operator
@@ -86,6 +88,8 @@ struct MeshSet {
 cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap,
                       int W);
 void set_free(MeshSet& m);
+// Release the status word and the pinned read-back slot of a set.
+void set_release(MeshSet& m);
 cudaError_t upload_tab(MeshSet& m);
 void set_used(MeshSet& m);
 cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap, int W);

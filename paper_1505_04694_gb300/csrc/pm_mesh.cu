@@ -8,12 +8,64 @@
 // deferred-update commit (pm_ops.cu).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "pm_internal.cuh"
 
 namespace pm {
 
 namespace {
+
+// Pinned host memory for per-round read-backs, shared by all mesh sets of the
+// process: page-locking is slow and gets slower after many allocate/free
+// cycles, so slots of one arena are handed out and recycled instead.
+constexpr size_t kPinnedSlot = 16384;
+constexpr size_t kPinnedBlock = 64 * kPinnedSlot;
+std::mutex g_pin_mu;
+std::vector<void*> g_pin_free;
+
+void* pinned_get() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    char* blk = nullptr;
+    if (cudaMallocHost((void**)&blk, kPinnedBlock) != cudaSuccess) return nullptr;
+    for (size_t i = 0; i < kPinnedBlock / kPinnedSlot; ++i) g_pin_free.push_back(blk + i * kPinnedSlot);
+  }
+  void* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return p;
+}
+
+void pinned_put(void* p) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+// One device allocation per store, carved into 256-byte aligned arrays:
+// pools fragmented by many small blocks make each allocation slow, so a mesh
+// set asks for one block instead of one per array.
+struct Carver {
+  std::vector<std::pair<void**, size_t>> req;
+  template <class T>
+  void add(T** p, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    req.push_back({(void**)p, (bytes + 255) & ~size_t(255)});
+  }
+  cudaError_t commit(MeshSet& m) {
+    size_t total = 0;
+    for (auto& r : req) total += r.second;
+    char* base = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&base, total, m.stream);
+    if (e != cudaSuccess) return e;
+    m.allocs.push_back(base);
+    size_t off = 0;
+    for (auto& r : req) {
+      *r.first = base + off;
+      off += r.second;
+    }
+    return cudaMemsetAsync(base, 0, total, m.stream);
+  }
+};
 
 template <class T>
 cudaError_t dalloc(MeshSet& m, T** p, size_t count, bool zero) {
@@ -418,24 +470,22 @@ cudaError_t refresh_sizes(MeshSet& m) {
   return e;
 }
 
-static cudaError_t alloc_store(MeshSet& m, Store& S, bool zero) {
-  cudaError_t e;
+static void carve_store(Carver& cv, Store& S) {
   size_t V = S.vslots, E = S.eslots, W = S.W;
-  if ((e = dalloc(m, &S.xy, V, zero))) return e;
-  if ((e = dalloc(m, &S.M, V, zero))) return e;
-  if ((e = dalloc(m, &S.vflag, V, true))) return e;
-  if ((e = dalloc(m, &S.EN, E, zero))) return e;
-  if ((e = dalloc(m, &S.qK, E, zero))) return e;
-  if ((e = dalloc(m, &S.NN, V * W, false))) return e;
-  if ((e = dalloc(m, &S.NNlen, V, true))) return e;
-  if ((e = dalloc(m, &S.NE, V * W, false))) return e;
-  if ((e = dalloc(m, &S.NElen, V, true))) return e;
-  if ((e = dalloc(m, &S.touch, V, true))) return e;
-  if ((e = dalloc(m, &S.evc, V, true))) return e;
-  if ((e = dalloc(m, &S.evs, V, true))) return e;
-  if ((e = dalloc(m, &S.evm, V, true))) return e;
-  if ((e = dalloc(m, &S.evr, V, true))) return e;
-  return cudaSuccess;
+  cv.add(&S.xy, V);
+  cv.add(&S.M, V);
+  cv.add(&S.vflag, V);
+  cv.add(&S.EN, E);
+  cv.add(&S.qK, E);
+  cv.add(&S.NN, V * W);
+  cv.add(&S.NNlen, V);
+  cv.add(&S.NE, V * W);
+  cv.add(&S.NElen, V);
+  cv.add(&S.touch, V);
+  cv.add(&S.evc, V);
+  cv.add(&S.evs, V);
+  cv.add(&S.evm, V);
+  cv.add(&S.evr, V);
 }
 
 cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap,
@@ -460,15 +510,48 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   S.W = W;
   S.vslots = (int)vs;
   S.eslots = (int)es;
-  if ((e = alloc_store(m, S, true))) return e;
   m.B = S;
-  if ((e = alloc_store(m, m.B, false))) return e;
-  // table
+  Carver cv;
+  carve_store(cv, S);
+  carve_store(cv, m.B);
   size_t tab_bytes = (size_t)n * (6 * sizeof(int) + 2 * sizeof(uint32_t) + 2 * sizeof(int) +
                                   2 * sizeof(unsigned long long) + 3 * sizeof(double) +
                                   sizeof(double4)) + 64;
   char* t = nullptr;
-  if ((e = dalloc(m, &t, tab_bytes, true))) return e;
+  cv.add(&t, tab_bytes);
+  Work& w = m.w;
+  cv.add(&w.D[0], vs);
+  cv.add(&w.D[1], vs);
+  cv.add(&w.C, vs);
+  cv.add(&w.Sl, vs);
+  cv.add(&w.A, vs);
+  cv.add(&w.P, vs);
+  cv.add(&w.target, vs);
+  cv.add(&w.opA, vs);
+  cv.add(&w.opK2, vs);
+  cv.add(&w.mvxy, vs);
+  cv.add(&w.mvM, vs);
+  cv.add(&w.dmark, vs);
+  cv.add(&w.amark, vs);
+  cv.add(&w.cmark, vs);
+  cv.add(&w.smark, vs);
+  cv.add(&w.pmark, vs);
+  cv.add(&w.vcnt, vs + 1);
+  cv.add(&w.vscan, vs + 1);
+  cv.add(&w.vmask, vs);
+  cv.add(&w.ecnt, es + 1);
+  cv.add(&w.escan, es + 1);
+  cv.add(&w.emid, es);
+  cv.add(&w.E, vs);
+  // each interior edge gives at most two items and a planar mesh has < 3V edges
+  cv.add(&w.items, (size_t)vs * 6 + 64);
+  cv.add(&w.gains, (size_t)vs * W);
+  cv.add(&w.counts, CN_NUM + 2 * n + 8);
+  int tiles = scan_tiles((int)std::max(vs, es) + 1);
+  cv.add(&m.scan.state, tiles);
+  cv.add(&m.scan.ticket, 1);
+  m.scan.tiles_cap = tiles;
+  if ((e = cv.commit(m))) return e;
   m.tabmem = t;
   MeshTab& T = S.tab;
   // 32-byte, then 8-byte aligned members first
@@ -489,45 +572,20 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   T.had = (int*)t; t += n * sizeof(int);
   T.active = (int*)t; t += n * sizeof(int);
   m.B.tab = T;
-  // work
-  Work& w = m.w;
-  if ((e = dalloc(m, &w.D[0], vs, false))) return e;
-  if ((e = dalloc(m, &w.D[1], vs, false))) return e;
-  if ((e = dalloc(m, &w.C, vs, false))) return e;
-  if ((e = dalloc(m, &w.Sl, vs, false))) return e;
-  if ((e = dalloc(m, &w.A, vs, false))) return e;
-  if ((e = dalloc(m, &w.P, vs, false))) return e;
-  if ((e = dalloc(m, &w.target, vs, false))) return e;
-  if ((e = dalloc(m, &w.opA, vs, false))) return e;
-  if ((e = dalloc(m, &w.opK2, vs, false))) return e;
-  if ((e = dalloc(m, &w.mvxy, vs, false))) return e;
-  if ((e = dalloc(m, &w.mvM, vs, false))) return e;
-  if ((e = dalloc(m, &w.dmark, vs, true))) return e;
-  if ((e = dalloc(m, &w.amark, vs, true))) return e;
-  if ((e = dalloc(m, &w.cmark, vs, true))) return e;
-  if ((e = dalloc(m, &w.smark, vs, true))) return e;
-  if ((e = dalloc(m, &w.pmark, vs, true))) return e;
-  if ((e = dalloc(m, &w.vcnt, vs + 1, false))) return e;
-  if ((e = dalloc(m, &w.vscan, vs + 1, false))) return e;
-  if ((e = dalloc(m, &w.vmask, vs, false))) return e;
-  if ((e = dalloc(m, &w.ecnt, es + 1, false))) return e;
-  if ((e = dalloc(m, &w.escan, es + 1, false))) return e;
-  if ((e = dalloc(m, &w.emid, es, false))) return e;
-  if ((e = dalloc(m, &w.E, vs, false))) return e;
-  // each interior edge gives at most two items and a planar mesh has < 3V edges
-  if ((e = dalloc(m, &w.items, (size_t)vs * 6 + 64, false))) return e;
-  if ((e = dalloc(m, &w.gains, (size_t)vs * W, false))) return e;
-  if ((e = dalloc(m, &w.counts, CN_NUM + 2 * n + 8, true))) return e;
-  int tiles = scan_tiles((int)std::max(vs, es) + 1);
-  if ((e = dalloc(m, &m.scan.state, tiles, true))) return e;
-  if ((e = dalloc(m, &m.scan.ticket, 1, true))) return e;
-  m.scan.tiles_cap = tiles;
   if (!m.st) {
-    if ((e = cudaMalloc(&m.st, sizeof(DevStatus)))) return e;
+    if ((e = cudaMallocAsync((void**)&m.st, sizeof(DevStatus), m.stream))) return e;
     if ((e = cudaMemsetAsync(m.st, 0, sizeof(DevStatus), m.stream))) return e;
-    if ((e = cudaMallocHost(&m.hst, sizeof(DevStatus)))) return e;
-    if ((e = cudaMallocHost(&m.hcounts, (CN_NUM + 2 * std::max(n, 1024) + 8) * sizeof(int))))
-      return e;
+    size_t need = 64 + (CN_NUM + 2 * (size_t)std::max(n, 1024) + 8) * sizeof(int);
+    if (need <= kPinnedSlot) {
+      m.pinned = pinned_get();
+      if (!m.pinned) return cudaErrorMemoryAllocation;
+      m.pinned_own = false;
+    } else {
+      if ((e = cudaMallocHost(&m.pinned, need))) return e;
+      m.pinned_own = true;
+    }
+    m.hst = (DevStatus*)m.pinned;
+    m.hcounts = (int*)((char*)m.pinned + 64);
   }
   return cudaSuccess;
 }
@@ -535,6 +593,19 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
 void set_free(MeshSet& m) {
   for (void* p : m.allocs) cudaFreeAsync(p, m.stream);
   m.allocs.clear();
+}
+
+void set_release(MeshSet& m) {
+  if (m.st) cudaFreeAsync(m.st, m.stream);
+  cudaStreamSynchronize(m.stream);
+  if (m.pinned) {
+    if (m.pinned_own) cudaFreeHost(m.pinned);
+    else pinned_put(m.pinned);
+  }
+  m.st = nullptr;
+  m.pinned = nullptr;
+  m.hst = nullptr;
+  m.hcounts = nullptr;
 }
 
 // Move the meshes into new regions of capacity vcap/ecap and row width W.
@@ -593,12 +664,18 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
 
 // Widen the adjacency rows to W (contents are rebuilt by the caller); every
 // other array, worklist and stamp keeps its place.
+// Frees `p` only when it is an allocation of its own (arrays carved from the
+// store's block go with the block).
+static void free_if_own(MeshSet& m, void* p) {
+  auto it = std::find(m.allocs.begin(), m.allocs.end(), p);
+  if (it == m.allocs.end()) return;
+  cudaFreeAsync(p, m.stream);
+  m.allocs.erase(it);
+}
+
 cudaError_t grow_rows(MeshSet& m, int W) {
-  int* ptrs[4] = {m.S.NN, m.S.NE, m.B.NN, m.B.NE};
-  for (int* p : ptrs) {
-    cudaFreeAsync(p, m.stream);
-    m.allocs.erase(std::remove(m.allocs.begin(), m.allocs.end(), (void*)p), m.allocs.end());
-  }
+  void* ptrs[4] = {m.S.NN, m.S.NE, m.B.NN, m.B.NE};
+  for (void* p : ptrs) free_if_own(m, p);
   size_t n = (size_t)m.S.vslots * W;
   cudaError_t e;
   if ((e = dalloc(m, &m.S.NN, n, false))) return e;
@@ -607,8 +684,7 @@ cudaError_t grow_rows(MeshSet& m, int W) {
   if ((e = dalloc(m, &m.B.NE, n, false))) return e;
   m.S.W = W;
   m.B.W = W;
-  cudaFreeAsync(m.w.gains, m.stream);
-  m.allocs.erase(std::remove(m.allocs.begin(), m.allocs.end(), (void*)m.w.gains), m.allocs.end());
+  free_if_own(m, m.w.gains);
   return dalloc(m, &m.w.gains, n, false);
 }
 

@@ -248,3 +248,124 @@ def test_anisotropic_20m_first_rounds_bit_exact_and_invariants():
     ok, why = MC.unit_square_ok(xy, tri, tol=1e-9)
     assert ok, why
     assert st["collapses"] > 0 and st["flips"] > 0 and st["splits"] > 0
+
+
+def test_batch_sample_of_the_512_mesh_recipe_bit_exact():
+    """16 meshes of the batch recipe (those with the smallest expected
+    output), adapted in one pm_adapt_batch, against the oracle mesh by mesh."""
+    import math as _m
+
+    ws = inputs.batch_workloads()
+
+    def expected(w):
+        m = w.m[0]
+        return (4 / _m.sqrt(3)) * _m.sqrt(m[0] * m[2] - m[1] ** 2)
+
+    pick = sorted(range(len(ws)), key=lambda i: expected(ws[i]))[:16]
+    meshes, params = [], []
+    for i in pick:
+        g = pm.Mesh.from_host(ws[i].xy, ws[i].tri, device=0)
+        g.set_metric(ws[i].m)
+        meshes.append(g)
+        params.append(gp(ws[i].params.seed))
+    stats = pm.adapt_batch(meshes, params)
+    for i, g, st in zip(pick, meshes, stats):
+        o = O.OracleMesh(ws[i].xy, ws[i].tri).set_metric(ws[i].m)
+        so = o.adapt(op(ws[i].params.seed))
+        assert_same_mesh(g.get_mesh(), o.get_mesh(), ws[i].name)
+        for k in STAT_KEYS:
+            assert st[k] == so[k], (ws[i].name, k, st[k], so[k])
+
+
+@pytest.mark.slow
+def test_gradient_workload_reference_fd_and_opt_smoothing():
+    """The adapted mesh of the 2M workload (~1M vertices), produced by the
+    oracle itself: GPU quality gradient against the oracle's (1e-12) and
+    against central differences at 1,000 vertices (1e-6); then 20 rounds of
+    optimisation-based smoothing, bit-exact."""
+    torch = pytest.importorskip("torch")
+    from paper_1505_04694_gb300.autograd import quality
+
+    w = inputs.anisotropic_2m()
+    o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    o.adapt(op(w.params.seed))
+    xy0, tri0, m0 = o.get_mesh()
+    assert xy0.shape[0] > 1_000_000
+    o2 = O.OracleMesh(xy0, tri0).set_metric(m0)
+    qo, do, mo = o2.quality()
+    dev = torch.device("cuda:0")
+    xy = torch.tensor(xy0, device=dev, requires_grad=True)
+    m = torch.tensor(m0, device=dev, requires_grad=True)
+    tri = torch.tensor(tri0, dtype=torch.int32, device=dev)
+    q = quality(xy, m, tri)
+    q.backward()
+    gx, gm = xy.grad.cpu().numpy(), m.grad.cpu().numpy()
+    assert abs(float(q.detach()) - qo) <= 1e-12 * abs(qo)
+    assert np.linalg.norm(gx - do) <= 1e-12 * np.linalg.norm(do)
+    assert np.linalg.norm(gm - mo) <= 1e-12 * np.linalg.norm(mo)
+    # central differences of the ball quality sum at 1,000 seeded vertices
+    rng = np.random.default_rng(4)
+    vs = rng.choice(xy0.shape[0], 1000, replace=False)
+    order = np.argsort(tri0.ravel() // 1, kind="stable")
+    corners = tri0.ravel()[order]
+    starts = np.searchsorted(corners, np.arange(xy0.shape[0] + 1))
+    elems = order // 3
+    def perimeter_third(t):
+        k = m0[t].mean(axis=0)
+        p = xy0[t]
+        d = p[[1, 2, 0]] - p
+        L = np.sqrt(k[0] * d[:, 0] ** 2 + 2 * k[1] * d[:, 0] * d[:, 1] + k[2] * d[:, 1] ** 2)
+        return L.sum() / 3.0
+
+    # error over all sampled vertices at once (one norm per component class:
+    # coordinates and metric entries have different units); after smoothing
+    # many vertices sit at a local optimum whose tiny gradient is below the
+    # differences' roundoff, so a per-vertex ratio would measure noise
+    acc = {"xy": [0.0, 0.0], "m": [0.0, 0.0]}
+    skipped = 0
+    for v in vs:
+        ball = tri0[elems[starts[v]:starts[v + 1]]]
+        # F(x) has a jump in its second derivative at x = 1: differences across
+        # it lose an order of accuracy, so such balls are left out and counted
+        if any(abs(perimeter_third(t) - 1.0) < 1e-4 for t in ball):
+            skipped += 1
+            continue
+        nb = np.unique(ball)
+        lmin = np.min(np.hypot(*(xy0[nb[nb != v]] - xy0[v]).T))
+
+        def ball_sum(xy_v, m_v):
+            s = 0.0
+            for t in ball:
+                pxy = xy0[t].copy()
+                pm_ = m0[t].copy()
+                pxy[t == v] = xy_v
+                pm_[t == v] = m_v
+                s += O.tri_quality(t, pxy, pm_)
+            return s
+
+        an = np.concatenate([gx[v], gm[v]])
+        fd = np.zeros(5)
+        for j in range(5):
+            h = 1e-6 * (lmin if j < 2 else max(m0[v, 0], m0[v, 2]))
+            xp, mp = xy0[v].copy(), m0[v].copy()
+            xm, mm = xy0[v].copy(), m0[v].copy()
+            if j < 2:
+                xp[j] += h
+                xm[j] -= h
+            else:
+                mp[j - 2] += h
+                mm[j - 2] -= h
+            fd[j] = (ball_sum(xp, mp) - ball_sum(xm, mm)) / (2 * h)
+        for key, sl in (("xy", slice(0, 2)), ("m", slice(2, 5))):
+            acc[key][0] += float(np.sum((an[sl] - fd[sl]) ** 2))
+            acc[key][1] += float(np.sum(fd[sl] ** 2))
+    for key, (num, den) in acc.items():
+        assert (num / den) ** 0.5 <= 1e-6, (key, (num / den) ** 0.5)
+    assert skipped < 100, skipped
+    # 20 rounds of optimisation-based smoothing, GPU against the oracle
+    g = pm.Mesh.from_host(xy0, tri0, device=0)
+    g.set_metric(m0)
+    sg = g.opt_smooth(gp(4, opt_smooth_rounds=20))
+    so = o2.opt_smooth(op(4, opt_smooth_rounds=20))
+    assert sg["moves"] == so["moves"] and sg["moves"] > 0
+    assert_same_raw(g.get_raw(), o2.get_raw(), "opt smoothing")
