@@ -574,14 +574,11 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params, p
   for (int i = 0; i < n && !st; ++i) {
     MeshSet& s = meshes[i]->set;
     if (b.nv[i] > s.vcap[0] || b.ne[i] > s.ecap[0] || b.S.W != s.S.W) {
+      // the mesh's old contents are replaced below: new storage, nothing copied
       std::vector<int> v1 = {std::max(s.vcap[0], b.vcap[i])}, e1 = {std::max(s.ecap[0], b.ecap[i])};
-      cudaError_t e = cudaSuccess;
-      if (b.nv[i] > s.vcap[0] || b.ne[i] > s.ecap[0]) e = grow(s, v1, e1, s.S.W);
-      st = cuda_status(e, "growing a mesh");
-      if (!st && b.S.W != s.S.W) {
-        std::vector<int> vv = s.vcap, ee = s.ecap;
-        st = cuda_status(grow(s, vv, ee, b.S.W), "widening rows");
-      }
+      set_free(s);
+      st = cuda_status(set_alloc(s, v1, e1, b.S.W), "growing a mesh");
+      s.lo_coarsen = s.lo_swap = s.lo_refine = s.tag;
     }
     if (st) break;
     s.nv[0] = b.nv[i];

@@ -120,6 +120,18 @@ __device__ __forceinline__ void warp_append(bool pred, int val, int* list, int* 
   if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
+template <class T>
+__device__ __forceinline__ void warp_append_t(bool pred, T val, T* list, int* count) {
+  unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m == 0) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
 // Append once per round: the stamp array holds the tag of the last round in
 // which the slot was appended.
 __device__ __forceinline__ bool stamp_first(int* stamp, int slot, int tag) {

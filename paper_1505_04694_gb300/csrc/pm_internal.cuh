@@ -50,11 +50,15 @@ struct Work {
   int* E = nullptr;                // vertices evaluated in full this round
   int2* items = nullptr;           // flip candidates (vertex, edge slots) of this round
   double* gains = nullptr;         // gain of each (vertex, ball-element slot), vslots * W
+  int2* items2 = nullptr;          // second wave list (vertex, candidate rank)
+  int* cand = nullptr;             // collapse candidates of each vertex by (length, id), vslots * W
+  int* ncand = nullptr;
   int* counts = nullptr;           // device counters (see CountIdx)
 };
 
 enum CountIdx {
-  CN_D0 = 0, CN_D1 = 1, CN_C = 2, CN_S = 3, CN_A = 4, CN_P = 5, CN_E = 6, CN_I = 7, CN_NUM = 8
+  CN_D0 = 0, CN_D1 = 1, CN_C = 2, CN_S = 3, CN_A = 4, CN_P = 5, CN_E = 6, CN_I = 7, CN_I2 = 8,
+  CN_NUM = 10
 };
 
 // Everything the library keeps on the device for a set of meshes.

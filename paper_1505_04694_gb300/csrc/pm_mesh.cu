@@ -546,6 +546,9 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   // each interior edge gives at most two items and a planar mesh has < 3V edges
   cv.add(&w.items, (size_t)vs * 6 + 64);
   cv.add(&w.gains, (size_t)vs * W);
+  cv.add(&w.items2, vs);
+  cv.add(&w.cand, (size_t)vs * W);
+  cv.add(&w.ncand, vs);
   cv.add(&w.counts, CN_NUM + 2 * n + 8);
   int tiles = scan_tiles((int)std::max(vs, es) + 1);
   cv.add(&m.scan.state, tiles);
@@ -685,6 +688,8 @@ cudaError_t grow_rows(MeshSet& m, int W) {
   m.S.W = W;
   m.B.W = W;
   free_if_own(m, m.w.gains);
+  free_if_own(m, m.w.cand);
+  if ((e = dalloc(m, &m.w.cand, n, false))) return e;
   return dalloc(m, &m.w.gains, n, false);
 }
 

@@ -230,11 +230,42 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band) {
   return true;
 }
 
-// Target of v (local id) or -1: the first neighbour, by (metric length, id),
-// shorter than L_low whose collapse is valid.
-__device__ int coarsen_target(const Store& S, int v, MeshCtx c) {
+// Collapse candidates of v: neighbours with metric length below L_low (a
+// boundary vertex: only along boundary edges), sorted by (length, id) into
+// out[0..n).  Corners and dead vertices have none.
+__device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out) {
   uint8_t f = S.vflag[v];
-  if (!(f & VF_ALIVE) || (f & VF_CORNER)) return -1;
+  if (!(f & VF_ALIVE) || (f & VF_CORNER)) return 0;
+  const bool bnd = (f & VF_BND) != 0;
+  const int* nn = nn_row(S, v);
+  int nnl = S.NNlen[v];
+  const int* ne = ne_row(S, v);
+  int nel = S.NElen[v];
+  VD dv = load_vd(S, v);
+  const double L_low = S.tab.L_low[c.mi];
+  const double4 band = S.tab.band[c.mi];
+  double cl[MAXW];
+  int nc = 0;
+  for (int k = 0; k < nnl; ++k) {
+    int u = nn[k];
+    if (bnd && count_elems_with(S, ne, nel, c.eb, u) != 1) continue;
+    double L2 = metric_len2(dv, load_vd(S, c.vb + u));
+    if (!len_lt(L2, band.x, band.y, L_low)) continue;
+    double L = sqrt(L2);
+    int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
+    while (j > 0 && cl[j - 1] > L) {
+      cl[j] = cl[j - 1];
+      out[j] = out[j - 1];
+      --j;
+    }
+    cl[j] = L;
+    out[j] = u;
+    ++nc;
+  }
+  return nc;
+}
+
+__device__ __forceinline__ CoarsenCtx coarsen_ctx(const Store& S, int v, MeshCtx c) {
   CoarsenCtx x;
   x.S = &S;
   x.c = c;
@@ -245,55 +276,79 @@ __device__ int coarsen_target(const Store& S, int v, MeshCtx c) {
   x.ne = ne_row(S, v);
   x.nel = S.NElen[v];
   x.dv = load_vd(S, v);
-  x.bnd = (f & VF_BND) != 0;
-  const double L_low = S.tab.L_low[c.mi];
-  const double4 band = S.tab.band[c.mi];
-  double cl[MAXW];
-  int cw[MAXW];
-  int nc = 0;
-  for (int k = 0; k < x.nnl; ++k) {
-    int u = x.nn[k];
-    if (x.bnd && count_elems_with(S, x.ne, x.nel, c.eb, u) != 1) continue;
-    double L2 = metric_len2(x.dv, load_vd(S, c.vb + u));
-    if (!len_lt(L2, band.x, band.y, L_low)) continue;
-    double L = sqrt(L2);
-    int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
-    while (j > 0 && cl[j - 1] > L) {
-      cl[j] = cl[j - 1];
-      cw[j] = cw[j - 1];
-      --j;
-    }
-    cl[j] = L;
-    cw[j] = u;
-    ++nc;
-  }
-  for (int j = 0; j < nc; ++j)
-    if (collapse_valid(x, cw[j], band)) return cw[j];
-  return -1;
+  x.bnd = (S.vflag[v] & VF_BND) != 0;
+  return x;
 }
 
-__global__ void k_coarsen_eval(Store S, const int* D, const int* nDp, int* target, int* C,
-                               int* nC, int* cmark, int tag, int pass0) {
+// Collapse evaluation.  The target of v is the first candidate, by (metric
+// length, id), whose collapse is valid.  Pass 1 (per dirty vertex) reuses an
+// unchanged earlier result or lists v's sorted candidates; a dense pass then
+// checks every listed vertex's best candidate (one work item each), and a
+// last pass goes through the remaining candidates of the vertices whose best
+// one failed.
+__global__ void k_coarsen_scan(Store S, const int* D, const int* nDp, int* target, int* cand,
+                               int* ncand, int* C, int* nC, int* cmark, int tag, int pass0,
+                               int2* W0, int* nW0) {
   const int n = *nDp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
-    int v = 0, t = -1;
+    int v = 0;
+    bool reuse_cand = false, emit = false;
     if (i < n) {
       v = D[i];
       MeshCtx c = ctx_of(S, v);
       if (unchanged(S, v, c.vb, S.evc[v], pass0)) {
-        t = target[v];
+        reuse_cand = target[v] >= 0;
+        if (reuse_cand) {
+          cmark[v] = tag;
+          S.tab.had[c.mi] = 1;
+        }
       } else {
-        t = coarsen_target(S, v, c);
-        target[v] = t;
         S.evc[v] = tag;
-      }
-      if (t >= 0) {
-        cmark[v] = tag;
-        S.tab.had[c.mi] = 1;
+        int nc = coarsen_candidates(S, v, c, cand + (size_t)v * S.W);
+        ncand[v] = nc;
+        if (nc == 0) target[v] = -1;
+        emit = nc > 0;
       }
     }
-    warp_append(t >= 0, v, C, nC);
+    warp_append(reuse_cand, v, C, nC);
+    warp_append_t(emit, make_int2(v, 0), W0, nW0);
+  }
+}
+
+__global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2* Wout,
+                                int* nWout, int* target, const int* cand, const int* ncand,
+                                int* C, int* nC, int* cmark, int tag, int last) {
+  const int n = *nWin;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int v = 0;
+    bool found = false, next = false;
+    int k = 0;
+    if (i < n) {
+      int2 it = Win[i];
+      v = it.x;
+      k = it.y;
+      MeshCtx c = ctx_of(S, v);
+      CoarsenCtx x = coarsen_ctx(S, v, c);
+      const double4 band = S.tab.band[c.mi];
+      const int* cv = cand + (size_t)v * S.W;
+      int nc = ncand[v];
+      found = collapse_valid(x, cv[k], band);
+      if (last)
+        while (!found && ++k < nc) found = collapse_valid(x, cv[k], band);
+      if (found) {
+        target[v] = cv[k];
+        cmark[v] = tag;
+        S.tab.had[c.mi] = 1;
+      } else if (!last && k + 1 < nc) {
+        next = true;
+      } else {
+        target[v] = -1;
+      }
+    }
+    warp_append(found, v, C, nC);
+    if (!last) warp_append_t(next, make_int2(v, k + 1), Wout, nWout);
   }
 }
 
@@ -1166,7 +1221,7 @@ __device__ __forceinline__ int mid_id(const Store& S, int vb, int nv, const int*
 }
 
 __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long long* mask,
-                                  int stamp) {
+                                  int stamp, int4* owner) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     unsigned long long m = mask[s];
     if (!m) continue;
@@ -1192,6 +1247,7 @@ __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long
       S.vflag[slot] = (uint8_t)(VF_ALIVE | (bedge ? VF_BND : 0));
       S.touch[slot] = stamp;
       S.evc[slot] = S.evs[slot] = S.evm[slot] = S.evr[slot] = 0;
+      owner[slot] = make_int4(s - vb, b, 0, 0);  // the split edge (a, b)
     }
   }
 }
@@ -1273,6 +1329,80 @@ __global__ void k_refine_split(Store S, const int* escan, const int4* emid, int 
   }
 }
 
+// Children of parent element K (local id) of this round: K itself and, when
+// split, the extra slots ne + (escan[K] - escan[eb]) onwards.
+__device__ __forceinline__ int refine_children(const Store& S, int mi, int eb, const int* escan,
+                                               const int4* emid, int K, int* out) {
+  int s = eb + K;
+  int4 md = emid[s];
+  out[0] = K;
+  int n = 1;
+  if (S.EN[s].w && md.w > 0) {
+    int first = S.tab.ne[mi] + (escan[s] - escan[eb]);
+    for (int j = 0; j < md.w; ++j) out[n++] = first + j;
+  }
+  return n;
+}
+
+// New rows of every vertex whose elements changed in this refinement round
+// (stamped), written to the spare buffer B: NE = the children of its old
+// elements that contain it (a new vertex: the children of the elements of its
+// split edge), NN = the other vertices of those, both sorted.
+__global__ void k_refine_rows(Store S, Store B, int vend, const int* vscan, const int* escan,
+                              const int4* emid, const int4* owner, int stamp, DevStatus* st) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < vend; s += gridDim.x * blockDim.x) {
+    if (S.touch[s] != stamp) continue;
+    int mi = mesh_of_vslot(S, s);
+    int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi], nv = S.tab.nv[mi];
+    int lu = s - vb;
+    // the old element row holding the parents: v's own, or for a new vertex
+    // that of its split edge's first end (the children that contain the new
+    // vertex are exactly those of the two parents on that edge)
+    int src = (lu < nv) ? s : vb + owner[s].x;
+    const int* ne = S.NE + (size_t)src * S.W;
+    int nel = S.NElen[src];
+    int eb_[MAXW], nb_[MAXW];
+    int ne2 = 0, nn2 = 0;
+    bool ok = true;
+    for (int k = 0; k < nel; ++k) {
+      int K = ne[k];
+      int ch[4];
+      int n = refine_children(S, mi, eb, escan, emid, K, ch);
+      for (int j = 0; j < n; ++j) {
+        int4 e = S.EN[eb + ch[j]];
+        if (e.x != lu && e.y != lu && e.z != lu) continue;
+        ok &= sorted_insert(eb_, ne2, MAXW, ch[j]);
+        int a = (e.x == lu) ? e.y : e.x;
+        int b = (e.z == lu) ? e.y : e.z;
+        ok &= sorted_insert(nb_, nn2, MAXW, a);
+        ok &= sorted_insert(nb_, nn2, MAXW, b);
+      }
+    }
+    if (!ok || ne2 > S.W || nn2 > S.W) {
+      atomicExch(&st->overflow, 1);
+      atomicMax(&st->maxdeg, max(ne2, nn2));
+      continue;
+    }
+    int* wn = B.NN + (size_t)s * B.W;
+    int* we = B.NE + (size_t)s * B.W;
+    for (int k = 0; k < nn2; ++k) wn[k] = nb_[k];
+    for (int k = 0; k < ne2; ++k) we[k] = eb_[k];
+    B.NNlen[s] = nn2;
+    B.NElen[s] = ne2;
+  }
+}
+
+__global__ void k_refine_rows_copy(Store S, Store B, int vend, int stamp) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < vend; s += gridDim.x * blockDim.x) {
+    if (S.touch[s] != stamp) continue;
+    int a = B.NNlen[s], b = B.NElen[s];
+    for (int k = 0; k < a; ++k) S.NN[(size_t)s * S.W + k] = B.NN[(size_t)s * B.W + k];
+    for (int k = 0; k < b; ++k) S.NE[(size_t)s * S.W + k] = B.NE[(size_t)s * B.W + k];
+    S.NNlen[s] = a;
+    S.NElen[s] = b;
+  }
+}
+
 __global__ void k_refine_sizes(Store S, const int* vscan, const int* escan) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.nmesh) return;
@@ -1347,8 +1477,16 @@ int op_coarsen(MeshSet& m, int max_rounds) {
     int nxt = 1 - cur;
     zero_counts(m, CN_C, 3);
     zero_counts(m, nxt, 1);
-    PM_LAUNCH(k_coarsen_eval, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.target,
-              w.C, w.counts + CN_C, w.cmark, tag, pass0);
+    zero_counts(m, CN_I, 2);
+    PM_LAUNCH(k_coarsen_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.target,
+              w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, pass0, w.items,
+              w.counts + CN_I);
+    // one dense wave checking every vertex's best candidate, then the
+    // remaining candidates of the vertices whose best one failed
+    PM_LAUNCH(k_coarsen_check, gv, BLOCK, 0, m.stream, m.S, w.items, w.counts + CN_I, w.items2,
+              w.counts + CN_I2, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 0);
+    PM_LAUNCH(k_coarsen_check, gv, BLOCK, 0, m.stream, m.S, w.items2, w.counts + CN_I2, w.items,
+              w.counts + CN_I, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 1);
     PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
               w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
     PM_LAUNCH(k_coarsen_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.target, w.A,
@@ -1468,16 +1606,25 @@ int op_refine(MeshSet& m, int max_rounds) {
       continue;
     }
     const int stamp = tag + 1;
+    const int vend = m.vbase.back() + m.nv.back() + newv.back();  // above every new vertex
     PM_LAUNCH(k_refine_vtotals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan);
-    PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, stamp);
+    PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, stamp, w.opA);
     PM_LAUNCH(k_refine_count, ge, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid);
     scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
     PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid, stamp);
+    // rows of the vertices whose elements changed, through the spare buffer
+    PM_LAUNCH(k_refine_rows, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, w.vscan,
+              w.escan, w.emid, w.opA, stamp, m.st);
+    PM_LAUNCH(k_refine_rows_copy, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, stamp);
     PM_LAUNCH(k_refine_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan);
     cudaError_t e = refresh_sizes(m);
     if (e != cudaSuccess) return PM_ERR_CUDA;
-    int err = rebuild_adjacency(m, false, nullptr);
+    int err = sync_status(m);
     if (err) return err;
+    if (m.hst->overflow) {  // a row outgrew W: rebuild every row with wider ones
+      err = rebuild_adjacency(m, false, nullptr);
+      if (err) return err;
+    }
   }
   if (!complete) m.lo_refine = m.tag;
   return PM_OK;
