@@ -148,7 +148,9 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params,
 /* Copy out the mesh, compacted (live vertices and elements in ascending slot
  * order) with every triangle rotated so its smallest vertex id comes first.
  * Two-call protocol: with null arrays only *nv and *ne are written.
- * xy[2*nv], tri[3*ne], m[3*nv] may each be null. */
+ * xy[2*nv], tri[3*ne], m[3*nv] may each be null.  Host arrays in page-locked
+ * memory (cudaHostAlloc / pinned) are filled by direct DMA; pageable ones go
+ * through the driver's staging copy, several times slower. */
 pm_status pm_get_mesh(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
                       double* m);
 pm_status pm_get_mesh_dev(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,

@@ -599,30 +599,34 @@ pm_status pm_get_mesh(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int32_t*
   MeshSet& m = h->set;
   DeviceGuard g(m.device);
   int n1 = 0, n2 = 0;
-  int err = compact_out(m, 0, nullptr, nullptr, nullptr, &n1, &n2);
-  if (err) return (pm_status)err;
-  *nv = n1;
-  *ne = n2;
-  if (!xy && !tri && !M) return PM_OK;
-  double *dxy = nullptr, *dm = nullptr;
-  int32_t* dtri = nullptr;
-  cudaError_t e = cudaSuccess;
-  if (xy) e = cudaMallocAsync(&dxy, std::max(n1, 1) * 2 * sizeof(double), m.stream);
-  if (!e && M) e = cudaMallocAsync(&dm, std::max(n1, 1) * 3 * sizeof(double), m.stream);
-  if (!e && tri) e = cudaMallocAsync(&dtri, std::max(n2, 1) * 3 * sizeof(int32_t), m.stream);
-  pm_status s = cuda_status(e, "output buffers");
-  if (!s) {
-    err = compact_out(m, 0, dxy, dtri, dm, &n1, &n2);
-    if (err) s = (pm_status)err;
+  if (!xy && !tri && !M) {
+    int err = compact_out(m, 0, nullptr, nullptr, nullptr, &n1, &n2);
+    if (err) return (pm_status)err;
+    *nv = n1;
+    *ne = n2;
+    return PM_OK;
   }
+  // one compaction into device buffers sized by the used slots (an upper
+  // bound of the live counts), then the copies of the live part
+  const size_t vb = std::max(m.nv[0], 1), eb = std::max(m.ne[0], 1);
+  char* buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&buf, vb * 5 * sizeof(double) + eb * 3 * sizeof(int32_t),
+                                  m.stream);
+  pm_status s = cuda_status(e, "output buffers");
+  if (s) return s;
+  double* dxy = (double*)buf;
+  double* dm = dxy + 2 * vb;
+  int32_t* dtri = (int32_t*)(dm + 3 * vb);
+  int err = compact_out(m, 0, xy ? dxy : nullptr, tri ? dtri : nullptr, M ? dm : nullptr, &n1, &n2);
+  if (err) s = (pm_status)err;
   if (!s) {
+    *nv = n1;
+    *ne = n2;
     if (xy) cudaMemcpyAsync(xy, dxy, n1 * 2 * sizeof(double), cudaMemcpyDeviceToHost, m.stream);
     if (M) cudaMemcpyAsync(M, dm, n1 * 3 * sizeof(double), cudaMemcpyDeviceToHost, m.stream);
     if (tri) cudaMemcpyAsync(tri, dtri, n2 * 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, m.stream);
   }
-  if (dxy) cudaFreeAsync(dxy, m.stream);
-  if (dm) cudaFreeAsync(dm, m.stream);
-  if (dtri) cudaFreeAsync(dtri, m.stream);
+  cudaFreeAsync(buf, m.stream);
   err = sync_status(m);
   return s ? s : (pm_status)err;
 }

@@ -120,6 +120,34 @@ __device__ __forceinline__ void warp_append(bool pred, int val, int* list, int* 
   if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
+// Room for `cnt` items of this lane in a list: one atomic per warp, the
+// lanes' ranges in lane order.  Returns the first slot of this lane.  All 32
+// lanes of the warp must call it.
+__device__ __forceinline__ int warp_reserve(int cnt, int* count) {
+  const int lane = threadIdx.x & 31;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && total > 0) base = atomicAdd(count, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - cnt;
+}
+
+// Writes vb + row[k] for every set bit k of `bits`, from slot `pos` on.
+__device__ __forceinline__ void write_row_bits(unsigned long long bits, const int* row, int vb,
+                                               int* list, int pos) {
+  while (bits) {
+    int k = __ffsll((long long)bits) - 1;
+    bits &= bits - 1ull;
+    list[pos++] = vb + row[k];
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void warp_append_t(bool pred, T val, T* list, int* count) {
   unsigned m = __ballot_sync(0xffffffffu, pred);

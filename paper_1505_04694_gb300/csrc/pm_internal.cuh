@@ -47,6 +47,8 @@ struct Work {
   int* ecnt = nullptr;             // per-element counts, eslots + 1
   int* escan = nullptr;
   int4* emid = nullptr;            // refine: midpoint ids per element edge
+  int* elist = nullptr;            // refine: elements split this round, eslots
+  int* clist = nullptr;            // refine: their children's slots, eslots
   int* E = nullptr;                // vertices evaluated in full this round
   int2* items = nullptr;           // flip candidates (vertex, edge slots) of this round
   double* gains = nullptr;         // gain of each (vertex, ball-element slot), vslots * W
@@ -58,7 +60,7 @@ struct Work {
 
 enum CountIdx {
   CN_D0 = 0, CN_D1 = 1, CN_C = 2, CN_S = 3, CN_A = 4, CN_P = 5, CN_E = 6, CN_I = 7, CN_I2 = 8,
-  CN_NUM = 10
+  CN_EL = 9, CN_CL = 10, CN_DONE = 11, CN_NUM = 12
 };
 
 // Everything the library keeps on the device for a set of meshes.

@@ -318,6 +318,21 @@ __global__ void k_mesh_totals(Store S, const int* vscan, const int* escan, int* 
   out[2 * i + 1] = escan[eb + S.tab.ne[i]] - escan[eb];
 }
 
+// One slot per thread.  Rows move in 16-byte chunks (W is a multiple of 4 and
+// rows start W-aligned); entries past the row length read as -1.
+__device__ __forceinline__ void renum_row(const int* row, int len, int* out, const int* scan,
+                                          int base, int first) {
+  for (int k = 0; k < len; k += 4) {
+    int4 q = *reinterpret_cast<const int4*>(row + k);
+    int4 r;
+    r.x = scan[base + q.x] - first;
+    r.y = (k + 1 < len) ? scan[base + q.y] - first : -1;
+    r.z = (k + 2 < len) ? scan[base + q.z] - first : -1;
+    r.w = (k + 3 < len) ? scan[base + q.w] - first : -1;
+    *reinterpret_cast<int4*>(out + k) = r;
+  }
+}
+
 __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vused; s += gridDim.x * blockDim.x) {
     int mi;
@@ -335,12 +350,8 @@ __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) 
     B.evm[ns] = A.evm[s];
     B.evr[ns] = A.evr[s];
     int a = A.NNlen[s], b = A.NElen[s];
-    const int* nn = A.NN + (size_t)s * A.W;
-    const int* ne = A.NE + (size_t)s * A.W;
-    int* nn2 = B.NN + (size_t)ns * B.W;
-    int* ne2 = B.NE + (size_t)ns * B.W;
-    for (int k = 0; k < a; ++k) nn2[k] = vscan[vb + nn[k]] - v0;
-    for (int k = 0; k < b; ++k) ne2[k] = escan[eb + ne[k]] - e0;
+    renum_row(A.NN + (size_t)s * A.W, a, B.NN + (size_t)ns * B.W, vscan, vb, v0);
+    renum_row(A.NE + (size_t)s * A.W, b, B.NE + (size_t)ns * B.W, escan, eb, e0);
     B.NNlen[ns] = a;
     B.NElen[ns] = b;
   }
@@ -542,6 +553,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   cv.add(&w.ecnt, es + 1);
   cv.add(&w.escan, es + 1);
   cv.add(&w.emid, es);
+  cv.add(&w.elist, es);
+  cv.add(&w.clist, es);
   cv.add(&w.E, vs);
   // each interior edge gives at most two items and a planar mesh has < 3V edges
   cv.add(&w.items, (size_t)vs * 6 + 64);

@@ -102,9 +102,10 @@ __device__ __forceinline__ bool unchanged(const Store& S, int v, int vb, int et,
   if (S.touch[v] > et) return false;
   const int* nn = S.NN + (size_t)v * S.W;
   int nnl = S.NNlen[v];
-  for (int k = 0; k < nnl; ++k)
-    if (S.touch[vb + nn[k]] > et) return false;
-  return true;
+  bool same = true;
+#pragma unroll 4
+  for (int k = 0; k < nnl; ++k) same &= S.touch[vb + nn[k]] <= et;
+  return same;
 }
 
 // ---- worklist initialisation ---------------------------------------------------
@@ -148,12 +149,10 @@ __global__ void k_select(Store S, const int* C, const int* nCp, const int* cmark
       const int* nn = nn_row(S, v);
       int nnl = S.NNlen[v];
       win = true;
+#pragma unroll 4
       for (int k = 0; k < nnl; ++k) {
         int u = nn[k];
-        if (cmark[c.vb + u] == tag && prio((uint32_t)u, seed, r) > pv) {
-          win = false;
-          break;
-        }
+        win &= !(cmark[c.vb + u] == tag && prio((uint32_t)u, seed, r) > pv);
       }
       if (win) smark[v] = tag;
       else if (keep) lose = stamp_first(kmark, v, tag);
@@ -161,6 +160,45 @@ __global__ void k_select(Store S, const int* C, const int* nCp, const int* cmark
     warp_append(win, v, Sl, nS);
     if (keep) warp_append(lose, v, keep, nkeep);
   }
+}
+
+// Whether candidate v is a local maximum of the priority among this round's
+// candidates (cmark == tag) in its neighbourhood.
+__device__ __forceinline__ bool local_max(const Store& S, int v, const int* cmark, int tag) {
+  MeshCtx c = ctx_of(S, v);
+  uint32_t seed = S.tab.seed[c.mi], r = S.tab.r[c.mi];
+  uint32_t pv = prio((uint32_t)(v - c.vb), seed, r);
+  const int* nn = nn_row(S, v);
+  int nnl = S.NNlen[v];
+  bool win = true;
+#pragma unroll 4
+  for (int k = 0; k < nnl; ++k) {
+    int u = nn[k];
+    win &= !(cmark[c.vb + u] == tag && prio((uint32_t)u, seed, r) > pv);
+  }
+  return win;
+}
+
+// End of a fused select-and-apply launch: the last block to finish advances
+// the round counter of every mesh that formed candidates (every block has
+// read the counters by then) and re-arms the block counter.
+__device__ __forceinline__ void round_done(const Store& S, unsigned* done) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < S.nmesh; i += blockDim.x) {
+    if (S.tab.had[i]) {
+      S.tab.r[i] += 1;
+      S.tab.had[i] = 0;
+    }
+  }
+  if (threadIdx.x == 0) *done = 0;
 }
 
 // ---- coarsening (Sec. 2.4.1) ---------------------------------------------------
@@ -355,18 +393,14 @@ __global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2*
 // Apply the collapses of S: elements containing edge (v, w) die, the other
 // ball elements take w in v's place (slot and orientation kept), v dies.
 // Neighbours of v are affected (rows change) and dirty for the next round.
-__global__ void k_coarsen_apply(Store S, const int* Sl, const int* nSp, const int* target,
-                                int* A, int* nA, int* amark, int* Dn, int* nDn, int* dmark,
-                                int tag) {
-  advance_rounds(S);
-  const int n = *nSp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
-    bool ok = i < n;
-    int v = 0, nnl = 0, mi = 0, vb = 0;
+__device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v,
+                                                  const int* target, int* A, int* nA,
+                                                  int* amark, int* Dn, int* nDn, int* dmark,
+                                                  int tag) {
+  {
+    int nnl = 0, mi = 0, vb = 0;
     const int* nn = nullptr;
     if (ok) {
-      v = Sl[i];
       MeshCtx c = ctx_of(S, v);
       mi = c.mi;
       vb = c.vb;
@@ -392,16 +426,42 @@ __global__ void k_coarsen_apply(Store S, const int* Sl, const int* nSp, const in
       nnl = S.NNlen[v];
     }
     count_op(S, ok, mi);
-    int kmax = warp_max(nnl);
-    for (int k = 0; k < kmax; ++k) {
-      bool has = ok && k < nnl;
-      int s = has ? vb + nn[k] : 0;
-      bool fa = has && stamp_first(amark, s, tag);
-      warp_append(fa, s, A, nA);
-      bool fd = has && stamp_first(dmark, s, tag);
-      warp_append(fd, s, Dn, nDn);
+    unsigned long long fa = 0, fd = 0;
+#pragma unroll 4
+    for (int k = 0; k < nnl; ++k) {
+      int s = vb + nn[k];
+      if (stamp_first(amark, s, tag)) fa |= 1ull << k;
+      if (stamp_first(dmark, s, tag)) fd |= 1ull << k;
     }
+    int pa = warp_reserve(__popcll(fa), nA);
+    int pd = warp_reserve(__popcll(fd), nDn);
+    write_row_bits(fa, nn, vb, A, pa);
+    write_row_bits(fd, nn, vb, Dn, pd);
   }
+}
+
+// One round's independent set and its collapses: a winner applies its
+// collapse at once (no other vertex of the round reads what a collapse
+// writes); losers stay dirty for the next round.
+__global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
+                                       int* smark, int tag, const int* target, int* A, int* nA,
+                                       int* amark, int* Dn, int* nDn, int* dmark,
+                                       unsigned* done) {
+  const int n = *nCp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool win = false, lose = false;
+    int v = 0;
+    if (i < n) {
+      v = C[i];
+      win = local_max(S, v, cmark, tag);
+      if (win) smark[v] = tag;
+      else lose = stamp_first(dmark, v, tag);
+    }
+    warp_append(lose, v, Dn, nDn);
+    coarsen_apply_one(S, win, v, target, A, nA, amark, Dn, nDn, dmark, tag);
+  }
+  round_done(S, done);
 }
 
 // Deferred-update commit of a coarsening round for affected vertex u:
@@ -422,14 +482,20 @@ __global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const in
     int nb[MAXW], eb[MAXW];
     int nn2 = 0, ne2 = 0;
     bool ok = true;
-    for (int k = 0; k < nel; ++k) {
-      int K = ne[k];
-      if (S.EN[c.eb + K].w) ok &= sorted_insert(eb, ne2, MAXW, K);
-    }
+    // gather the per-entry facts first so that their loads overlap
+    unsigned long long alive = 0, sel = 0;
+#pragma unroll 4
+    for (int k = 0; k < nel; ++k)
+      if (S.EN[c.eb + ne[k]].w) alive |= 1ull << k;
+#pragma unroll 4
+    for (int k = 0; k < nnl; ++k)
+      if (smark[c.vb + nn[k]] == tag) sel |= 1ull << k;
+    for (int k = 0; k < nel; ++k)
+      if ((alive >> k) & 1ull) ok &= sorted_insert(eb, ne2, MAXW, ne[k]);
     for (int k = 0; k < nnl; ++k) {
       int x = nn[k];
       int xs = c.vb + x;
-      if (smark[xs] != tag) {
+      if (!((sel >> k) & 1ull)) {
         ok &= sorted_insert(nb, nn2, MAXW, x);
         continue;
       }
@@ -465,6 +531,21 @@ __global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const in
 
 // ---- swapping (Sec. 2.4.3) ------------------------------------------------------
 
+// Warp-aggregated append of a work item into a list of capacity `cap`.
+__device__ __forceinline__ void append_item(bool pred, int2 val, int2* list, int* count, int cap,
+                                            DevStatus* st) {
+  unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m == 0) return;
+  int lane = threadIdx.x & 31, leader = __ffs(m) - 1, base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) {
+    int pos = base + __popc(m & ((1u << lane) - 1u));
+    if (pos < cap) list[pos] = val;
+    else set_err(st, PM_ERR_CAPACITY);
+  }
+}
+
 // Flip evaluation in three passes so that the FP64 work runs on full warps.
 // Pass 1 (per dirty vertex): reuse an unchanged earlier result, or list the
 // vertex's interior edges whose two elements' cached minimum quality is below
@@ -499,44 +580,54 @@ __global__ void k_swap_scan(Store S, const int* D, const int* nDp, const int4* o
     warp_append(eval, v, E, nE);
     const int lv = v - c.vb;
     const double qt = eval ? S.tab.q_thresh[c.mi] : 0.0;
-    int kmax = warp_max(nel);
-    for (int k1 = 0; k1 < kmax; ++k1) {
-      bool emit = false;
-      int k2 = -1;
-      if (eval && k1 < nel) {
-        gains[(size_t)v * S.W + k1] = -1.0;
-        int4 e = S.EN[c.eb + ne[k1]];
+    // An edge (v, w) qualifies only when one of its two elements has quality
+    // below q_thresh, so the pairs are found from v's poor elements alone.
+    unsigned long long poor = 0;
+    for (int k = 0; k < nel; ++k) {
+      gains[(size_t)v * S.W + k] = -1.0;
+      if (S.qK[c.eb + ne[k]] < qt) poor |= 1ull << k;
+    }
+    for (;;) {
+      bool any = poor != 0ull;
+      if (!__any_sync(0xffffffffu, any)) break;
+      // pair (K1 = kb, K2): K2 holds the directed edge w -> v
+      bool emit1 = false, emit2 = false;
+      int a1 = 0, a2 = 0;
+      if (any) {
+        int kb = __ffsll((long long)poor) - 1;
+        poor &= poor - 1ull;
+        int4 e = S.EN[c.eb + ne[kb]];
         int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;   // after v
         int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;  // before v
-        for (int k = 0; k < nel; ++k) {
+        int k2 = -1, k1 = -1;
+        int d2 = 0, c1 = 0;
+        for (int k = 0; k < nel && (k2 < 0 || k1 < 0); ++k) {
+          if (k == kb) continue;
           int4 f = S.EN[c.eb + ne[k]];
+          int nx = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
           int pv = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
-          if (pv == w) {
+          if (k2 < 0 && pv == w) {
             k2 = k;
-            break;
+            d2 = nx;
+          }
+          if (k1 < 0 && nx == cc) {
+            k1 = k;
+            c1 = pv;
           }
         }
         if (k2 >= 0) {
-          double q1 = S.qK[c.eb + ne[k1]], q2 = S.qK[c.eb + ne[k2]];
-          double qold = (q1 < q2) ? q1 : q2;
-          if (qold < qt) {
-            int4 f = S.EN[c.eb + ne[k2]];
-            int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
-            emit = !row_has(nn_row(S, c.vb + d), S.NNlen[c.vb + d], cc);
-          }
+          emit1 = !row_has(nn_row(S, c.vb + d2), S.NNlen[c.vb + d2], cc);
+          a1 = kb | (k2 << 8);
+        }
+        // pair (K1 = k1, K2 = kb) when K1 is not poor itself (else it is
+        // listed from K1's side): w' = cc, c' = c1, d' = w
+        if (k1 >= 0 && !(S.qK[c.eb + ne[k1]] < qt)) {
+          emit2 = !row_has(nn_row(S, c.vb + w), S.NNlen[c.vb + w], c1);
+          a2 = k1 | (kb << 8);
         }
       }
-      unsigned m = __ballot_sync(0xffffffffu, emit);
-      if (m) {
-        int lane = threadIdx.x & 31, leader = __ffs(m) - 1, base = 0;
-        if (lane == leader) base = atomicAdd(nI, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        int pos = base + __popc(m & ((1u << lane) - 1u));
-        if (emit) {
-          if (pos < icap) items[pos] = make_int2(v, k1 | (k2 << 8));
-          else set_err(st, PM_ERR_CAPACITY);
-        }
-      }
+      append_item(emit1, make_int2(v, a1), items, nI, icap, st);
+      append_item(emit2, make_int2(v, a2), items, nI, icap, st);
     }
   }
 }
@@ -629,18 +720,13 @@ __global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double*
   }
 }
 
-__global__ void k_swap_apply(Store S, const int* Sl, const int* nSp, const int4* opA,
-                             const int* opK2, int* A, int* nA, int* amark, int* Dn, int* nDn,
-                             int* dmark, int tag) {
-  advance_rounds(S);
-  const int n = *nSp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
-    bool ok = i < n;
+__device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, const int4* opA,
+                                               const int* opK2, int* A, int* nA, int* amark,
+                                               int* Dn, int* nDn, int* dmark, int tag) {
+  {
     int mi = 0;
     int t[4] = {0, 0, 0, 0};
     if (ok) {
-      int v = Sl[i];
       MeshCtx c = ctx_of(S, v);
       mi = c.mi;
       int lv = v - c.vb;
@@ -658,14 +744,48 @@ __global__ void k_swap_apply(Store S, const int* Sl, const int* nSp, const int4*
       t[3] = c.vb + op.z;
     }
     count_op(S, ok, mi);
+    bool fa[4], fd[4];
+    int na = 0, nd = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      bool fa = ok && stamp_first(amark, t[k], tag);
-      warp_append(fa, t[k], A, nA);
-      bool fd = ok && stamp_first(dmark, t[k], tag);
-      warp_append(fd, t[k], Dn, nDn);
+      fa[k] = ok && stamp_first(amark, t[k], tag);
+      fd[k] = ok && stamp_first(dmark, t[k], tag);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      na += fa[k];
+      nd += fd[k];
+    }
+    int pa = warp_reserve(na, nA);
+    int pd = warp_reserve(nd, nDn);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (fa[k]) A[pa++] = t[k];
+      if (fd[k]) Dn[pd++] = t[k];
     }
   }
+}
+
+// One round's independent set and its flips (see k_coarsen_select_apply).
+__global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
+                                    int* smark, int tag, const int4* opA, const int* opK2, int* A,
+                                    int* nA, int* amark, int* Dn, int* nDn, int* dmark,
+                                    unsigned* done) {
+  const int n = *nCp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool win = false, lose = false;
+    int v = 0;
+    if (i < n) {
+      v = C[i];
+      win = local_max(S, v, cmark, tag);
+      if (win) smark[v] = tag;
+      else lose = stamp_first(dmark, v, tag);
+    }
+    warp_append(lose, v, Dn, nDn);
+    swap_apply_one(S, win, v, opA, opK2, A, nA, amark, Dn, nDn, dmark, tag);
+  }
+  round_done(S, done);
 }
 
 // Deferred-update commit of a swap round for affected vertex u, from the
@@ -688,10 +808,15 @@ __global__ void k_swap_commit(Store S, const int* A, const int* nAp, const int4*
     for (int k = 0; k < nel; ++k) eb[k] = ne[k];
     int nn2 = nnl, ne2 = nel;
     bool ok = true;
+    unsigned long long sel = 0;
+#pragma unroll 4
+    for (int k = 0; k < nnl; ++k)
+      if (smark[c.vb + nn[k]] == tag) sel |= 1ull << k;
+    const bool self = smark[u] == tag;
     for (int k = -1; k < nnl; ++k) {
+      if (k < 0 ? !self : !((sel >> k) & 1ull)) continue;
       int x = (k < 0) ? lu : nn[k];
       int xs = c.vb + x;
-      if (smark[xs] != tag) continue;
       int4 op = opA[xs];
       int K2 = opK2[xs];
       if (x == lu) {
@@ -728,6 +853,7 @@ __global__ void k_swap_commit(Store S, const int* A, const int* nAp, const int4*
 __device__ __forceinline__ double ball_min_quality(const Store& S, MeshCtx c, const int* ne,
                                                    int nel, double* qsum) {
   double qmin = 0.0, sum = 0.0;
+#pragma unroll 4
   for (int k = 0; k < nel; ++k) {
     double q = S.qK[c.eb + ne[k]];
     if (k == 0 || q < qmin) qmin = q;
@@ -1004,18 +1130,14 @@ __global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mv
 
 // Move the members of S; live interior neighbours become pending for the next
 // sweep (stamp pmark with the sweep tag).
-__global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const double2* mvxy,
-                               const double4* mvM, const double* qball, int* P, int* nP,
-                               int* pmark, int ptag, int stamp) {
-  advance_rounds(S);
-  const int n = *nSp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
-    bool ok = i < n;
+__device__ __forceinline__ void smooth_apply_one(const Store& S, bool ok, int v,
+                                                 const double2* mvxy, const double4* mvM,
+                                                 const double* qball, int* P, int* nP,
+                                                 int* pmark, int ptag, int stamp) {
+  {
     int mi = 0, vb = 0, nnl = 0;
     const int* nn = nullptr;
     if (ok) {
-      int v = Sl[i];
       MeshCtx c = ctx_of(S, v);
       mi = c.mi;
       vb = c.vb;
@@ -1031,18 +1153,39 @@ __global__ void k_smooth_apply(Store S, const int* Sl, const int* nSp, const dou
       nnl = S.NNlen[v];
     }
     count_op(S, ok, mi);
-    int kmax = warp_max(nnl);
-    for (int k = 0; k < kmax; ++k) {
-      bool has = ok && k < nnl;
-      int s = has ? vb + nn[k] : 0;
-      bool take = false;
-      if (has) {
-        uint8_t f = S.vflag[s];
-        take = (f & VF_ALIVE) && !(f & VF_BND) && stamp_first(pmark, s, ptag);
-      }
-      warp_append(take, s, P, nP);
+    unsigned long long take = 0;
+#pragma unroll 4
+    for (int k = 0; k < nnl; ++k) {
+      int s = vb + nn[k];
+      uint8_t f = S.vflag[s];
+      if ((f & VF_ALIVE) && !(f & VF_BND) && stamp_first(pmark, s, ptag)) take |= 1ull << k;
     }
+    int pp = warp_reserve(__popcll(take), nP);
+    write_row_bits(take, nn, vb, P, pp);
   }
+}
+
+// One round's independent set and its moves (see k_coarsen_select_apply).
+__global__ void k_smooth_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
+                                      int* smark, int tag, int* Dn, int* nDn, int* dmark,
+                                      const double2* mvxy, const double4* mvM,
+                                      const double* qball, int* P, int* nP, int* pmark, int ptag,
+                                      int stamp, unsigned* done) {
+  const int n = *nCp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    bool win = false, lose = false;
+    int v = 0;
+    if (i < n) {
+      v = C[i];
+      win = local_max(S, v, cmark, tag);
+      if (win) smark[v] = tag;
+      else lose = stamp_first(dmark, v, tag);
+    }
+    warp_append(lose, v, Dn, nDn);
+    smooth_apply_one(S, win, v, mvxy, mvM, qball, P, nP, pmark, ptag, stamp);
+  }
+  round_done(S, done);
 }
 
 // Optimisation-based smoothing of one member of S (gradient ascent of the
@@ -1158,7 +1301,11 @@ __global__ void k_stamp_list(Store S, const int* L, const int* nLp, int* cmark, 
 
 // Mark edges (a, b), a < b, longer than L_up: bit k of vmask[a] for NN entry k.
 // A vertex unchanged since it was marked earlier in this pass keeps its mask;
-// one unchanged since the end of an earlier complete pass has none.
+// one unchanged since the end of an earlier complete pass has none.  The mask
+// reads a's own row and the positions and metrics of a and its neighbours;
+// inside one call vertices keep their positions and metrics until the
+// operator loop ends (smoothing runs after it), so a's own stamp tells
+// whether anything the mask read has changed: every change of a's row stamps a.
 __global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int tag, int pass0,
                               int lo) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
@@ -1166,9 +1313,11 @@ __global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int t
     int vb = S.tab.vbase[mi];
     unsigned long long m = 0;
     bool live = s - vb < S.tab.nv[mi] && S.tab.active[mi] && (S.vflag[s] & VF_ALIVE);
-    if (live && unchanged(S, s, vb, S.evr[s], pass0)) {
+    const int et = live ? S.evr[s] : 0;
+    const bool same = live && S.touch[s] <= et;
+    if (same && et > pass0) {
       m = mask[s];
-    } else if (live && unchanged(S, s, vb, S.evr[s], lo)) {
+    } else if (same && et > lo) {
       m = 0;
     } else if (live) {
       S.evr[s] = tag;
@@ -1252,96 +1401,115 @@ __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long
   }
 }
 
-// Children per live element (1..4) and the midpoint ids of its edges.
+// Extra children per live element (0..3); an element that splits gets the
+// midpoint ids of its edges and joins the split list.
 __global__ void k_refine_count(Store S, const int* vscan, const unsigned long long* mask,
-                               int* ecnt, int4* emid) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
-    int mi = mesh_of_eslot(S, s);
-    int eb = S.tab.ebase[mi];
+                               int* ecnt, int4* emid, int* elist, int* nel) {
+  for (int i0 = blockIdx.x * blockDim.x; i0 < S.eused; i0 += gridDim.x * blockDim.x) {
+    int s = i0 + threadIdx.x;
     int extra = 0;
-    if (s - eb < S.tab.ne[mi] && S.tab.active[mi]) {
-      int4 e = S.EN[s];
-      if (e.w) {
-        int vb = S.tab.vbase[mi], nv = S.tab.nv[mi];
-        int m0 = mid_id(S, vb, nv, vscan, mask, e.x, e.y);
-        int m1 = mid_id(S, vb, nv, vscan, mask, e.y, e.z);
-        int m2 = mid_id(S, vb, nv, vscan, mask, e.z, e.x);
-        extra = (m0 >= 0) + (m1 >= 0) + (m2 >= 0);
-        emid[s] = make_int4(m0, m1, m2, extra);
+    if (s < S.eused) {
+      int mi = mesh_of_eslot(S, s);
+      int eb = S.tab.ebase[mi];
+      if (s - eb < S.tab.ne[mi] && S.tab.active[mi]) {
+        int4 e = S.EN[s];
+        if (e.w) {
+          int vb = S.tab.vbase[mi], nv = S.tab.nv[mi];
+          int m0 = mid_id(S, vb, nv, vscan, mask, e.x, e.y);
+          int m1 = mid_id(S, vb, nv, vscan, mask, e.y, e.z);
+          int m2 = mid_id(S, vb, nv, vscan, mask, e.z, e.x);
+          extra = (m0 >= 0) + (m1 >= 0) + (m2 >= 0);
+          if (extra) emid[s] = make_int4(m0, m1, m2, extra);
+        }
       }
+      ecnt[s] = extra;
     }
-    ecnt[s] = extra;
+    warp_append(extra > 0, s, elist, nel);
   }
 }
 
 // Templates: one split -> (a,m,o),(m,b,o); two splits -> (m0,u1,m1) plus the
 // trapezoid (u0,m0,m1,u2) cut along its metric-shorter diagonal; three
 // splits -> four children.  The first child keeps the parent's slot, the rest
-// take ne + scan(extra children) in parent order.
-__global__ void k_refine_split(Store S, const int* escan, const int4* emid, int stamp) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
-    int mi = mesh_of_eslot(S, s);
-    int eb = S.tab.ebase[mi];
-    if (!(s - eb < S.tab.ne[mi]) || !S.tab.active[mi]) continue;
-    int4 e = S.EN[s];
-    if (!e.w) continue;
-    int4 md = emid[s];
-    if (md.w == 0) continue;
-    int vb = S.tab.vbase[mi];
-    int nslot = eb + S.tab.ne[mi] + (escan[s] - escan[eb]);
-    auto put = [&](int slot, int a, int b, int c) {
-      S.EN[slot] = make_int4(a, b, c, 1);
-      S.qK[slot] = quality_c(a, b, c, load_vd(S, vb + a), load_vd(S, vb + b), load_vd(S, vb + c));
-    };
-    int t[3] = {e.x, e.y, e.z};
-    int mm[3] = {md.x, md.y, md.z};
+// take ne + scan(extra children) in parent order.  Every child slot joins
+// the list whose qualities k_refine_quality computes.
+__global__ void k_refine_split(Store S, const int* escan, const int4* emid, const int* elist,
+                               const int* nelp, int* clist, int* ncl, int stamp) {
+  const int n = *nelp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int s = 0, nslot = 0, extra = 0;
+    if (i < n) {
+      s = elist[i];
+      int mi = mesh_of_eslot(S, s);
+      int eb = S.tab.ebase[mi];
+      int4 e = S.EN[s];
+      int4 md = emid[s];
+      extra = md.w;
+      int vb = S.tab.vbase[mi];
+      nslot = eb + S.tab.ne[mi] + (escan[s] - escan[eb]);
+      auto put = [&](int slot, int a, int b, int c) { S.EN[slot] = make_int4(a, b, c, 1); };
+      int t[3] = {e.x, e.y, e.z};
+      int mm[3] = {md.x, md.y, md.z};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      S.touch[vb + t[k]] = stamp;
-      if (mm[k] >= 0) S.touch[vb + mm[k]] = stamp;
-    }
-    if (md.w == 1) {
-      int i = (mm[0] >= 0) ? 0 : (mm[1] >= 0) ? 1 : 2;
-      int a = t[i], b = t[(i + 1) % 3], o = t[(i + 2) % 3], m = mm[i];
-      put(s, a, m, o);
-      put(nslot, m, b, o);
-    } else if (md.w == 2) {
-      int j = (mm[0] < 0) ? 0 : (mm[1] < 0) ? 1 : 2;
-      int q = (j + 1) % 3;
-      int u0 = t[q], u1 = t[(q + 1) % 3], u2 = t[(q + 2) % 3];
-      int m0 = mm[q], m1 = mm[(q + 1) % 3];
-      put(s, m0, u1, m1);
-      double d1 = metric_len(load_vd(S, vb + u0), load_vd(S, vb + m1));
-      double d2 = metric_len(load_vd(S, vb + m0), load_vd(S, vb + u2));
-      if (d1 <= d2) {
-        put(nslot, u0, m0, m1);
-        put(nslot + 1, u0, m1, u2);
-      } else {
-        put(nslot, u0, m0, u2);
-        put(nslot + 1, m0, m1, u2);
+      for (int k = 0; k < 3; ++k) {
+        S.touch[vb + t[k]] = stamp;
+        if (mm[k] >= 0) S.touch[vb + mm[k]] = stamp;
       }
-    } else {
-      put(s, t[0], mm[0], mm[2]);
-      put(nslot, mm[0], t[1], mm[1]);
-      put(nslot + 1, mm[2], mm[1], t[2]);
-      put(nslot + 2, mm[0], mm[1], mm[2]);
+      if (md.w == 1) {
+        int j = (mm[0] >= 0) ? 0 : (mm[1] >= 0) ? 1 : 2;
+        int a = t[j], b = t[(j + 1) % 3], o = t[(j + 2) % 3], m = mm[j];
+        put(s, a, m, o);
+        put(nslot, m, b, o);
+      } else if (md.w == 2) {
+        int j = (mm[0] < 0) ? 0 : (mm[1] < 0) ? 1 : 2;
+        int q = (j + 1) % 3;
+        int u0 = t[q], u1 = t[(q + 1) % 3], u2 = t[(q + 2) % 3];
+        int m0 = mm[q], m1 = mm[(q + 1) % 3];
+        put(s, m0, u1, m1);
+        double d1 = metric_len(load_vd(S, vb + u0), load_vd(S, vb + m1));
+        double d2 = metric_len(load_vd(S, vb + m0), load_vd(S, vb + u2));
+        if (d1 <= d2) {
+          put(nslot, u0, m0, m1);
+          put(nslot + 1, u0, m1, u2);
+        } else {
+          put(nslot, u0, m0, u2);
+          put(nslot + 1, m0, m1, u2);
+        }
+      } else {
+        put(s, t[0], mm[0], mm[2]);
+        put(nslot, mm[0], t[1], mm[1]);
+        put(nslot + 1, mm[2], mm[1], t[2]);
+        put(nslot + 2, mm[0], mm[1], mm[2]);
+      }
     }
+    warp_append(i < n, s, clist, ncl);
+    for (int j = 0; j < 3; ++j) warp_append(j < extra, nslot + j, clist, ncl);
+  }
+}
+
+// Cached quality of every child written this round (one element per thread).
+__global__ void k_refine_quality(Store S, const int* clist, const int* nclp) {
+  const int n = *nclp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int slot = clist[i];
+    int vb = S.tab.vbase[mesh_of_eslot(S, slot)];
+    int4 e = S.EN[slot];
+    S.qK[slot] = quality_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
+                           load_vd(S, vb + e.z));
   }
 }
 
 // Children of parent element K (local id) of this round: K itself and, when
 // split, the extra slots ne + (escan[K] - escan[eb]) onwards.
 __device__ __forceinline__ int refine_children(const Store& S, int mi, int eb, const int* escan,
-                                               const int4* emid, int K, int* out) {
+                                               int K, int* out) {
   int s = eb + K;
-  int4 md = emid[s];
+  int e0 = escan[s], extra = escan[s + 1] - e0;
   out[0] = K;
-  int n = 1;
-  if (S.EN[s].w && md.w > 0) {
-    int first = S.tab.ne[mi] + (escan[s] - escan[eb]);
-    for (int j = 0; j < md.w; ++j) out[n++] = first + j;
-  }
-  return n;
+  int first = S.tab.ne[mi] + (e0 - escan[eb]);
+  for (int j = 0; j < extra; ++j) out[1 + j] = first + j;
+  return 1 + extra;
 }
 
 // New rows of every vertex whose elements changed in this refinement round
@@ -1349,7 +1517,7 @@ __device__ __forceinline__ int refine_children(const Store& S, int mi, int eb, c
 // elements that contain it (a new vertex: the children of the elements of its
 // split edge), NN = the other vertices of those, both sorted.
 __global__ void k_refine_rows(Store S, Store B, int vend, const int* vscan, const int* escan,
-                              const int4* emid, const int4* owner, int stamp, DevStatus* st) {
+                              const int4* owner, int stamp, DevStatus* st) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < vend; s += gridDim.x * blockDim.x) {
     if (S.touch[s] != stamp) continue;
     int mi = mesh_of_vslot(S, s);
@@ -1367,7 +1535,7 @@ __global__ void k_refine_rows(Store S, Store B, int vend, const int* vscan, cons
     for (int k = 0; k < nel; ++k) {
       int K = ne[k];
       int ch[4];
-      int n = refine_children(S, mi, eb, escan, emid, K, ch);
+      int n = refine_children(S, mi, eb, escan, K, ch);
       for (int j = 0; j < n; ++j) {
         int4 e = S.EN[eb + ch[j]];
         if (e.x != lu && e.y != lu && e.z != lu) continue;
@@ -1487,10 +1655,9 @@ int op_coarsen(MeshSet& m, int max_rounds) {
               w.counts + CN_I2, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 0);
     PM_LAUNCH(k_coarsen_check, gv, BLOCK, 0, m.stream, m.S, w.items2, w.counts + CN_I2, w.items,
               w.counts + CN_I, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 1);
-    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
-              w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
-    PM_LAUNCH(k_coarsen_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.target, w.A,
-              w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt, w.dmark, tag);
+    PM_LAUNCH(k_coarsen_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
+              w.smark, tag, w.target, w.A, w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt,
+              w.dmark, (unsigned*)(w.counts + CN_DONE));
     PM_LAUNCH(k_coarsen_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target,
               w.smark, tag, m.st);
     RoundIO io = read_round(m);
@@ -1530,10 +1697,9 @@ int op_swap(MeshSet& m, int max_rounds) {
               w.counts + CN_I, w.gains);
     PM_LAUNCH(k_swap_pick, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
               w.opK2, w.C, w.counts + CN_C, w.cmark, tag);
-    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
-              w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
-    PM_LAUNCH(k_swap_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.opA, w.opK2,
-              w.A, w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt, w.dmark, tag);
+    PM_LAUNCH(k_swap_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
+              w.smark, tag, w.opA, w.opK2, w.A, w.counts + CN_A, w.amark, w.D[nxt],
+              w.counts + nxt, w.dmark, (unsigned*)(w.counts + CN_DONE));
     PM_LAUNCH(k_swap_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2,
               w.smark, tag, m.st);
     RoundIO io = read_round(m);
@@ -1609,12 +1775,16 @@ int op_refine(MeshSet& m, int max_rounds) {
     const int vend = m.vbase.back() + m.nv.back() + newv.back();  // above every new vertex
     PM_LAUNCH(k_refine_vtotals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan);
     PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, stamp, w.opA);
-    PM_LAUNCH(k_refine_count, ge, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid);
+    zero_counts(m, CN_EL, 2);
+    PM_LAUNCH(k_refine_count, ge, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid,
+              w.elist, w.counts + CN_EL);
     scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
-    PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid, stamp);
+    PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid, w.elist,
+              w.counts + CN_EL, w.clist, w.counts + CN_CL, stamp);
+    PM_LAUNCH(k_refine_quality, ge, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL);
     // rows of the vertices whose elements changed, through the spare buffer
     PM_LAUNCH(k_refine_rows, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, w.vscan,
-              w.escan, w.emid, w.opA, stamp, m.st);
+              w.escan, w.opA, stamp, m.st);
     PM_LAUNCH(k_refine_rows_copy, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, stamp);
     PM_LAUNCH(k_refine_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan);
     cudaError_t e = refresh_sizes(m);
@@ -1654,10 +1824,9 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
       PM_LAUNCH(k_smooth_eval, grid_for(m, (long long)m.S.vused * TW), BLOCK, 0, m.stream, m.S,
                 w.E, w.counts + CN_E, w.mvxy, w.mvM, w.gains, w.C, w.counts + CN_C, w.cmark, tag,
                 prof_work("k_smooth_eval"));
-      PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark,
-                tag, w.Sl, w.counts + CN_S, w.D[nxt], w.counts + nxt, w.dmark);
-      PM_LAUNCH(k_smooth_apply, gv, BLOCK, 0, m.stream, m.S, w.Sl, w.counts + CN_S, w.mvxy,
-                w.mvM, w.gains, w.P, w.counts + CN_P, w.pmark, ptag, tag + 1);
+      PM_LAUNCH(k_smooth_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C,
+                w.cmark, w.smark, tag, w.D[nxt], w.counts + nxt, w.dmark, w.mvxy, w.mvM, w.gains,
+                w.P, w.counts + CN_P, w.pmark, ptag, tag + 1, (unsigned*)(w.counts + CN_DONE));
       RoundIO io = read_round(m);
       if (io.err) return io.err;
       if (io.nC == 0) break;

@@ -14,8 +14,8 @@ namespace pm {
 
 namespace {
 
-constexpr int SCAN_THREADS = 128;
-constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;  // per thread, consecutive (four int4 loads)
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr long long SPIN_LIMIT = 1LL << 22;
 
@@ -24,10 +24,13 @@ __device__ __forceinline__ unsigned long long pack(unsigned epoch, unsigned flag
   return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | val;
 }
 
+__device__ __forceinline__ unsigned long long load_state(const unsigned long long* p) {
+  return *((volatile const unsigned long long*)p);
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan(const int* __restrict__ in, int* __restrict__ out, int n, unsigned long long* state,
        int* ticket, unsigned epoch, DevStatus* st) {
-  __shared__ int s_items[SCAN_TILE];
   __shared__ int s_warp[SCAN_THREADS / 32];
   __shared__ int s_tile;
   __shared__ int s_excl;
@@ -38,21 +41,29 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, unsigned long l
   }
   __syncthreads();
   const int tile = s_tile;
-  const long long base = (long long)tile * SCAN_TILE;
-  // coalesced load into shared memory
-  for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_THREADS) {
-    long long g = base + k;
-    s_items[k] = (g < n) ? in[g] : 0;
+  const long long first = (long long)tile * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  if (first + SCAN_ITEMS <= n) {
+    const int4* p = reinterpret_cast<const int4*>(in + first);
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
+      int4 x = p[q];
+      v[4 * q] = x.x;
+      v[4 * q + 1] = x.y;
+      v[4 * q + 2] = x.z;
+      v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) v[j] = (first + j < n) ? in[first + j] : 0;
   }
-  __syncthreads();
-  int local[SCAN_ITEMS];
   int sum = 0;
 #pragma unroll
   for (int j = 0; j < SCAN_ITEMS; ++j) {
-    local[j] = sum;
-    sum += s_items[threadIdx.x * SCAN_ITEMS + j];
+    int x = v[j];
+    v[j] = sum;
+    sum += x;
   }
-  // block scan of thread sums
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int incl = sum;
 #pragma unroll
@@ -69,54 +80,72 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, unsigned long l
     if (w < wid) wpre += x;
     total += x;
   }
-  const int texcl = wpre + incl - sum;
-  // decoupled look-back by thread 0
-  if (threadIdx.x == 0) {
+  // decoupled look-back by warp 0, 32 predecessors at a time
+  if (wid == 0) {
     int excl = 0;
     if (tile == 0) {
-      atomicExch(state + tile, pack(epoch, 2, (unsigned)total));
+      if (lane == 0) atomicExch(state, pack(epoch, 2, (unsigned)total));
     } else {
-      atomicExch(state + tile, pack(epoch, 1, (unsigned)total));
-      int j = tile - 1;
-      while (j >= 0) {
-        unsigned long long w;
-        long long spins = 0;
-        for (;;) {
-          w = *((volatile unsigned long long*)(state + j));
-          if ((unsigned)(w >> 34) == (epoch & 0x3FFFFFFFu) && ((w >> 32) & 3u) != 0) break;
-          if (++spins > SPIN_LIMIT) break;
-          if (spins > 64) __nanosleep(64);
+      if (lane == 0) atomicExch(state + tile, pack(epoch, 1, (unsigned)total));
+      int j = tile - 1;  // newest predecessor not yet added
+      bool done = false, fail = false;
+      while (!done && !fail) {
+        int idx = j - lane;
+        unsigned flag = 3u;  // lanes beyond tile 0 act as an inclusive zero
+        unsigned val = 0;
+        if (idx >= 0) {
+          long long spins = 0;
+          for (;;) {
+            unsigned long long w = load_state(state + idx);
+            flag = ((unsigned)(w >> 34) == (epoch & 0x3FFFFFFFu)) ? (unsigned)((w >> 32) & 3u) : 0u;
+            if (flag != 0u) {
+              val = (unsigned)(w & 0xFFFFFFFFu);
+              break;
+            }
+            if (++spins > SPIN_LIMIT) break;
+            if (spins > 32) __nanosleep(64);
+          }
+          if (flag == 0u) fail = true;
         }
-        if (spins > SPIN_LIMIT) {
-          s_fail = 1;
-          break;
-        }
-        excl += (int)(unsigned)(w & 0xFFFFFFFFu);
-        if (((w >> 32) & 3u) == 2u) break;
-        --j;
+        fail = __any_sync(0xffffffffu, fail);
+        if (fail) break;
+        // the nearest predecessor holding an inclusive prefix ends the walk
+        unsigned incl_mask = __ballot_sync(0xffffffffu, flag >= 2u);
+        int stop = incl_mask ? (__ffs(incl_mask) - 1) : 32;
+        int add = (lane <= stop && lane < 32 && idx >= 0) ? (int)val : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+        excl += add;
+        if (incl_mask) done = true;
+        else j -= 32;
       }
-      if (!s_fail) {
+      if (fail) {
+        if (lane == 0) s_fail = 1;
+      } else if (lane == 0) {
         __threadfence();
         atomicExch(state + tile, pack(epoch, 2, (unsigned)(excl + total)));
       }
     }
-    s_excl = excl;
+    if (lane == 0) s_excl = excl;
   }
   __syncthreads();
   if (s_fail) {
     if (threadIdx.x == 0) set_err(st, PM_ERR_TIMEOUT);
     return;
   }
-  const int off = s_excl + texcl;
+  const int off = s_excl + wpre + incl - sum;
+  if (first + SCAN_ITEMS <= n) {
+    int4* p = reinterpret_cast<int4*>(out + first);
 #pragma unroll
-  for (int j = 0; j < SCAN_ITEMS; ++j) s_items[threadIdx.x * SCAN_ITEMS + j] = off + local[j];
-  __syncthreads();
-  for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_THREADS) {
-    long long g = base + k;
-    if (g < n) out[g] = s_items[k];
+    for (int q = 0; q < SCAN_ITEMS / 4; ++q)
+      p[q] = make_int4(off + v[4 * q], off + v[4 * q + 1], off + v[4 * q + 2], off + v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+      if (first + j < n) out[first + j] = off + v[j];
   }
   // the last tile also writes the grand total at out[n]
-  if (threadIdx.x == 0 && base + SCAN_TILE >= n) out[n] = s_excl + total;
+  if (threadIdx.x == 0 && (long long)tile * SCAN_TILE + SCAN_TILE >= n) out[n] = s_excl + total;
 }
 
 }  // namespace

@@ -243,11 +243,27 @@ class Mesh:
         _check(lib.pm_get_mesh(self.h, _i(nv), _i(ne), None, None, None), "pm_get_mesh")
         return int(nv[0]), int(ne[0])
 
-    def get_mesh(self):
+    def get_mesh(self, out=None):
+        """Compacted mesh (xy[nv, 2], tri[ne, 3] int32, m[nv, 3]) in host arrays.
+
+        out: optional (xy, tri, m) C-contiguous arrays of those dtypes with at
+        least nv / ne rows, for example views of page-locked (pinned) memory,
+        which the device fills by direct DMA; views of their first rows are
+        returned."""
         nv, ne = self.sizes()
-        xy = np.zeros((nv, 2))
-        tri = np.zeros((ne, 3), np.int32)
-        m = np.zeros((nv, 3))
+        if out is None:
+            xy = np.empty((nv, 2))
+            tri = np.empty((ne, 3), np.int32)
+            m = np.empty((nv, 3))
+        else:
+            bxy, btri, bm = out
+            for arr, rows, cols, dt in ((bxy, nv, 2, np.float64), (btri, ne, 3, np.int32),
+                                        (bm, nv, 3, np.float64)):
+                if (arr.dtype != dt or arr.ndim != 2 or arr.shape[1] != cols
+                        or arr.shape[0] < rows or not arr.flags.c_contiguous):
+                    raise ValueError(f"output array needs shape (>={rows}, {cols}), dtype {dt}, "
+                                     "C order")
+            xy, tri, m = bxy[:nv], btri[:ne], bm[:nv]
         a = np.zeros(1, np.int32)
         b = np.zeros(1, np.int32)
         _check(lib.pm_get_mesh(self.h, _i(a), _i(b), _d(xy), _i(tri), _d(m)), "pm_get_mesh")

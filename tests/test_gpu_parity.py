@@ -75,6 +75,26 @@ def test_small_uniform_adapt_bit_exact():
     assert g.sizes() == (3281, 6400)
 
 
+def test_get_mesh_into_pinned_buffers():
+    """get_mesh(out=...) into larger page-locked arrays returns the same mesh
+    as get_mesh() into fresh arrays, as views of the buffers' first rows."""
+    torch = pytest.importorskip("torch")
+    w = inputs.psi_workload(17, 3000, True, 21)
+    g = pm.Mesh.from_host(w.xy, w.tri, device=0)
+    g.set_metric(w.m)
+    g.adapt(gp(21))
+    ref = g.get_mesh()
+    cap = 2 * ref[1].shape[0] + 7
+    out = (torch.empty((cap, 2), dtype=torch.float64).pin_memory().numpy(),
+           torch.empty((cap, 3), dtype=torch.int32).pin_memory().numpy(),
+           torch.empty((cap, 3), dtype=torch.float64).pin_memory().numpy())
+    got = g.get_mesh(out=out)
+    assert_same_mesh(got, ref, "pinned output")
+    assert got[0].ctypes.data == out[0].ctypes.data and got[1].ctypes.data == out[1].ctypes.data
+    with pytest.raises(ValueError):
+        g.get_mesh(out=(out[0][:3], out[1], out[2]))
+
+
 @pytest.mark.parametrize("n,T,seed", [(9, 400, 5), (17, 3000, 21), (25, 8000, 22), (33, 20000, 2),
                                       (65, 100000, 2)])
 def test_psi_adapt_bit_exact(n, T, seed):
