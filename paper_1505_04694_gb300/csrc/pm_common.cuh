@@ -57,11 +57,13 @@ struct Store {
   int* NE;
   int* NElen;
   // Change stamps: touch[v] is the (odd) round stamp of the last change of
-  // v's rows or position; evc/evs/evm/evr are the (even) round tags of v's
-  // last collapse / flip / smoothing / split evaluation.  An evaluation whose
-  // inputs (v, its rows, its neighbours' rows and positions) carry no newer
-  // stamp would give the same answer again.
+  // v's rows or position; ntouch[v] the stamp of the last change of a vertex
+  // that was v's neighbour after that change; evc/evs/evm/evr are the (even)
+  // round tags of v's last collapse / flip / smoothing / split evaluation.
+  // An evaluation whose inputs (v, its rows, its neighbours' rows and
+  // positions) carry no newer stamp would give the same answer again.
   int* touch;
+  int* ntouch;
   int* evc;
   int* evs;
   int* evm;

@@ -58,10 +58,16 @@ struct Work {
   int* counts = nullptr;           // device counters (see CountIdx)
 };
 
+// The per-round counters sit between the two dirty-list counts so that one
+// memset clears them together with the next round's list (zero_round).
 enum CountIdx {
-  CN_D0 = 0, CN_D1 = 1, CN_C = 2, CN_S = 3, CN_A = 4, CN_P = 5, CN_E = 6, CN_I = 7, CN_I2 = 8,
-  CN_EL = 9, CN_CL = 10, CN_DONE = 11, CN_NUM = 12
+  CN_D0 = 0, CN_C = 1, CN_S = 2, CN_A = 3, CN_E = 4, CN_I = 5, CN_I2 = 6, CN_D1 = 7,
+  CN_P = 8, CN_EL = 9, CN_CL = 10, CN_DONE = 11,
+  CN_RES = 12,  // persistent rounds: rounds run, list index after, pass complete (3)
+  CN_BAR = 15,  // persistent rounds: grid barrier words (2)
+  CN_NUM = 18
 };
+constexpr int cn_list(int i) { return i == 0 ? CN_D0 : CN_D1; }
 
 // Everything the library keeps on the device for a set of meshes.
 struct MeshSet {

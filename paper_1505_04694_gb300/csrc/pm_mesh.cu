@@ -98,6 +98,7 @@ __global__ void k_relayout_v(Store A, Store B) {
     B.M[ns] = A.M[s];
     B.vflag[ns] = A.vflag[s];
     B.touch[ns] = A.touch[s];
+    B.ntouch[ns] = A.ntouch[s];
     B.evc[ns] = A.evc[s];
     B.evs[ns] = A.evs[s];
     B.evm[ns] = A.evm[s];
@@ -345,6 +346,7 @@ __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) 
     B.M[ns] = A.M[s];
     B.vflag[ns] = A.vflag[s];
     B.touch[ns] = A.touch[s];
+    B.ntouch[ns] = A.ntouch[s];
     B.evc[ns] = A.evc[s];
     B.evs[ns] = A.evs[s];
     B.evm[ns] = A.evm[s];
@@ -493,6 +495,7 @@ static void carve_store(Carver& cv, Store& S) {
   cv.add(&S.NE, V * W);
   cv.add(&S.NElen, V);
   cv.add(&S.touch, V);
+  cv.add(&S.ntouch, V);
   cv.add(&S.evc, V);
   cv.add(&S.evs, V);
   cv.add(&S.evm, V);
@@ -790,6 +793,7 @@ int renumber(MeshSet& m) {
   std::swap(m.S.NE, m.B.NE);
   std::swap(m.S.NElen, m.B.NElen);
   std::swap(m.S.touch, m.B.touch);
+  std::swap(m.S.ntouch, m.B.ntouch);
   std::swap(m.S.evc, m.B.evc);
   std::swap(m.S.evs, m.B.evs);
   std::swap(m.S.evm, m.B.evm);

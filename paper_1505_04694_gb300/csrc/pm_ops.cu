@@ -17,6 +17,8 @@
 // in device memory, so a round needs no host round trip until the candidate
 // count is read to decide termination.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "pm_internal.cuh"
 
@@ -95,17 +97,20 @@ __device__ __forceinline__ void refresh_ball_quality(const Store& S, int vb, int
 
 // Inputs of v's evaluation unchanged since tag `et`?  Evaluations read v's
 // rows, the elements and vertices of its ball and the rows and positions of
-// its neighbours; every change to those stamps v or a neighbour.  Only
+// its neighbours; every change to those stamps v (touch) or, for a change of
+// a neighbour x, every vertex adjacent to x after the change (ntouch).  An
+// edge (v, x) that exists now existed at x's last change (adding it would
+// have changed x again), so ntouch[v] covers every current neighbour.  Only
 // evaluations newer than `lo` count.
 __device__ __forceinline__ bool unchanged(const Store& S, int v, int vb, int et, int lo) {
-  if (et <= lo) return false;
-  if (S.touch[v] > et) return false;
-  const int* nn = S.NN + (size_t)v * S.W;
-  int nnl = S.NNlen[v];
-  bool same = true;
+  return et > lo && S.touch[v] <= et && S.ntouch[v] <= et;
+}
+
+// Stamps the neighbours in `row` (local ids) after a change of their vertex.
+__device__ __forceinline__ void stamp_neighbours(const Store& S, const int* row, int len, int vb,
+                                                 int stamp) {
 #pragma unroll 4
-  for (int k = 0; k < nnl; ++k) same &= S.touch[vb + nn[k]] <= et;
-  return same;
+  for (int k = 0; k < len; ++k) S.ntouch[vb + row[k]] = stamp;
 }
 
 // ---- worklist initialisation ---------------------------------------------------
@@ -324,9 +329,10 @@ __device__ __forceinline__ CoarsenCtx coarsen_ctx(const Store& S, int v, MeshCtx
 // checks every listed vertex's best candidate (one work item each), and a
 // last pass goes through the remaining candidates of the vertices whose best
 // one failed.
-__global__ void k_coarsen_scan(Store S, const int* D, const int* nDp, int* target, int* cand,
-                               int* ncand, int* C, int* nC, int* cmark, int tag, int pass0,
-                               int2* W0, int* nW0) {
+__device__ __forceinline__ void coarsen_scan_phase(Store S, const int* D, const int* nDp,
+                                                   int* target, int* cand, int* ncand, int* C,
+                                                   int* nC, int* cmark, int tag, int pass0,
+                                                   int2* W0, int* nW0) {
   const int n = *nDp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -354,9 +360,16 @@ __global__ void k_coarsen_scan(Store S, const int* D, const int* nDp, int* targe
   }
 }
 
-__global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2* Wout,
-                                int* nWout, int* target, const int* cand, const int* ncand,
-                                int* C, int* nC, int* cmark, int tag, int last) {
+__global__ void k_coarsen_scan(Store S, const int* D, const int* nDp, int* target, int* cand,
+                               int* ncand, int* C, int* nC, int* cmark, int tag, int pass0,
+                               int2* W0, int* nW0) {
+  coarsen_scan_phase(S, D, nDp, target, cand, ncand, C, nC, cmark, tag, pass0, W0, nW0);
+}
+
+__device__ __forceinline__ void coarsen_check_phase(Store S, const int2* Win, const int* nWin,
+                                                    int2* Wout, int* nWout, int* target,
+                                                    const int* cand, const int* ncand, int* C,
+                                                    int* nC, int* cmark, int tag, int last) {
   const int n = *nWin;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -388,6 +401,12 @@ __global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2*
     warp_append(found, v, C, nC);
     if (!last) warp_append_t(next, make_int2(v, k + 1), Wout, nWout);
   }
+}
+
+__global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2* Wout, int* nWout,
+                                int* target, const int* cand, const int* ncand, int* C, int* nC,
+                                int* cmark, int tag, int last) {
+  coarsen_check_phase(S, Win, nWin, Wout, nWout, target, cand, ncand, C, nC, cmark, tag, last);
 }
 
 // Apply the collapses of S: elements containing edge (v, w) die, the other
@@ -443,10 +462,11 @@ __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v
 // One round's independent set and its collapses: a winner applies its
 // collapse at once (no other vertex of the round reads what a collapse
 // writes); losers stay dirty for the next round.
-__global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
-                                       int* smark, int tag, const int* target, int* A, int* nA,
-                                       int* amark, int* Dn, int* nDn, int* dmark,
-                                       unsigned* done) {
+__device__ __forceinline__ void coarsen_select_apply_phase(Store S, const int* C, const int* nCp,
+                                                           const int* cmark, int* smark, int tag,
+                                                           const int* target, int* A, int* nA,
+                                                           int* amark, int* Dn, int* nDn,
+                                                           int* dmark) {
   const int n = *nCp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -461,6 +481,12 @@ __global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, co
     warp_append(lose, v, Dn, nDn);
     coarsen_apply_one(S, win, v, target, A, nA, amark, Dn, nDn, dmark, tag);
   }
+}
+
+__global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
+                                       int* smark, int tag, const int* target, int* A, int* nA,
+                                       int* amark, int* Dn, int* nDn, int* dmark, unsigned* done) {
+  coarsen_select_apply_phase(S, C, nCp, cmark, smark, tag, target, A, nA, amark, Dn, nDn, dmark);
   round_done(S, done);
 }
 
@@ -468,8 +494,9 @@ __global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, co
 //   NN(u) <- (NN(u) minus collapsed neighbours) + their targets, and when u is
 //            the target of x: + NN(x) minus u;
 //   NE(u) <- live elements of NE(u) + (when u is the target of x) NE(x).
-__global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const int* target,
-                                 const int* smark, int tag, DevStatus* st) {
+__device__ __forceinline__ void coarsen_commit_phase(Store S, const int* A, const int* nAp,
+                                                     const int* target, const int* smark, int tag,
+                                                     DevStatus* st) {
   const int n = *nAp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int u = A[i];
@@ -526,7 +553,13 @@ __global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const in
     for (int k = 0; k < ne2; ++k) we[k] = eb[k];
     S.NNlen[u] = nn2;
     S.NElen[u] = ne2;
+    stamp_neighbours(S, nb, nn2, c.vb, tag + 1);
   }
+}
+
+__global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const int* target,
+                                 const int* smark, int tag, DevStatus* st) {
+  coarsen_commit_phase(S, A, nAp, target, smark, tag, st);
 }
 
 // ---- swapping (Sec. 2.4.3) ------------------------------------------------------
@@ -550,9 +583,10 @@ __device__ __forceinline__ void append_item(bool pred, int2 val, int2* list, int
 // Pass 1 (per dirty vertex): reuse an unchanged earlier result, or list the
 // vertex's interior edges whose two elements' cached minimum quality is below
 // q_thresh and whose flip would not duplicate an edge.
-__global__ void k_swap_scan(Store S, const int* D, const int* nDp, const int4* opA, int* C,
-                            int* nC, int* cmark, int tag, int pass0, int* E, int* nE,
-                            int2* items, int* nI, int icap, double* gains, DevStatus* st) {
+__device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int* nDp,
+                                                const int4* opA, int* C, int* nC, int* cmark,
+                                                int tag, int pass0, int* E, int* nE, int2* items,
+                                                int* nI, int icap, double* gains, DevStatus* st) {
   const int n = *nDp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -632,9 +666,16 @@ __global__ void k_swap_scan(Store S, const int* D, const int* nDp, const int4* o
   }
 }
 
+__global__ void k_swap_scan(Store S, const int* D, const int* nDp, const int4* opA, int* C, int* nC,
+                            int* cmark, int tag, int pass0, int* E, int* nE, int2* items, int* nI,
+                            int icap, double* gains, DevStatus* st) {
+  swap_scan_phase(S, D, nDp, opA, C, nC, cmark, tag, pass0, E, nE, items, nI, icap, gains, st);
+}
+
 // Pass 2 (per listed edge, dense FP64): both flipped elements counter-
 // clockwise and their minimum quality above the old minimum -> the gain.
-__global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* gains) {
+__device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, const int* nIp,
+                                                double* gains) {
   const int n = *nIp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int2 it = items[i];
@@ -665,10 +706,15 @@ __global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* 
   }
 }
 
+__global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* gains) {
+  swap_edge_phase(S, items, nIp, gains);
+}
+
 // Pass 3 (per evaluated vertex): largest strictly positive gain, ties to the
 // smallest w; the flip record (w, c, d, K1, K2) of the winner.
-__global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double* gains,
-                            int4* opA, int* opK2, int* C, int* nC, int* cmark, int tag) {
+__device__ __forceinline__ void swap_pick_phase(Store S, const int* E, const int* nEp,
+                                                const double* gains, int4* opA, int* opK2, int* C,
+                                                int* nC, int* cmark, int tag) {
   const int n = *nEp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -720,6 +766,11 @@ __global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double*
   }
 }
 
+__global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double* gains, int4* opA,
+                            int* opK2, int* C, int* nC, int* cmark, int tag) {
+  swap_pick_phase(S, E, nEp, gains, opA, opK2, C, nC, cmark, tag);
+}
+
 __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, const int4* opA,
                                                const int* opK2, int* A, int* nA, int* amark,
                                                int* Dn, int* nDn, int* dmark, int tag) {
@@ -767,10 +818,11 @@ __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, c
 }
 
 // One round's independent set and its flips (see k_coarsen_select_apply).
-__global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
-                                    int* smark, int tag, const int4* opA, const int* opK2, int* A,
-                                    int* nA, int* amark, int* Dn, int* nDn, int* dmark,
-                                    unsigned* done) {
+__device__ __forceinline__ void swap_select_apply_phase(Store S, const int* C, const int* nCp,
+                                                        const int* cmark, int* smark, int tag,
+                                                        const int4* opA, const int* opK2, int* A,
+                                                        int* nA, int* amark, int* Dn, int* nDn,
+                                                        int* dmark) {
   const int n = *nCp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -785,6 +837,13 @@ __global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const
     warp_append(lose, v, Dn, nDn);
     swap_apply_one(S, win, v, opA, opK2, A, nA, amark, Dn, nDn, dmark, tag);
   }
+}
+
+__global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
+                                    int* smark, int tag, const int4* opA, const int* opK2, int* A,
+                                    int* nA, int* amark, int* Dn, int* nDn, int* dmark,
+                                    unsigned* done) {
+  swap_select_apply_phase(S, C, nCp, cmark, smark, tag, opA, opK2, A, nA, amark, Dn, nDn, dmark);
   round_done(S, done);
 }
 
@@ -792,8 +851,9 @@ __global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const
 // flips of u itself and of its S neighbours (records w, c, d, K1, K2):
 //   u == v: NN -w, NE -K2;  u == w: NN -v, NE -K1;
 //   u == c: NN +d, NE +K2;  u == d: NN +c, NE +K1.
-__global__ void k_swap_commit(Store S, const int* A, const int* nAp, const int4* opA,
-                              const int* opK2, const int* smark, int tag, DevStatus* st) {
+__device__ __forceinline__ void swap_commit_phase(Store S, const int* A, const int* nAp,
+                                                  const int4* opA, const int* opK2,
+                                                  const int* smark, int tag, DevStatus* st) {
   const int n = *nAp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int u = A[i];
@@ -845,7 +905,13 @@ __global__ void k_swap_commit(Store S, const int* A, const int* nAp, const int4*
     for (int k = 0; k < ne2; ++k) ne[k] = eb[k];
     S.NNlen[u] = nn2;
     S.NElen[u] = ne2;
+    stamp_neighbours(S, nb, nn2, c.vb, tag + 1);
   }
+}
+
+__global__ void k_swap_commit(Store S, const int* A, const int* nAp, const int4* opA,
+                              const int* opK2, const int* smark, int tag, DevStatus* st) {
+  swap_commit_phase(S, A, nAp, opA, opK2, smark, tag, st);
 }
 
 // ---- smoothing (Sec. 2.4.4) -------------------------------------------------------
@@ -866,8 +932,9 @@ __device__ __forceinline__ double ball_min_quality(const Store& S, MeshCtx c, co
 // Smoothing evaluation in two passes.  Pass 1 (per pending vertex): reuse an
 // unchanged earlier result, drop vertices whose ball is already good enough
 // (cached qualities), list the rest for the full move evaluation.
-__global__ void k_smooth_scan(Store S, const int* D, const int* nDp, double4* mvM, int* C,
-                              int* nC, int* cmark, int tag, int pass0, int* E, int* nE) {
+__device__ __forceinline__ void smooth_scan_phase(Store S, const int* D, const int* nDp,
+                                                  double4* mvM, int* C, int* nC, int* cmark,
+                                                  int tag, int pass0, int* E, int* nE) {
   const int n = *nDp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -895,6 +962,11 @@ __global__ void k_smooth_scan(Store S, const int* D, const int* nDp, double4* mv
     warp_append(reuse_cand, v, C, nC);
     warp_append(eval, v, E, nE);
   }
+}
+
+__global__ void k_smooth_scan(Store S, const int* D, const int* nDp, double4* mvM, int* C, int* nC,
+                              int* cmark, int tag, int pass0, int* E, int* nE) {
+  smooth_scan_phase(S, D, nDp, mvM, C, nC, cmark, tag, pass0, E, nE);
 }
 
 // ---- tile-parallel evaluation: 8 lanes per vertex, one ball element each ----
@@ -1091,9 +1163,10 @@ __device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c
 }
 
 // Pass 2 (one 8-lane tile per listed vertex): the full quality-constrained move.
-__global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mvxy, double4* mvM,
-                              double* qball, int* C, int* nC, int* cmark, int tag,
-                              unsigned long long* work) {
+__device__ __forceinline__ void smooth_eval_phase(Store S, const int* E, const int* nEp,
+                                                  double2* mvxy, double4* mvM, double* qball,
+                                                  int* C, int* nC, int* cmark, int tag,
+                                                  unsigned long long* work) {
   const int n = *nEp;
   const Tile t = tile_of();
   const int tiles_per_block = blockDim.x / TW;
@@ -1128,6 +1201,12 @@ __global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mv
   }
 }
 
+__global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mvxy, double4* mvM,
+                              double* qball, int* C, int* nC, int* cmark, int tag,
+                              unsigned long long* work) {
+  smooth_eval_phase(S, E, nEp, mvxy, mvM, qball, C, nC, cmark, tag, work);
+}
+
 // Move the members of S; live interior neighbours become pending for the next
 // sweep (stamp pmark with the sweep tag).
 __device__ __forceinline__ void smooth_apply_one(const Store& S, bool ok, int v,
@@ -1151,6 +1230,7 @@ __device__ __forceinline__ void smooth_apply_one(const Store& S, bool ok, int v,
       for (int k = 0; k < nel; ++k) S.qK[c.eb + ne[k]] = qball[(size_t)v * S.W + k];
       nn = nn_row(S, v);
       nnl = S.NNlen[v];
+      stamp_neighbours(S, nn, nnl, vb, stamp);
     }
     count_op(S, ok, mi);
     unsigned long long take = 0;
@@ -1166,11 +1246,12 @@ __device__ __forceinline__ void smooth_apply_one(const Store& S, bool ok, int v,
 }
 
 // One round's independent set and its moves (see k_coarsen_select_apply).
-__global__ void k_smooth_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
-                                      int* smark, int tag, int* Dn, int* nDn, int* dmark,
-                                      const double2* mvxy, const double4* mvM,
-                                      const double* qball, int* P, int* nP, int* pmark, int ptag,
-                                      int stamp, unsigned* done) {
+__device__ __forceinline__ void smooth_select_apply_phase(Store S, const int* C, const int* nCp,
+                                                          const int* cmark, int* smark, int tag,
+                                                          int* Dn, int* nDn, int* dmark,
+                                                          const double2* mvxy, const double4* mvM,
+                                                          const double* qball, int* P, int* nP,
+                                                          int* pmark, int ptag, int stamp) {
   const int n = *nCp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -1185,6 +1266,15 @@ __global__ void k_smooth_select_apply(Store S, const int* C, const int* nCp, con
     warp_append(lose, v, Dn, nDn);
     smooth_apply_one(S, win, v, mvxy, mvM, qball, P, nP, pmark, ptag, stamp);
   }
+}
+
+__global__ void k_smooth_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
+                                      int* smark, int tag, int* Dn, int* nDn, int* dmark,
+                                      const double2* mvxy, const double4* mvM, const double* qball,
+                                      int* P, int* nP, int* pmark, int ptag, int stamp,
+                                      unsigned* done) {
+  smooth_select_apply_phase(S, C, nCp, cmark, smark, tag, Dn, nDn, dmark, mvxy, mvM, qball, P, nP,
+                            pmark, ptag, stamp);
   round_done(S, done);
 }
 
@@ -1281,6 +1371,7 @@ __global__ void k_opt_apply(Store S, const int* Sl, const int* nSp, double* qbal
         const int* ne = ne_row(S, v);
         int nel = S.NElen[v];
         for (int k = 0; k < nel; ++k) S.qK[c.eb + ne[k]] = qb[k];
+        stamp_neighbours(S, nn_row(S, v), S.NNlen[v], c.vb, stamp);
       }
     }
     count_op(S, moved && t.tl == 0, mi);
@@ -1564,10 +1655,12 @@ __global__ void k_refine_rows_copy(Store S, Store B, int vend, int stamp) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < vend; s += gridDim.x * blockDim.x) {
     if (S.touch[s] != stamp) continue;
     int a = B.NNlen[s], b = B.NElen[s];
-    for (int k = 0; k < a; ++k) S.NN[(size_t)s * S.W + k] = B.NN[(size_t)s * B.W + k];
+    const int* nn = B.NN + (size_t)s * B.W;
+    for (int k = 0; k < a; ++k) S.NN[(size_t)s * S.W + k] = nn[k];
     for (int k = 0; k < b; ++k) S.NE[(size_t)s * S.W + k] = B.NE[(size_t)s * B.W + k];
     S.NNlen[s] = a;
     S.NElen[s] = b;
+    stamp_neighbours(S, nn, a, S.tab.vbase[mesh_of_vslot(S, s)], stamp);
   }
 }
 
@@ -1578,6 +1671,198 @@ __global__ void k_refine_sizes(Store S, const int* vscan, const int* escan) {
   int nv = S.tab.nv[i], ne = S.tab.ne[i];
   S.tab.nv[i] = nv + (vscan[vb + nv] - vscan[vb]);
   S.tab.ne[i] = ne + (escan[eb + ne] - escan[eb]);
+}
+
+// ---- persistent rounds ------------------------------------------------------------
+//
+// Once a pass's dirty list is small, a round does little work and its cost is
+// launch and synchronisation latency.  Such rounds run back to back inside one
+// cooperative launch (every block resident): the phases are the same device
+// functions as the one-kernel-per-phase rounds, separated by a grid-wide
+// barrier, and the host reads back once when the launch ends.  The launch
+// returns when a round finds no candidate (the pass is complete), when the
+// next round's list outgrows `limit`, on a row overflow or an error, or after
+// `max_rounds` rounds.
+
+constexpr unsigned long long kBarrierNs = 2000000000ull;  // a barrier wait gives up after 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
+
+// Grid-wide barrier: bar[0] counts the blocks that arrived, bar[1] is the
+// generation.  Returns false (the caller leaves the kernel) when a wait ran
+// out (PM_ERR_TIMEOUT is recorded) or when any phase recorded an error.
+__device__ bool grid_barrier(unsigned* bar, DevStatus* st) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen_p = bar + 1;
+    const unsigned gen = *gen_p;
+    int ok = 1;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen_p == gen) {
+        if (ld_volatile(&st->err) != 0) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > kBarrierNs) {
+          set_err(st, PM_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok && ld_volatile(&st->err) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct RoundArgs {
+  Store S;
+  Work w;
+  DevStatus* st;
+  unsigned* bar;       // barrier words (2)
+  int* res;            // out: rounds run, list index after, pass complete
+  int cur;             // list index the first round reads
+  int tag0;            // tag of the first round (then +2 per round)
+  int pass0;
+  int max_rounds;
+  int limit;           // leave when the next list holds more entries
+  int icap;            // swap: capacity of the item list
+  int ptag;            // smoothing: stamp of the next sweep's list
+  unsigned long long* work;  // smoothing: counted FP64 work (profiling) or null
+};
+
+// Counters of round r (C, S, A, E, I, I2 and the list it fills), cleared by
+// block 0 before the round's first barrier.
+__device__ __forceinline__ void clear_round(int* cnt, int nxt) {
+  if (blockIdx.x == 0 && threadIdx.x < 7) cnt[(nxt == 0 ? CN_D0 : CN_C) + threadIdx.x] = 0;
+}
+
+__device__ __forceinline__ void finish_rounds(const RoundArgs& a, int r, int cur, bool complete) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.res[0] = r;
+    a.res[1] = cur;
+    a.res[2] = complete ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_coarsen_rounds(RoundArgs a) {
+  const Work& w = a.w;
+  int* cnt = w.counts;
+  int cur = a.cur, r = 0;
+  bool complete = false;
+  while (r < a.max_rounds) {
+    const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
+    clear_round(cnt, nxt);
+    if (!grid_barrier(a.bar, a.st)) return;
+    coarsen_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.target, w.cand, w.ncand, w.C,
+                       cnt + CN_C, w.cmark, tag, a.pass0, w.items, cnt + CN_I);
+    if (!grid_barrier(a.bar, a.st)) return;
+    coarsen_check_phase(a.S, w.items, cnt + CN_I, w.items2, cnt + CN_I2, w.target, w.cand,
+                        w.ncand, w.C, cnt + CN_C, w.cmark, tag, 0);
+    if (!grid_barrier(a.bar, a.st)) return;
+    coarsen_check_phase(a.S, w.items2, cnt + CN_I2, w.items, cnt + CN_I, w.target, w.cand,
+                        w.ncand, w.C, cnt + CN_C, w.cmark, tag, 1);
+    if (!grid_barrier(a.bar, a.st)) return;
+    coarsen_select_apply_phase(a.S, w.C, cnt + CN_C, w.cmark, w.smark, tag, w.target, w.A,
+                               cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
+    if (!grid_barrier(a.bar, a.st)) return;
+    const int nC = ld_volatile(cnt + CN_C), nD = ld_volatile(cnt + cn_list(nxt));
+    advance_rounds(a.S);
+    coarsen_commit_phase(a.S, w.A, cnt + CN_A, w.target, w.smark, tag, a.st);
+    if (!grid_barrier(a.bar, a.st)) return;
+    ++r;
+    if (nC == 0) {
+      complete = true;
+      break;
+    }
+    cur = nxt;
+    if (ld_volatile(&a.st->overflow) != 0 || nD > a.limit) break;
+  }
+  finish_rounds(a, r, cur, complete);
+}
+
+__global__ void __launch_bounds__(256) k_swap_rounds(RoundArgs a) {
+  const Work& w = a.w;
+  int* cnt = w.counts;
+  int cur = a.cur, r = 0;
+  bool complete = false;
+  while (r < a.max_rounds) {
+    const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
+    clear_round(cnt, nxt);
+    if (!grid_barrier(a.bar, a.st)) return;
+    swap_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.opA, w.C, cnt + CN_C, w.cmark, tag,
+                    a.pass0, w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st);
+    if (!grid_barrier(a.bar, a.st)) return;
+    swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains);
+    if (!grid_barrier(a.bar, a.st)) return;
+    swap_pick_phase(a.S, w.E, cnt + CN_E, w.gains, w.opA, w.opK2, w.C, cnt + CN_C, w.cmark, tag);
+    if (!grid_barrier(a.bar, a.st)) return;
+    swap_select_apply_phase(a.S, w.C, cnt + CN_C, w.cmark, w.smark, tag, w.opA, w.opK2, w.A,
+                            cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
+    if (!grid_barrier(a.bar, a.st)) return;
+    const int nC = ld_volatile(cnt + CN_C), nD = ld_volatile(cnt + cn_list(nxt));
+    advance_rounds(a.S);
+    swap_commit_phase(a.S, w.A, cnt + CN_A, w.opA, w.opK2, w.smark, tag, a.st);
+    if (!grid_barrier(a.bar, a.st)) return;
+    ++r;
+    if (nC == 0) {
+      complete = true;
+      break;
+    }
+    cur = nxt;
+    if (ld_volatile(&a.st->overflow) != 0 || nD > a.limit) break;
+  }
+  finish_rounds(a, r, cur, complete);
+}
+
+__global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
+  const Work& w = a.w;
+  int* cnt = w.counts;
+  int cur = a.cur, r = 0;
+  bool complete = false;
+  while (r < a.max_rounds) {
+    const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
+    clear_round(cnt, nxt);
+    if (!grid_barrier(a.bar, a.st)) return;
+    smooth_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.mvM, w.C, cnt + CN_C, w.cmark, tag,
+                      a.pass0, w.E, cnt + CN_E);
+    if (!grid_barrier(a.bar, a.st)) return;
+    smooth_eval_phase(a.S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, cnt + CN_C, w.cmark, tag,
+                      a.work);
+    if (!grid_barrier(a.bar, a.st)) return;
+    smooth_select_apply_phase(a.S, w.C, cnt + CN_C, w.cmark, w.smark, tag, w.D[nxt],
+                              cnt + cn_list(nxt), w.dmark, w.mvxy, w.mvM, w.gains, w.P,
+                              cnt + CN_P, w.pmark, a.ptag, tag + 1);
+    if (!grid_barrier(a.bar, a.st)) return;
+    const int nC = ld_volatile(cnt + CN_C), nD = ld_volatile(cnt + cn_list(nxt));
+    advance_rounds(a.S);
+    // every block has read the counters before block 0 clears them
+    if (!grid_barrier(a.bar, a.st)) return;
+    ++r;
+    if (nC == 0) {
+      complete = true;
+      break;
+    }
+    cur = nxt;
+    if (nD > a.limit) break;
+  }
+  finish_rounds(a, r, cur, complete);
 }
 
 // ---- host helpers --------------------------------------------------------------
@@ -1604,10 +1889,115 @@ void zero_counts(MeshSet& m, int first, int num) {
   cudaMemsetAsync(m.w.counts + first, 0, num * sizeof(int), m.stream);
 }
 
+// The counters of a new round (C, S, A, E, I, I2) and of the list it fills
+// (D[nxt]); the list it reads keeps its count.
+void zero_round(MeshSet& m, int nxt) {
+  static_assert(CN_D0 == 0 && CN_C == 1 && CN_I2 == 6 && CN_D1 == 7, "counter layout");
+  zero_counts(m, nxt == 0 ? CN_D0 : CN_C, 7);
+}
+
+// A row overflow leaves some rows unwritten and the neighbour stamps of the
+// rebuilt rows unset: rows are rebuilt from the elements and no evaluation
+// made before is reused (every lo_* and the callers' pass start move to now).
+int after_overflow(MeshSet& m) {
+  int err = rebuild_adjacency(m, false, nullptr);
+  m.lo_coarsen = m.lo_swap = m.lo_refine = m.tag;
+  return err;
+}
+
 int after_round(MeshSet& m, const RoundIO& io) {
   if (io.err) return io.err;
-  if (io.overflow) return rebuild_adjacency(m, false, nullptr);
+  if (io.overflow) return after_overflow(m);
   return PM_OK;
+}
+
+// Persistent rounds take over once a pass's list holds at most this many
+// vertices (and hand back when the next list outgrows it).
+constexpr int kRoundsLimit = 8192;
+constexpr int kRoundsThreads = 256;
+
+// Blocks of a cooperative launch of the persistent round kernels on this
+// device (one per SM when every kernel fits, else 0: rounds stay one kernel
+// per phase).
+int rounds_grid(MeshSet& m) {
+  static std::mutex mu;
+  static int cache[64];
+  static bool known[64];
+  std::lock_guard<std::mutex> lk(mu);
+  const int dev = m.device;
+  if (dev < 0 || dev >= 64) return 0;
+  if (!known[dev]) {
+    int coop = 0, blocks = 1 << 30;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const void* ks[] = {(const void*)k_coarsen_rounds, (const void*)k_swap_rounds,
+                        (const void*)k_smooth_rounds};
+    for (const void* k : ks) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kRoundsThreads, 0) != cudaSuccess)
+        b = 0;
+      blocks = std::min(blocks, b);
+    }
+    cudaGetLastError();
+    cache[dev] = (coop && blocks >= 1) ? m.num_sms : 0;
+    known[dev] = true;
+  }
+  return cache[dev];
+}
+
+RoundArgs round_args(MeshSet& m, int cur, int pass0, long long max_rounds) {
+  RoundArgs a;
+  a.S = m.S;
+  a.w = m.w;
+  a.st = m.st;
+  a.bar = (unsigned*)(m.w.counts + CN_BAR);
+  a.res = m.w.counts + CN_RES;
+  a.cur = cur;
+  a.tag0 = m.tag + 2;
+  a.pass0 = pass0;
+  a.max_rounds = (int)std::min<long long>(max_rounds, 1 << 30);
+  a.limit = kRoundsLimit;
+  a.icap = 0;
+  a.ptag = 0;
+  a.work = nullptr;
+  return a;
+}
+
+struct RoundsOut {
+  int rounds = 0;    // rounds run, the last one empty when the pass completed
+  int cur = 0;       // list the next round reads
+  int complete = 0;
+  RoundIO io{0, 0, 0};
+};
+
+// One cooperative launch of persistent rounds, then the read-back of every
+// counter and the status.  Advances the tag past the rounds that ran.
+int run_rounds(MeshSet& m, const void* kernel, const char* name, RoundArgs& a, RoundsOut& out) {
+  void* args[] = {&a};
+  __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED);
+  int slot = g_prof_on ? prof_begin(name, m.stream) : -1;
+  cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(rounds_grid(m)),
+                                              dim3(kRoundsThreads), args, 0, m.stream);
+  if (slot >= 0) prof_end(slot, m.stream);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("cooperative launch: ") + cudaGetErrorString(e));
+    return PM_ERR_CUDA;
+  }
+  out.io = read_round(m);
+  if (out.io.err) return out.io.err;
+  out.rounds = m.hcounts[CN_RES];
+  out.cur = m.hcounts[CN_RES + 1];
+  out.complete = m.hcounts[CN_RES + 2];
+  m.tag += 2 * out.rounds;
+  return PM_OK;
+}
+
+// Entries of the list a pass starts from (one read-back).
+int list_count(MeshSet& m, int idx, int* n) {
+  cudaMemcpyAsync(m.hcounts + idx, m.w.counts + idx, sizeof(int), cudaMemcpyDeviceToHost,
+                  m.stream);
+  int err = sync_status(m);
+  *n = m.hcounts[idx];
+  return err;
 }
 
 }  // namespace
@@ -1634,20 +2024,40 @@ cudaError_t fetch_ops(MeshSet& m, std::vector<unsigned long long>& ops) {
 int op_coarsen(MeshSet& m, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vused);
-  const int pass0 = m.tag;
+  int pass0 = m.tag;
+  const bool persist = rounds_grid(m) > 0;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evc,
             m.lo_coarsen);
+  int nlist = -1;  // entries of the list the next round reads, when known
+  if (persist) {
+    int err = list_count(m, CN_D0, &nlist);
+    if (err) return err;
+  }
   int cur = 0;
   bool complete = false;
-  for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
+  for (long long nr = 0; max_rounds == 0 || nr < max_rounds;) {
+    if (m.lo_coarsen > pass0) pass0 = m.lo_coarsen;  // rows were rebuilt after an overflow
+    if (persist && nlist >= 0 && nlist <= kRoundsLimit) {
+      RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
+      RoundsOut o;
+      int err = run_rounds(m, (const void*)k_coarsen_rounds, "k_coarsen_rounds", a, o);
+      if (err) return err;
+      nr += o.rounds - o.complete;
+      cur = o.cur;
+      if (o.complete) {
+        complete = true;
+        break;
+      }
+      if ((err = after_round(m, o.io))) return err;
+      nlist = m.hcounts[cn_list(cur)];
+      continue;
+    }
     int tag = (m.tag += 2);
     int nxt = 1 - cur;
-    zero_counts(m, CN_C, 3);
-    zero_counts(m, nxt, 1);
-    zero_counts(m, CN_I, 2);
-    PM_LAUNCH(k_coarsen_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.target,
-              w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, pass0, w.items,
+    zero_round(m, nxt);
+    PM_LAUNCH(k_coarsen_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
+              w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, pass0, w.items,
               w.counts + CN_I);
     // one dense wave checking every vertex's best candidate, then the
     // remaining candidates of the vertices whose best one failed
@@ -1656,8 +2066,8 @@ int op_coarsen(MeshSet& m, int max_rounds) {
     PM_LAUNCH(k_coarsen_check, gv, BLOCK, 0, m.stream, m.S, w.items2, w.counts + CN_I2, w.items,
               w.counts + CN_I, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 1);
     PM_LAUNCH(k_coarsen_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
-              w.smark, tag, w.target, w.A, w.counts + CN_A, w.amark, w.D[nxt], w.counts + nxt,
-              w.dmark, (unsigned*)(w.counts + CN_DONE));
+              w.smark, tag, w.target, w.A, w.counts + CN_A, w.amark, w.D[nxt],
+              w.counts + cn_list(nxt), w.dmark, (unsigned*)(w.counts + CN_DONE));
     PM_LAUNCH(k_coarsen_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target,
               w.smark, tag, m.st);
     RoundIO io = read_round(m);
@@ -1669,6 +2079,8 @@ int op_coarsen(MeshSet& m, int max_rounds) {
     int err = after_round(m, io);
     if (err) return err;
     cur = nxt;
+    ++nr;
+    nlist = m.hcounts[cn_list(cur)];
   }
   if (!complete) m.lo_coarsen = m.tag;  // some vertex may still have a collapse
   return PM_OK;
@@ -1678,28 +2090,50 @@ int op_coarsen(MeshSet& m, int max_rounds) {
 int op_swap(MeshSet& m, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vused);
-  const int pass0 = m.tag;
+  int pass0 = m.tag;
+  const int icap = m.S.vslots * 6 + 64;
+  const bool persist = rounds_grid(m) > 0;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evs,
             m.lo_swap);
+  int nlist = -1;
+  if (persist) {
+    int err = list_count(m, CN_D0, &nlist);
+    if (err) return err;
+  }
   int cur = 0;
   bool complete = false;
-  for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
+  for (long long nr = 0; max_rounds == 0 || nr < max_rounds;) {
+    if (m.lo_swap > pass0) pass0 = m.lo_swap;  // rows were rebuilt after an overflow
+    if (persist && nlist >= 0 && nlist <= kRoundsLimit) {
+      RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
+      a.icap = icap;
+      RoundsOut o;
+      int err = run_rounds(m, (const void*)k_swap_rounds, "k_swap_rounds", a, o);
+      if (err) return err;
+      nr += o.rounds - o.complete;
+      cur = o.cur;
+      if (o.complete) {
+        complete = true;
+        break;
+      }
+      if ((err = after_round(m, o.io))) return err;
+      nlist = m.hcounts[cn_list(cur)];
+      continue;
+    }
     int tag = (m.tag += 2);
     int nxt = 1 - cur;
-    zero_counts(m, CN_C, 3);
-    zero_counts(m, nxt, 1);
-    zero_counts(m, CN_E, 2);
-    PM_LAUNCH(k_swap_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.opA, w.C,
-              w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E, w.items,
-              w.counts + CN_I, m.S.vslots * 6 + 64, w.gains, m.st);
+    zero_round(m, nxt);
+    PM_LAUNCH(k_swap_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur), w.opA,
+              w.C, w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E, w.items,
+              w.counts + CN_I, icap, w.gains, m.st);
     PM_LAUNCH(k_swap_edge, grid_for(m, 6LL * m.S.vslots, 16), BLOCK, 0, m.stream, m.S, w.items,
               w.counts + CN_I, w.gains);
     PM_LAUNCH(k_swap_pick, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
               w.opK2, w.C, w.counts + CN_C, w.cmark, tag);
     PM_LAUNCH(k_swap_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
               w.smark, tag, w.opA, w.opK2, w.A, w.counts + CN_A, w.amark, w.D[nxt],
-              w.counts + nxt, w.dmark, (unsigned*)(w.counts + CN_DONE));
+              w.counts + cn_list(nxt), w.dmark, (unsigned*)(w.counts + CN_DONE));
     PM_LAUNCH(k_swap_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2,
               w.smark, tag, m.st);
     RoundIO io = read_round(m);
@@ -1711,6 +2145,8 @@ int op_swap(MeshSet& m, int max_rounds) {
     int err = after_round(m, io);
     if (err) return err;
     cur = nxt;
+    ++nr;
+    nlist = m.hcounts[cn_list(cur)];
   }
   if (!complete) m.lo_swap = m.tag;
   return PM_OK;
@@ -1792,7 +2228,7 @@ int op_refine(MeshSet& m, int max_rounds) {
     int err = sync_status(m);
     if (err) return err;
     if (m.hst->overflow) {  // a row outgrew W: rebuild every row with wider ones
-      err = rebuild_adjacency(m, false, nullptr);
+      err = after_overflow(m);
       if (err) return err;
     }
   }
@@ -1805,8 +2241,14 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vused);
   const int pass0 = m.tag;
+  const bool persist = rounds_grid(m) > 0;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0, nullptr, 0);
+  int nlist = -1;
+  if (persist) {
+    int err = list_count(m, CN_D0, &nlist);
+    if (err) return err;
+  }
   long long nr = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int ptag = (m.tag += 2);  // stamp of the next sweep's pending list
@@ -1814,31 +2256,45 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
     int cur = 0;
     bool moved = false;
     while (max_rounds == 0 || nr < max_rounds) {
+      if (persist && nlist >= 0 && nlist <= kRoundsLimit) {
+        RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
+        a.ptag = ptag;
+        RoundsOut o;
+        int err = run_rounds(m, (const void*)k_smooth_rounds, "k_smooth_rounds", a, o);
+        if (err) return err;
+        nr += o.rounds - o.complete;
+        if (o.rounds - o.complete > 0) moved = true;
+        cur = o.cur;
+        nlist = m.hcounts[cn_list(cur)];
+        if (o.complete) break;
+        continue;
+      }
       int tag = (m.tag += 2);
       int nxt = 1 - cur;
-      zero_counts(m, CN_C, 2);
-      zero_counts(m, nxt, 1);
-      zero_counts(m, CN_E, 1);
-      PM_LAUNCH(k_smooth_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cur, w.mvM, w.C,
-                w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E);
+      zero_round(m, nxt);
+      PM_LAUNCH(k_smooth_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
+                w.mvM, w.C, w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E);
       PM_LAUNCH(k_smooth_eval, grid_for(m, (long long)m.S.vused * TW), BLOCK, 0, m.stream, m.S,
                 w.E, w.counts + CN_E, w.mvxy, w.mvM, w.gains, w.C, w.counts + CN_C, w.cmark, tag,
                 prof_work("k_smooth_eval"));
       PM_LAUNCH(k_smooth_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C,
-                w.cmark, w.smark, tag, w.D[nxt], w.counts + nxt, w.dmark, w.mvxy, w.mvM, w.gains,
-                w.P, w.counts + CN_P, w.pmark, ptag, tag + 1, (unsigned*)(w.counts + CN_DONE));
+                w.cmark, w.smark, tag, w.D[nxt], w.counts + cn_list(nxt), w.dmark, w.mvxy, w.mvM,
+                w.gains, w.P, w.counts + CN_P, w.pmark, ptag, tag + 1,
+                (unsigned*)(w.counts + CN_DONE));
       RoundIO io = read_round(m);
       if (io.err) return io.err;
       if (io.nC == 0) break;
       ++nr;
       moved = true;
       cur = nxt;
+      nlist = m.hcounts[cn_list(cur)];
     }
     if (!moved) break;
     // the next sweep's pending list becomes the current list
     std::swap(w.D[0], w.P);
     cudaMemcpyAsync(w.counts + CN_D0, w.counts + CN_P, sizeof(int), cudaMemcpyDeviceToDevice,
                     m.stream);
+    nlist = m.hcounts[CN_P];
   }
   return PM_OK;
 }
