@@ -185,7 +185,7 @@ pm_status begin_call(MeshSet& m, const pm_params* P, int stride) {
   pm_status s = cuda_status(upload_tab(m), "mesh table");
   if (s) return s;
   cudaMemsetAsync(m.S.tab.r, 0, m.nmesh * sizeof(uint32_t), m.stream);
-  cudaMemsetAsync(m.S.tab.had, 0, m.nmesh * sizeof(int), m.stream);
+  cudaMemsetAsync(m.S.tab.had, 0, 2 * m.nmesh * sizeof(int), m.stream);
   cudaMemsetAsync(m.S.tab.active, 0xFF, m.nmesh * sizeof(int), m.stream);
   cudaMemsetAsync(m.st, 0, sizeof(DevStatus), m.stream);
   zero_ops(m);

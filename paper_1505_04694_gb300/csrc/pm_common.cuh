@@ -30,7 +30,7 @@ struct MeshTab {
   int* ne;      // used element slots
   uint32_t* seed;
   uint32_t* r;  // round counter of the current call
-  int* had;     // 1 when the mesh formed candidates this round
+  int* had;     // 1 when the mesh formed candidates this round (2 * nmesh)
   int* active;  // mesh takes part in the current phase
   unsigned long long* ops;       // operations applied in the current call
   unsigned long long* iter_ops;  // operations of the current outer iteration

@@ -64,7 +64,8 @@ enum CountIdx {
   CN_D0 = 0, CN_C = 1, CN_S = 2, CN_A = 3, CN_E = 4, CN_I = 5, CN_I2 = 6, CN_D1 = 7,
   CN_P = 8, CN_EL = 9, CN_CL = 10, CN_DONE = 11,
   CN_RES = 12,  // persistent rounds: rounds run, list index after, pass complete (3)
-  CN_BAR = 15,  // persistent rounds: grid barrier words (2)
+  CN_BAR = 15,  // persistent rounds: grid barrier arrivals
+  CN_C2 = 16,   // persistent rounds: candidates of odd rounds
   CN_NUM = 18
 };
 constexpr int cn_list(int i) { return i == 0 ? CN_D0 : CN_D1; }

@@ -528,7 +528,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   Carver cv;
   carve_store(cv, S);
   carve_store(cv, m.B);
-  size_t tab_bytes = (size_t)n * (6 * sizeof(int) + 2 * sizeof(uint32_t) + 2 * sizeof(int) +
+  size_t tab_bytes = (size_t)n * (6 * sizeof(int) + 2 * sizeof(uint32_t) + 3 * sizeof(int) +
                                   2 * sizeof(unsigned long long) + 3 * sizeof(double) +
                                   sizeof(double4)) + 64;
   char* t = nullptr;
@@ -588,7 +588,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   T.ne = (int*)t; t += n * sizeof(int);
   T.seed = (uint32_t*)t; t += n * sizeof(uint32_t);
   T.r = (uint32_t*)t; t += n * sizeof(uint32_t);
-  T.had = (int*)t; t += n * sizeof(int);
+  T.had = (int*)t; t += 2 * n * sizeof(int);  // two sets: persistent rounds alternate
   T.active = (int*)t; t += n * sizeof(int);
   m.B.tab = T;
   if (!m.st) {

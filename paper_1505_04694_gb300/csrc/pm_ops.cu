@@ -409,6 +409,47 @@ __global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2*
   coarsen_check_phase(S, Win, nWin, Wout, nWout, target, cand, ncand, C, nC, cmark, tag, last);
 }
 
+// One thread per listed vertex, listing and checking at once (persistent
+// rounds): reuse or re-evaluate, then the candidates in order until one is a
+// valid collapse.  Same results as coarsen_scan_phase and the two check passes.
+__device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const int* nDp,
+                                                   int* target, int* cand, int* ncand, int* C,
+                                                   int* nC, int* cmark, int tag, int pass0) {
+  const int n = *nDp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int v = 0;
+    bool found = false;
+    if (i < n) {
+      v = D[i];
+      MeshCtx c = ctx_of(S, v);
+      if (unchanged(S, v, c.vb, S.evc[v], pass0)) {
+        found = target[v] >= 0;
+      } else {
+        S.evc[v] = tag;
+        int* cv = cand + (size_t)v * S.W;
+        int nc = coarsen_candidates(S, v, c, cv);
+        ncand[v] = nc;
+        if (nc > 0) {
+          CoarsenCtx x = coarsen_ctx(S, v, c);
+          const double4 band = S.tab.band[c.mi];
+          for (int k = 0; k < nc && !found; ++k)
+            if (collapse_valid(x, cv[k], band)) {
+              found = true;
+              target[v] = cv[k];
+            }
+        }
+        if (!found) target[v] = -1;
+      }
+      if (found) {
+        cmark[v] = tag;
+        S.tab.had[c.mi] = 1;
+      }
+    }
+    warp_append(found, v, C, nC);
+  }
+}
+
 // Apply the collapses of S: elements containing edge (v, w) die, the other
 // ball elements take w in v's place (slot and orientation kept), v dies.
 // Neighbours of v are affected (rows change) and dirty for the next round.
@@ -674,6 +715,36 @@ __global__ void k_swap_scan(Store S, const int* D, const int* nDp, const int4* o
 
 // Pass 2 (per listed edge, dense FP64): both flipped elements counter-
 // clockwise and their minimum quality above the old minimum -> the gain.
+// Gain of flipping edge (v, w) shared by K1 = (v, w, c) and K2 = (v, d, w)
+// (ball slots k1, k2 of v): both new elements counter-clockwise and their
+// minimum quality above the old minimum, else -1.  The flip's c and d go to
+// *cc and *d.
+__device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, const int* ne,
+                                            int k1, int k2, int* cc_out, int* d_out) {
+  int K1 = ne[k1], K2 = ne[k2];
+  int4 e = S.EN[c.eb + K1];
+  int4 f = S.EN[c.eb + K2];
+  int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
+  int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;
+  int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+  *cc_out = cc;
+  *d_out = d;
+  double q1 = S.qK[c.eb + K1], q2 = S.qK[c.eb + K2];
+  double qold = (q1 < q2) ? q1 : q2;
+  VD dv = load_vd(S, c.vb + lv), dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc),
+     dd = load_vd(S, c.vb + d);
+  double gain = -1.0;
+  if (orient_c(lv, d, cc, dv, dd, dc) > 0.0 && orient_c(d, w, cc, dd, dw, dc) > 0.0) {
+    // gain = min(n1, n2) - qold > 0 exactly when both exceed qold
+    double n1 = quality_c(lv, d, cc, dv, dd, dc);
+    if (n1 > qold) {
+      double n2 = quality_c(d, w, cc, dd, dw, dc);
+      if (n2 > qold) gain = ((n1 < n2) ? n1 : n2) - qold;
+    }
+  }
+  return gain;
+}
+
 __device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, const int* nIp,
                                                 double* gains) {
   const int n = *nIp;
@@ -681,28 +752,8 @@ __device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, cons
     int2 it = items[i];
     int v = it.x, k1 = it.y & 0xFF, k2 = it.y >> 8;
     MeshCtx c = ctx_of(S, v);
-    int lv = v - c.vb;
-    const int* ne = ne_row(S, v);
-    int K1 = ne[k1], K2 = ne[k2];
-    int4 e = S.EN[c.eb + K1];
-    int4 f = S.EN[c.eb + K2];
-    int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
-    int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;
-    int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
-    double q1 = S.qK[c.eb + K1], q2 = S.qK[c.eb + K2];
-    double qold = (q1 < q2) ? q1 : q2;
-    VD dv = load_vd(S, v), dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc),
-       dd = load_vd(S, c.vb + d);
-    double gain = -1.0;
-    if (orient_c(lv, d, cc, dv, dd, dc) > 0.0 && orient_c(d, w, cc, dd, dw, dc) > 0.0) {
-      // gain = min(n1, n2) - qold > 0 exactly when both exceed qold
-      double n1 = quality_c(lv, d, cc, dv, dd, dc);
-      if (n1 > qold) {
-        double n2 = quality_c(d, w, cc, dd, dw, dc);
-        if (n2 > qold) gain = ((n1 < n2) ? n1 : n2) - qold;
-      }
-    }
-    gains[(size_t)v * S.W + k1] = gain;
+    int cc, d;
+    gains[(size_t)v * S.W + k1] = flip_gain(S, c, v - c.vb, ne_row(S, v), k1, k2, &cc, &d);
   }
 }
 
@@ -1677,12 +1728,19 @@ __global__ void k_refine_sizes(Store S, const int* vscan, const int* escan) {
 //
 // Once a pass's dirty list is small, a round does little work and its cost is
 // launch and synchronisation latency.  Such rounds run back to back inside one
-// cooperative launch (every block resident): the phases are the same device
-// functions as the one-kernel-per-phase rounds, separated by a grid-wide
-// barrier, and the host reads back once when the launch ends.  The launch
+// cooperative launch (every block resident), with a grid-wide barrier between
+// the phases and one read-back when the launch ends.  A collapse round
+// evaluates in one phase (coarsen_eval_phase) and takes three barriers;
+// smoothing keeps its scan and tile-parallel evaluation (three barriers);
+// flips keep their scan, item-parallel gains and pick (five).  The launch
 // returns when a round finds no candidate (the pass is complete), when the
 // next round's list outgrows `limit`, on a row overflow or an error, or after
 // `max_rounds` rounds.
+//
+// Counters are reset where no block can still read or write them: the
+// candidate count alternates between two slots (C of even rounds, C2 of odd
+// ones); the other slot and the lists a round fills are cleared by block 0
+// at least one barrier before their first use and after their last read.
 
 constexpr unsigned long long kBarrierNs = 2000000000ull;  // a barrier wait gives up after 2 s
 
@@ -1694,24 +1752,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
 
-// Grid-wide barrier: bar[0] counts the blocks that arrived, bar[1] is the
-// generation.  Returns false (the caller leaves the kernel) when a wait ran
-// out (PM_ERR_TIMEOUT is recorded) or when any phase recorded an error.
-__device__ bool grid_barrier(unsigned* bar, DevStatus* st) {
+// Grid-wide barrier on a counter of arrivals that only grows (zeroed before
+// the launch): the k-th barrier waits for k * gridDim.x arrivals.  Thread 0
+// of each block publishes the block's writes (__syncthreads, then a
+// device-wide fence), arrives, waits, and fences again before the block
+// reads what the other blocks wrote.  Returns false (the caller leaves the
+// kernel) when the wait ran out (PM_ERR_TIMEOUT is recorded) or when any
+// phase recorded an error.
+__device__ bool grid_barrier(unsigned* bar, unsigned& target, DevStatus* st) {
   __shared__ int s_ok;
+  target += gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen_p = bar + 1;
-    const unsigned gen = *gen_p;
     int ok = 1;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if ((int)(arrived - target) < 0) {
+      const volatile unsigned* vb = bar;
       const unsigned long long t0 = global_ns();
-      while (*gen_p == gen) {
+      while ((int)(*vb - target) < 0) {
         if (ld_volatile(&st->err) != 0) {
           ok = 0;
           break;
@@ -1721,7 +1780,6 @@ __device__ bool grid_barrier(unsigned* bar, DevStatus* st) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -1735,23 +1793,18 @@ struct RoundArgs {
   Store S;
   Work w;
   DevStatus* st;
-  unsigned* bar;       // barrier words (2)
+  unsigned* bar;       // barrier arrivals (zeroed before the launch)
   int* res;            // out: rounds run, list index after, pass complete
   int cur;             // list index the first round reads
   int tag0;            // tag of the first round (then +2 per round)
   int pass0;
   int max_rounds;
   int limit;           // leave when the next list holds more entries
-  int icap;            // swap: capacity of the item list
+  int icap;            // flips: capacity of the item list
   int ptag;            // smoothing: stamp of the next sweep's list
-  unsigned long long* work;  // smoothing: counted FP64 work (profiling) or null
 };
 
-// Counters of round r (C, S, A, E, I, I2 and the list it fills), cleared by
-// block 0 before the round's first barrier.
-__device__ __forceinline__ void clear_round(int* cnt, int nxt) {
-  if (blockIdx.x == 0 && threadIdx.x < 7) cnt[(nxt == 0 ? CN_D0 : CN_C) + threadIdx.x] = 0;
-}
+__device__ __forceinline__ int* cand_count(int* cnt, int r) { return cnt + ((r & 1) ? CN_C2 : CN_C); }
 
 __device__ __forceinline__ void finish_rounds(const RoundArgs& a, int r, int cur, bool complete) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1761,107 +1814,127 @@ __device__ __forceinline__ void finish_rounds(const RoundArgs& a, int r, int cur
   }
 }
 
-__global__ void __launch_bounds__(256) k_coarsen_rounds(RoundArgs a) {
+// Rounds of collapses: [evaluate] B1 [select + apply] B2 [commit] B3; rounds
+// of flips: [scan] B1 [gains] [pick] [select + apply] [commit], five
+// barriers.  Block 0 clears, before B1 of round r: A and the list round r
+// fills (both last read before the last barrier of round r - 1); right after
+// B1: the candidate slot of round r + 1 (last read before the last barrier of
+// round r - 1); flips, after the pick: E and the item count (read by the pick
+// and the gains).
+template <bool FLIP>
+__device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
   const Work& w = a.w;
   int* cnt = w.counts;
+  unsigned target = 0;
   int cur = a.cur, r = 0;
   bool complete = false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *cand_count(cnt, 0) = 0;
+    cnt[CN_E] = cnt[CN_I] = 0;
+  }
+  if (!grid_barrier(a.bar, target, a.st)) return;
   while (r < a.max_rounds) {
     const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
-    clear_round(cnt, nxt);
-    if (!grid_barrier(a.bar, a.st)) return;
-    coarsen_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.target, w.cand, w.ncand, w.C,
-                       cnt + CN_C, w.cmark, tag, a.pass0, w.items, cnt + CN_I);
-    if (!grid_barrier(a.bar, a.st)) return;
-    coarsen_check_phase(a.S, w.items, cnt + CN_I, w.items2, cnt + CN_I2, w.target, w.cand,
-                        w.ncand, w.C, cnt + CN_C, w.cmark, tag, 0);
-    if (!grid_barrier(a.bar, a.st)) return;
-    coarsen_check_phase(a.S, w.items2, cnt + CN_I2, w.items, cnt + CN_I, w.target, w.cand,
-                        w.ncand, w.C, cnt + CN_C, w.cmark, tag, 1);
-    if (!grid_barrier(a.bar, a.st)) return;
-    coarsen_select_apply_phase(a.S, w.C, cnt + CN_C, w.cmark, w.smark, tag, w.target, w.A,
-                               cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
-    if (!grid_barrier(a.bar, a.st)) return;
-    const int nC = ld_volatile(cnt + CN_C), nD = ld_volatile(cnt + cn_list(nxt));
+    int* nC = cand_count(cnt, r);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      cnt[CN_A] = 0;
+      cnt[cn_list(nxt)] = 0;
+    }
+    if (FLIP) {
+      // flips keep their three passes: the gains are many per vertex, and
+      // item-parallel FP64 beats two barriers saved
+      swap_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.opA, w.C, nC, w.cmark, tag, a.pass0,
+                      w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
+      swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      swap_pick_phase(a.S, w.E, cnt + CN_E, w.gains, w.opA, w.opK2, w.C, nC, w.cmark, tag);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = cnt[CN_I] = 0;
+    } else {
+      coarsen_eval_phase(a.S, w.D[cur], cnt + cn_list(cur), w.target, w.cand, w.ncand, w.C, nC,
+                         w.cmark, tag, a.pass0);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
+    }
+    if (FLIP)
+      swap_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.opA, w.opK2, w.A,
+                              cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
+    else
+      coarsen_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.target, w.A, cnt + CN_A,
+                                 w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
+    if (!grid_barrier(a.bar, target, a.st)) return;
+    const int nc = ld_volatile(nC), nd = ld_volatile(cnt + cn_list(nxt));
     advance_rounds(a.S);
-    coarsen_commit_phase(a.S, w.A, cnt + CN_A, w.target, w.smark, tag, a.st);
-    if (!grid_barrier(a.bar, a.st)) return;
+    if (FLIP)
+      swap_commit_phase(a.S, w.A, cnt + CN_A, w.opA, w.opK2, w.smark, tag, a.st);
+    else
+      coarsen_commit_phase(a.S, w.A, cnt + CN_A, w.target, w.smark, tag, a.st);
+    if (!grid_barrier(a.bar, target, a.st)) return;
     ++r;
-    if (nC == 0) {
+    if (nc == 0) {
       complete = true;
       break;
     }
     cur = nxt;
-    if (ld_volatile(&a.st->overflow) != 0 || nD > a.limit) break;
+    if (ld_volatile(&a.st->overflow) != 0 || nd > a.limit) break;
   }
+  // the host reads the candidates of the last round from the C slot
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_C] = ld_volatile(cand_count(cnt, r - 1));
   finish_rounds(a, r, cur, complete);
 }
 
-__global__ void __launch_bounds__(256) k_swap_rounds(RoundArgs a) {
-  const Work& w = a.w;
-  int* cnt = w.counts;
-  int cur = a.cur, r = 0;
-  bool complete = false;
-  while (r < a.max_rounds) {
-    const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
-    clear_round(cnt, nxt);
-    if (!grid_barrier(a.bar, a.st)) return;
-    swap_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.opA, w.C, cnt + CN_C, w.cmark, tag,
-                    a.pass0, w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st);
-    if (!grid_barrier(a.bar, a.st)) return;
-    swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains);
-    if (!grid_barrier(a.bar, a.st)) return;
-    swap_pick_phase(a.S, w.E, cnt + CN_E, w.gains, w.opA, w.opK2, w.C, cnt + CN_C, w.cmark, tag);
-    if (!grid_barrier(a.bar, a.st)) return;
-    swap_select_apply_phase(a.S, w.C, cnt + CN_C, w.cmark, w.smark, tag, w.opA, w.opK2, w.A,
-                            cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
-    if (!grid_barrier(a.bar, a.st)) return;
-    const int nC = ld_volatile(cnt + CN_C), nD = ld_volatile(cnt + cn_list(nxt));
-    advance_rounds(a.S);
-    swap_commit_phase(a.S, w.A, cnt + CN_A, w.opA, w.opK2, w.smark, tag, a.st);
-    if (!grid_barrier(a.bar, a.st)) return;
-    ++r;
-    if (nC == 0) {
-      complete = true;
-      break;
-    }
-    cur = nxt;
-    if (ld_volatile(&a.st->overflow) != 0 || nD > a.limit) break;
-  }
-  finish_rounds(a, r, cur, complete);
-}
+__global__ void __launch_bounds__(256) k_coarsen_rounds(RoundArgs a) { topo_rounds<false>(a); }
 
+__global__ void __launch_bounds__(256) k_swap_rounds(RoundArgs a) { topo_rounds<true>(a); }
+
+// Rounds of smoothing moves: [scan] B1 [evaluate] B2 [select + apply] B3.
+// Block 0 clears, before B1 of round r: the list round r fills (last read by
+// round r - 1's scan and by its decision, both before B1 of round r); between
+// B1 and B2: the candidate slot of round r + 1 (last read after B3 of round
+// r - 1); between B2 and B3: E (read by the evaluation before B2).  The round
+// counters advance after B3 from the flag set of the round's parity, so that
+// round r + 1's evaluation can set the other set meanwhile.
 __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
   const Work& w = a.w;
   int* cnt = w.counts;
+  unsigned target = 0;
   int cur = a.cur, r = 0;
   bool complete = false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *cand_count(cnt, 0) = 0;
+    cnt[CN_E] = 0;
+  }
+  if (!grid_barrier(a.bar, target, a.st)) return;
   while (r < a.max_rounds) {
     const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
-    clear_round(cnt, nxt);
-    if (!grid_barrier(a.bar, a.st)) return;
-    smooth_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.mvM, w.C, cnt + CN_C, w.cmark, tag,
-                      a.pass0, w.E, cnt + CN_E);
-    if (!grid_barrier(a.bar, a.st)) return;
-    smooth_eval_phase(a.S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, cnt + CN_C, w.cmark, tag,
-                      a.work);
-    if (!grid_barrier(a.bar, a.st)) return;
-    smooth_select_apply_phase(a.S, w.C, cnt + CN_C, w.cmark, w.smark, tag, w.D[nxt],
-                              cnt + cn_list(nxt), w.dmark, w.mvxy, w.mvM, w.gains, w.P,
-                              cnt + CN_P, w.pmark, a.ptag, tag + 1);
-    if (!grid_barrier(a.bar, a.st)) return;
-    const int nC = ld_volatile(cnt + CN_C), nD = ld_volatile(cnt + cn_list(nxt));
-    advance_rounds(a.S);
-    // every block has read the counters before block 0 clears them
-    if (!grid_barrier(a.bar, a.st)) return;
+    int* nC = cand_count(cnt, r);
+    Store S = a.S;
+    S.tab.had = a.S.tab.had + (r & 1) * S.nmesh;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[cn_list(nxt)] = 0;
+    smooth_scan_phase(S, w.D[cur], cnt + cn_list(cur), w.mvM, w.C, nC, w.cmark, tag, a.pass0, w.E,
+                      cnt + CN_E);
+    if (!grid_barrier(a.bar, target, a.st)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
+    smooth_eval_phase(S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, nC, w.cmark, tag, nullptr);
+    if (!grid_barrier(a.bar, target, a.st)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = 0;
+    smooth_select_apply_phase(S, w.C, nC, w.cmark, w.smark, tag, w.D[nxt], cnt + cn_list(nxt),
+                              w.dmark, w.mvxy, w.mvM, w.gains, w.P, cnt + CN_P, w.pmark, a.ptag,
+                              tag + 1);
+    if (!grid_barrier(a.bar, target, a.st)) return;
+    const int nc = ld_volatile(nC), nd = ld_volatile(cnt + cn_list(nxt));
+    advance_rounds(S);
     ++r;
-    if (nC == 0) {
+    if (nc == 0) {
       complete = true;
       break;
     }
     cur = nxt;
-    if (nD > a.limit) break;
+    if (nd > a.limit) break;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_C] = ld_volatile(cand_count(cnt, r - 1));
   finish_rounds(a, r, cur, complete);
 }
 
@@ -1958,7 +2031,6 @@ RoundArgs round_args(MeshSet& m, int cur, int pass0, long long max_rounds) {
   a.limit = kRoundsLimit;
   a.icap = 0;
   a.ptag = 0;
-  a.work = nullptr;
   return a;
 }
 
@@ -1973,6 +2045,7 @@ struct RoundsOut {
 // counter and the status.  Advances the tag past the rounds that ran.
 int run_rounds(MeshSet& m, const void* kernel, const char* name, RoundArgs& a, RoundsOut& out) {
   void* args[] = {&a};
+  cudaMemsetAsync(a.bar, 0, sizeof(unsigned), m.stream);
   __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED);
   int slot = g_prof_on ? prof_begin(name, m.stream) : -1;
   cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(rounds_grid(m)),
