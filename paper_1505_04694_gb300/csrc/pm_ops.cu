@@ -253,24 +253,36 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band) {
   }
   if (common != (bedge ? 1 : 2)) return false;
   VD dw = load_vd(S, ws);
-  for (int k = 0; k < x.nel; ++k) {
-    int4 e = S.EN[x.c.eb + x.ne[k]];
-    if (e.x == u || e.y == u || e.z == u) continue;
-    int i0 = e.x, i1 = e.y, i2 = e.z;
-    VD d0 = (i0 == x.lv) ? dw : load_vd(S, x.c.vb + i0);
-    VD d1 = (i1 == x.lv) ? dw : load_vd(S, x.c.vb + i1);
-    VD d2 = (i2 == x.lv) ? dw : load_vd(S, x.c.vb + i2);
-    if (i0 == x.lv) i0 = u;
-    if (i1 == x.lv) i1 = u;
-    if (i2 == x.lv) i2 = u;
-    if (!(orient_c(i0, i1, i2, d0, d1, d2) > 0.0)) return false;
+  // every test below is evaluated (no early exit inside a group of four) so
+  // that the loads of a group overlap
+  bool ok = true;
+  for (int k0 = 0; k0 < x.nel && ok; k0 += 4) {
+#pragma unroll
+    for (int k = k0; k < k0 + 4; ++k) {
+      if (k >= x.nel) break;
+      int4 e = S.EN[x.c.eb + x.ne[k]];
+      if (e.x == u || e.y == u || e.z == u) continue;
+      int i0 = e.x, i1 = e.y, i2 = e.z;
+      VD d0 = (i0 == x.lv) ? dw : load_vd(S, x.c.vb + i0);
+      VD d1 = (i1 == x.lv) ? dw : load_vd(S, x.c.vb + i1);
+      VD d2 = (i2 == x.lv) ? dw : load_vd(S, x.c.vb + i2);
+      if (i0 == x.lv) i0 = u;
+      if (i1 == x.lv) i1 = u;
+      if (i2 == x.lv) i2 = u;
+      ok &= orient_c(i0, i1, i2, d0, d1, d2) > 0.0;
+    }
   }
-  for (int k = 0; k < x.nnl; ++k) {
-    int y = x.nn[k];
-    if (y == u || row_has(nnw, nnwl, y)) continue;
-    if (len_gt(metric_len2(dw, load_vd(S, x.c.vb + y)), band.z, band.w, L_up)) return false;
+  if (!ok) return false;
+  for (int k0 = 0; k0 < x.nnl && ok; k0 += 4) {
+#pragma unroll
+    for (int k = k0; k < k0 + 4; ++k) {
+      if (k >= x.nnl) break;
+      int y = x.nn[k];
+      if (y == u || row_has(nnw, nnwl, y)) continue;
+      ok &= !len_gt(metric_len2(dw, load_vd(S, x.c.vb + y)), band.z, band.w, L_up);
+    }
   }
-  return true;
+  return ok;
 }
 
 // Collapse candidates of v: neighbours with metric length below L_low (a
@@ -287,12 +299,15 @@ __device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out) {
   VD dv = load_vd(S, v);
   const double L_low = S.tab.L_low[c.mi];
   const double4 band = S.tab.band[c.mi];
-  double cl[MAXW];
+  double cl[MAXW], len2[MAXW];
+  // squared lengths first, four neighbours at a time so that their loads overlap
+#pragma unroll 4
+  for (int k = 0; k < nnl; ++k) len2[k] = metric_len2(dv, load_vd(S, c.vb + nn[k]));
   int nc = 0;
   for (int k = 0; k < nnl; ++k) {
     int u = nn[k];
     if (bnd && count_elems_with(S, ne, nel, c.eb, u) != 1) continue;
-    double L2 = metric_len2(dv, load_vd(S, c.vb + u));
+    double L2 = len2[k];
     if (!len_lt(L2, band.x, band.y, L_low)) continue;
     double L = sqrt(L2);
     int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
@@ -605,6 +620,10 @@ __global__ void k_coarsen_commit(Store S, const int* A, const int* nAp, const in
 
 // ---- swapping (Sec. 2.4.3) ------------------------------------------------------
 
+// Balls of at most this many elements take the register path of the flip
+// scan (the ball's vertices gathered once); larger ones search the elements.
+constexpr int kBallFast = 16;
+
 // Warp-aggregated append of a work item into a list of capacity `cap`.
 __device__ __forceinline__ void append_item(bool pred, int2 val, int2* list, int* count, int cap,
                                             DevStatus* st) {
@@ -661,6 +680,60 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
     for (int k = 0; k < nel; ++k) {
       gains[(size_t)v * S.W + k] = -1.0;
       if (S.qK[c.eb + ne[k]] < qt) poor |= 1ull << k;
+    }
+    if (__all_sync(0xffffffffu, nel <= kBallFast)) {
+      // the ball's vertices after and before v, gathered once into registers
+      int nx[kBallFast], pv[kBallFast];
+#pragma unroll
+      for (int k = 0; k < kBallFast; ++k) {
+        nx[k] = pv[k] = -1;
+        if (k < nel) {
+          int4 f = S.EN[c.eb + ne[k]];
+          nx[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+          pv[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
+        }
+      }
+      for (;;) {
+        bool any = poor != 0ull;
+        if (!__any_sync(0xffffffffu, any)) break;
+        bool emit1 = false, emit2 = false;
+        int a1 = 0, a2 = 0;
+        if (any) {
+          int kb = __ffsll((long long)poor) - 1;
+          poor &= poor - 1ull;
+          int w = -1, cc = -1;
+#pragma unroll
+          for (int k = 0; k < kBallFast; ++k)
+            if (k == kb) {
+              w = nx[k];
+              cc = pv[k];
+            }
+          int k2 = -1, k1 = -1, d2 = 0, c1 = 0;
+#pragma unroll
+          for (int k = kBallFast - 1; k >= 0; --k) {  // the first match wins
+            if (k == kb || k >= nel) continue;
+            if (pv[k] == w) {
+              k2 = k;
+              d2 = nx[k];
+            }
+            if (nx[k] == cc) {
+              k1 = k;
+              c1 = pv[k];
+            }
+          }
+          if (k2 >= 0) {
+            emit1 = !row_has(nn_row(S, c.vb + d2), S.NNlen[c.vb + d2], cc);
+            a1 = kb | (k2 << 8);
+          }
+          if (k1 >= 0 && !(S.qK[c.eb + ne[k1]] < qt)) {
+            emit2 = !row_has(nn_row(S, c.vb + w), S.NNlen[c.vb + w], c1);
+            a2 = k1 | (kb << 8);
+          }
+        }
+        append_item(emit1, make_int2(v, a1), items, nI, icap, st);
+        append_item(emit2, make_int2(v, a2), items, nI, icap, st);
+      }
+      continue;
     }
     for (;;) {
       bool any = poor != 0ull;
