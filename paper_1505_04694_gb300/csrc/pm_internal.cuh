@@ -23,6 +23,10 @@ struct ScanWork {
 
 int scan_tiles(int n);
 void scan_exclusive(const int* in, int* out, int n, ScanWork& w, DevStatus* st, cudaStream_t s);
+void scan_alive_vertices(const Store& S, int* out, int n, ScanWork& w, DevStatus* st,
+                         cudaStream_t s);
+void scan_alive_elements(const Store& S, int* out, int n, ScanWork& w, DevStatus* st,
+                         cudaStream_t s);
 
 // Per-round worklists and marks (slot-indexed scratch, sized with the store).
 struct Work {
@@ -155,7 +159,7 @@ inline void launch(const char* name, K kern, dim3 g, dim3 b, size_t sh, cudaStre
 
 #define PM_LAUNCH(k, g, b, sh, s, ...) ::pm::launch(#k, k, g, b, sh, s, __VA_ARGS__)
 
-inline int grid_for(const MeshSet& m, long long n, int per_sm = 8) {
+inline int grid_for(const MeshSet& m, long long n, int per_sm = 16) {
   long long want = (n + BLOCK - 1) / BLOCK;
   long long cap = (long long)m.num_sms * per_sm;
   if (want < 1) want = 1;

@@ -296,21 +296,14 @@ __global__ void k_qcache_all(Store S) {
 
 // ---- renumbering -----------------------------------------------------------
 
-__global__ void k_flags_v(Store S, int* cnt) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
-    int mi;
-    cnt[s] = (vslot_used(S, s, mi) && (S.vflag[s] & VF_ALIVE)) ? 1 : 0;
-  }
+// The compacted counts become the used slots of every mesh.
+__global__ void k_set_sizes(Store S, const int* tot) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nmesh) return;
+  S.tab.nv[i] = tot[2 * i];
+  S.tab.ne[i] = tot[2 * i + 1];
 }
 
-__global__ void k_flags_e(Store S, int* cnt) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
-    int mi;
-    cnt[s] = (eslot_used(S, s, mi) && S.EN[s].w) ? 1 : 0;
-  }
-}
-
-// Per-mesh live counts from the scans: n_i = scan[base_i + used_i] - scan[base_i].
 __global__ void k_mesh_totals(Store S, const int* vscan, const int* escan, int* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.nmesh) return;
@@ -766,16 +759,15 @@ int validate_mesh(MeshSet& m) {
 // slot order), adjacency remapped (rows stay sorted: the map is monotone).
 int renumber(MeshSet& m) {
   Work& w = m.w;
-  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, w.vcnt);
-  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, w.ecnt);
-  scan_exclusive(w.vcnt, w.vscan, m.S.vused, m.scan, m.st, m.stream);
-  scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
+  scan_alive_vertices(m.S, w.vscan, m.S.vused, m.scan, m.st, m.stream);
+  scan_alive_elements(m.S, w.escan, m.S.eused, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
   PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
   // the second buffer's flags must read "dead" beyond the new counts
   cudaMemsetAsync(m.B.vflag, 0, m.S.vslots, m.stream);
   PM_LAUNCH(k_renum_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
   PM_LAUNCH(k_renum_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
+  PM_LAUNCH(k_set_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, tot);
   cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   int err = sync_status(m);
   if (err) return err;
@@ -799,13 +791,7 @@ int renumber(MeshSet& m) {
   std::swap(m.S.evm, m.B.evm);
   std::swap(m.S.evr, m.B.evr);
   set_used(m);
-  std::vector<int> t(2 * m.nmesh);
-  for (int i = 0; i < m.nmesh; ++i) {
-    t[i] = m.nv[i];
-    t[m.nmesh + i] = m.ne[i];
-  }
-  cudaMemcpyAsync(m.S.tab.nv, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, m.stream);
-  return sync_status(m);
+  return PM_OK;
 }
 
 // Compacted, canonically rotated copy of mesh `mesh` into device buffers
@@ -813,10 +799,8 @@ int renumber(MeshSet& m) {
 int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
                 int* ne_out) {
   Work& w = m.w;
-  PM_LAUNCH(k_flags_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, w.vcnt);
-  PM_LAUNCH(k_flags_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, w.ecnt);
-  scan_exclusive(w.vcnt, w.vscan, m.S.vused, m.scan, m.st, m.stream);
-  scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
+  scan_alive_vertices(m.S, w.vscan, m.S.vused, m.scan, m.st, m.stream);
+  scan_alive_elements(m.S, w.escan, m.S.eused, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
   PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
   if (xy || mt)

@@ -28,9 +28,69 @@ __device__ __forceinline__ unsigned long long load_state(const unsigned long lon
   return *((volatile const unsigned long long*)p);
 }
 
+// Inputs of the scan: an int array, or the 0/1 alive flags of the used
+// vertex or element slots of a store (read directly, no flag array).
+struct IntInput {
+  const int* in;
+  __device__ __forceinline__ void load16(long long first, long long n, int* v) const {
+    if (first + SCAN_ITEMS <= n) {
+      const int4* p = reinterpret_cast<const int4*>(in + first);
+#pragma unroll
+      for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
+        int4 x = p[q];
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < SCAN_ITEMS; ++j) v[j] = (first + j < n) ? in[first + j] : 0;
+    }
+  }
+};
+
+struct VertexAlive {
+  Store S;
+  __device__ __forceinline__ void load16(long long first, long long n, int* v) const {
+    uint4 f = make_uint4(0, 0, 0, 0);
+    if (first + SCAN_ITEMS <= n) f = *reinterpret_cast<const uint4*>(S.vflag + first);
+    const unsigned w[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+      const long long s = first + j;
+      unsigned flag = (first + SCAN_ITEMS <= n) ? (w[j >> 2] >> (8 * (j & 3))) & 0xFFu
+                                                : (s < n ? S.vflag[s] : 0u);
+      int alive = 0;
+      if (s < n && (flag & VF_ALIVE)) {
+        const int mi = mesh_of_vslot(S, (int)s);
+        alive = (int)s - S.tab.vbase[mi] < S.tab.nv[mi];
+      }
+      v[j] = alive;
+    }
+  }
+};
+
+struct ElementAlive {
+  Store S;
+  __device__ __forceinline__ void load16(long long first, long long n, int* v) const {
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+      const long long s = first + j;
+      int alive = 0;
+      if (s < n && S.EN[s].w) {
+        const int mi = mesh_of_eslot(S, (int)s);
+        alive = (int)s - S.tab.ebase[mi] < S.tab.ne[mi];
+      }
+      v[j] = alive;
+    }
+  }
+};
+
+template <class Input>
 __global__ void __launch_bounds__(SCAN_THREADS)
-k_scan(const int* __restrict__ in, int* __restrict__ out, int n, unsigned long long* state,
-       int* ticket, unsigned epoch, DevStatus* st) {
+k_scan(Input input, int* __restrict__ out, int n, unsigned long long* state, int* ticket,
+       unsigned epoch, DevStatus* st) {
   __shared__ int s_warp[SCAN_THREADS / 32];
   __shared__ int s_tile;
   __shared__ int s_excl;
@@ -43,20 +103,7 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, unsigned long l
   const int tile = s_tile;
   const long long first = (long long)tile * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
   int v[SCAN_ITEMS];
-  if (first + SCAN_ITEMS <= n) {
-    const int4* p = reinterpret_cast<const int4*>(in + first);
-#pragma unroll
-    for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
-      int4 x = p[q];
-      v[4 * q] = x.x;
-      v[4 * q + 1] = x.y;
-      v[4 * q + 2] = x.z;
-      v[4 * q + 3] = x.w;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) v[j] = (first + j < n) ? in[first + j] : 0;
-  }
+  input.load16(first, n, v);
   int sum = 0;
 #pragma unroll
   for (int j = 0; j < SCAN_ITEMS; ++j) {
@@ -152,10 +199,10 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, unsigned long l
 
 int scan_tiles(int n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
 
-// Exclusive scan of in[0..n) into out[0..n]; out[n] holds the total.
-// `state` needs scan_tiles(n) words and is never cleared (epochs tell runs
-// apart); `ticket` is reset here.
-void scan_exclusive(const int* in, int* out, int n, ScanWork& w, DevStatus* st, cudaStream_t s) {
+namespace {
+
+template <class Input>
+void scan_run(Input input, int* out, int n, ScanWork& w, DevStatus* st, cudaStream_t s) {
   if (n <= 0) {
     cudaMemsetAsync(out, 0, sizeof(int), s);
     return;
@@ -164,7 +211,28 @@ void scan_exclusive(const int* in, int* out, int n, ScanWork& w, DevStatus* st, 
   cudaMemsetAsync(w.ticket, 0, sizeof(int), s);
   w.epoch = (w.epoch + 1) & 0x3FFFFFFFu;
   if (w.epoch == 0) w.epoch = 1;
-  PM_LAUNCH(k_scan, tiles, SCAN_THREADS, 0, s, in, out, n, w.state, w.ticket, w.epoch, st);
+  PM_LAUNCH(k_scan<Input>, tiles, SCAN_THREADS, 0, s, input, out, n, w.state, w.ticket, w.epoch,
+            st);
+}
+
+}  // namespace
+
+// Exclusive scan of in[0..n) into out[0..n]; out[n] holds the total.
+// `state` needs scan_tiles(n) words and is never cleared (epochs tell runs
+// apart); `ticket` is reset here.
+void scan_exclusive(const int* in, int* out, int n, ScanWork& w, DevStatus* st, cudaStream_t s) {
+  scan_run(IntInput{in}, out, n, w, st, s);
+}
+
+// The same over the alive flags of the used vertex (element) slots [0, n).
+void scan_alive_vertices(const Store& S, int* out, int n, ScanWork& w, DevStatus* st,
+                         cudaStream_t s) {
+  scan_run(VertexAlive{S}, out, n, w, st, s);
+}
+
+void scan_alive_elements(const Store& S, int* out, int n, ScanWork& w, DevStatus* st,
+                         cudaStream_t s) {
+  scan_run(ElementAlive{S}, out, n, w, st, s);
 }
 
 }  // namespace pm
