@@ -106,6 +106,18 @@ __device__ __forceinline__ bool unchanged(const Store& S, int v, int vb, int et,
   return et > lo && S.touch[v] <= et && S.ntouch[v] <= et;
 }
 
+// Measurement only: adds every lane's count of FP64 operations to *work
+// (one atomic per warp).  All 32 lanes must call it.  The counts follow the
+// arithmetic as written: a metric length 17 operations, an orientation 8, a
+// quality 77, a square root or a division 1.
+constexpr unsigned kOpsLen2 = 17, kOpsOrient = 8, kOpsQuality = 77;
+
+__device__ __forceinline__ void add_work(unsigned long long* work, unsigned ops) {
+  if (!work) return;
+  unsigned tot = __reduce_add_sync(0xffffffffu, ops);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(work, (unsigned long long)tot);
+}
+
 // Stamps the neighbours in `row` (local ids) after a change of their vertex.
 __device__ __forceinline__ void stamp_neighbours(const Store& S, const int* row, int len, int vb,
                                                  int stamp) {
@@ -227,7 +239,7 @@ __device__ __forceinline__ double S_L_up(const CoarsenCtx& x) { return x.S->tab.
 
 // Validity of collapsing v onto local neighbour u: link condition, all
 // remaining ball elements counter-clockwise, no new edge longer than L_up.
-__device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band) {
+__device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band, unsigned& ops) {
   const double L_up = S_L_up(x);
   const Store& S = *x.S;
   bool bedge = count_elems_with(S, x.ne, x.nel, x.c.eb, u) == 1;
@@ -270,6 +282,7 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band) {
       if (i1 == x.lv) i1 = u;
       if (i2 == x.lv) i2 = u;
       ok &= orient_c(i0, i1, i2, d0, d1, d2) > 0.0;
+      ops += kOpsOrient;
     }
   }
   if (!ok) return false;
@@ -280,6 +293,7 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band) {
       int y = x.nn[k];
       if (y == u || row_has(nnw, nnwl, y)) continue;
       ok &= !len_gt(metric_len2(dw, load_vd(S, x.c.vb + y)), band.z, band.w, L_up);
+      ops += kOpsLen2;
     }
   }
   return ok;
@@ -288,7 +302,7 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band) {
 // Collapse candidates of v: neighbours with metric length below L_low (a
 // boundary vertex: only along boundary edges), sorted by (length, id) into
 // out[0..n).  Corners and dead vertices have none.
-__device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out) {
+__device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out, unsigned& ops) {
   uint8_t f = S.vflag[v];
   if (!(f & VF_ALIVE) || (f & VF_CORNER)) return 0;
   const bool bnd = (f & VF_BND) != 0;
@@ -303,6 +317,7 @@ __device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out) {
   // squared lengths first, four neighbours at a time so that their loads overlap
 #pragma unroll 4
   for (int k = 0; k < nnl; ++k) len2[k] = metric_len2(dv, load_vd(S, c.vb + nn[k]));
+  ops += kOpsLen2 * nnl;
   int nc = 0;
   for (int k = 0; k < nnl; ++k) {
     int u = nn[k];
@@ -310,6 +325,7 @@ __device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out) {
     double L2 = len2[k];
     if (!len_lt(L2, band.x, band.y, L_low)) continue;
     double L = sqrt(L2);
+    ++ops;
     int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
     while (j > 0 && cl[j - 1] > L) {
       cl[j] = cl[j - 1];
@@ -364,7 +380,8 @@ __device__ __forceinline__ void coarsen_scan_phase(Store S, const int* D, const 
         }
       } else {
         S.evc[v] = tag;
-        int nc = coarsen_candidates(S, v, c, cand + (size_t)v * S.W);
+        unsigned ops = 0;
+        int nc = coarsen_candidates(S, v, c, cand + (size_t)v * S.W, ops);
         ncand[v] = nc;
         if (nc == 0) target[v] = -1;
         emit = nc > 0;
@@ -400,9 +417,10 @@ __device__ __forceinline__ void coarsen_check_phase(Store S, const int2* Win, co
       const double4 band = S.tab.band[c.mi];
       const int* cv = cand + (size_t)v * S.W;
       int nc = ncand[v];
-      found = collapse_valid(x, cv[k], band);
+      unsigned ops = 0;
+      found = collapse_valid(x, cv[k], band, ops);
       if (last)
-        while (!found && ++k < nc) found = collapse_valid(x, cv[k], band);
+        while (!found && ++k < nc) found = collapse_valid(x, cv[k], band, ops);
       if (found) {
         target[v] = cv[k];
         cmark[v] = tag;
@@ -429,12 +447,14 @@ __global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2*
 // valid collapse.  Same results as coarsen_scan_phase and the two check passes.
 __device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const int* nDp,
                                                    int* target, int* cand, int* ncand, int* C,
-                                                   int* nC, int* cmark, int tag, int pass0) {
+                                                   int* nC, int* cmark, int tag, int pass0,
+                                                   unsigned long long* work) {
   const int n = *nDp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
     int v = 0;
     bool found = false;
+    unsigned ops = 0;
     if (i < n) {
       v = D[i];
       MeshCtx c = ctx_of(S, v);
@@ -443,13 +463,13 @@ __device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const 
       } else {
         S.evc[v] = tag;
         int* cv = cand + (size_t)v * S.W;
-        int nc = coarsen_candidates(S, v, c, cv);
+        int nc = coarsen_candidates(S, v, c, cv, ops);
         ncand[v] = nc;
         if (nc > 0) {
           CoarsenCtx x = coarsen_ctx(S, v, c);
           const double4 band = S.tab.band[c.mi];
           for (int k = 0; k < nc && !found; ++k)
-            if (collapse_valid(x, cv[k], band)) {
+            if (collapse_valid(x, cv[k], band, ops)) {
               found = true;
               target[v] = cv[k];
             }
@@ -462,6 +482,7 @@ __device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const 
       }
     }
     warp_append(found, v, C, nC);
+    add_work(work, ops);
   }
 }
 
@@ -471,7 +492,7 @@ __device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const 
 __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v,
                                                   const int* target, int* A, int* nA,
                                                   int* amark, int* Dn, int* nDn, int* dmark,
-                                                  int tag) {
+                                                  int tag, unsigned& ops) {
   {
     int nnl = 0, mi = 0, vb = 0;
     const int* nn = nullptr;
@@ -493,6 +514,7 @@ __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v
           if (e.y == lv) e.y = w;
           if (e.z == lv) e.z = w;
           S.qK[c.eb + ne[k]] = elem_quality(S, c.vb, e);
+          ops += kOpsQuality;
         }
         *pe = e;
       }
@@ -522,12 +544,14 @@ __device__ __forceinline__ void coarsen_select_apply_phase(Store S, const int* C
                                                            const int* cmark, int* smark, int tag,
                                                            const int* target, int* A, int* nA,
                                                            int* amark, int* Dn, int* nDn,
-                                                           int* dmark) {
+                                                           int* dmark,
+                                                           unsigned long long* work) {
   const int n = *nCp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
     bool win = false, lose = false;
     int v = 0;
+    unsigned ops = 0;
     if (i < n) {
       v = C[i];
       win = local_max(S, v, cmark, tag);
@@ -535,14 +559,16 @@ __device__ __forceinline__ void coarsen_select_apply_phase(Store S, const int* C
       else lose = stamp_first(dmark, v, tag);
     }
     warp_append(lose, v, Dn, nDn);
-    coarsen_apply_one(S, win, v, target, A, nA, amark, Dn, nDn, dmark, tag);
+    coarsen_apply_one(S, win, v, target, A, nA, amark, Dn, nDn, dmark, tag, ops);
+    add_work(work, ops);
   }
 }
 
 __global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
                                        int* smark, int tag, const int* target, int* A, int* nA,
                                        int* amark, int* Dn, int* nDn, int* dmark, unsigned* done) {
-  coarsen_select_apply_phase(S, C, nCp, cmark, smark, tag, target, A, nA, amark, Dn, nDn, dmark);
+  coarsen_select_apply_phase(S, C, nCp, cmark, smark, tag, target, A, nA, amark, Dn, nDn, dmark,
+                             nullptr);
   round_done(S, done);
 }
 
@@ -793,7 +819,8 @@ __global__ void k_swap_scan(Store S, const int* D, const int* nDp, const int4* o
 // minimum quality above the old minimum, else -1.  The flip's c and d go to
 // *cc and *d.
 __device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, const int* ne,
-                                            int k1, int k2, int* cc_out, int* d_out) {
+                                            int k1, int k2, int* cc_out, int* d_out,
+                                            unsigned& ops) {
   int K1 = ne[k1], K2 = ne[k2];
   int4 e = S.EN[c.eb + K1];
   int4 f = S.EN[c.eb + K2];
@@ -807,31 +834,47 @@ __device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, c
   VD dv = load_vd(S, c.vb + lv), dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc),
      dd = load_vd(S, c.vb + d);
   double gain = -1.0;
-  if (orient_c(lv, d, cc, dv, dd, dc) > 0.0 && orient_c(d, w, cc, dd, dw, dc) > 0.0) {
+  bool o1 = orient_c(lv, d, cc, dv, dd, dc) > 0.0;
+  ops += kOpsOrient;
+  if (o1 && orient_c(d, w, cc, dd, dw, dc) > 0.0) {
+    ops += kOpsOrient + kOpsQuality;
     // gain = min(n1, n2) - qold > 0 exactly when both exceed qold
     double n1 = quality_c(lv, d, cc, dv, dd, dc);
     if (n1 > qold) {
+      ops += kOpsQuality;
       double n2 = quality_c(d, w, cc, dd, dw, dc);
-      if (n2 > qold) gain = ((n1 < n2) ? n1 : n2) - qold;
+      if (n2 > qold) {
+        gain = ((n1 < n2) ? n1 : n2) - qold;
+        ops += 1;
+      }
     }
+  } else if (o1) {
+    ops += kOpsOrient;
   }
   return gain;
 }
 
 __device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, const int* nIp,
-                                                double* gains) {
+                                                double* gains, unsigned long long* work) {
   const int n = *nIp;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int2 it = items[i];
-    int v = it.x, k1 = it.y & 0xFF, k2 = it.y >> 8;
-    MeshCtx c = ctx_of(S, v);
-    int cc, d;
-    gains[(size_t)v * S.W + k1] = flip_gain(S, c, v - c.vb, ne_row(S, v), k1, k2, &cc, &d);
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    int i = i0 + threadIdx.x;
+    unsigned ops = 0;
+    if (i < n) {
+      int2 it = items[i];
+      int v = it.x, k1 = it.y & 0xFF, k2 = it.y >> 8;
+      MeshCtx c = ctx_of(S, v);
+      int cc, d;
+      gains[(size_t)v * S.W + k1] =
+          flip_gain(S, c, v - c.vb, ne_row(S, v), k1, k2, &cc, &d, ops);
+    }
+    add_work(work, ops);
   }
 }
 
-__global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* gains) {
-  swap_edge_phase(S, items, nIp, gains);
+__global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* gains,
+                            unsigned long long* work) {
+  swap_edge_phase(S, items, nIp, gains, work);
 }
 
 // Pass 3 (per evaluated vertex): largest strictly positive gain, ties to the
@@ -897,7 +940,8 @@ __global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double*
 
 __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, const int4* opA,
                                                const int* opK2, int* A, int* nA, int* amark,
-                                               int* Dn, int* nDn, int* dmark, int tag) {
+                                               int* Dn, int* nDn, int* dmark, int tag,
+                                               unsigned& ops) {
   {
     int mi = 0;
     int t[4] = {0, 0, 0, 0};
@@ -913,6 +957,7 @@ __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, c
       S.EN[c.eb + K2] = t2;
       S.qK[c.eb + op.w] = elem_quality(S, c.vb, t1);
       S.qK[c.eb + K2] = elem_quality(S, c.vb, t2);
+      ops += 2 * kOpsQuality;
       t[0] = v;
       t[1] = c.vb + op.x;
       t[2] = c.vb + op.y;
@@ -946,12 +991,13 @@ __device__ __forceinline__ void swap_select_apply_phase(Store S, const int* C, c
                                                         const int* cmark, int* smark, int tag,
                                                         const int4* opA, const int* opK2, int* A,
                                                         int* nA, int* amark, int* Dn, int* nDn,
-                                                        int* dmark) {
+                                                        int* dmark, unsigned long long* work) {
   const int n = *nCp;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
     int i = i0 + threadIdx.x;
     bool win = false, lose = false;
     int v = 0;
+    unsigned ops = 0;
     if (i < n) {
       v = C[i];
       win = local_max(S, v, cmark, tag);
@@ -959,7 +1005,8 @@ __device__ __forceinline__ void swap_select_apply_phase(Store S, const int* C, c
       else lose = stamp_first(dmark, v, tag);
     }
     warp_append(lose, v, Dn, nDn);
-    swap_apply_one(S, win, v, opA, opK2, A, nA, amark, Dn, nDn, dmark, tag);
+    swap_apply_one(S, win, v, opA, opK2, A, nA, amark, Dn, nDn, dmark, tag, ops);
+    add_work(work, ops);
   }
 }
 
@@ -967,7 +1014,8 @@ __global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const
                                     int* smark, int tag, const int4* opA, const int* opK2, int* A,
                                     int* nA, int* amark, int* Dn, int* nDn, int* dmark,
                                     unsigned* done) {
-  swap_select_apply_phase(S, C, nCp, cmark, smark, tag, opA, opK2, A, nA, amark, Dn, nDn, dmark);
+  swap_select_apply_phase(S, C, nCp, cmark, smark, tag, opA, opK2, A, nA, amark, Dn, nDn, dmark,
+                          nullptr);
   round_done(S, done);
 }
 
@@ -1875,6 +1923,7 @@ struct RoundArgs {
   int limit;           // leave when the next list holds more entries
   int icap;            // flips: capacity of the item list
   int ptag;            // smoothing: stamp of the next sweep's list
+  unsigned long long* work;  // counted FP64 work (measurement) or null
 };
 
 __device__ __forceinline__ int* cand_count(int* cnt, int r) { return cnt + ((r & 1) ? CN_C2 : CN_C); }
@@ -1920,23 +1969,23 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
                       w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st);
       if (!grid_barrier(a.bar, target, a.st)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
-      swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains);
+      swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains, a.work);
       if (!grid_barrier(a.bar, target, a.st)) return;
       swap_pick_phase(a.S, w.E, cnt + CN_E, w.gains, w.opA, w.opK2, w.C, nC, w.cmark, tag);
       if (!grid_barrier(a.bar, target, a.st)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = cnt[CN_I] = 0;
     } else {
       coarsen_eval_phase(a.S, w.D[cur], cnt + cn_list(cur), w.target, w.cand, w.ncand, w.C, nC,
-                         w.cmark, tag, a.pass0);
+                         w.cmark, tag, a.pass0, a.work);
       if (!grid_barrier(a.bar, target, a.st)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
     }
     if (FLIP)
       swap_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.opA, w.opK2, w.A,
-                              cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
+                              cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work);
     else
       coarsen_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.target, w.A, cnt + CN_A,
-                                 w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark);
+                                 w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work);
     if (!grid_barrier(a.bar, target, a.st)) return;
     const int nc = ld_volatile(nC), nd = ld_volatile(cnt + cn_list(nxt));
     advance_rounds(a.S);
@@ -1990,7 +2039,7 @@ __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
                       cnt + CN_E);
     if (!grid_barrier(a.bar, target, a.st)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
-    smooth_eval_phase(S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, nC, w.cmark, tag, nullptr);
+    smooth_eval_phase(S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, nC, w.cmark, tag, a.work);
     if (!grid_barrier(a.bar, target, a.st)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = 0;
     smooth_select_apply_phase(S, w.C, nC, w.cmark, w.smark, tag, w.D[nxt], cnt + cn_list(nxt),
@@ -2104,6 +2153,7 @@ RoundArgs round_args(MeshSet& m, int cur, int pass0, long long max_rounds) {
   a.limit = kRoundsLimit;
   a.icap = 0;
   a.ptag = 0;
+  a.work = nullptr;
   return a;
 }
 
@@ -2117,6 +2167,7 @@ struct RoundsOut {
 // One cooperative launch of persistent rounds, then the read-back of every
 // counter and the status.  Advances the tag past the rounds that ran.
 int run_rounds(MeshSet& m, const void* kernel, const char* name, RoundArgs& a, RoundsOut& out) {
+  a.work = prof_work(name);
   void* args[] = {&a};
   cudaMemsetAsync(a.bar, 0, sizeof(unsigned), m.stream);
   __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED);
@@ -2274,7 +2325,7 @@ int op_swap(MeshSet& m, int max_rounds) {
               w.C, w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E, w.items,
               w.counts + CN_I, icap, w.gains, m.st);
     PM_LAUNCH(k_swap_edge, grid_for(m, 6LL * m.S.vslots, 16), BLOCK, 0, m.stream, m.S, w.items,
-              w.counts + CN_I, w.gains);
+              w.counts + CN_I, w.gains, prof_work("k_swap_edge"));
     PM_LAUNCH(k_swap_pick, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
               w.opK2, w.C, w.counts + CN_C, w.cmark, tag);
     PM_LAUNCH(k_swap_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
