@@ -1579,9 +1579,9 @@ __global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int t
     const int et = live ? S.evr[s] : 0;
     const bool same = live && S.touch[s] <= et;
     if (same && et > pass0) {
-      m = mask[s];
+      m = mask[s];  // kept as it is
     } else if (same && et > lo) {
-      m = 0;
+      mask[s] = 0;
     } else if (live) {
       S.evr[s] = tag;
       int la = s - vb;
@@ -1590,13 +1590,17 @@ __global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int t
       VD da = load_vd(S, s);
       const double L_up = S.tab.L_up[mi];
       const double4 band = S.tab.band[mi];
-      for (int k = 0; k < nnl; ++k) {
-        int b = nn[k];
-        if (b <= la) continue;
-        if (len_gt(metric_len2(da, load_vd(S, vb + b)), band.z, band.w, L_up)) m |= 1ull << k;
-      }
+      // the row is sorted, so the neighbours above la form a suffix; four
+      // lengths at a time so that their loads overlap
+      int k0 = 0;
+      while (k0 < nnl && nn[k0] <= la) ++k0;
+#pragma unroll 4
+      for (int k = k0; k < nnl; ++k)
+        if (len_gt(metric_len2(da, load_vd(S, vb + nn[k])), band.z, band.w, L_up)) m |= 1ull << k;
+      mask[s] = m;
+    } else {
+      mask[s] = 0;
     }
-    mask[s] = m;
     cnt[s] = __popcll(m);
   }
 }
