@@ -221,6 +221,20 @@ pm_status run_counted(MeshSet& m, F&& f, std::vector<long long>& acc,
   return PM_OK;
 }
 
+// Runs one operator and queues the read-back of its operation counts into
+// pinned slot `slot` without waiting (the caller reads them after its next
+// synchronisation).
+template <class F>
+pm_status run_counted_async(MeshSet& m, F&& f, int slot) {
+  zero_ops(m);
+  int err = f();
+  if (err) return (pm_status)err;
+  return cuda_status(cudaMemcpyAsync(m.hops + (size_t)slot * m.nmesh, m.S.tab.ops,
+                                     m.nmesh * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, m.stream),
+                     "reading counters");
+}
+
 pm_status fill_stats(MeshSet& m, const CallStats& cs, double t0, pm_stats* out, int n) {
   if (!out) return PM_OK;
   std::vector<uint32_t> r(m.nmesh);
@@ -261,20 +275,22 @@ pm_status adapt_set(MeshSet& m, const pm_params* P, int stride, CallStats& cs) {
     if (!any) break;
     cudaMemcpyAsync(m.S.tab.active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice,
                     m.stream);
-    std::vector<long long> c(n, 0), sw(n, 0), rf(n, 0);
     pm_status s;
     const int mr = P[0].max_rounds;
-    if ((s = run_counted(m, [&] { return op_coarsen(m, mr); }, c))) return s;
-    if ((s = run_counted(m, [&] { return op_swap(m, mr); }, sw))) return s;
-    if ((s = run_counted(m, [&] { return op_refine(m, mr); }, rf))) return s;
-    int err = renumber(m);
+    if ((s = run_counted_async(m, [&] { return op_coarsen(m, mr); }, 0))) return s;
+    if ((s = run_counted_async(m, [&] { return op_swap(m, mr); }, 1))) return s;
+    if ((s = run_counted_async(m, [&] { return op_refine(m, mr); }, 2))) return s;
+    int err = renumber(m);  // ends with a synchronisation: the counts have arrived
     if (err) return (pm_status)err;
+    const unsigned long long* h = m.hops;
     for (int i = 0; i < n; ++i) {
+      const long long c_i = (long long)h[i], sw_i = (long long)h[n + i];
+      const long long rf_i = (long long)h[2 * n + i];
       if (!active[i]) continue;
-      cs.collapses[i] += c[i];
-      cs.flips[i] += sw[i];
-      cs.splits[i] += rf[i];
-      if (c[i] + sw[i] + rf[i] == 0) {
+      cs.collapses[i] += c_i;
+      cs.flips[i] += sw_i;
+      cs.splits[i] += rf_i;
+      if (c_i + sw_i + rf_i == 0) {
         cs.converged[i] = 1;
         active[i] = 0;
       }

@@ -91,6 +91,7 @@ struct MeshSet {
   DevStatus* st = nullptr;     // device
   DevStatus* hst = nullptr;    // pinned host
   int* hcounts = nullptr;      // pinned host copy of w.counts
+  unsigned long long* hops = nullptr;  // pinned: operation counts of three operators (3 * nmesh)
   void* pinned = nullptr;      // slot of the process-wide pinned arena (hst, hcounts)
   bool pinned_own = false;     // slot too small: a private pinned allocation
   void* tabmem = nullptr;      // device block holding MeshTab arrays

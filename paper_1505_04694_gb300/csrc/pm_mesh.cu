@@ -29,7 +29,8 @@ void* pinned_get() {
   if (g_pin_free.empty()) {
     char* blk = nullptr;
     if (cudaMallocHost((void**)&blk, kPinnedBlock) != cudaSuccess) return nullptr;
-    for (size_t i = 0; i < kPinnedBlock / kPinnedSlot; ++i) g_pin_free.push_back(blk + i * kPinnedSlot);
+    for (size_t i = 0; i < kPinnedBlock / kPinnedSlot; ++i)
+      g_pin_free.push_back(blk + i * kPinnedSlot);
   }
   void* p = g_pin_free.back();
   g_pin_free.pop_back();
@@ -587,7 +588,9 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   if (!m.st) {
     if ((e = cudaMallocAsync((void**)&m.st, sizeof(DevStatus), m.stream))) return e;
     if ((e = cudaMemsetAsync(m.st, 0, sizeof(DevStatus), m.stream))) return e;
-    size_t need = 64 + (CN_NUM + 2 * (size_t)std::max(n, 1024) + 8) * sizeof(int);
+    const size_t counts_bytes = (CN_NUM + 2 * (size_t)std::max(n, 1024) + 8) * sizeof(int);
+    const size_t ops_off = 64 + ((counts_bytes + 7) & ~size_t(7));
+    size_t need = ops_off + 3 * (size_t)n * sizeof(unsigned long long);
     if (need <= kPinnedSlot) {
       m.pinned = pinned_get();
       if (!m.pinned) return cudaErrorMemoryAllocation;
@@ -598,6 +601,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
     }
     m.hst = (DevStatus*)m.pinned;
     m.hcounts = (int*)((char*)m.pinned + 64);
+    m.hops = (unsigned long long*)((char*)m.pinned + ops_off);
   }
   return cudaSuccess;
 }
@@ -635,6 +639,7 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
   n2.st = m.st;
   n2.hst = m.hst;
   n2.hcounts = m.hcounts;
+  n2.hops = m.hops;
   n2.num_sms = m.num_sms;
   cudaError_t e = set_alloc(n2, vcap, ecap, W);
   if (e != cudaSuccess) {
@@ -806,7 +811,8 @@ int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int*
   if (xy || mt)
     PM_LAUNCH(k_out_v, grid_for(m, m.nv[mesh]), BLOCK, 0, m.stream, m.S, mesh, w.vscan, xy, mt);
   if (tri)
-    PM_LAUNCH(k_out_e, grid_for(m, m.ne[mesh]), BLOCK, 0, m.stream, m.S, mesh, w.vscan, w.escan, tri);
+    PM_LAUNCH(k_out_e, grid_for(m, m.ne[mesh]), BLOCK, 0, m.stream, m.S, mesh, w.vscan, w.escan,
+              tri);
   cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   int err = sync_status(m);
   if (err) return err;

@@ -1930,7 +1930,9 @@ struct RoundArgs {
   unsigned long long* work;  // counted FP64 work (measurement) or null
 };
 
-__device__ __forceinline__ int* cand_count(int* cnt, int r) { return cnt + ((r & 1) ? CN_C2 : CN_C); }
+__device__ __forceinline__ int* cand_count(int* cnt, int r) {
+  return cnt + ((r & 1) ? CN_C2 : CN_C);
+}
 
 __device__ __forceinline__ void finish_rounds(const RoundArgs& a, int r, int cur, bool complete) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -2424,10 +2426,16 @@ int op_refine(MeshSet& m, int max_rounds) {
               w.escan, w.opA, stamp, m.st);
     PM_LAUNCH(k_refine_rows_copy, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, stamp);
     PM_LAUNCH(k_refine_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan);
-    cudaError_t e = refresh_sizes(m);
-    if (e != cudaSuccess) return PM_ERR_CUDA;
+    // the new sizes and the status in one read-back
+    int* hsz = m.hcounts + CN_NUM;
+    cudaMemcpyAsync(hsz, m.S.tab.nv, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
     int err = sync_status(m);
     if (err) return err;
+    for (int i = 0; i < m.nmesh; ++i) {
+      m.nv[i] = hsz[i];
+      m.ne[i] = hsz[m.nmesh + i];
+    }
+    set_used(m);
     if (m.hst->overflow) {  // a row outgrew W: rebuild every row with wider ones
       err = after_overflow(m);
       if (err) return err;

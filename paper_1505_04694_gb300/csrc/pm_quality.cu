@@ -211,7 +211,8 @@ int quality_mesh(MeshSet& m, double* qsum_host, double* dxy_host, double* dm_hos
     dsum(qel, ne, part, out, s);
     if (grad) PM_LAUNCH(k_vgather_store, gridn(nv), 128, 0, s, m.S, 0, eg, dxy, dm);
     cudaMemcpyAsync(qsum_host, out, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (dxy_host) cudaMemcpyAsync(dxy_host, dxy, nv * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (dxy_host)
+      cudaMemcpyAsync(dxy_host, dxy, nv * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (dm_host) cudaMemcpyAsync(dm_host, dm, nv * 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
   }
   for (void* p : {(void*)qel, (void*)part, (void*)eg, (void*)dxy, (void*)dm})
