@@ -1961,7 +1961,9 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
     cnt[CN_E] = cnt[CN_I] = 0;
   }
   if (!grid_barrier(a.bar, target, a.st)) return;
-  while (r < a.max_rounds) {
+  // a first list longer than the limit is left to the one-kernel-per-phase rounds
+  const bool too_long = ld_volatile(cnt + cn_list(cur)) > a.limit;
+  while (!too_long && r < a.max_rounds) {
     const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
     int* nC = cand_count(cnt, r);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -2009,7 +2011,8 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
     if (ld_volatile(&a.st->overflow) != 0 || nd > a.limit) break;
   }
   // the host reads the candidates of the last round from the C slot
-  if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_C] = ld_volatile(cand_count(cnt, r - 1));
+  if (blockIdx.x == 0 && threadIdx.x == 0 && r > 0)
+    cnt[CN_C] = ld_volatile(cand_count(cnt, r - 1));
   finish_rounds(a, r, cur, complete);
 }
 
@@ -2035,7 +2038,9 @@ __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
     cnt[CN_E] = 0;
   }
   if (!grid_barrier(a.bar, target, a.st)) return;
-  while (r < a.max_rounds) {
+  // a first list longer than the limit is left to the one-kernel-per-phase rounds
+  const bool too_long = ld_volatile(cnt + cn_list(cur)) > a.limit;
+  while (!too_long && r < a.max_rounds) {
     const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
     int* nC = cand_count(cnt, r);
     Store S = a.S;
@@ -2062,7 +2067,8 @@ __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
     cur = nxt;
     if (nd > a.limit) break;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_C] = ld_volatile(cand_count(cnt, r - 1));
+  if (blockIdx.x == 0 && threadIdx.x == 0 && r > 0)
+    cnt[CN_C] = ld_volatile(cand_count(cnt, r - 1));
   finish_rounds(a, r, cur, complete);
 }
 
@@ -2194,15 +2200,6 @@ int run_rounds(MeshSet& m, const void* kernel, const char* name, RoundArgs& a, R
   return PM_OK;
 }
 
-// Entries of the list a pass starts from (one read-back).
-int list_count(MeshSet& m, int idx, int* n) {
-  cudaMemcpyAsync(m.hcounts + idx, m.w.counts + idx, sizeof(int), cudaMemcpyDeviceToHost,
-                  m.stream);
-  int err = sync_status(m);
-  *n = m.hcounts[idx];
-  return err;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -2232,11 +2229,9 @@ int op_coarsen(MeshSet& m, int max_rounds) {
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evc,
             m.lo_coarsen);
-  int nlist = -1;  // entries of the list the next round reads, when known
-  if (persist) {
-    int err = list_count(m, CN_D0, &nlist);
-    if (err) return err;
-  }
+  // entries of the list the next round reads; unknown (0) at first: the
+  // persistent launch itself hands a long first list back
+  int nlist = 0;
   int cur = 0;
   bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds;) {
@@ -2299,11 +2294,7 @@ int op_swap(MeshSet& m, int max_rounds) {
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evs,
             m.lo_swap);
-  int nlist = -1;
-  if (persist) {
-    int err = list_count(m, CN_D0, &nlist);
-    if (err) return err;
-  }
+  int nlist = 0;  // unknown at first (see op_coarsen)
   int cur = 0;
   bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds;) {
@@ -2453,11 +2444,7 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
   const bool persist = rounds_grid(m) > 0;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0, nullptr, 0);
-  int nlist = -1;
-  if (persist) {
-    int err = list_count(m, CN_D0, &nlist);
-    if (err) return err;
-  }
+  int nlist = 0;  // unknown at first (see op_coarsen)
   long long nr = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int ptag = (m.tag += 2);  // stamp of the next sweep's pending list
