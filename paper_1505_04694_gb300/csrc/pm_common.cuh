@@ -246,14 +246,31 @@ __device__ __forceinline__ double metric_len2(const VD& a, const VD& b) {
 // sqrt(L2) > t and sqrt(L2) < t decided exactly without the square root
 // outside a band of relative width 1e-9 around t: lo2 <= (t(1-1e-9))^2 and
 // hi2 >= (t(1+1e-9))^2, far wider than the rounding of sqrt or of the squares.
+// Comparisons decided on the bit patterns of doubles: GB300 issues FP64
+// compares on its scarce FP64 pipe, 64-bit integer compares elsewhere.  For
+// non-NaN operands they equal the floating-point comparison when the right
+// side b satisfies the stated range: every double below +0 (negatives and -0)
+// has a negative pattern, and non-negative doubles order as their patterns.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// a > b for b >= +0 (b not -0)
+__device__ __forceinline__ bool dgt(double a, double b) { return dbits(a) > dbits(b); }
+// a < b for b > 0
+__device__ __forceinline__ bool dlt(double a, double b) { return dbits(a) < dbits(b); }
+// a >= 0.0 (true for -0 as well)
+__device__ __forceinline__ bool dge0(double a) {
+  long long x = dbits(a);
+  return x >= 0 || x == (long long)0x8000000000000000ull;
+}
+
+// Band tests of a squared length against positive squared bounds.
 __device__ __forceinline__ bool len_gt(double L2, double lo2, double hi2, double t) {
-  if (L2 > hi2) return true;
-  if (L2 < lo2) return false;
+  if (dgt(L2, hi2)) return true;
+  if (dlt(L2, lo2)) return false;
   return sqrt(L2) > t;
 }
 __device__ __forceinline__ bool len_lt(double L2, double lo2, double hi2, double t) {
-  if (L2 < lo2) return true;
-  if (L2 > hi2) return false;
+  if (dlt(L2, lo2)) return true;
+  if (dgt(L2, hi2)) return false;
   return sqrt(L2) < t;
 }
 
@@ -301,7 +318,7 @@ __device__ __forceinline__ double quality_c(int i0, int i1, int i2, VD a, VD b, 
   double area = 0.5 * orient3(a, b, c);
   double AM = sqrt(k00 * k11 - k01 * k01) * area;
   double xx = P * THIRD;
-  double s = (xx <= 1.0) ? xx : 1.0 / xx;
+  double s = !dgt(xx, 1.0) ? xx : 1.0 / xx;  // xx <= 1
   double f = s * (2.0 - s);
   double F = (f * f) * f;
   return ((QC * AM) / (P * P)) * F;

@@ -281,7 +281,7 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band, unsigne
       if (i0 == x.lv) i0 = u;
       if (i1 == x.lv) i1 = u;
       if (i2 == x.lv) i2 = u;
-      ok &= orient_c(i0, i1, i2, d0, d1, d2) > 0.0;
+      ok &= dgt(orient_c(i0, i1, i2, d0, d1, d2), 0.0);
       ops += kOpsOrient;
     }
   }
@@ -327,7 +327,7 @@ __device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out, un
     double L = sqrt(L2);
     ++ops;
     int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
-    while (j > 0 && cl[j - 1] > L) {
+    while (j > 0 && dgt(cl[j - 1], L)) {
       cl[j] = cl[j - 1];
       out[j] = out[j - 1];
       --j;
@@ -705,7 +705,7 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
     unsigned long long poor = 0;
     for (int k = 0; k < nel; ++k) {
       gains[(size_t)v * S.W + k] = -1.0;
-      if (S.qK[c.eb + ne[k]] < qt) poor |= 1ull << k;
+      if (dlt(S.qK[c.eb + ne[k]], qt)) poor |= 1ull << k;
     }
     if (__all_sync(0xffffffffu, nel <= kBallFast)) {
       // the ball's vertices after and before v, gathered once into registers
@@ -751,7 +751,7 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
             emit1 = !row_has(nn_row(S, c.vb + d2), S.NNlen[c.vb + d2], cc);
             a1 = kb | (k2 << 8);
           }
-          if (k1 >= 0 && !(S.qK[c.eb + ne[k1]] < qt)) {
+          if (k1 >= 0 && !dlt(S.qK[c.eb + ne[k1]], qt)) {
             emit2 = !row_has(nn_row(S, c.vb + w), S.NNlen[c.vb + w], c1);
             a2 = k1 | (kb << 8);
           }
@@ -795,7 +795,7 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
         }
         // pair (K1 = k1, K2 = kb) when K1 is not poor itself (else it is
         // listed from K1's side): w' = cc, c' = c1, d' = w
-        if (k1 >= 0 && !(S.qK[c.eb + ne[k1]] < qt)) {
+        if (k1 >= 0 && !dlt(S.qK[c.eb + ne[k1]], qt)) {
           emit2 = !row_has(nn_row(S, c.vb + w), S.NNlen[c.vb + w], c1);
           a2 = k1 | (kb << 8);
         }
@@ -830,21 +830,21 @@ __device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, c
   *cc_out = cc;
   *d_out = d;
   double q1 = S.qK[c.eb + K1], q2 = S.qK[c.eb + K2];
-  double qold = (q1 < q2) ? q1 : q2;
+  double qold = dlt(q1, q2) ? q1 : q2;
   VD dv = load_vd(S, c.vb + lv), dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc),
      dd = load_vd(S, c.vb + d);
   double gain = -1.0;
-  bool o1 = orient_c(lv, d, cc, dv, dd, dc) > 0.0;
+  bool o1 = dgt(orient_c(lv, d, cc, dv, dd, dc), 0.0);
   ops += kOpsOrient;
-  if (o1 && orient_c(d, w, cc, dd, dw, dc) > 0.0) {
+  if (o1 && dgt(orient_c(d, w, cc, dd, dw, dc), 0.0)) {
     ops += kOpsOrient + kOpsQuality;
     // gain = min(n1, n2) - qold > 0 exactly when both exceed qold
     double n1 = quality_c(lv, d, cc, dv, dd, dc);
-    if (n1 > qold) {
+    if (dgt(n1, qold)) {
       ops += kOpsQuality;
       double n2 = quality_c(d, w, cc, dd, dw, dc);
-      if (n2 > qold) {
-        gain = ((n1 < n2) ? n1 : n2) - qold;
+      if (dgt(n2, qold)) {
+        gain = (dlt(n1, n2) ? n1 : n2) - qold;
         ops += 1;
       }
     }
@@ -897,10 +897,10 @@ __device__ __forceinline__ void swap_pick_phase(Store S, const int* E, const int
       int bw = 0, bk = -1;
       for (int k = 0; k < nel; ++k) {
         double g = gains[(size_t)v * S.W + k];
-        if (!(g > 0.0)) continue;
+        if (!dgt(g, 0.0)) continue;
         int4 e = S.EN[c.eb + ne[k]];
         int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
-        if (!found || g > best || (g == best && w < bw)) {
+        if (!found || dgt(g, best) || (dbits(g) == dbits(best) && w < bw)) {
           found = true;
           best = g;
           bw = w;
@@ -1094,7 +1094,7 @@ __device__ __forceinline__ double ball_min_quality(const Store& S, MeshCtx c, co
 #pragma unroll 4
   for (int k = 0; k < nel; ++k) {
     double q = S.qK[c.eb + ne[k]];
-    if (k == 0 || q < qmin) qmin = q;
+    if (k == 0 || dlt(q, qmin)) qmin = q;
     sum = sum + q;
   }
   if (qsum) *qsum = sum;
@@ -1126,7 +1126,7 @@ __device__ __forceinline__ void smooth_scan_phase(Store S, const int* D, const i
         uint8_t f = S.vflag[v];
         if ((f & VF_ALIVE) && !(f & VF_BND)) {
           double qold = ball_min_quality(S, c, ne_row(S, v), S.NElen[v], nullptr);
-          eval = qold < S.tab.q_thresh[c.mi];
+          eval = dlt(qold, S.tab.q_thresh[c.mi]);
         }
         if (!eval) mvM[v].w = 0.0;
       }
@@ -1171,7 +1171,7 @@ __device__ __forceinline__ double tmin(const Tile& t, double x) {
 #pragma unroll
   for (int o = TW / 2; o > 0; o >>= 1) {
     double y = __shfl_xor_sync(t.mask, x, o, TW);
-    x = (y < x) ? y : x;
+    x = dlt(y, x) ? y : x;
   }
   return x;
 }
@@ -1188,7 +1188,7 @@ __device__ double tile_ball_quality(const Tile& t, const Store& S, MeshCtx c, co
   for (int base = 0; base < nel; base += TW) {
     int k = base + t.tl;
     double q = (k < nel) ? S.qK[c.eb + ne[k]] : 1e300;
-    qmin = (q < qmin) ? q : qmin;
+    qmin = dlt(q, qmin) ? q : qmin;
     if (qsum) {
       int cnt = min(TW, nel - base);
       for (int j = 0; j < cnt; ++j) sum = sum + tshfl(t, q, j);
@@ -1220,7 +1220,7 @@ __device__ bool tile_interpolate(const Tile& t, const Store& S, MeshCtx c, const
       s0 = orient3(px, b, d);
       s1 = orient3(a, px, d);
       s2 = orient3(a, b, px);
-      inside = s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0;
+      inside = dge0(s0) && dge0(s1) && dge0(s2);
     }
     unsigned bal = (__ballot_sync(t.mask, inside) >> t.shift) & 0xFFu;
     if (bal) {
@@ -1256,9 +1256,9 @@ __device__ bool tile_ball_after_move(const Tile& t, const Store& S, MeshCtx c, i
       VD a = (e.x == lv) ? nvd : load_vd(S, c.vb + e.x);
       VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
       VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
-      if (orient_c(e.x, e.y, e.z, a, b, d) > 0.0) {
+      if (dgt(orient_c(e.x, e.y, e.z, a, b, d), 0.0)) {
         q = quality_c(e.x, e.y, e.z, a, b, d);
-        if (strict ? !(q > floor) : (q < floor)) ok = false;
+        if (strict ? !dgt(q, floor) : dlt(q, floor)) ok = false;
         if (qout) qout[k] = q;
       } else {
         ok = false;
@@ -1288,7 +1288,7 @@ __device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c
   const int* ne = ne_row(S, v);
   int nel = S.NElen[v];
   double qold = tile_ball_quality(t, S, c, ne, nel, nullptr);
-  if (!(qold < S.tab.q_thresh[c.mi])) return false;
+  if (!dlt(qold, S.tab.q_thresh[c.mi])) return false;
   const int* nn = nn_row(S, v);
   int nnl = S.NNlen[v];
   double4 mv = S.M[v];
@@ -1317,7 +1317,7 @@ __device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c
   }
   ops = 17 * nnl + 3;
   double det = a00 * a11 - a01 * a01;
-  if (!(det > 0.0)) return false;
+  if (!dgt(det, 0.0)) return false;
   double x = (a11 * b0 - a01 * b1) / det;
   double y = (a00 * b1 - a01 * b0) / det;
   ops += 8;
@@ -1736,7 +1736,7 @@ __global__ void k_refine_split(Store S, const int* escan, const int4* emid, cons
         put(s, m0, u1, m1);
         double d1 = metric_len(load_vd(S, vb + u0), load_vd(S, vb + m1));
         double d2 = metric_len(load_vd(S, vb + m0), load_vd(S, vb + u2));
-        if (d1 <= d2) {
+        if (!dgt(d1, d2)) {
           put(nslot, u0, m0, m1);
           put(nslot + 1, u0, m1, u2);
         } else {
