@@ -40,6 +40,17 @@ __device__ __forceinline__ MeshCtx ctx_of(const Store& S, int slot) {
   return c;
 }
 
+// Which thread takes list entry i.  Contiguous: consecutive entries to
+// consecutive threads of a block (coalesced list reads, for long lists).
+// Interleaved (`il`): entry i to block i mod gridDim.x, so that a short list
+// spreads over every SM instead of the first few blocks; that matters when
+// an entry's work is FP64, whose issue cost per warp is the same for one
+// active lane as for 32.
+__device__ __forceinline__ int grank(bool il) {
+  return il ? threadIdx.x * gridDim.x + blockIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ int gsize() { return gridDim.x * blockDim.x; }
+
 __device__ __forceinline__ const int* nn_row(const Store& S, int slot) {
   return S.NN + (size_t)slot * S.W;
 }
@@ -448,10 +459,10 @@ __global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2*
 __device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const int* nDp,
                                                    int* target, int* cand, int* ncand, int* C,
                                                    int* nC, int* cmark, int tag, int pass0,
-                                                   unsigned long long* work) {
+                                                   unsigned long long* work, bool il = false) {
   const int n = *nDp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     int v = 0;
     bool found = false;
     unsigned ops = 0;
@@ -545,10 +556,11 @@ __device__ __forceinline__ void coarsen_select_apply_phase(Store S, const int* C
                                                            const int* target, int* A, int* nA,
                                                            int* amark, int* Dn, int* nDn,
                                                            int* dmark,
-                                                           unsigned long long* work) {
+                                                           unsigned long long* work,
+                                                           bool il = false) {
   const int n = *nCp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     bool win = false, lose = false;
     int v = 0;
     unsigned ops = 0;
@@ -578,9 +590,9 @@ __global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, co
 //   NE(u) <- live elements of NE(u) + (when u is the target of x) NE(x).
 __device__ __forceinline__ void coarsen_commit_phase(Store S, const int* A, const int* nAp,
                                                      const int* target, const int* smark, int tag,
-                                                     DevStatus* st) {
+                                                     DevStatus* st, bool il = false) {
   const int n = *nAp;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = grank(il); i < n; i += gsize()) {
     int u = A[i];
     S.touch[u] = tag + 1;
     MeshCtx c = ctx_of(S, u);
@@ -672,10 +684,11 @@ __device__ __forceinline__ void append_item(bool pred, int2 val, int2* list, int
 __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int* nDp,
                                                 const int4* opA, int* C, int* nC, int* cmark,
                                                 int tag, int pass0, int* E, int* nE, int2* items,
-                                                int* nI, int icap, double* gains, DevStatus* st) {
+                                                int* nI, int icap, double* gains, DevStatus* st,
+                                                bool il = false) {
   const int n = *nDp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     int v = 0, nel = 0;
     bool reuse_cand = false, eval = false;
     MeshCtx c{0, 0, 0};
@@ -855,10 +868,11 @@ __device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, c
 }
 
 __device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, const int* nIp,
-                                                double* gains, unsigned long long* work) {
+                                                double* gains, unsigned long long* work,
+                                                bool il = false) {
   const int n = *nIp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     unsigned ops = 0;
     if (i < n) {
       int2 it = items[i];
@@ -881,10 +895,10 @@ __global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* 
 // smallest w; the flip record (w, c, d, K1, K2) of the winner.
 __device__ __forceinline__ void swap_pick_phase(Store S, const int* E, const int* nEp,
                                                 const double* gains, int4* opA, int* opK2, int* C,
-                                                int* nC, int* cmark, int tag) {
+                                                int* nC, int* cmark, int tag, bool il = false) {
   const int n = *nEp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     int v = 0;
     bool found = false;
     if (i < n) {
@@ -991,10 +1005,11 @@ __device__ __forceinline__ void swap_select_apply_phase(Store S, const int* C, c
                                                         const int* cmark, int* smark, int tag,
                                                         const int4* opA, const int* opK2, int* A,
                                                         int* nA, int* amark, int* Dn, int* nDn,
-                                                        int* dmark, unsigned long long* work) {
+                                                        int* dmark, unsigned long long* work,
+                                                        bool il = false) {
   const int n = *nCp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     bool win = false, lose = false;
     int v = 0;
     unsigned ops = 0;
@@ -1025,9 +1040,10 @@ __global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const
 //   u == c: NN +d, NE +K2;  u == d: NN +c, NE +K1.
 __device__ __forceinline__ void swap_commit_phase(Store S, const int* A, const int* nAp,
                                                   const int4* opA, const int* opK2,
-                                                  const int* smark, int tag, DevStatus* st) {
+                                                  const int* smark, int tag, DevStatus* st,
+                                                  bool il = false) {
   const int n = *nAp;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = grank(il); i < n; i += gsize()) {
     int u = A[i];
     S.touch[u] = tag + 1;
     MeshCtx c = ctx_of(S, u);
@@ -1106,10 +1122,11 @@ __device__ __forceinline__ double ball_min_quality(const Store& S, MeshCtx c, co
 // (cached qualities), list the rest for the full move evaluation.
 __device__ __forceinline__ void smooth_scan_phase(Store S, const int* D, const int* nDp,
                                                   double4* mvM, int* C, int* nC, int* cmark,
-                                                  int tag, int pass0, int* E, int* nE) {
+                                                  int tag, int pass0, int* E, int* nE,
+                                                  bool il = false) {
   const int n = *nDp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     int v = 0;
     bool reuse_cand = false, eval = false;
     if (i < n) {
@@ -1338,12 +1355,14 @@ __device__ bool tile_smooth_eval(const Tile& t, const Store& S, int v, MeshCtx c
 __device__ __forceinline__ void smooth_eval_phase(Store S, const int* E, const int* nEp,
                                                   double2* mvxy, double4* mvM, double* qball,
                                                   int* C, int* nC, int* cmark, int tag,
-                                                  unsigned long long* work) {
+                                                  unsigned long long* work, bool il = false) {
   const int n = *nEp;
   const Tile t = tile_of();
   const int tiles_per_block = blockDim.x / TW;
-  for (int j0 = blockIdx.x * tiles_per_block; j0 < n; j0 += gridDim.x * tiles_per_block) {
-    int j = j0 + threadIdx.x / TW;
+  const int tile_rank = il ? (threadIdx.x / TW) * gridDim.x + blockIdx.x
+                          : blockIdx.x * tiles_per_block + threadIdx.x / TW;
+  for (int j0 = 0; j0 < n; j0 += gridDim.x * tiles_per_block) {
+    int j = j0 + tile_rank;
     int v = 0, ops = 0;
     bool cand = false;
     if (j < n) {
@@ -1423,10 +1442,11 @@ __device__ __forceinline__ void smooth_select_apply_phase(Store S, const int* C,
                                                           int* Dn, int* nDn, int* dmark,
                                                           const double2* mvxy, const double4* mvM,
                                                           const double* qball, int* P, int* nP,
-                                                          int* pmark, int ptag, int stamp) {
+                                                          int* pmark, int ptag, int stamp,
+                                                          bool il = false) {
   const int n = *nCp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
     bool win = false, lose = false;
     int v = 0;
     if (i < n) {
@@ -1974,33 +1994,34 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
       // flips keep their three passes: the gains are many per vertex, and
       // item-parallel FP64 beats two barriers saved
       swap_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.opA, w.C, nC, w.cmark, tag, a.pass0,
-                      w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st);
+                      w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
-      swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains, a.work);
+      swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains, a.work, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
-      swap_pick_phase(a.S, w.E, cnt + CN_E, w.gains, w.opA, w.opK2, w.C, nC, w.cmark, tag);
+      swap_pick_phase(a.S, w.E, cnt + CN_E, w.gains, w.opA, w.opK2, w.C, nC, w.cmark, tag, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = cnt[CN_I] = 0;
     } else {
       coarsen_eval_phase(a.S, w.D[cur], cnt + cn_list(cur), w.target, w.cand, w.ncand, w.C, nC,
-                         w.cmark, tag, a.pass0, a.work);
+                         w.cmark, tag, a.pass0, a.work, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
     }
     if (FLIP)
       swap_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.opA, w.opK2, w.A,
-                              cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work);
+                              cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work,
+                              true);
     else
       coarsen_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.target, w.A, cnt + CN_A,
-                                 w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work);
+                                 w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work, true);
     if (!grid_barrier(a.bar, target, a.st)) return;
     const int nc = ld_volatile(nC), nd = ld_volatile(cnt + cn_list(nxt));
     advance_rounds(a.S);
     if (FLIP)
-      swap_commit_phase(a.S, w.A, cnt + CN_A, w.opA, w.opK2, w.smark, tag, a.st);
+      swap_commit_phase(a.S, w.A, cnt + CN_A, w.opA, w.opK2, w.smark, tag, a.st, true);
     else
-      coarsen_commit_phase(a.S, w.A, cnt + CN_A, w.target, w.smark, tag, a.st);
+      coarsen_commit_phase(a.S, w.A, cnt + CN_A, w.target, w.smark, tag, a.st, true);
     if (!grid_barrier(a.bar, target, a.st)) return;
     ++r;
     if (nc == 0) {
@@ -2047,15 +2068,16 @@ __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
     S.tab.had = a.S.tab.had + (r & 1) * S.nmesh;
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[cn_list(nxt)] = 0;
     smooth_scan_phase(S, w.D[cur], cnt + cn_list(cur), w.mvM, w.C, nC, w.cmark, tag, a.pass0, w.E,
-                      cnt + CN_E);
+                      cnt + CN_E, true);
     if (!grid_barrier(a.bar, target, a.st)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
-    smooth_eval_phase(S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, nC, w.cmark, tag, a.work);
+    smooth_eval_phase(S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, nC, w.cmark, tag, a.work,
+                      true);
     if (!grid_barrier(a.bar, target, a.st)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = 0;
     smooth_select_apply_phase(S, w.C, nC, w.cmark, w.smark, tag, w.D[nxt], cnt + cn_list(nxt),
                               w.dmark, w.mvxy, w.mvM, w.gains, w.P, cnt + CN_P, w.pmark, a.ptag,
-                              tag + 1);
+                              tag + 1, true);
     if (!grid_barrier(a.bar, target, a.st)) return;
     const int nc = ld_volatile(nC), nd = ld_volatile(cnt + cn_list(nxt));
     advance_rounds(S);
