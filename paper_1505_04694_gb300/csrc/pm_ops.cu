@@ -2142,7 +2142,7 @@ int after_round(MeshSet& m, const RoundIO& io) {
 
 // Persistent rounds take over once a pass's list holds at most this many
 // vertices (and hand back when the next list outgrows it).
-constexpr int kRoundsLimit = 8192;
+constexpr int kRoundsLimit = 131072;
 constexpr int kRoundsThreads = 256;
 
 // Blocks of a cooperative launch of the persistent round kernels on this
