@@ -92,6 +92,8 @@ struct MeshSet {
   DevStatus* hst = nullptr;    // pinned host
   int* hcounts = nullptr;      // pinned host copy of w.counts
   unsigned long long* hops = nullptr;  // pinned: operation counts of three operators (3 * nmesh)
+  char* hup = nullptr;                 // pinned: staging of the per-mesh table for upload_tab
+  cudaEvent_t upev = nullptr;          // the last table upload has left the staging
   void* pinned = nullptr;      // slot of the process-wide pinned arena (hst, hcounts)
   bool pinned_own = false;     // slot too small: a private pinned allocation
   void* tabmem = nullptr;      // device block holding MeshTab arrays

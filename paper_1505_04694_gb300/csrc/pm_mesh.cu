@@ -20,6 +20,10 @@ namespace {
 // process: page-locking is slow and gets slower after many allocate/free
 // cycles, so slots of one arena are handed out and recycled instead.
 constexpr size_t kPinnedSlot = 16384;
+// staging per mesh of upload_tab: band (double4), L_low/L_up/q_thresh, six
+// ints, the seed
+constexpr size_t kTabUploadBytes = sizeof(double4) + 3 * sizeof(double) + 6 * sizeof(int) +
+                                   sizeof(uint32_t);
 constexpr size_t kPinnedBlock = 64 * kPinnedSlot;
 std::mutex g_pin_mu;
 std::vector<void*> g_pin_free;
@@ -423,9 +427,15 @@ void set_used(MeshSet& m) {
 }
 
 cudaError_t upload_tab(MeshSet& m) {
-  int n = m.nmesh;
+  const int n = m.nmesh;
   set_used(m);
-  std::vector<int> ints(6 * n);
+  // staging in pinned memory (no stream synchronisation); the previous upload
+  // of this set has normally long left it
+  if (m.upev) cudaEventSynchronize(m.upev);
+  double4* band = (double4*)m.hup;
+  double* dbl = (double*)(band + n);
+  int* ints = (int*)(dbl + 3 * n);
+  uint32_t* seed = (uint32_t*)(ints + 6 * n);
   for (int i = 0; i < n; ++i) {
     ints[i] = m.vbase[i];
     ints[n + i] = m.vcap[i];
@@ -433,33 +443,25 @@ cudaError_t upload_tab(MeshSet& m) {
     ints[3 * n + i] = m.ecap[i];
     ints[4 * n + i] = m.nv[i];
     ints[5 * n + i] = m.ne[i];
-  }
-  cudaError_t e = cudaMemcpyAsync(m.S.tab.vbase, ints.data(), ints.size() * sizeof(int),
-                                  cudaMemcpyHostToDevice, m.stream);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(m.S.tab.seed, m.seed.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice,
-                      m.stream);
-  if (e != cudaSuccess) return e;
-  std::vector<double> dbl(3 * n);
-  for (int i = 0; i < n; ++i) {
+    seed[i] = m.seed[i];
     dbl[i] = m.L_low[i];
     dbl[n + i] = m.L_up[i];
     dbl[2 * n + i] = m.q_thresh[i];
-  }
-  e = cudaMemcpyAsync(m.S.tab.L_low, dbl.data(), dbl.size() * sizeof(double),
-                      cudaMemcpyHostToDevice, m.stream);
-  if (e != cudaSuccess) return e;
-  std::vector<double4> band(n);
-  for (int i = 0; i < n; ++i) {
     double a = m.L_low[i], b = m.L_up[i];
     double alo = a * (1.0 - 1e-9), ahi = a * (1.0 + 1e-9);
     double blo = b * (1.0 - 1e-9), bhi = b * (1.0 + 1e-9);
     band[i] = make_double4(alo * alo, ahi * ahi, blo * blo, bhi * bhi);
   }
-  e = cudaMemcpyAsync(m.S.tab.band, band.data(), n * sizeof(double4), cudaMemcpyHostToDevice,
-                      m.stream);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(m.stream);  // host vectors go out of scope
+  cudaError_t e = cudaMemcpyAsync(m.S.tab.vbase, ints, 6 * n * sizeof(int), cudaMemcpyHostToDevice,
+                                  m.stream);
+  if (!e) e = cudaMemcpyAsync(m.S.tab.seed, seed, n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                              m.stream);
+  if (!e) e = cudaMemcpyAsync(m.S.tab.L_low, dbl, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
+                              m.stream);
+  if (!e) e = cudaMemcpyAsync(m.S.tab.band, band, n * sizeof(double4), cudaMemcpyHostToDevice,
+                              m.stream);
+  if (!e && m.upev) e = cudaEventRecord(m.upev, m.stream);
+  return e;
 }
 
 // Read back the per-mesh used-slot counts (nv, ne) into the host mirror.
@@ -590,7 +592,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
     if ((e = cudaMemsetAsync(m.st, 0, sizeof(DevStatus), m.stream))) return e;
     const size_t counts_bytes = (CN_NUM + 2 * (size_t)std::max(n, 1024) + 8) * sizeof(int);
     const size_t ops_off = 64 + ((counts_bytes + 7) & ~size_t(7));
-    size_t need = ops_off + 3 * (size_t)n * sizeof(unsigned long long);
+    const size_t up_off = (ops_off + 3 * (size_t)n * sizeof(unsigned long long) + 63) & ~size_t(63);
+    size_t need = up_off + (size_t)n * kTabUploadBytes;
     if (need <= kPinnedSlot) {
       m.pinned = pinned_get();
       if (!m.pinned) return cudaErrorMemoryAllocation;
@@ -602,6 +605,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
     m.hst = (DevStatus*)m.pinned;
     m.hcounts = (int*)((char*)m.pinned + 64);
     m.hops = (unsigned long long*)((char*)m.pinned + ops_off);
+    m.hup = (char*)m.pinned + up_off;
+    if ((e = cudaEventCreateWithFlags(&m.upev, cudaEventDisableTiming))) return e;
   }
   return cudaSuccess;
 }
@@ -618,10 +623,14 @@ void set_release(MeshSet& m) {
     if (m.pinned_own) cudaFreeHost(m.pinned);
     else pinned_put(m.pinned);
   }
+  if (m.upev) cudaEventDestroy(m.upev);
   m.st = nullptr;
   m.pinned = nullptr;
   m.hst = nullptr;
   m.hcounts = nullptr;
+  m.hops = nullptr;
+  m.hup = nullptr;
+  m.upev = nullptr;
 }
 
 // Move the meshes into new regions of capacity vcap/ecap and row width W.
@@ -640,6 +649,8 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
   n2.hst = m.hst;
   n2.hcounts = m.hcounts;
   n2.hops = m.hops;
+  n2.hup = m.hup;
+  n2.upev = m.upev;
   n2.num_sms = m.num_sms;
   cudaError_t e = set_alloc(n2, vcap, ecap, W);
   if (e != cudaSuccess) {
