@@ -2142,7 +2142,8 @@ int after_round(MeshSet& m, const RoundIO& io) {
 
 // Persistent rounds take over once a pass's list holds at most this many
 // vertices (and hand back when the next list outgrows it).
-constexpr int kRoundsLimit = 131072;
+constexpr int kRoundsLimit = 131072;        // collapse and flip passes
+constexpr int kSmoothRoundsLimit = 131072;  // smoothing sweeps
 constexpr int kRoundsThreads = 256;
 
 // Blocks of a cooperative launch of the persistent round kernels on this
@@ -2474,9 +2475,10 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
     int cur = 0;
     bool moved = false;
     while (max_rounds == 0 || nr < max_rounds) {
-      if (persist && nlist >= 0 && nlist <= kRoundsLimit) {
+      if (persist && nlist >= 0 && nlist <= kSmoothRoundsLimit) {
         RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
         a.ptag = ptag;
+        a.limit = kSmoothRoundsLimit;
         RoundsOut o;
         int err = run_rounds(m, (const void*)k_smooth_rounds, "k_smooth_rounds", a, o);
         if (err) return err;
