@@ -129,6 +129,25 @@ __device__ __forceinline__ void add_work(unsigned long long* work, unsigned ops)
   if ((threadIdx.x & 31) == 0 && tot) atomicAdd(work, (unsigned long long)tot);
 }
 
+// qK of every listed element slot, one element per thread.
+__device__ __forceinline__ void elem_quality_phase(const Store& S, const int* list, const int* np,
+                                                   unsigned long long* work, bool il = false) {
+  const int n = *np;
+  for (int i0 = 0; i0 < n; i0 += gsize()) {
+    int i = i0 + grank(il);
+    unsigned ops = 0;
+    if (i < n) {
+      int slot = list[i];
+      int vb = S.tab.vbase[mesh_of_eslot(S, slot)];
+      int4 e = S.EN[slot];
+      S.qK[slot] = quality_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
+                             load_vd(S, vb + e.z));
+      ops = kOpsQuality;
+    }
+    add_work(work, ops);
+  }
+}
+
 // Stamps the neighbours in `row` (local ids) after a change of their vertex.
 __device__ __forceinline__ void stamp_neighbours(const Store& S, const int* row, int len, int vb,
                                                  int stamp) {
@@ -500,13 +519,18 @@ __device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const 
 // Apply the collapses of S: elements containing edge (v, w) die, the other
 // ball elements take w in v's place (slot and orientation kept), v dies.
 // Neighbours of v are affected (rows change) and dirty for the next round.
+// The qualities of the elements that change are not computed here: their
+// slots join list Q and a dense pass computes them (one element per thread
+// instead of a serial chain of qualities per collapse).
 __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v,
                                                   const int* target, int* A, int* nA,
                                                   int* amark, int* Dn, int* nDn, int* dmark,
-                                                  int tag, unsigned& ops) {
+                                                  int tag, int* Q, int* nQ) {
   {
-    int nnl = 0, mi = 0, vb = 0;
+    int nnl = 0, mi = 0, vb = 0, eb = 0;
     const int* nn = nullptr;
+    const int* ne_v = nullptr;
+    unsigned long long qbits = 0;
     if (ok) {
       MeshCtx c = ctx_of(S, v);
       mi = c.mi;
@@ -524,16 +548,23 @@ __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v
           if (e.x == lv) e.x = w;
           if (e.y == lv) e.y = w;
           if (e.z == lv) e.z = w;
-          S.qK[c.eb + ne[k]] = elem_quality(S, c.vb, e);
-          ops += kOpsQuality;
+          qbits |= 1ull << k;
         }
         *pe = e;
       }
       S.vflag[v] = (uint8_t)(S.vflag[v] & ~VF_ALIVE);
       nn = nn_row(S, v);
       nnl = S.NNlen[v];
+      ne_v = ne;
+      eb = c.eb;
     }
     count_op(S, ok, mi);
+    int pq = warp_reserve(__popcll(qbits), nQ);
+    while (qbits) {
+      int k = __ffsll((long long)qbits) - 1;
+      qbits &= qbits - 1ull;
+      Q[pq++] = eb + ne_v[k];
+    }
     unsigned long long fa = 0, fd = 0;
 #pragma unroll 4
     for (int k = 0; k < nnl; ++k) {
@@ -556,14 +587,13 @@ __device__ __forceinline__ void coarsen_select_apply_phase(Store S, const int* C
                                                            const int* target, int* A, int* nA,
                                                            int* amark, int* Dn, int* nDn,
                                                            int* dmark,
-                                                           unsigned long long* work,
+                                                           int* Q, int* nQ,
                                                            bool il = false) {
   const int n = *nCp;
   for (int i0 = 0; i0 < n; i0 += gsize()) {
     int i = i0 + grank(il);
     bool win = false, lose = false;
     int v = 0;
-    unsigned ops = 0;
     if (i < n) {
       v = C[i];
       win = local_max(S, v, cmark, tag);
@@ -571,16 +601,16 @@ __device__ __forceinline__ void coarsen_select_apply_phase(Store S, const int* C
       else lose = stamp_first(dmark, v, tag);
     }
     warp_append(lose, v, Dn, nDn);
-    coarsen_apply_one(S, win, v, target, A, nA, amark, Dn, nDn, dmark, tag, ops);
-    add_work(work, ops);
+    coarsen_apply_one(S, win, v, target, A, nA, amark, Dn, nDn, dmark, tag, Q, nQ);
   }
 }
 
 __global__ void k_coarsen_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
                                        int* smark, int tag, const int* target, int* A, int* nA,
-                                       int* amark, int* Dn, int* nDn, int* dmark, unsigned* done) {
+                                       int* amark, int* Dn, int* nDn, int* dmark, int* Q, int* nQ,
+                                       unsigned* done) {
   coarsen_select_apply_phase(S, C, nCp, cmark, smark, tag, target, A, nA, amark, Dn, nDn, dmark,
-                             nullptr);
+                             Q, nQ);
   round_done(S, done);
 }
 
@@ -1775,16 +1805,11 @@ __global__ void k_refine_split(Store S, const int* escan, const int4* emid, cons
   }
 }
 
-// Cached quality of every child written this round (one element per thread).
-__global__ void k_refine_quality(Store S, const int* clist, const int* nclp) {
-  const int n = *nclp;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int slot = clist[i];
-    int vb = S.tab.vbase[mesh_of_eslot(S, slot)];
-    int4 e = S.EN[slot];
-    S.qK[slot] = quality_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
-                           load_vd(S, vb + e.z));
-  }
+// Cached quality of every listed element slot (one element per thread): the
+// children of a refinement round, the elements a collapse round changed.
+__global__ void k_refine_quality(Store S, const int* clist, const int* nclp,
+                                 unsigned long long* work) {
+  elem_quality_phase(S, clist, nclp, work);
 }
 
 // Children of parent element K (local id) of this round: K itself and, when
@@ -1989,6 +2014,7 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       cnt[CN_A] = 0;
       cnt[cn_list(nxt)] = 0;
+      cnt[CN_CL] = 0;  // collapses: elements whose quality changes
     }
     if (FLIP) {
       // flips keep their three passes: the gains are many per vertex, and
@@ -2014,14 +2040,17 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
                               true);
     else
       coarsen_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.target, w.A, cnt + CN_A,
-                                 w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work, true);
+                                 w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, w.clist,
+                                 cnt + CN_CL, true);
     if (!grid_barrier(a.bar, target, a.st)) return;
     const int nc = ld_volatile(nC), nd = ld_volatile(cnt + cn_list(nxt));
     advance_rounds(a.S);
     if (FLIP)
       swap_commit_phase(a.S, w.A, cnt + CN_A, w.opA, w.opK2, w.smark, tag, a.st, true);
-    else
+    else {
       coarsen_commit_phase(a.S, w.A, cnt + CN_A, w.target, w.smark, tag, a.st, true);
+      elem_quality_phase(a.S, w.clist, cnt + CN_CL, a.work, true);
+    }
     if (!grid_barrier(a.bar, target, a.st)) return;
     ++r;
     if (nc == 0) {
@@ -2286,11 +2315,14 @@ int op_coarsen(MeshSet& m, int max_rounds) {
               w.counts + CN_I2, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 0);
     PM_LAUNCH(k_coarsen_check, gv, BLOCK, 0, m.stream, m.S, w.items2, w.counts + CN_I2, w.items,
               w.counts + CN_I, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 1);
+    zero_counts(m, CN_CL, 1);
     PM_LAUNCH(k_coarsen_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
               w.smark, tag, w.target, w.A, w.counts + CN_A, w.amark, w.D[nxt],
-              w.counts + cn_list(nxt), w.dmark, (unsigned*)(w.counts + CN_DONE));
+              w.counts + cn_list(nxt), w.dmark, w.clist, w.counts + CN_CL,
+              (unsigned*)(w.counts + CN_DONE));
     PM_LAUNCH(k_coarsen_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target,
               w.smark, tag, m.st);
+    PM_LAUNCH(k_refine_quality, gv, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
     RoundIO io = read_round(m);
     if (io.err) return io.err;
     if (io.nC == 0) {
@@ -2434,7 +2466,7 @@ int op_refine(MeshSet& m, int max_rounds) {
     scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
     PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid, w.elist,
               w.counts + CN_EL, w.clist, w.counts + CN_CL, stamp);
-    PM_LAUNCH(k_refine_quality, ge, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL);
+    PM_LAUNCH(k_refine_quality, ge, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
     // rows of the vertices whose elements changed, through the spare buffer
     PM_LAUNCH(k_refine_rows, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, w.vscan,
               w.escan, w.opA, stamp, m.st);
