@@ -982,12 +982,14 @@ __global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double*
   swap_pick_phase(S, E, nEp, gains, opA, opK2, C, nC, cmark, tag);
 }
 
+// The two new elements' qualities are left to a dense pass (their slots join
+// list Q), as for collapses.
 __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, const int4* opA,
                                                const int* opK2, int* A, int* nA, int* amark,
-                                               int* Dn, int* nDn, int* dmark, int tag,
-                                               unsigned& ops) {
+                                               int* Dn, int* nDn, int* dmark, int tag, int* Q,
+                                               int* nQ) {
   {
-    int mi = 0;
+    int mi = 0, q1 = 0, q2 = 0;
     int t[4] = {0, 0, 0, 0};
     if (ok) {
       MeshCtx c = ctx_of(S, v);
@@ -999,9 +1001,8 @@ __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, c
       int4 t2 = make_int4(op.z, op.x, op.y, 1);  // K2 = (d, w, c)
       S.EN[c.eb + op.w] = t1;
       S.EN[c.eb + K2] = t2;
-      S.qK[c.eb + op.w] = elem_quality(S, c.vb, t1);
-      S.qK[c.eb + K2] = elem_quality(S, c.vb, t2);
-      ops += 2 * kOpsQuality;
+      q1 = c.eb + op.w;
+      q2 = c.eb + K2;
       t[0] = v;
       t[1] = c.vb + op.x;
       t[2] = c.vb + op.y;
@@ -1022,10 +1023,15 @@ __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, c
     }
     int pa = warp_reserve(na, nA);
     int pd = warp_reserve(nd, nDn);
+    int pq = warp_reserve(ok ? 2 : 0, nQ);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (fa[k]) A[pa++] = t[k];
       if (fd[k]) Dn[pd++] = t[k];
+    }
+    if (ok) {
+      Q[pq] = q1;
+      Q[pq + 1] = q2;
     }
   }
 }
@@ -1035,14 +1041,13 @@ __device__ __forceinline__ void swap_select_apply_phase(Store S, const int* C, c
                                                         const int* cmark, int* smark, int tag,
                                                         const int4* opA, const int* opK2, int* A,
                                                         int* nA, int* amark, int* Dn, int* nDn,
-                                                        int* dmark, unsigned long long* work,
+                                                        int* dmark, int* Q, int* nQ,
                                                         bool il = false) {
   const int n = *nCp;
   for (int i0 = 0; i0 < n; i0 += gsize()) {
     int i = i0 + grank(il);
     bool win = false, lose = false;
     int v = 0;
-    unsigned ops = 0;
     if (i < n) {
       v = C[i];
       win = local_max(S, v, cmark, tag);
@@ -1050,17 +1055,16 @@ __device__ __forceinline__ void swap_select_apply_phase(Store S, const int* C, c
       else lose = stamp_first(dmark, v, tag);
     }
     warp_append(lose, v, Dn, nDn);
-    swap_apply_one(S, win, v, opA, opK2, A, nA, amark, Dn, nDn, dmark, tag, ops);
-    add_work(work, ops);
+    swap_apply_one(S, win, v, opA, opK2, A, nA, amark, Dn, nDn, dmark, tag, Q, nQ);
   }
 }
 
 __global__ void k_swap_select_apply(Store S, const int* C, const int* nCp, const int* cmark,
                                     int* smark, int tag, const int4* opA, const int* opK2, int* A,
-                                    int* nA, int* amark, int* Dn, int* nDn, int* dmark,
-                                    unsigned* done) {
+                                    int* nA, int* amark, int* Dn, int* nDn, int* dmark, int* Q,
+                                    int* nQ, unsigned* done) {
   swap_select_apply_phase(S, C, nCp, cmark, smark, tag, opA, opK2, A, nA, amark, Dn, nDn, dmark,
-                          nullptr);
+                          Q, nQ);
   round_done(S, done);
 }
 
@@ -2014,7 +2018,7 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       cnt[CN_A] = 0;
       cnt[cn_list(nxt)] = 0;
-      cnt[CN_CL] = 0;  // collapses: elements whose quality changes
+      cnt[CN_CL] = 0;  // elements whose quality changes
     }
     if (FLIP) {
       // flips keep their three passes: the gains are many per vertex, and
@@ -2036,8 +2040,8 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
     }
     if (FLIP)
       swap_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.opA, w.opK2, w.A,
-                              cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, a.work,
-                              true);
+                              cnt + CN_A, w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, w.clist,
+                              cnt + CN_CL, true);
     else
       coarsen_select_apply_phase(a.S, w.C, nC, w.cmark, w.smark, tag, w.target, w.A, cnt + CN_A,
                                  w.amark, w.D[nxt], cnt + cn_list(nxt), w.dmark, w.clist,
@@ -2047,10 +2051,9 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
     advance_rounds(a.S);
     if (FLIP)
       swap_commit_phase(a.S, w.A, cnt + CN_A, w.opA, w.opK2, w.smark, tag, a.st, true);
-    else {
+    else
       coarsen_commit_phase(a.S, w.A, cnt + CN_A, w.target, w.smark, tag, a.st, true);
-      elem_quality_phase(a.S, w.clist, cnt + CN_CL, a.work, true);
-    }
+    elem_quality_phase(a.S, w.clist, cnt + CN_CL, a.work, true);
     if (!grid_barrier(a.bar, target, a.st)) return;
     ++r;
     if (nc == 0) {
@@ -2380,11 +2383,14 @@ int op_swap(MeshSet& m, int max_rounds) {
               w.counts + CN_I, w.gains, prof_work("k_swap_edge"));
     PM_LAUNCH(k_swap_pick, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
               w.opK2, w.C, w.counts + CN_C, w.cmark, tag);
+    zero_counts(m, CN_CL, 1);
     PM_LAUNCH(k_swap_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
               w.smark, tag, w.opA, w.opK2, w.A, w.counts + CN_A, w.amark, w.D[nxt],
-              w.counts + cn_list(nxt), w.dmark, (unsigned*)(w.counts + CN_DONE));
+              w.counts + cn_list(nxt), w.dmark, w.clist, w.counts + CN_CL,
+              (unsigned*)(w.counts + CN_DONE));
     PM_LAUNCH(k_swap_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2,
               w.smark, tag, m.st);
+    PM_LAUNCH(k_refine_quality, gv, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
     RoundIO io = read_round(m);
     if (io.err) return io.err;
     if (io.nC == 0) {
