@@ -2174,7 +2174,8 @@ int after_round(MeshSet& m, const RoundIO& io) {
 
 // Persistent rounds take over once a pass's list holds at most this many
 // vertices (and hand back when the next list outgrows it).
-constexpr int kRoundsLimit = 131072;        // collapse and flip passes
+constexpr int kRoundsLimit = 131072;        // collapse passes
+constexpr int kSwapRoundsLimit = 131072;    // flip passes (each vertex lists about six edges)
 constexpr int kSmoothRoundsLimit = 131072;  // smoothing sweeps
 constexpr int kRoundsThreads = 256;
 
@@ -2357,9 +2358,10 @@ int op_swap(MeshSet& m, int max_rounds) {
   bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds;) {
     if (m.lo_swap > pass0) pass0 = m.lo_swap;  // rows were rebuilt after an overflow
-    if (persist && nlist >= 0 && nlist <= kRoundsLimit) {
+    if (persist && nlist >= 0 && nlist <= kSwapRoundsLimit) {
       RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
       a.icap = icap;
+      a.limit = kSwapRoundsLimit;
       RoundsOut o;
       int err = run_rounds(m, (const void*)k_swap_rounds, "k_swap_rounds", a, o);
       if (err) return err;
