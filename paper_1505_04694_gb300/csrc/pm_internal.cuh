@@ -70,6 +70,7 @@ enum CountIdx {
   CN_RES = 12,  // persistent rounds: rounds run, list index after, pass complete (3)
   CN_BAR = 15,  // persistent rounds: grid barrier arrivals
   CN_C2 = 16,   // persistent rounds: candidates of odd rounds
+  CN_RENUM = 17,  // renumbering: 1 when some mesh's compaction is not the identity
   CN_NUM = 18
 };
 constexpr int cn_list(int i) { return i == 0 ? CN_D0 : CN_D1; }

@@ -309,12 +309,17 @@ __global__ void k_set_sizes(Store S, const int* tot) {
   S.tab.ne[i] = tot[2 * i + 1];
 }
 
-__global__ void k_mesh_totals(Store S, const int* vscan, const int* escan, int* out) {
+// Live counts of every mesh; with `changed`, records whether any mesh has a
+// dead slot (its compaction is not the identity).
+__global__ void k_mesh_totals(Store S, const int* vscan, const int* escan, int* out,
+                              int* changed) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.nmesh) return;
   int vb = S.tab.vbase[i], eb = S.tab.ebase[i];
   out[2 * i] = vscan[vb + S.tab.nv[i]] - vscan[vb];
   out[2 * i + 1] = escan[eb + S.tab.ne[i]] - escan[eb];
+  if (changed && (out[2 * i] != S.tab.nv[i] || out[2 * i + 1] != S.tab.ne[i]))
+    atomicOr(changed, 1);
 }
 
 // One slot per thread.  Rows move in 16-byte chunks (W is a multiple of 4 and
@@ -332,7 +337,9 @@ __device__ __forceinline__ void renum_row(const int* row, int len, int* out, con
   }
 }
 
-__global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) {
+__global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan,
+                          const int* changed) {
+  if (!*changed) return;  // nothing died since the last compaction
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!vslot_used(A, s, mi)) continue;
@@ -357,7 +364,9 @@ __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan) 
   }
 }
 
-__global__ void k_renum_e(Store A, Store B, const int* vscan, const int* escan) {
+__global__ void k_renum_e(Store A, Store B, const int* vscan, const int* escan,
+                          const int* changed) {
+  if (!*changed) return;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.eused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!eslot_used(A, s, mi)) continue;
@@ -778,18 +787,28 @@ int renumber(MeshSet& m) {
   scan_alive_vertices(m.S, w.vscan, m.S.vused, m.scan, m.st, m.stream);
   scan_alive_elements(m.S, w.escan, m.S.eused, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
-  PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
+  int* changed = w.counts + CN_RENUM;
+  cudaMemsetAsync(changed, 0, sizeof(int), m.stream);
+  PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot,
+            changed);
   // the second buffer's flags must read "dead" beyond the new counts
   cudaMemsetAsync(m.B.vflag, 0, m.S.vslots, m.stream);
-  PM_LAUNCH(k_renum_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
-  PM_LAUNCH(k_renum_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan);
+  PM_LAUNCH(k_renum_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan,
+            changed);
+  PM_LAUNCH(k_renum_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan,
+            changed);
   PM_LAUNCH(k_set_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, tot);
   cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
+  cudaMemcpyAsync(m.hcounts + 2 * m.nmesh, changed, sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   int err = sync_status(m);
   if (err) return err;
   for (int i = 0; i < m.nmesh; ++i) {
     m.nv[i] = m.hcounts[2 * i];
     m.ne[i] = m.hcounts[2 * i + 1];
+  }
+  if (!m.hcounts[2 * m.nmesh]) {  // no dead slot: the compaction is the identity
+    set_used(m);
+    return PM_OK;
   }
   std::swap(m.S.xy, m.B.xy);
   std::swap(m.S.M, m.B.M);
@@ -818,7 +837,8 @@ int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int*
   scan_alive_vertices(m.S, w.vscan, m.S.vused, m.scan, m.st, m.stream);
   scan_alive_elements(m.S, w.escan, m.S.eused, m.scan, m.st, m.stream);
   int* tot = w.counts + CN_NUM;
-  PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot);
+  PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot,
+            (int*)nullptr);
   if (xy || mt)
     PM_LAUNCH(k_out_v, grid_for(m, m.nv[mesh]), BLOCK, 0, m.stream, m.S, mesh, w.vscan, xy, mt);
   if (tri)
