@@ -200,6 +200,13 @@ uint64_t pm_kernel_launches(void);
 pm_status pm_profile_enable(const char* kernel_substring);
 pm_status pm_profile_read(double* total_ms, int64_t* launches, double* work);
 
+/* Measurement support: the FP64 add and multiply throughput of the current
+ * device, in G operations per second, from a kernel that keeps every SM's
+ * FP64 pipe busy with independent additions and multiplications (no fused
+ * multiply-add).  Runs on the default stream and synchronises; about 20 ms.
+ * The paper has no counterpart. */
+pm_status pm_fp64_peak(double* gops);
+
 /* pm_quality_arrays_dev for callers that cannot allocate device memory
  * during the call (a framework that has already reserved the device memory
  * for its own allocator, a latency-bound loop, or a program that allows no

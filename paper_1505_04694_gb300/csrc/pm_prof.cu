@@ -23,6 +23,24 @@ unsigned long long* g_work = nullptr;  // device counter of the profiled kernel'
 std::vector<ProfEvent> g_pool;
 size_t g_used = 0;
 
+// Eight independent chains per thread, each step one multiplication and one
+// addition (the library is compiled without contraction): the FP64 pipe is
+// the only limit.  `out` keeps the result alive.
+__global__ void k_fp64_peak(int iters, double seed, double* out) {
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = seed + j + threadIdx.x * 1e-3;
+  const double m = 0.999999999, c = 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = a[j] * m + c;
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t += a[j];
+  if (t == 12345.678) out[0] = t;  // never true; keeps the chains
+}
+
 }  // namespace
 
 int prof_begin(const char* name, cudaStream_t s) {
@@ -72,6 +90,37 @@ pm_status pm_profile_enable(const char* kernel_substring) {
     }
     if (cudaMemset(g_work, 0, sizeof(unsigned long long)) != cudaSuccess) return PM_ERR_CUDA;
   }
+  return PM_OK;
+}
+
+pm_status pm_fp64_peak(double* gops) {
+  if (!gops) return PM_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PM_ERR_CUDA;
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double)) != cudaSuccess) return PM_ERR_CUDA;
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    k_fp64_peak<<<blocks, threads>>>(iters, 1.0 + rep, out);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;  // the first run warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (cudaGetLastError() != cudaSuccess) return PM_ERR_CUDA;
+  const double ops = 2.0 * 8.0 * iters * (double)blocks * threads;
+  *gops = ops / (best * 1e-3) / 1e9;
   return PM_OK;
 }
 

@@ -29,7 +29,8 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_smooth", "pm_adapt", "pm_opt_smooth", "pm_adapt_batch", "pm_get_mesh",
            "pm_get_mesh_dev", "pm_get_raw", "pm_adjacency", "pm_quality",
            "pm_quality_arrays_dev", "pm_status_string", "pm_last_error", "pm_kernel_launches",
-           "pm_profile_enable", "pm_profile_read", "pm_quality_arrays_noalloc_dev"]
+           "pm_profile_enable", "pm_profile_read", "pm_quality_arrays_noalloc_dev",
+           "pm_fp64_peak"]
 
 
 class PmParams(C.Structure):
@@ -97,6 +98,8 @@ def _load():
     L.pm_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_double)]
     L.pm_profile_read.restype = C.c_int
+    L.pm_fp64_peak.argtypes = [C.POINTER(C.c_double)]
+    L.pm_fp64_peak.restype = C.c_int
     L.pm_status_string.argtypes = [C.c_int]
     L.pm_status_string.restype = C.c_char_p
     L.pm_last_error.argtypes = []
@@ -354,6 +357,13 @@ def profile_enable(kernel_substring):
     """Time every launch of library kernels whose name contains the string."""
     _check(lib.pm_profile_enable(kernel_substring.encode() if kernel_substring else None),
            "pm_profile_enable")
+
+
+def fp64_peak():
+    """Measured FP64 add/multiply throughput of the current device, G ops/s."""
+    g = C.c_double()
+    _check(lib.pm_fp64_peak(C.byref(g)), "pm_fp64_peak")
+    return float(g.value)
 
 
 def profile_read():
