@@ -280,7 +280,7 @@ pm_status adapt_set(MeshSet& m, const pm_params* P, int stride, CallStats& cs) {
     if ((s = run_counted_async(m, [&] { return op_coarsen(m, mr); }, 0))) return s;
     if ((s = run_counted_async(m, [&] { return op_swap(m, mr); }, 1))) return s;
     if ((s = run_counted_async(m, [&] { return op_refine(m, mr); }, 2))) return s;
-    int err = renumber(m);  // ends with a synchronisation: the counts have arrived
+    int err = renumber(m, false);  // synchronises: the op counts have arrived
     if (err) return (pm_status)err;
     const unsigned long long* h = m.hops;
     for (int i = 0; i < n; ++i) {
@@ -308,7 +308,7 @@ pm_status adapt_set(MeshSet& m, const pm_params* P, int stride, CallStats& cs) {
   if ((s = run_counted(m, [&] { return op_smooth(m, sweeps, mr); }, cs.moves))) return s;
   if (opt > 0)
     if ((s = run_counted(m, [&] { return op_opt_smooth(m, opt, mr); }, cs.moves))) return s;
-  int err = renumber(m);
+  int err = renumber(m, true);
   return (pm_status)err;
 }
 

@@ -68,6 +68,13 @@ struct Store {
   int* evs;
   int* evm;
   int* evr;
+  // Vertex numbering.  A vertex's id is its slot offset in its mesh's region,
+  // except after a renumbering that left the slots in place: lid[v] is then
+  // v's id (its rank among the live slots of its mesh at that renumbering,
+  // slots appended since counting on from there) and voff[mesh] is the number
+  // of dead slots the ids skip.  Null when ids are the slot offsets.
+  int* lid;
+  int* voff;
   MeshTab tab;
 };
 
@@ -417,6 +424,11 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 __device__ __forceinline__ uint32_t prio(uint32_t v, uint32_t seed, uint32_t r) {
   uint32_t sr = seed + 0x9E3779B9u * r;
   return fmix32(v ^ sr);
+}
+
+// Id of the vertex in slot s of the mesh whose region starts at vb.
+__device__ __forceinline__ uint32_t vid_of(const Store& S, int s, int vb) {
+  return S.lid ? (uint32_t)S.lid[s] : (uint32_t)(s - vb);
 }
 
 }  // namespace pm

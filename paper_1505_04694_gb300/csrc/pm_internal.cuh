@@ -98,6 +98,8 @@ struct MeshSet {
   void* pinned = nullptr;      // slot of the process-wide pinned arena (hst, hcounts)
   bool pinned_own = false;     // slot too small: a private pinned allocation
   void* tabmem = nullptr;      // device block holding MeshTab arrays
+  int* lidbuf = nullptr;       // S.lid and S.voff when in use (vslots, nmesh)
+  int* voffbuf = nullptr;
   int tag = 0;                 // per-round tag (even); the round's change stamp is tag + 1
   // evaluations with tags at or below these are stale for that operator
   int lo_coarsen = 0, lo_swap = 0, lo_refine = 0;
@@ -115,7 +117,7 @@ cudaError_t upload_tab(MeshSet& m);
 void set_used(MeshSet& m);
 cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap, int W);
 int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev);
-int renumber(MeshSet& m);
+int renumber(MeshSet& m, bool final);
 int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
                 int* ne_out);
 int sync_status(MeshSet& m);

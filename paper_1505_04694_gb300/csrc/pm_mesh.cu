@@ -108,6 +108,7 @@ __global__ void k_relayout_v(Store A, Store B) {
     B.evs[ns] = A.evs[s];
     B.evm[ns] = A.evm[s];
     B.evr[ns] = A.evr[s];
+    if (A.lid && B.lid) B.lid[ns] = A.lid[s];
     int wn = A.W < B.W ? A.W : B.W;
     int a = A.NNlen[s], b = A.NElen[s];
     B.NNlen[ns] = a;
@@ -364,6 +365,20 @@ __global__ void k_renum_v(Store A, Store B, const int* vscan, const int* escan,
   }
 }
 
+// Renumbering in place: every live vertex's id becomes its rank among the
+// live slots of its mesh; ids of slots appended later skip the dead slots.
+__global__ void k_renum_ids(Store S, const int* vscan, const int* tot, int* lid, int* voff) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!vslot_used(S, s, mi)) continue;
+    if (!(S.vflag[s] & VF_ALIVE)) continue;
+    int vb = S.tab.vbase[mi];
+    lid[s] = vscan[s] - vscan[vb];
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nmesh; i += gridDim.x * blockDim.x)
+    voff[i] = S.tab.nv[i] - tot[2 * i];
+}
+
 __global__ void k_renum_e(Store A, Store B, const int* vscan, const int* escan,
                           const int* changed) {
   if (!*changed) return;
@@ -529,6 +544,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   S.W = W;
   S.vslots = (int)vs;
   S.eslots = (int)es;
+  S.lid = S.voff = nullptr;
   m.B = S;
   Carver cv;
   carve_store(cv, S);
@@ -571,6 +587,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   cv.add(&w.cand, (size_t)vs * W);
   cv.add(&w.ncand, vs);
   cv.add(&w.counts, CN_NUM + 2 * n + 8);
+  cv.add(&m.lidbuf, vs);
+  cv.add(&m.voffbuf, n);
   int tiles = scan_tiles((int)std::max(vs, es) + 1);
   cv.add(&m.scan.state, tiles);
   cv.add(&m.scan.ticket, 1);
@@ -677,6 +695,11 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
                   m.stream);
   cudaMemcpyAsync(n2.S.tab.ops, m.S.tab.ops, 2 * nm * sizeof(unsigned long long),
                   cudaMemcpyDeviceToDevice, m.stream);
+  if (m.S.lid) {  // ids that are not slot offsets move with their slots
+    n2.S.lid = n2.lidbuf;
+    n2.S.voff = n2.voffbuf;
+    cudaMemcpyAsync(n2.voffbuf, m.S.voff, nm * sizeof(int), cudaMemcpyDeviceToDevice, m.stream);
+  }
   PM_LAUNCH(k_relayout_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, n2.S);
   PM_LAUNCH(k_relayout_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, n2.S);
   e = cudaGetLastError();
@@ -691,6 +714,8 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
   m.w = n2.w;
   m.scan = n2.scan;
   m.tabmem = n2.tabmem;
+  m.lidbuf = n2.lidbuf;
+  m.voffbuf = n2.voffbuf;
   m.allocs = n2.allocs;
   n2.allocs.clear();
   // per-round stamp arrays start at zero, below every later tag; scratch that
@@ -780,9 +805,13 @@ int validate_mesh(MeshSet& m) {
   return sync_status(m);
 }
 
-// Stable compaction of every mesh (live vertices and elements in ascending
-// slot order), adjacency remapped (rows stay sorted: the map is monotone).
-int renumber(MeshSet& m) {
+// Renumbering of every mesh: live vertices and elements in ascending slot
+// order take consecutive ids (adjacency keeps its order: the map is monotone).
+// The final renumbering of a call, or one that finds many dead slots, moves
+// the live slots together (compaction); the others leave every slot in place
+// and record the new vertex ids (only the priorities read id values; every
+// other use of an id is an order, which both numberings share).
+int renumber(MeshSet& m, bool final) {
   Work& w = m.w;
   scan_alive_vertices(m.S, w.vscan, m.S.vused, m.scan, m.st, m.stream);
   scan_alive_elements(m.S, w.escan, m.S.eused, m.scan, m.st, m.stream);
@@ -791,24 +820,41 @@ int renumber(MeshSet& m) {
   cudaMemsetAsync(changed, 0, sizeof(int), m.stream);
   PM_LAUNCH(k_mesh_totals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot,
             changed);
-  // the second buffer's flags must read "dead" beyond the new counts
-  cudaMemsetAsync(m.B.vflag, 0, m.S.vslots, m.stream);
-  PM_LAUNCH(k_renum_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan,
-            changed);
-  PM_LAUNCH(k_renum_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan,
-            changed);
-  PM_LAUNCH(k_set_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, tot);
+  // compaction into the second buffer set (skipped on the device when no
+  // slot died); the host swaps the sets afterwards
+  auto compact = [&] {
+    // the second buffer's flags must read "dead" beyond the new counts
+    cudaMemsetAsync(m.B.vflag, 0, m.S.vslots, m.stream);
+    PM_LAUNCH(k_renum_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan,
+              changed);
+    PM_LAUNCH(k_renum_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.B, w.vscan, w.escan,
+              changed);
+    PM_LAUNCH(k_set_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, tot);
+  };
+  if (final) compact();  // queued before the read-back: one synchronisation
   cudaMemcpyAsync(m.hcounts, tot, 2 * m.nmesh * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   cudaMemcpyAsync(m.hcounts + 2 * m.nmesh, changed, sizeof(int), cudaMemcpyDeviceToHost, m.stream);
   int err = sync_status(m);
   if (err) return err;
+  if (!m.hcounts[2 * m.nmesh]) return PM_OK;  // no dead slot: every id stays
+  if (!final) {
+    long long vdead = 0, edead = 0;
+    for (int i = 0; i < m.nmesh; ++i) {
+      vdead += m.nv[i] - m.hcounts[2 * i];
+      edead += m.ne[i] - m.hcounts[2 * i + 1];
+    }
+    if (8 * vdead <= m.S.vused && 8 * edead <= m.S.eused) {
+      m.S.lid = m.lidbuf;
+      m.S.voff = m.voffbuf;
+      PM_LAUNCH(k_renum_ids, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, w.vscan, tot,
+                m.lidbuf, m.voffbuf);
+      return PM_OK;
+    }
+    compact();
+  }
   for (int i = 0; i < m.nmesh; ++i) {
     m.nv[i] = m.hcounts[2 * i];
     m.ne[i] = m.hcounts[2 * i + 1];
-  }
-  if (!m.hcounts[2 * m.nmesh]) {  // no dead slot: the compaction is the identity
-    set_used(m);
-    return PM_OK;
   }
   std::swap(m.S.xy, m.B.xy);
   std::swap(m.S.M, m.B.M);
@@ -825,6 +871,7 @@ int renumber(MeshSet& m) {
   std::swap(m.S.evs, m.B.evs);
   std::swap(m.S.evm, m.B.evm);
   std::swap(m.S.evr, m.B.evr);
+  m.S.lid = m.S.voff = nullptr;  // ids are the slot offsets again
   set_used(m);
   return PM_OK;
 }

@@ -192,14 +192,16 @@ __global__ void k_select(Store S, const int* C, const int* nCp, const int* cmark
       v = C[i];
       MeshCtx c = ctx_of(S, v);
       uint32_t seed = S.tab.seed[c.mi], r = S.tab.r[c.mi];
-      uint32_t pv = prio((uint32_t)(v - c.vb), seed, r);
+      uint32_t pv = prio(vid_of(S, v, c.vb), seed, r);
       const int* nn = nn_row(S, v);
       int nnl = S.NNlen[v];
       win = true;
 #pragma unroll 4
       for (int k = 0; k < nnl; ++k) {
-        int u = nn[k];
-        win &= !(cmark[c.vb + u] == tag && prio((uint32_t)u, seed, r) > pv);
+        int u = c.vb + nn[k];
+        int cu = cmark[u];
+        uint32_t iu = vid_of(S, u, c.vb);
+        win &= !(cu == tag && prio(iu, seed, r) > pv);
       }
       if (win) smark[v] = tag;
       else if (keep) lose = stamp_first(kmark, v, tag);
@@ -214,14 +216,16 @@ __global__ void k_select(Store S, const int* C, const int* nCp, const int* cmark
 __device__ __forceinline__ bool local_max(const Store& S, int v, const int* cmark, int tag) {
   MeshCtx c = ctx_of(S, v);
   uint32_t seed = S.tab.seed[c.mi], r = S.tab.r[c.mi];
-  uint32_t pv = prio((uint32_t)(v - c.vb), seed, r);
+  uint32_t pv = prio(vid_of(S, v, c.vb), seed, r);
   const int* nn = nn_row(S, v);
   int nnl = S.NNlen[v];
   bool win = true;
 #pragma unroll 4
   for (int k = 0; k < nnl; ++k) {
-    int u = nn[k];
-    win &= !(cmark[c.vb + u] == tag && prio((uint32_t)u, seed, r) > pv);
+    int u = c.vb + nn[k];
+    int cu = cmark[u];
+    uint32_t iu = vid_of(S, u, c.vb);
+    win &= !(cu == tag && prio(iu, seed, r) > pv);
   }
   return win;
 }
@@ -1715,6 +1719,7 @@ __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long
                                0.5 * (da.m11 + db.m11), 0.0);
       bool bedge = count_elems_with(S, ne, nel, eb, b) == 1;
       S.vflag[slot] = (uint8_t)(VF_ALIVE | (bedge ? VF_BND : 0));
+      if (S.lid) S.lid[slot] = (slot - vb) - S.voff[mi];
       S.touch[slot] = stamp;
       S.evc[slot] = S.evs[slot] = S.evm[slot] = S.evr[slot] = 0;
       owner[slot] = make_int4(s - vb, b, 0, 0);  // the split edge (a, b)
@@ -2179,32 +2184,37 @@ constexpr int kSwapRoundsLimit = 131072;    // flip passes (each vertex lists ab
 constexpr int kSmoothRoundsLimit = 131072;  // smoothing sweeps
 constexpr int kRoundsThreads = 256;
 
-// Blocks of a cooperative launch of the persistent round kernels on this
-// device (one per SM when every kernel fits, else 0: rounds stay one kernel
-// per phase).
-int rounds_grid(MeshSet& m) {
+// Resident blocks per SM of a persistent round kernel: as many as its
+// registers allow, at most this many.
+constexpr int kRoundsBlocksPerSm = 1;
+
+// Blocks of a cooperative launch of the persistent round kernel `which`
+// (0 collapse, 1 flip, 2 smoothing) on this device: whole SMs' worth, or 0
+// when the device cannot run it cooperatively (rounds stay one kernel per
+// phase).
+int rounds_grid(MeshSet& m, int which) {
   static std::mutex mu;
-  static int cache[64];
+  static int cache[64][3];
   static bool known[64];
   std::lock_guard<std::mutex> lk(mu);
   const int dev = m.device;
-  if (dev < 0 || dev >= 64) return 0;
+  if (dev < 0 || dev >= 64 || which < 0 || which > 2) return 0;
   if (!known[dev]) {
-    int coop = 0, blocks = 1 << 30;
+    int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     const void* ks[] = {(const void*)k_coarsen_rounds, (const void*)k_swap_rounds,
                         (const void*)k_smooth_rounds};
-    for (const void* k : ks) {
+    for (int k = 0; k < 3; ++k) {
       int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kRoundsThreads, 0) != cudaSuccess)
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ks[k], kRoundsThreads, 0) !=
+          cudaSuccess)
         b = 0;
-      blocks = std::min(blocks, b);
+      cache[dev][k] = (coop && b >= 1) ? m.num_sms * std::min(b, kRoundsBlocksPerSm) : 0;
     }
     cudaGetLastError();
-    cache[dev] = (coop && blocks >= 1) ? m.num_sms : 0;
     known[dev] = true;
   }
-  return cache[dev];
+  return cache[dev][which];
 }
 
 RoundArgs round_args(MeshSet& m, int cur, int pass0, long long max_rounds) {
@@ -2234,13 +2244,14 @@ struct RoundsOut {
 
 // One cooperative launch of persistent rounds, then the read-back of every
 // counter and the status.  Advances the tag past the rounds that ran.
-int run_rounds(MeshSet& m, const void* kernel, const char* name, RoundArgs& a, RoundsOut& out) {
+int run_rounds(MeshSet& m, int which, const void* kernel, const char* name, RoundArgs& a,
+               RoundsOut& out) {
   a.work = prof_work(name);
   void* args[] = {&a};
   cudaMemsetAsync(a.bar, 0, sizeof(unsigned), m.stream);
   __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED);
   int slot = g_prof_on ? prof_begin(name, m.stream) : -1;
-  cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(rounds_grid(m)),
+  cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(rounds_grid(m, which)),
                                               dim3(kRoundsThreads), args, 0, m.stream);
   if (slot >= 0) prof_end(slot, m.stream);
   if (e != cudaSuccess) {
@@ -2281,7 +2292,7 @@ int op_coarsen(MeshSet& m, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vused);
   int pass0 = m.tag;
-  const bool persist = rounds_grid(m) > 0;
+  const bool persist = rounds_grid(m, 0) > 0;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evc,
             m.lo_coarsen);
@@ -2295,7 +2306,7 @@ int op_coarsen(MeshSet& m, int max_rounds) {
     if (persist && nlist >= 0 && nlist <= kRoundsLimit) {
       RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
       RoundsOut o;
-      int err = run_rounds(m, (const void*)k_coarsen_rounds, "k_coarsen_rounds", a, o);
+      int err = run_rounds(m, 0, (const void*)k_coarsen_rounds, "k_coarsen_rounds", a, o);
       if (err) return err;
       nr += o.rounds - o.complete;
       cur = o.cur;
@@ -2349,7 +2360,7 @@ int op_swap(MeshSet& m, int max_rounds) {
   const int gv = grid_for(m, m.S.vused);
   int pass0 = m.tag;
   const int icap = m.S.vslots * 6 + 64;
-  const bool persist = rounds_grid(m) > 0;
+  const bool persist = rounds_grid(m, 1) > 0;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evs,
             m.lo_swap);
@@ -2363,7 +2374,7 @@ int op_swap(MeshSet& m, int max_rounds) {
       a.icap = icap;
       a.limit = kSwapRoundsLimit;
       RoundsOut o;
-      int err = run_rounds(m, (const void*)k_swap_rounds, "k_swap_rounds", a, o);
+      int err = run_rounds(m, 1, (const void*)k_swap_rounds, "k_swap_rounds", a, o);
       if (err) return err;
       nr += o.rounds - o.complete;
       cur = o.cur;
@@ -2504,7 +2515,7 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
   Work& w = m.w;
   const int gv = grid_for(m, m.S.vused);
   const int pass0 = m.tag;
-  const bool persist = rounds_grid(m) > 0;
+  const bool persist = rounds_grid(m, 2) > 0;
   zero_counts(m, 0, CN_NUM);
   PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0, nullptr, 0);
   int nlist = 0;  // unknown at first (see op_coarsen)
@@ -2520,7 +2531,7 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
         a.ptag = ptag;
         a.limit = kSmoothRoundsLimit;
         RoundsOut o;
-        int err = run_rounds(m, (const void*)k_smooth_rounds, "k_smooth_rounds", a, o);
+        int err = run_rounds(m, 2, (const void*)k_smooth_rounds, "k_smooth_rounds", a, o);
         if (err) return err;
         nr += o.rounds - o.complete;
         if (o.rounds - o.complete > 0) moved = true;
