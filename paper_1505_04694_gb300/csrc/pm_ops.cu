@@ -1430,6 +1430,61 @@ __device__ __forceinline__ void smooth_eval_phase(Store S, const int* E, const i
   }
 }
 
+// Passes 1 and 2 in one (persistent rounds whose list fits one tile per
+// listed vertex): an evaluation whose inputs carry no newer stamp stands, the
+// others are made again.  The tile takes the stamp decision from lane 0, after every
+// lane has read the stamp (the shuffle) and before lane 0 overwrites it.
+__device__ __forceinline__ void smooth_scan_eval_phase(Store S, const int* D, const int* nDp,
+                                                       double2* mvxy, double4* mvM, double* qball,
+                                                       int* C, int* nC, int* cmark, int tag,
+                                                       int pass0, unsigned long long* work) {
+  const int n = *nDp;
+  const Tile t = tile_of();
+  const int tile_rank = (threadIdx.x / TW) * gridDim.x + blockIdx.x;
+  const int tiles = gridDim.x * (blockDim.x / TW);
+  for (int j0 = 0; j0 < n; j0 += tiles) {
+    int j = j0 + tile_rank;
+    int v = 0, ops = 0;
+    bool cand = false;
+    if (j < n) {
+      v = D[j];
+      MeshCtx c = ctx_of(S, v);
+      bool keep = unchanged(S, v, c.vb, S.evm[v], pass0);
+      keep = __shfl_sync(t.mask, keep, 0, TW);
+      if (keep) {
+        if (t.tl == 0) {
+          cand = mvM[v].w != 0.0;
+          if (cand) {
+            cmark[v] = tag;
+            S.tab.had[c.mi] = 1;
+          }
+        }
+      } else {
+        double2 X;
+        double4 Mv;
+        cand = tile_smooth_eval(t, S, v, c, X, Mv, qball + (size_t)v * S.W, ops);
+        if (t.tl == 0) {
+          S.evm[v] = tag;
+          if (cand) {
+            Mv.w = 1.0;  // marks a stored move
+            mvxy[v] = X;
+            mvM[v] = Mv;
+            cmark[v] = tag;
+            S.tab.had[c.mi] = 1;
+          } else {
+            mvM[v].w = 0.0;
+          }
+        }
+      }
+    }
+    warp_append(cand && t.tl == 0, v, C, nC);
+    if (work) {  // measurement only: one atomic per warp
+      unsigned tot = __reduce_add_sync(0xffffffffu, t.tl == 0 ? (unsigned)ops : 0u);
+      if ((threadIdx.x & 31) == 0 && tot) atomicAdd(work, (unsigned long long)tot);
+    }
+  }
+}
+
 __global__ void k_smooth_eval(Store S, const int* E, const int* nEp, double2* mvxy, double4* mvM,
                               double* qball, int* C, int* nC, int* cmark, int tag,
                               unsigned long long* work) {
@@ -2078,13 +2133,15 @@ __global__ void __launch_bounds__(256) k_coarsen_rounds(RoundArgs a) { topo_roun
 
 __global__ void __launch_bounds__(256) k_swap_rounds(RoundArgs a) { topo_rounds<true>(a); }
 
-// Rounds of smoothing moves: [scan] B1 [evaluate] B2 [select + apply] B3.
-// Block 0 clears, before B1 of round r: the list round r fills (last read by
-// round r - 1's scan and by its decision, both before B1 of round r); between
-// B1 and B2: the candidate slot of round r + 1 (last read after B3 of round
-// r - 1); between B2 and B3: E (read by the evaluation before B2).  The round
-// counters advance after B3 from the flag set of the round's parity, so that
-// round r + 1's evaluation can set the other set meanwhile.
+// Rounds of smoothing moves.  A round whose list fits one pass of the grid's
+// tiles: [scan + evaluate] B1 [select + apply] B2; a longer one: [scan] B1
+// [evaluate] B1' [select + apply] B2 (its tiles then go to the vertices that
+// need an evaluation only).  Block 0 clears, before B1 of round r: the list
+// round r fills (last read by round r - 1's scan and by its decision, both
+// before B1 of round r); after B1: the candidate slot of round r + 1 (last
+// read after B2 of round r - 1); after B1': E (read by the evaluation before
+// B1').  The round counters advance after B2 from the flag set of the round's
+// parity, so that round r + 1's evaluation can set the other set meanwhile.
 __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
   const Work& w = a.w;
   int* cnt = w.counts;
@@ -2098,20 +2155,30 @@ __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
   if (!grid_barrier(a.bar, target, a.st)) return;
   // a first list longer than the limit is left to the one-kernel-per-phase rounds
   const bool too_long = ld_volatile(cnt + cn_list(cur)) > a.limit;
+  const int tiles = gridDim.x * (blockDim.x / TW);
   while (!too_long && r < a.max_rounds) {
     const int tag = a.tag0 + 2 * r, nxt = 1 - cur;
     int* nC = cand_count(cnt, r);
     Store S = a.S;
     S.tab.had = a.S.tab.had + (r & 1) * S.nmesh;
+    // the list is complete since B2 of the last round: every block decides alike
+    const bool fused = ld_volatile(cnt + cn_list(cur)) <= tiles;
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[cn_list(nxt)] = 0;
-    smooth_scan_phase(S, w.D[cur], cnt + cn_list(cur), w.mvM, w.C, nC, w.cmark, tag, a.pass0, w.E,
-                      cnt + CN_E, true);
-    if (!grid_barrier(a.bar, target, a.st)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
-    smooth_eval_phase(S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, nC, w.cmark, tag, a.work,
-                      true);
-    if (!grid_barrier(a.bar, target, a.st)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = 0;
+    if (fused) {
+      smooth_scan_eval_phase(S, w.D[cur], cnt + cn_list(cur), w.mvxy, w.mvM, w.gains, w.C, nC,
+                             w.cmark, tag, a.pass0, a.work);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
+    } else {
+      smooth_scan_phase(S, w.D[cur], cnt + cn_list(cur), w.mvM, w.C, nC, w.cmark, tag, a.pass0,
+                        w.E, cnt + CN_E, true);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
+      smooth_eval_phase(S, w.E, cnt + CN_E, w.mvxy, w.mvM, w.gains, w.C, nC, w.cmark, tag, a.work,
+                        true);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CN_E] = 0;
+    }
     smooth_select_apply_phase(S, w.C, nC, w.cmark, w.smark, tag, w.D[nxt], cnt + cn_list(nxt),
                               w.dmark, w.mvxy, w.mvM, w.gains, w.P, cnt + CN_P, w.pmark, a.ptag,
                               tag + 1, true);
