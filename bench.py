@@ -42,10 +42,11 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="device-resident steps only (no e2e pass, no CPU baseline)")
     ap.add_argument("--workload", default="psi2m",
-                    choices=["psi2m", "psi20m", "paper550k", "batch", "grad"],
+                    choices=["psi2m", "psi20m", "paper550k", "batch", "grad", "psi_t"],
                     help="psi2m (default, the headline line); psi20m / paper550k: other "
                          "single-mesh sizes; batch: 512 meshes batched vs one mesh per "
-                         "launch; grad: quality forward+backward and optimisation smoothing")
+                         "launch; grad: quality forward+backward and optimisation smoothing; "
+                         "psi_t: time-dependent psi, each step re-adapts the last mesh")
     return ap.parse_args()
 
 
@@ -329,6 +330,98 @@ def run_grad(args, rank, world, local):
         }), flush=True)
 
 
+def run_time_series(args, rank, world, local):
+    """Sec. 4's time-dependent benchmark at the paper's size: after an
+    untimed adaptation at t = 0, every step re-adapts the previous step's
+    mesh to the metric of psi(x, y, t_k), t_k = k T / 50, evaluated on the
+    host at that mesh's vertices (input generation, untimed).  The timed step
+    is the metric upload from device memory, Algorithm 1 with smoothing, and
+    the compacted output."""
+    import numpy as np
+    import torch
+
+    from paper_1505_04694_gb300 import inputs, pm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = inputs.paper_550k()
+    target = 5.5e5
+    params = pm.Params(seed=w.params.seed)
+    g = pm.Mesh.from_host(w.xy, w.tri, cap_factor=2, device=local)
+    g.set_stream(stream.cuda_stream)  # the events below are recorded on this stream
+    g.set_metric(w.m)
+    g.adapt(params)
+    cap_out = 4_000_000
+    oxy = torch.empty((cap_out, 2), dtype=torch.float64, device=dev)
+    otri = torch.empty((cap_out, 3), dtype=torch.int32, device=dev)
+    om_ = torch.empty((cap_out, 3), dtype=torch.float64, device=dev)
+    k = 0
+
+    def next_metric():
+        nonlocal k
+        k += 1
+        xy, tri, _ = g.get_mesh()
+        return inputs.psi_metric(xy, tri, target, phase=inputs.psi_phase(k))
+
+    for _ in range(args.warmup):
+        g.set_metric(next_metric())
+        g.adapt(params)
+    launches = 0
+    total_ms = 0.0
+    tris = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            m_d = torch.tensor(next_metric(), dtype=torch.float64, device=dev)
+            torch.cuda.synchronize(dev)
+            l0 = pm.kernel_launches()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.set_metric_dev(m_d)
+            g.adapt(params)
+            nv, ne = g.get_mesh_dev(oxy, otri, om_)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            launches += pm.kernel_launches() - l0
+            tris += ne
+    # end to end: host metric in pinned memory, output into pinned arrays
+    out_h = (torch.empty((cap_out, 2), dtype=torch.float64).pin_memory().numpy(),
+             torch.empty((cap_out, 3), dtype=torch.int32).pin_memory().numpy(),
+             torch.empty((cap_out, 3), dtype=torch.float64).pin_memory().numpy())
+    e2e_s, e2e_tris, h2d, d2h = 0.0, 0, 0, 0
+    for _ in range(args.steps):
+        m_h = torch.from_numpy(next_metric()).pin_memory().numpy()
+        t = time.perf_counter()
+        g.set_metric(m_h)
+        g.adapt(params)
+        oxyh, otrih, omh = g.get_mesh(out=out_h)
+        e2e_s += time.perf_counter() - t
+        e2e_tris += otrih.shape[0]
+        h2d += m_h.nbytes
+        d2h += oxyh.nbytes + otrih.nbytes + omh.nbytes
+    g.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "adapted elements/s, time-dependent psi (each step re-adapts the last mesh)",
+            "value": tris / (total_ms / 1e3), "unit": "elements/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"time-dependent psi (Sec. 4), {w.name}, time steps "
+                                   f"{args.warmup + 1}..{args.warmup + args.steps} of 50 per "
+                                   f"period", "output_triangles_per_step": tris // args.steps},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_tris / e2e_s, "unit": "elements/s",
+                    "h2d_bytes_per_step": h2d // args.steps,
+                    "d2h_bytes_per_step": d2h // args.steps,
+                    "how": "pm_set_metric + pm_adapt + pm_get_mesh on the previous step's "
+                           "mesh, metric and output in pinned host buffers, wall clock"},
+            "gpu_launches": launches, "roofline": None,
+        }), flush=True)
+
+
 def cpu_baseline_run(samples=1):
     """Oracle (sequential C++) on the bounded sample; returns elements/s etc."""
     from oracle import oracle as O
@@ -385,6 +478,9 @@ def main():
         return
     if args.workload == "grad":
         run_grad(args, rank, world, local)
+        return
+    if args.workload == "psi_t":
+        run_time_series(args, rank, world, local)
         return
     import numpy as np
     import torch

@@ -76,40 +76,59 @@ def jitter_interior(xy: np.ndarray, n: int, amp: float, seed: int) -> np.ndarray
     return xy
 
 
-def psi_hessian(x: np.ndarray, y: np.ndarray):
-    """Analytic Hessian of psi at t = 0.
+def _phased(a: np.ndarray, phase: float) -> np.ndarray:
+    # at t = 0 the arguments stay exactly those of the time-independent field
+    return a if phase == 0.0 else a + phase
 
-    With D = sin(5y) - 2x, arctan(0.1/D) equals a piecewise constant minus
-    arctan(10 D), so the Hessian is smooth across D = 0:
+
+def psi_hessian(x: np.ndarray, y: np.ndarray, phase: float = 0.0):
+    """Analytic Hessian of psi(x, y, t) (Sec. 4), phase = 2 pi t / T.
+
+    With s = 5y + phase and D = sin(s) - 2x, arctan(0.1/D) equals a piecewise
+    constant minus arctan(10 D), so the Hessian is smooth across D = 0:
       g' = -10/(1+100 D^2),  g'' = 2000 D/(1+100 D^2)^2
-      H_xx = -250 sin(50x) + 4 g'',  H_xy = -10 cos(5y) g'',
-      H_yy = 25 cos(5y)^2 g'' - 25 sin(5y) g'.
+      H_xx = -250 sin(50x + phase) + 4 g'',  H_xy = -10 cos(s) g'',
+      H_yy = 25 cos(s)^2 g'' - 25 sin(s) g'.
     """
-    D = np.sin(5.0 * y) - 2.0 * x
+    s = _phased(5.0 * y, phase)
+    D = np.sin(s) - 2.0 * x
     den = 1.0 + 100.0 * D * D
     g1 = -10.0 / den
     g2 = 2000.0 * D / (den * den)
-    c5 = np.cos(5.0 * y)
-    hxx = -250.0 * np.sin(50.0 * x) + 4.0 * g2
+    c5 = np.cos(s)
+    hxx = -250.0 * np.sin(_phased(50.0 * x, phase)) + 4.0 * g2
     hxy = -10.0 * c5 * g2
-    hyy = 25.0 * c5 * c5 * g2 - 25.0 * np.sin(5.0 * y) * g1
+    hyy = 25.0 * c5 * c5 * g2 - 25.0 * np.sin(s) * g1
     return hxx, hxy, hyy
 
 
-def psi(x: np.ndarray, y: np.ndarray) -> np.ndarray:
-    """psi(x, y, t=0) itself (used only to check psi_hessian by differences)."""
-    return 0.1 * np.sin(50.0 * x) + np.arctan(-0.1 / (2.0 * x - np.sin(5.0 * y)))
+def psi(x: np.ndarray, y: np.ndarray, phase: float = 0.0) -> np.ndarray:
+    """psi(x, y, t) itself, phase = 2 pi t / T (used only to check psi_hessian
+    by differences)."""
+    return (0.1 * np.sin(_phased(50.0 * x, phase))
+            + np.arctan(-0.1 / (2.0 * x - np.sin(_phased(5.0 * y, phase)))))
 
 
-def _abs_hessian_metric(hxx, hxy, hyy, c, hmin, hmax):
-    """M = R diag(clamp(c |lambda_i|, 1/hmax^2, 1/hmin^2)) R^T per vertex."""
+def psi_phase(step: int, steps_per_period: int = 50) -> float:
+    """Phase 2 pi t / T of time step `step` when a period takes
+    `steps_per_period` steps (the paper averages over 50 time steps)."""
+    return 2.0 * math.pi * step / steps_per_period
+
+
+def _hessian_eig(hxx, hxy, hyy):
+    """Eigenvalues l1 >= l2 of the Hessian and the rotation of l1's vector."""
     tr = 0.5 * (hxx + hyy)
     dif = 0.5 * (hxx - hyy)
     rad = np.sqrt(dif * dif + hxy * hxy)
     l1 = tr + rad
     l2 = tr - rad
     theta = 0.5 * np.arctan2(2.0 * hxy, hxx - hyy)  # eigenvector of l1
-    ct, st = np.cos(theta), np.sin(theta)
+    return l1, l2, np.cos(theta), np.sin(theta)
+
+
+def _abs_hessian_metric(hxx, hxy, hyy, c, hmin, hmax, eig=None):
+    """M = R diag(clamp(c |lambda_i|, 1/hmax^2, 1/hmin^2)) R^T per vertex."""
+    l1, l2, ct, st = eig if eig is not None else _hessian_eig(hxx, hxy, hyy)
     lo, hi = 1.0 / (hmax * hmax), 1.0 / (hmin * hmin)
     a = np.clip(c * np.abs(l1), lo, hi)
     b = np.clip(c * np.abs(l2), lo, hi)
@@ -119,25 +138,35 @@ def _abs_hessian_metric(hxx, hxy, hyy, c, hmin, hmax):
     return np.stack([m00, m01, m11], axis=1)
 
 
-def estimated_elements(xy: np.ndarray, tri: np.ndarray, m: np.ndarray) -> float:
+def _areas(xy: np.ndarray, tri: np.ndarray) -> np.ndarray:
+    p = xy[tri]
+    return 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1])
+                        - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0]))
+
+
+def estimated_elements(xy: np.ndarray, tri: np.ndarray, m: np.ndarray,
+                       area: np.ndarray = None) -> float:
     """N = (4/sqrt 3) * sum_K area_K * mean_i sqrt(det M_i): the number of unit
     equilateral metric triangles that tile the domain."""
-    p = xy[tri]
-    area = 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1])
-                        - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0]))
+    if area is None:
+        area = _areas(xy, tri)
     sd = np.sqrt(np.maximum(m[:, 0] * m[:, 2] - m[:, 1] ** 2, 0.0))
     return float(4.0 / math.sqrt(3.0) * np.sum(area * sd[tri].mean(axis=1)))
 
 
 def psi_metric(xy: np.ndarray, tri: np.ndarray, target_elements: float,
-               hmin: float = 1e-3, hmax: float = 0.3) -> np.ndarray:
-    """|Hessian(psi)| metric scaled (bisection on c) so that the estimated
-    element count matches target_elements; sizes clamped to [hmin, hmax]."""
-    hxx, hxy, hyy = psi_hessian(xy[:, 0], xy[:, 1])
+               hmin: float = 1e-3, hmax: float = 0.3, phase: float = 0.0) -> np.ndarray:
+    """|Hessian(psi)| metric at phase 2 pi t / T, scaled (bisection on c) so
+    that the estimated element count matches target_elements; sizes clamped
+    to [hmin, hmax]."""
+    hxx, hxy, hyy = psi_hessian(xy[:, 0], xy[:, 1], phase)
+    eig = _hessian_eig(hxx, hxy, hyy)  # the parts that do not depend on c
+    area = _areas(xy, tri)
     lo, hi = 1e-8, 1e8
     for _ in range(200):
         mid = math.sqrt(lo * hi)
-        n = estimated_elements(xy, tri, _abs_hessian_metric(hxx, hxy, hyy, mid, hmin, hmax))
+        n = estimated_elements(xy, tri, _abs_hessian_metric(hxx, hxy, hyy, mid, hmin, hmax, eig),
+                               area)
         if n < target_elements:
             lo = mid
         else:

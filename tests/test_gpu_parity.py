@@ -109,6 +109,29 @@ def test_psi_adapt_bit_exact(n, T, seed):
         assert sg[k] == so[k], (k, sg[k], so[k])
 
 
+def test_time_dependent_psi_readapt_bit_exact():
+    """Sec. 4's time-dependent benchmark: every time step re-adapts the last
+    step's mesh to the metric of psi(x, y, t_k), t_k = k T / 50, evaluated at
+    that mesh's vertices."""
+    seed = 6
+    w = inputs.psi_workload(21, 4000, True, seed)
+    g, o = both(w, seed)
+    g.adapt(gp(seed))
+    o.adapt(op(seed))
+    for k in range(1, 4):
+        gm, om = g.get_mesh(), o.get_mesh()
+        assert_same_mesh(gm, om, f"time step {k - 1}")
+        m = inputs.psi_metric(gm[0], gm[1], 4000, phase=inputs.psi_phase(k))
+        g.set_metric(m)
+        o.set_metric(m)
+        sg = g.adapt(gp(seed))
+        so = o.adapt(op(seed))
+        for key in STAT_KEYS:
+            assert sg[key] == so[key], (k, key, sg[key], so[key])
+        assert sg["collapses"] + sg["splits"] + sg["flips"] > 0  # the field moved
+    assert_same_mesh(g.get_mesh(), o.get_mesh(), "time step 3")
+
+
 @pytest.mark.parametrize("opname", ["coarsen", "swap", "refine", "smooth", "opt_smooth"])
 def test_single_operator_raw_state_and_rows(opname):
     w = inputs.psi_workload(21, 6000, True, 9)

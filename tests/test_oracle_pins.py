@@ -568,21 +568,38 @@ def test_mesh_gradient_central_differences():
 
 # --- input generator -----------------------------------------------------------
 
-def test_psi_hessian_matches_differences():
+@pytest.mark.parametrize("step", [0, 7, 31])
+def test_psi_hessian_matches_differences(step):
+    """The time-dependent field of Sec. 4 at t = step T / 50."""
+    phase = inputs.psi_phase(step)
     rng = np.random.default_rng(9)
     x = rng.uniform(0, 1, 400)
     y = rng.uniform(0, 1, 400)
-    D = np.sin(5 * y) - 2 * x
+    D = np.sin(5 * y + phase) - 2 * x
     keep = np.abs(D) > 0.05
     x, y = x[keep], y[keep]
     h = 1e-4
-    hxx, hxy, hyy = inputs.psi_hessian(x, y)
-    f = inputs.psi
+    hxx, hxy, hyy = inputs.psi_hessian(x, y, phase)
+
+    def f(a, b):
+        return inputs.psi(a, b, phase)
+
     fxx = (f(x + h, y) - 2 * f(x, y) + f(x - h, y)) / h ** 2
     fyy = (f(x, y + h) - 2 * f(x, y) + f(x, y - h)) / h ** 2
     fxy = (f(x + h, y + h) - f(x + h, y - h) - f(x - h, y + h) + f(x - h, y - h)) / (4 * h * h)
     for a, b in ((hxx, fxx), (hxy, fxy), (hyy, fyy)):
         assert np.all(np.abs(a - b) <= 1e-3 * (1 + np.abs(a)))
+
+
+def test_psi_time_steps_are_periodic_and_start_at_the_static_field():
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, 200)
+    y = rng.uniform(0, 1, 200)
+    # phase 0 is the time-independent field bit for bit
+    assert np.array_equal(inputs.psi(x, y, inputs.psi_phase(0)), inputs.psi(x, y))
+    # 50 steps make one period
+    assert np.allclose(inputs.psi(x, y, inputs.psi_phase(50)), inputs.psi(x, y), atol=1e-9)
+    assert not np.allclose(inputs.psi(x, y, inputs.psi_phase(25)), inputs.psi(x, y), atol=1e-3)
 
 
 def test_psi_metric_hits_target_estimate():
