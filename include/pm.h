@@ -207,6 +207,17 @@ pm_status pm_profile_read(double* total_ms, int64_t* launches, double* work);
  * The paper has no counterpart. */
 pm_status pm_fp64_peak(double* gops);
 
+/* Test support: the bounded wait of the persistent rounds' grid barrier.  On
+ * the current device, one block per SM waits at a barrier that no arrival can
+ * complete; each block gives up after limit_ms (0 < limit_ms <= 2000) and
+ * records PM_ERR_TIMEOUT in the device status word.  *device_status receives
+ * that word, *elapsed_ms the kernel's duration.  Returns PM_OK when the
+ * kernel ran and ended (the device stays usable), PM_ERR_INVALID_ARG for a
+ * null pointer or a limit out of range, PM_ERR_CUDA / PM_ERR_OOM on a runtime
+ * failure.  Runs on the default stream and synchronises.  The paper has no
+ * counterpart. */
+pm_status pm_selftest_wait_timeout(double limit_ms, int32_t* device_status, double* elapsed_ms);
+
 /* pm_quality_arrays_dev for callers that cannot allocate device memory
  * during the call (a framework that has already reserved the device memory
  * for its own allocator, a latency-bound loop, or a program that allows no

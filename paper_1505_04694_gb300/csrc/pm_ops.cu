@@ -1993,7 +1993,8 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile con
 // reads what the other blocks wrote.  Returns false (the caller leaves the
 // kernel) when the wait ran out (PM_ERR_TIMEOUT is recorded) or when any
 // phase recorded an error.
-__device__ bool grid_barrier(unsigned* bar, unsigned& target, DevStatus* st) {
+__device__ bool grid_barrier(unsigned* bar, unsigned& target, DevStatus* st,
+                             unsigned long long limit_ns = kBarrierNs) {
   __shared__ int s_ok;
   target += gridDim.x;
   __syncthreads();
@@ -2009,7 +2010,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& target, DevStatus* st) {
           ok = 0;
           break;
         }
-        if (global_ns() - t0 > kBarrierNs) {
+        if (global_ns() - t0 > limit_ns) {
           set_err(st, PM_ERR_TIMEOUT);
           ok = 0;
           break;
@@ -2021,6 +2022,13 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& target, DevStatus* st) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Test support: every block waits at a barrier whose target lies one arrival
+// beyond the grid, so the wait can only end by its time limit.
+__global__ void k_selftest_barrier(unsigned* bar, DevStatus* st, unsigned long long limit_ns) {
+  unsigned target = 1;
+  grid_barrier(bar, target, st, limit_ns);
 }
 
 struct RoundArgs {
@@ -2656,3 +2664,49 @@ int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds) {
 }
 
 }  // namespace pm
+
+// Test support (see pm.h): a grid barrier that nothing completes gives up
+// after limit_ms and reports PM_ERR_TIMEOUT through the status word.
+extern "C" pm_status pm_selftest_wait_timeout(double limit_ms, int32_t* device_status,
+                                              double* elapsed_ms) {
+  using namespace pm;
+  if (!device_status || !elapsed_ms || !(limit_ms > 0.0) || !(limit_ms <= 2000.0))
+    return PM_ERR_INVALID_ARG;
+  int dev = 0, sms = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+    return PM_ERR_CUDA;
+  if (!coop || sms < 1) return PM_ERR_CUDA;
+  unsigned* bar = nullptr;
+  DevStatus* st = nullptr;
+  if (cudaMalloc(&bar, sizeof(unsigned)) != cudaSuccess) return PM_ERR_OOM;
+  if (cudaMalloc(&st, sizeof(DevStatus)) != cudaSuccess) {
+    cudaFree(bar);
+    return PM_ERR_OOM;
+  }
+  cudaMemset(bar, 0, sizeof(unsigned));
+  cudaMemset(st, 0, sizeof(DevStatus));
+  unsigned long long limit_ns = (unsigned long long)(limit_ms * 1e6);
+  void* args[] = {&bar, &st, &limit_ns};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_selftest_barrier, dim3(sms),
+                                              dim3(256), args, 0, 0);
+  cudaEventRecord(e1);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  DevStatus h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(bar);
+  cudaFree(st);
+  if (e != cudaSuccess) return PM_ERR_CUDA;
+  *device_status = h.err;
+  *elapsed_ms = ms;
+  return PM_OK;
+}

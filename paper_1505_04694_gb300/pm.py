@@ -30,7 +30,7 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_get_mesh_dev", "pm_get_raw", "pm_adjacency", "pm_quality",
            "pm_quality_arrays_dev", "pm_status_string", "pm_last_error", "pm_kernel_launches",
            "pm_profile_enable", "pm_profile_read", "pm_quality_arrays_noalloc_dev",
-           "pm_fp64_peak"]
+           "pm_fp64_peak", "pm_selftest_wait_timeout"]
 
 
 class PmParams(C.Structure):
@@ -100,6 +100,9 @@ def _load():
     L.pm_profile_read.restype = C.c_int
     L.pm_fp64_peak.argtypes = [C.POINTER(C.c_double)]
     L.pm_fp64_peak.restype = C.c_int
+    L.pm_selftest_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_double)]
+    L.pm_selftest_wait_timeout.restype = C.c_int
     L.pm_status_string.argtypes = [C.c_int]
     L.pm_status_string.restype = C.c_char_p
     L.pm_last_error.argtypes = []
@@ -364,6 +367,16 @@ def fp64_peak():
     g = C.c_double()
     _check(lib.pm_fp64_peak(C.byref(g)), "pm_fp64_peak")
     return float(g.value)
+
+
+def selftest_wait_timeout(limit_ms):
+    """Let a grid barrier that nothing completes run out after limit_ms:
+    returns (device status word, kernel ms)."""
+    st = C.c_int32()
+    ms = C.c_double()
+    _check(lib.pm_selftest_wait_timeout(limit_ms, C.byref(st), C.byref(ms)),
+           "pm_selftest_wait_timeout")
+    return int(st.value), float(ms.value)
 
 
 def profile_read():

@@ -231,6 +231,21 @@ def test_batch_equals_single_runs():
             assert st[k] == so[k], (w.name, k, st[k], so[k])
 
 
+def test_bounded_barrier_wait_times_out_and_device_stays_usable():
+    """A grid barrier that no arrival completes gives up after its limit and
+    reports PM_ERR_TIMEOUT (6) through the status word; the next call works."""
+    status, ms = pm.selftest_wait_timeout(50.0)
+    assert status == 6
+    assert 50.0 <= ms < 1000.0
+    with pytest.raises(pm.PmError):
+        pm.selftest_wait_timeout(0.0)
+    w = inputs.small_uniform()
+    g, o = both(w, 1)
+    g.adapt(gp(1))
+    o.adapt(op(1))
+    assert_same_mesh(g.get_mesh(), o.get_mesh(), "after a timed-out wait")
+
+
 def test_rejects_invalid_input():
     xy, tri = inputs.grid_mesh(5)
     bad = tri.copy()
