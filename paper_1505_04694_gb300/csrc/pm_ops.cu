@@ -58,8 +58,6 @@ __device__ __forceinline__ const int* ne_row(const Store& S, int slot) {
   return S.NE + (size_t)slot * S.W;
 }
 
-__device__ __forceinline__ int warp_max(int x) { return __reduce_max_sync(0xffffffffu, x); }
-
 // Per-mesh operation counter, aggregated over the lanes of a warp that share a
 // mesh (all lanes must call).
 __device__ __forceinline__ void count_op(const Store& S, bool pred, int mi) {
@@ -92,19 +90,6 @@ __device__ __forceinline__ int count_elems_with(const Store& S, const int* ne, i
   return c;
 }
 
-__device__ __forceinline__ double elem_quality(const Store& S, int vb, int4 e) {
-  return quality_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
-                   load_vd(S, vb + e.z));
-}
-
-// Refresh the cached quality of the live elements of v's ball.
-__device__ __forceinline__ void refresh_ball_quality(const Store& S, int vb, int eb, const int* ne,
-                                                     int nel) {
-  for (int k = 0; k < nel; ++k) {
-    int4 e = S.EN[eb + ne[k]];
-    if (e.w) S.qK[eb + ne[k]] = elem_quality(S, vb, e);
-  }
-}
 
 // Inputs of v's evaluation unchanged since tag `et`?  Evaluations read v's
 // rows, the elements and vertices of its ball and the rows and positions of
