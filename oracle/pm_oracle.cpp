@@ -545,6 +545,7 @@ bool interpolate_in_ball(const OMesh& m, int v, double X, double Y, Move& mv) {
     // X lies in the closed element when all three sub-triangles (X replacing
     // one vertex) are counter-clockwise or flat; its barycentric
     // coordinates are then the sub-triangle orientations over the element's
+    // own orientation.
     double o = orient3(d[0], d[1], d[2]);
     double s0 = orient3(px, d[1], d[2]);
     double s1 = orient3(d[0], px, d[2]);

@@ -1,0 +1,121 @@
+"""Every pin of the oracle must catch a plausible mistake.
+
+Each case compiles the oracle with one planted change (a dropped factor, a
+swapped index, a flipped comparison, a relaxed bound) into a private library
+and runs the pins named for it against that library in a child process: they
+must fail.  The oracle source itself is never modified.  CPU only.
+
+Changes that cannot alter any result on a valid mesh are not listed: dropping
+the duplicate-edge test of a flip (such a flip always inverts an element, so
+the orientation test rejects it first) and dropping the second orientation
+test of a flip (an inverted element has negative quality, so the gain test
+rejects it).
+"""
+import os
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+from oracle.build import FLAGS
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pm_oracle.cpp")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+# (what, text in the oracle, planted text, pins that must fail)
+MUTATIONS = [
+    ("metric length: off-diagonal term not doubled",
+     "double L2 = ((e00 * dx) * dx + ((2.0 * e01) * dx) * dy) + (e11 * dy) * dy;",
+     "double L2 = ((e00 * dx) * dx + (e01 * dx) * dy) + (e11 * dy) * dy;",
+     "rotated_anisotropic"),
+    ("orientation: wrong vertex in the second product",
+     "return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);",
+     "return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - q.x);",
+     "quality_equilateral_unit"),
+    ("quality: wrong shape factor",
+     "double f = s * (2.0 - s);",
+     "double f = s * (2.0 - s * s);",
+     "quality_right_isosceles"),
+    ("hash priority: wrong multiplier",
+     "h *= 0x85ebca6bu;",
+     "h *= 0x85ebca6du;",
+     "fmix32_published"),
+    ("independent set: non-candidate neighbours compete",
+     "if (inC[u] && prio((uint32_t)u, seed, m.r) > pv) {",
+     "if (prio((uint32_t)u, seed, m.r) > pv) {",
+     "independent_set_brute_force"),
+    ("collapse: boundary edges need two common neighbours",
+     "if (common != (bedge ? 1 : 2)) return false;",
+     "if (common != (bedge ? 2 : 2)) return false;",
+     "collapse_rule_brute_force"),
+    ("collapse: new-edge bound relaxed",
+     "if (metric_len(dw, m.vd(x)) > P.L_up) return false;",
+     "if (metric_len(dw, m.vd(x)) > 2.0 * P.L_up) return false;",
+     "collapse_rule_brute_force"),
+    ("flip: gain from the larger new quality",
+     "double qnew = (n1 < n2) ? n1 : n2;",
+     "double qnew = (n1 < n2) ? n2 : n1;",
+     "flip_rule_brute_force"),
+    ("flip: quality threshold doubled",
+     "double qold = (q1 < q2) ? q1 : q2;\n  if (!(qold < P.q_thresh)) return false;",
+     "double qold = (q1 < q2) ? q1 : q2;\n  if (!(qold < 2.0 * P.q_thresh)) return false;",
+     "flip_rule_brute_force"),
+    ("flip: the smallest gain wins",
+     "    if (!found || op.gain > best.gain) {",
+     "    if (!found || op.gain < best.gain) {",
+     "flip_rule_brute_force"),
+    ("refinement: the longer diagonal",
+     "if (d1 <= d2) {",
+     "if (d1 > d2) {",
+     "shorter_diagonal"),
+    ("smoothing: Laplacian weight transposed",
+     "b0 = b0 + (w00 * m.x[j] + w01 * m.y[j]);",
+     "b0 = b0 + (w00 * m.x[j] + w11 * m.y[j]);",
+     "laplacian_smoothing"),
+    ("smoothing: barycentric weights swapped",
+     "mv.m00 = (l0 * d[0].m00 + l1 * d[1].m00) + l2 * d[2].m00;",
+     "mv.m00 = (l1 * d[0].m00 + l0 * d[1].m00) + l2 * d[2].m00;",
+     "linear_metric"),
+]
+
+CHILD = textwrap.dedent("""
+    import sys
+    sys.path.insert(0, {root!r})
+    from oracle import build
+    build.build = lambda force=False: {lib!r}
+    import pytest
+    sys.exit(pytest.main(["-q", "-p", "no:cacheprovider", {pins!r}, "-k", {sel!r}]))
+""")
+
+
+def run_pins(tmp_path, src, sel):
+    """Compile `src` as the oracle and run the pins `sel` against it in a
+    child process; returns pytest's exit status and output."""
+    path = tmp_path / "pm_oracle.cpp"
+    path.write_text(src)
+    lib = tmp_path / "liboracle.so"
+    subprocess.check_call(["g++", *FLAGS, str(path), "-o", str(lib)])
+    code = CHILD.format(root=ROOT, lib=str(lib), pins=PINS, sel=sel)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    return r.returncode, r.stdout
+
+
+def test_selected_pins_pass_on_the_unchanged_oracle(tmp_path):
+    with open(SRC) as f:
+        src = f.read()
+    sel = " or ".join(sorted({m[3] for m in MUTATIONS}))
+    status, out = run_pins(tmp_path, src, sel)
+    assert status == 0, out[-3000:]
+
+
+@pytest.mark.parametrize("what,old,new,sel", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, what, old, new, sel):
+    with open(SRC) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"{what}: the planted site must occur once"
+    status, out = run_pins(tmp_path, src.replace(old, new), sel)
+    # pytest's exit status 1: tests ran and some failed (5 would mean none ran)
+    assert status == 1, f"{what}: pins {sel!r} did not fail\n{out[-3000:]}"

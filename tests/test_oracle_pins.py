@@ -61,6 +61,30 @@ def test_edge_length_anisotropic_axis():
     assert abs(O.edge_length(np.zeros(2), m, np.array([0.0, 0.6]), m) - 2.0) < 1e-14
 
 
+def test_edge_length_rotated_anisotropic_closed_form():
+    """End metrics R diag(a_i, b_i) R^T sharing the rotation R: their mean is
+    R diag((a1+a2)/2, (b1+b2)/2) R^T, so an edge alpha u1 + beta u2 (u1, u2
+    the columns of R) has metric length sqrt(((a1+a2)/2) alpha^2 +
+    ((b1+b2)/2) beta^2)."""
+    rng = np.random.default_rng(11)
+
+    def rotated(th, a, b):
+        c, s = math.cos(th), math.sin(th)
+        return np.array([a * c * c + b * s * s, (a - b) * c * s, a * s * s + b * c * c])
+
+    for _ in range(200):
+        th = rng.uniform(0.0, math.pi)
+        a1, b1, a2, b2 = 10.0 ** rng.uniform(-1.0, 4.0, 4)
+        al, be = rng.normal(size=2)
+        u1 = np.array([math.cos(th), math.sin(th)])
+        u2 = np.array([-math.sin(th), math.cos(th)])
+        xa = rng.uniform(0.0, 1.0, 2)
+        xb = xa + al * u1 + be * u2
+        L = O.edge_length(xa, rotated(th, a1, b1), xb, rotated(th, a2, b2))
+        ref = math.sqrt(0.5 * (a1 + a2) * al * al + 0.5 * (b1 + b2) * be * be)
+        assert abs(L - ref) <= 1e-11 * ref
+
+
 def equilateral(h, x0=0.3, y0=0.1, rot=0.0):
     pts = []
     for k in range(3):
@@ -322,6 +346,27 @@ def test_refine_one_and_two_splits():
     assert tri6.shape[0] == 2 and oxy6.shape[0] == 4
 
 
+def test_refine_two_splits_cut_along_the_metric_shorter_diagonal():
+    """S11: with two edges split, the trapezoid beside the corner child is cut
+    along its diagonal that is shorter in the metric, which need not be the
+    Euclidean shorter one."""
+    pts = {"A": (0.0, 0.0), "B": (4.0, 0.0), "C": (0.0, 1.5), "mAB": (2.0, 0.0),
+           "mBC": (2.0, 0.75)}
+    xy = np.array([pts["A"], pts["B"], pts["C"]])  # AB and BC too long, CA not
+    u = np.array([2.0, 0.75]) / math.hypot(2.0, 0.75)
+    M_dir = np.outer(u, u) + 0.1 * np.eye(2)  # lengths along A -> mBC count most
+    # Euclidean: |A mBC| = 2.14 < |mAB C| = 2.5; in M_dir: 2.24 > 1.56
+    for M, want, other in ((np.eye(2), ("A", "mBC"), ("mAB", "C")),
+                           (M_dir, ("mAB", "C"), ("A", "mBC"))):
+        m = np.tile([M[0, 0], M[0, 1], M[1, 1]], (3, 1))
+        oxy, tri, _ = _single_triangle_refine(xy, m, 2.0)
+        assert tri.shape[0] == 3 and oxy.shape[0] == 5
+        idx = {k: int(np.nonzero((oxy == np.array(v)).all(axis=1))[0][0]) for k, v in pts.items()}
+        edges = {frozenset((int(t[i]), int(t[(i + 1) % 3]))) for t in tri for i in range(3)}
+        assert frozenset((idx[want[0]], idx[want[1]])) in edges
+        assert frozenset((idx[other[0]], idx[other[1]])) not in edges
+
+
 # --- brute force for the collapse and flip rules (Sec. 2.4.1, 2.4.3) ---------
 
 def tiny_meshes():
@@ -371,8 +416,11 @@ def brute_collapse_valid(xy, tris, corner, v, w, L_up, elen):
     return True
 
 
-def test_collapse_rule_brute_force():
+# L_up = 1.3 makes rule (iii) (no new edge longer than L_up) decide cases too
+@pytest.mark.parametrize("L_up", [2.5, 1.3])
+def test_collapse_rule_brute_force(L_up):
     checked = 0
+    by_iii = 0  # candidates rejected by rule (iii) alone
     for xy, tri, m in tiny_meshes():
         om = O.OracleMesh(xy, tri).set_metric(m)
         tris = [tuple(int(a) for a in t) for t in tri]
@@ -381,7 +429,7 @@ def test_collapse_rule_brute_force():
         NN, _ = MC.adjacency(tris, xy.shape[0])
         bedges = MC.boundary_edges(tris)
         bverts = {a for e in bedges for a in e}
-        p = O.make_params(L_low=1.0, L_up=2.5)
+        p = O.make_params(L_low=1.0, L_up=L_up)
 
         def elen(a, b):
             return O.edge_length(xy[a], m[a], xy[b], m[b])
@@ -401,18 +449,25 @@ def test_collapse_rule_brute_force():
                     if brute_collapse_valid(xy, tris, corner, v, w, p.L_up, elen):
                         expect = w
                         break
+                    by_iii += brute_collapse_valid(xy, tris, corner, v, w, math.inf, elen)
             assert om.coarsen_target(v, p) == expect, (v, cands)
             checked += len(cands)
     assert checked > 50
+    if L_up < 2.0:
+        assert by_iii > 5
 
 
-def test_flip_rule_brute_force():
+# q_thresh = 1 lists every edge; on these meshes the improving flips have old
+# qualities from 0.03 to 0.67 (median 0.14), so 0.15 lets the threshold decide
+@pytest.mark.parametrize("q_thresh", [1.0, 0.15])
+def test_flip_rule_brute_force(q_thresh):
     n_flip = 0
+    by_thresh = 0  # flips with a positive gain that the threshold rules out
     for xy, tri, m in tiny_meshes():
         om = O.OracleMesh(xy, tri).set_metric(m)
         tris = [tuple(int(a) for a in t) for t in tri]
         NN, NE = MC.adjacency(tris, xy.shape[0])
-        p = O.make_params(q_thresh=1.0)
+        p = O.make_params(q_thresh=q_thresh)
 
         def q_of(t):
             return O.tri_quality(np.array(t), xy[list(t)], m[list(t)])
@@ -434,6 +489,7 @@ def test_flip_rule_brute_force():
                     continue
                 qold = min(q_of(K1[0]), q_of(K2[0]))
                 if not qold < p.q_thresh:
+                    by_thresh += min(q_of(T1), q_of(T2)) - qold > 0
                     continue
                 gain = min(q_of(T1), q_of(T2)) - qold
                 if gain > 0 and (best is None or gain > best):
@@ -442,6 +498,22 @@ def test_flip_rule_brute_force():
             assert got == bw, v
             n_flip += got >= 0
     assert n_flip > 20
+    if q_thresh < 1.0:
+        assert by_thresh > 5
+
+
+def test_flip_never_recreates_an_existing_edge():
+    """S10: a flip at a degree-3 vertex would join its two opposite vertices a
+    second time (and, the quad being non-convex, invert an element).  A point
+    P near corner A of triangle ABC, joined to the corners, has three poor
+    elements (q_thresh = 1 lists every edge); no flip is taken."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [0.08, 0.07]])  # A, B, C, P
+    tri = np.array([[0, 1, 3], [1, 2, 3], [2, 0, 3]])
+    m = np.tile([1.0, 0.0, 1.0], (4, 1))
+    om = O.OracleMesh(xy, tri).set_metric(m)
+    p = O.make_params(q_thresh=1.0)
+    for v in range(4):
+        assert om.swap_target(v, p)[0] == -1, v
 
 
 # --- round-equals-sequential and invariants ---------------------------------
@@ -506,6 +578,28 @@ def test_laplacian_smoothing_metric_weighted_target():
     raw = om.get_raw()
     if raw["xy"][0].any():
         assert np.abs(raw["xy"][0]).max() < 1e-14
+
+
+def test_smoothing_interpolates_a_linear_metric_field_exactly():
+    """Barycentric interpolation (S12) reproduces a field that is linear in
+    (x, y): the moved vertex's new metric is the field at its new place."""
+    m0, mx, my = np.array([4.0, 0.3, 5.0]), np.array([0.5, 0.1, -0.4]), np.array([-0.3, 0.2, 0.6])
+
+    def field(p):
+        return m0 + p[0] * mx + p[1] * my
+
+    for off in ((0.21, -0.13), (-0.3, 0.17), (0.05, 0.33)):
+        xy, tri = hex_patch(off)
+        m = np.array([field(p) for p in xy])
+        om = O.OracleMesh(xy, tri).set_metric(m)
+        st = om.smooth(O.make_params(q_thresh=1.01, max_smooth_sweeps=1))
+        assert st["moves"] == 1, off
+        raw = om.get_raw()
+        x_new = raw["xy"][0]
+        assert np.abs(x_new - np.array(off)).max() > 1e-3  # it moved
+        np.testing.assert_allclose(raw["m"][0], field(x_new), rtol=1e-13, atol=1e-13)
+        # the ring keeps its metric
+        np.testing.assert_array_equal(raw["m"][1:], m[1:])
 
 
 def test_smoothing_never_lowers_ball_min_quality():
