@@ -9,7 +9,9 @@ Changes that cannot alter any result on a valid mesh are not listed: dropping
 the duplicate-edge test of a flip (such a flip always inverts an element, so
 the orientation test rejects it first) and dropping the second orientation
 test of a flip (an inverted element has negative quality, so the gain test
-rejects it).
+rejects it).  Nor is leaving a flip's two opposite vertices unmarked: a flip
+they would enable is found from its other end, and on the test meshes every
+pass still ends with nothing left to do.
 """
 import os
 import subprocess
@@ -78,6 +80,18 @@ MUTATIONS = [
      "mv.m00 = (l0 * d[0].m00 + l1 * d[1].m00) + l2 * d[2].m00;",
      "mv.m00 = (l1 * d[0].m00 + l0 * d[1].m00) + l2 * d[2].m00;",
      "linear_metric"),
+    ("smoothing: a move that gains nothing is taken",
+     "  return qmin > qold;\n}",
+     "  return qmin >= qold;\n}",
+     "strict_gain"),
+    ("refinement: a midpoint takes one end's metric",
+     "      m.m00.push_back(0.5 * (da.m00 + db.m00));",
+     "      m.m00.push_back(0.5 * (da.m00 + da.m00));",
+     "linear_metric_field"),
+    ("collapse: neighbours not marked for re-evaluation",
+     "      for (int x : m.NN[v]) dirty[x] = 1;",
+     "      for (int x : m.NN[v]) dirty[x] = dirty[x];",
+     "nothing_left"),
 ]
 
 CHILD = textwrap.dedent("""

@@ -367,6 +367,19 @@ def test_refine_two_splits_cut_along_the_metric_shorter_diagonal():
         assert frozenset((idx[other[0]], idx[other[1]])) not in edges
 
 
+def test_refine_midpoints_reproduce_a_linear_metric_field():
+    """A new vertex takes the mean of its edge's end metrics (S11): a metric
+    field linear in (x, y) is reproduced exactly at every midpoint (dyadic
+    coordinates and coefficients keep the arithmetic exact)."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.25, 0.75]])
+    m0, mx, my = np.array([4.0, 0.5, 3.0]), np.array([2.0, -0.25, 1.0]), np.array([-1.0, 0.75, 2.0])
+    m = np.array([m0 + p[0] * mx + p[1] * my for p in xy])
+    oxy, tri, om_ = _single_triangle_refine(xy, m, 0.5)
+    assert oxy.shape[0] == 6
+    for p, mm in zip(oxy, om_):
+        np.testing.assert_array_equal(mm, m0 + p[0] * mx + p[1] * my)
+
+
 # --- brute force for the collapse and flip rules (Sec. 2.4.1, 2.4.3) ---------
 
 def tiny_meshes():
@@ -516,6 +529,24 @@ def test_flip_never_recreates_an_existing_edge():
         assert om.swap_target(v, p)[0] == -1, v
 
 
+@pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (25, 8000, 22)])
+def test_passes_end_with_nothing_left_to_do(n, T, seed):
+    """Propagation (Sec. 2.4.5): a collapse or flip pass loops until nothing
+    changes, so when it returns no live vertex has a valid collapse, or an
+    improving flip, left.  A change whose neighbours were not marked for
+    re-evaluation leaves one behind."""
+    w = inputs.psi_workload(n, T, True, seed)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    p = O.make_params(seed=seed)
+    om.refine(p)
+    assert om.coarsen(p)["collapses"] > 100
+    alive = np.nonzero(om.get_raw()["valive"])[0]
+    assert all(om.coarsen_target(int(v), p) < 0 for v in alive)
+    assert om.swap(p)["flips"] > 100
+    alive = np.nonzero(om.get_raw()["valive"])[0]
+    assert all(om.swap_target(int(v), p)[0] < 0 for v in alive)
+
+
 # --- round-equals-sequential and invariants ---------------------------------
 
 @pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (25, 8000, 22), (33, 20000, 2)])
@@ -600,6 +631,21 @@ def test_smoothing_interpolates_a_linear_metric_field_exactly():
         np.testing.assert_allclose(raw["m"][0], field(x_new), rtol=1e-13, atol=1e-13)
         # the ring keeps its metric
         np.testing.assert_array_equal(raw["m"][1:], m[1:])
+
+
+def test_smoothing_moves_only_for_a_strict_gain():
+    """A vertex already at its Laplacian target would gain nothing by moving:
+    no move is made (smoothing must raise the local quality, Sec. 2.4.4).
+    The centre of the diamond (+-1, 0), (0, +-1) under a uniform metric is
+    its neighbours' mean exactly, so the evaluated move goes nowhere and its
+    ball keeps every quality bit for bit."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [-1.0, 0.0], [0.0, -1.0]])
+    tri = np.array([[0, 1, 2], [0, 2, 3], [0, 3, 4], [0, 4, 1]])
+    m = np.tile([1.0, 0.0, 1.0], (5, 1))
+    om = O.OracleMesh(xy, tri).set_metric(m)
+    st = om.smooth(O.make_params(q_thresh=1.01, max_smooth_sweeps=3))
+    assert st["moves"] == 0
+    np.testing.assert_array_equal(om.get_raw()["xy"], xy)
 
 
 def test_smoothing_never_lowers_ball_min_quality():
