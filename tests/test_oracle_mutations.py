@@ -92,6 +92,18 @@ MUTATIONS = [
      "      for (int x : m.NN[v]) dirty[x] = 1;",
      "      for (int x : m.NN[v]) dirty[x] = dirty[x];",
      "nothing_left"),
+    ("refinement: stops after three rounds",
+     "    int64_t n = refine_round(m, P, st);\n    if (n == 0) break;",
+     "    int64_t n = refine_round(m, P, st);\n    if (n == 0 || rounds == 3) break;",
+     "no_edge_too_long"),
+    ("Algorithm 1: stops after one iteration",
+     "    if (n == 0) {\n      local.converged = 1;",
+     "    if (n >= 0) {\n      local.converged = 1;",
+     "round_equals_sequential"),
+    ("boundary: corner test inverted",
+     "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) != 0.0 ? 1 : 0;",
+     "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) == 0.0 ? 1 : 0;",
+     "collapse_rule_brute_force"),
 ]
 
 CHILD = textwrap.dedent("""

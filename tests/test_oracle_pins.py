@@ -547,6 +547,23 @@ def test_passes_end_with_nothing_left_to_do(n, T, seed):
     assert all(om.swap_target(int(v), p)[0] < 0 for v in alive)
 
 
+@pytest.mark.parametrize("n,T,seed", [(9, 4000, 5), (17, 20000, 21)])
+def test_refinement_ends_with_no_edge_too_long(n, T, seed):
+    """Refinement (Sec. 2.4.2) splits every edge longer than L_up and repeats
+    until none is left: when it returns, every edge is at most L_up."""
+    w = inputs.psi_workload(n, T, True, seed)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    p = O.make_params(seed=seed)
+    st = om.refine(p)
+    assert st["rounds"] > 2
+    raw = om.get_raw()
+    xy, m = raw["xy"], raw["m"]
+    edges = {tuple(sorted((int(t[i]), int(t[(i + 1) % 3]))))
+             for t, a in zip(raw["tri"], raw["talive"]) if a for i in range(3)}
+    longest = max(O.edge_length(xy[a], m[a], xy[b], m[b]) for a, b in edges)
+    assert longest <= p.L_up
+
+
 # --- round-equals-sequential and invariants ---------------------------------
 
 @pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (25, 8000, 22), (33, 20000, 2)])
