@@ -100,6 +100,18 @@ MUTATIONS = [
      "    if (n == 0) {\n      local.converged = 1;",
      "    if (n >= 0) {\n      local.converged = 1;",
      "round_equals_sequential"),
+    ("quality gradient: sign lost past the ideal perimeter",
+     "  double gxx = left ? gs : -(gs / (xx * xx));",
+     "  double gxx = left ? gs : (gs / (xx * xx));",
+     "gradient_central_differences"),
+    ("quality gradient: off-diagonal determinant partial halved",
+     "  double gk01 = -(2.0 * k01) * gdet;",
+     "  double gk01 = -(k01) * gdet;",
+     "gradient_central_differences"),
+    ("quality gradient: canonical slots not mapped back",
+     "    for (int j = 0; j < 5; ++j) g[(s + k) % 3][j] = cg[k][j];",
+     "    for (int j = 0; j < 5; ++j) g[k][j] = cg[k][j];",
+     "gradient_central_differences"),
     ("boundary: corner test inverted",
      "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) != 0.0 ? 1 : 0;",
      "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) == 0.0 ? 1 : 0;",
