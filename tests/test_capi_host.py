@@ -45,6 +45,13 @@ def test_argument_checks_need_no_device(pm):
     assert pm.lib.pm_mesh_destroy(None) == 0
     assert pm.lib.pm_status_string(6) == b"device wait timed out"
     assert b"null" in pm.lib.pm_last_error() or pm.lib.pm_last_error() != b""
+    # measurement and test support check their arguments before any device call
+    assert pm.lib.pm_fp64_peak(None) == 1
+    st32, ms = C.c_int32(), C.c_double()
+    assert pm.lib.pm_selftest_wait_timeout(50.0, None, C.byref(ms)) == 1
+    assert pm.lib.pm_selftest_wait_timeout(50.0, C.byref(st32), None) == 1
+    for bad in (0.0, -1.0, 2000.5, float("nan")):
+        assert pm.lib.pm_selftest_wait_timeout(bad, C.byref(st32), C.byref(ms)) == 1
 
 
 def test_out_of_range_ids_rejected_on_host(pm):
