@@ -1950,8 +1950,9 @@ __global__ void k_refine_sizes(Store S, const int* vscan, const int* escan) {
 // cooperative launch (every block resident), with a grid-wide barrier between
 // the phases and one read-back when the launch ends.  A collapse round
 // evaluates in one phase (coarsen_eval_phase) and takes three barriers;
-// smoothing keeps its scan and tile-parallel evaluation (three barriers);
-// flips keep their scan, item-parallel gains and pick (five).  The launch
+// smoothing scans and evaluates in one tile-parallel phase when the list fits
+// one pass of tiles (two barriers), else keeps the scan apart (three); flips
+// keep their scan, item-parallel gains and pick (five).  The launch
 // returns when a round finds no candidate (the pass is complete), when the
 // next round's list outgrows `limit`, on a row overflow or an error, or after
 // `max_rounds` rounds.
