@@ -126,7 +126,9 @@ pm_status pm_set_metric_dev(pm_mesh* mesh, const double* m);
  *   pm_smooth   quality-constrained Laplacian smoothing, then
  *               opt_smooth_rounds rounds of optimisation-based smoothing;
  *   pm_adapt    Algorithm 1 (Sec. 2.3) followed by smoothing; renumbers
- *               after every iteration and at the end.
+ *               after every iteration (new vertex ids, slots left in
+ *               place) and compacts the slots at the end, so that on
+ *               return ids and slots agree as after a full compaction.
  * `stats` may be null. */
 pm_status pm_coarsen(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
 pm_status pm_refine(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
