@@ -26,8 +26,10 @@
 //
 // Parity status of each function is stated at its definition; those marked
 // "convention" are readings of passages the paper leaves open (the choice of
-// collapse target, flip edge, refinement diagonal, smoothing target) and are
-// pinned only through brute force, round-equals-sequential and invariants.
+// collapse target, flip edge, refinement diagonal, smoothing target,
+// optimisation step); each is pinned through quantities the tests compute
+// independently (brute force, closed forms, the gradient), besides
+// round-equals-sequential and the invariants.
 
 #include <algorithm>
 #include <array>
@@ -513,7 +515,8 @@ void apply_flip(OMesh& m, int v, const SwapOp& op, std::vector<Rec>& recs) {
 // barycentric interpolation at x* in the ball element that contains it; the
 // move is kept only when every ball element stays counter-clockwise and the
 // minimum ball quality strictly increases.  Parity: convention, pinned by the
-// closed-form regular-patch case and the monotone property.
+// closed-form regular-patch cases, exact reproduction of a linear metric
+// field, the strict-gain case and the monotone property.
 // ---------------------------------------------------------------------------
 
 struct Move {
@@ -613,8 +616,9 @@ bool smooth_eval(const OMesh& m, int v, const Params& P, Move& mv) {
 // respect to v's coordinates (metric held fixed), step 0.1 * shortest
 // incident Euclidean edge / |g|, halved up to five times; a step is kept when
 // all elements stay counter-clockwise, the minimum quality does not drop and
-// the quality sum increases.  Parity: convention, pinned by the monotone
-// property and by the gradient pins.
+// the quality sum increases.  Parity: convention, pinned by the step rule
+// checked against the finite-difference-pinned gradient and the Euclidean
+// edge lengths, and by the monotone property.
 bool opt_eval(const OMesh& m, int v, Move& mv) {
   if (!m.valive[v] || m.vbnd[v]) return false;
   double gx = 0.0, gy = 0.0;
@@ -805,7 +809,9 @@ int64_t op_swap(OMesh& m, const Params& P, Stats& st) {
 // for elements, so they are reproducible.  Convention for the two-split
 // template: the trapezoid is cut along its metric-shorter diagonal (tie: the
 // one from the first unsplit-edge vertex).  Parity: convention, pinned by the
-// closed-form uniform-grid count and by invariants.
+// closed-form uniform-grid count, a two-split case whose metric-shorter
+// diagonal is the Euclidean longer one, linear metric fields at midpoints,
+// and invariants.
 int64_t refine_round(OMesh& m, const Params& P, Stats& st) {
   int nv0 = m.nv(), ne0 = m.ne();
   // mid[a] = list of (b, new id), b ascending

@@ -112,6 +112,14 @@ MUTATIONS = [
      "    for (int j = 0; j < 5; ++j) g[(s + k) % 3][j] = cg[k][j];",
      "    for (int j = 0; j < 5; ++j) g[k][j] = cg[k][j];",
      "gradient_central_differences"),
+    ("optimisation smoothing: first step doubled",
+     "  double alpha = (0.1 * lmin) / gn;",
+     "  double alpha = (0.2 * lmin) / gn;",
+     "step_rule"),
+    ("optimisation smoothing: step along a swapped gradient component",
+     "    double X = m.x[v] + alpha * gx;",
+     "    double X = m.x[v] + alpha * gy;",
+     "step_rule"),
     ("boundary: corner test inverted",
      "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) != 0.0 ? 1 : 0;",
      "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) == 0.0 ? 1 : 0;",

@@ -679,6 +679,41 @@ def test_smoothing_never_lowers_ball_min_quality():
     assert om.check() == 0
 
 
+def test_opt_smoothing_follows_its_step_rule():
+    """G2, checked through independent quantities: in one round every moved
+    vertex went along the gradient of the quality sum (pinned by finite
+    differences), by 0.1 x its shortest incident Euclidean edge x 2^-k,
+    k <= 5; its ball's minimum quality did not drop and the sum rose."""
+    w = inputs.psi_workload(25, 8000, True, 6)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    om.refine(O.make_params(seed=6))
+    raw0 = om.get_raw()
+    _, dxy, _ = om.quality(grad=True)
+    om.opt_smooth(O.make_params(seed=6, opt_smooth_rounds=1, max_rounds=1))
+    raw1 = om.get_raw()
+    xy0, xy1 = raw0["xy"], raw1["xy"]
+    moved = np.nonzero((xy1 != xy0).any(axis=1))[0]
+    assert moved.size > 100
+    live = [tuple(int(a) for a in t) for t, a in zip(raw0["tri"], raw0["talive"]) if a]
+    ball = {}
+    for t in live:
+        for a in t:
+            ball.setdefault(a, []).append(t)
+    ks = set()
+    for v in moved:
+        d, g = xy1[v] - xy0[v], dxy[v]
+        assert abs(d[0] * g[1] - d[1] * g[0]) <= 1e-9 * np.linalg.norm(d) * np.linalg.norm(g)
+        assert d @ g > 0
+        lmin = min(math.hypot(*(xy0[u] - xy0[v])) for t in ball[v] for u in t if u != v)
+        k = -math.log2(np.linalg.norm(d) / (0.1 * lmin))
+        assert abs(k - round(k)) < 1e-9 and 0 <= round(k) <= 5, k
+        ks.add(round(k))
+        q0 = [O.tri_quality(np.array(t), xy0[list(t)], raw0["m"][list(t)]) for t in ball[v]]
+        q1 = [O.tri_quality(np.array(t), xy1[list(t)], raw1["m"][list(t)]) for t in ball[v]]
+        assert min(q1) >= min(q0) and sum(q1) > sum(q0)
+    assert 0 in ks and len(ks) > 2
+
+
 def test_opt_smoothing_increases_quality_sum():
     w = inputs.psi_workload(25, 8000, True, 6)
     om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
