@@ -80,6 +80,14 @@ MUTATIONS = [
      "mv.m00 = (l0 * d[0].m00 + l1 * d[1].m00) + l2 * d[2].m00;",
      "mv.m00 = (l1 * d[0].m00 + l0 * d[1].m00) + l2 * d[2].m00;",
      "linear_metric"),
+    ("smoothing: sign error in the 2x2 solve",
+     "  double X = (a11 * b0 - a01 * b1) / det;",
+     "  double X = (a11 * b0 + a01 * b1) / det;",
+     "moves_with_the_patch"),
+    ("smoothing: second right-hand side with swapped weights",
+     "    b1 = b1 + (w01 * m.x[j] + w11 * m.y[j]);",
+     "    b1 = b1 + (w11 * m.x[j] + w01 * m.y[j]);",
+     "moves_with_the_patch"),
     ("smoothing: a move that gains nothing is taken",
      "  return qmin > qold;\n}",
      "  return qmin >= qold;\n}",

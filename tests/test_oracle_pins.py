@@ -628,6 +628,36 @@ def test_laplacian_smoothing_metric_weighted_target():
         assert np.abs(raw["xy"][0]).max() < 1e-14
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_smoothing_target_moves_with_the_patch(seed):
+    """The metric-weighted Laplacian target (S12) is covariant: translating the
+    patch translates the new position, and rotating points and metrics
+    together (M -> R M R^T) rotates it.  Varying metrics keep the weighted
+    mean away from the plain centroid."""
+    rng = np.random.default_rng(seed)
+    m = np.array([[1.0 + rng.uniform(-0.3, 0.3), rng.uniform(-0.2, 0.2), 1.0 + rng.uniform(-0.3, 0.3)]
+                  for _ in range(7)])
+    xy, tri = hex_patch((0.3, -0.2))
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+
+    def rotated(mm):
+        Mr = R @ np.array([[mm[0], mm[1]], [mm[1], mm[2]]]) @ R.T
+        return [Mr[0, 0], Mr[0, 1], Mr[1, 1]]
+
+    def new_centre(pts, mets):
+        om = O.OracleMesh(pts, tri).set_metric(mets)
+        assert om.smooth(O.make_params(q_thresh=1.01, max_smooth_sweeps=1))["moves"] == 1
+        return om.get_raw()["xy"][0]
+
+    X = new_centre(xy, m)
+    assert np.linalg.norm(X - xy[0]) > 0.1
+    t = np.array([0.25, -0.125])
+    np.testing.assert_allclose(new_centre(xy + t, m) - t, X, atol=1e-14)
+    np.testing.assert_allclose(R.T @ new_centre(xy @ R.T, np.array([rotated(r) for r in m])), X,
+                               atol=1e-14)
+
+
 def test_smoothing_interpolates_a_linear_metric_field_exactly():
     """Barycentric interpolation (S12) reproduces a field that is linear in
     (x, y): the moved vertex's new metric is the field at its new place."""
