@@ -44,6 +44,10 @@ MUTATIONS = [
      "h *= 0x85ebca6bu;",
      "h *= 0x85ebca6du;",
      "fmix32_published"),
+    ("independent set: round counter starts at 1",
+     "  uint32_t sr = seed + 0x9E3779B9u * r;",
+     "  uint32_t sr = seed + 0x9E3779B9u * (r + 1u);",
+     "round_zero"),
     ("independent set: non-candidate neighbours compete",
      "if (inC[u] && prio((uint32_t)u, seed, m.r) > pv) {",
      "if (prio((uint32_t)u, seed, m.r) > pv) {",

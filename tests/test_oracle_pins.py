@@ -270,6 +270,27 @@ def test_independent_set_brute_force():
             assert S.any()  # the global maximum candidate is always selected
 
 
+@pytest.mark.parametrize("seed", [12345, 2 ** 32 - 7])
+def test_first_collapse_round_uses_round_zero_priorities(seed):
+    """S5: r counts a call's rounds from 0, so the first round ranks vertices
+    by fmix32(v ^ seed) (fmix32 pinned by the published vectors).  The
+    vertices that die in a one-round collapse call are exactly the local
+    maxima of that priority among the vertices with a valid collapse."""
+    w = inputs.psi_workload(17, 1000, True, 3)  # coarser target: many collapses
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    nv = w.xy.shape[0]
+    NN, _ = MC.adjacency([tuple(int(a) for a in t) for t in w.tri], nv)
+    p = O.make_params(seed=seed)
+    cand = {v for v in range(nv) if om.coarsen_target(v, p) >= 0}
+    pr = {v: O.fmix32(v ^ seed) for v in cand}
+    S = {v for v in cand if all(u not in cand or pr[u] < pr[v] for u in NN[v])}
+    assert len(S) > 8
+    st = om.coarsen(O.make_params(seed=seed, max_rounds=1))
+    assert st["collapses"] == len(S)
+    dead = set(np.nonzero(om.get_raw()["valive"] == 0)[0].tolist())
+    assert dead == S
+
+
 # --- small uniform case: hand-derived result ---------------------------------
 
 def read_golden(name):
