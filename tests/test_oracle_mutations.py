@@ -100,6 +100,14 @@ MUTATIONS = [
      "      m.m00.push_back(0.5 * (da.m00 + db.m00));",
      "      m.m00.push_back(0.5 * (da.m00 + da.m00));",
      "linear_metric_field"),
+    ("smoothing: neighbours of a moved vertex not pending for the next sweep",
+     "          if (m.valive[j] && !m.vbnd[j]) next[j] = 1;",
+     "          if (false && m.valive[j] && !m.vbnd[j]) next[j] = 1;",
+     "only_moved_vertices"),
+    ("smoothing: one sweep only",
+     "    if (moved_sweep == 0) break;",
+     "    break;",
+     "only_moved_vertices"),
     ("collapse: neighbours not marked for re-evaluation",
      "      for (int x : m.NN[v]) dirty[x] = 1;",
      "      for (int x : m.NN[v]) dirty[x] = dirty[x];",

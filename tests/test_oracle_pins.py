@@ -716,6 +716,30 @@ def test_smoothing_moves_only_for_a_strict_gain():
     np.testing.assert_array_equal(om.get_raw()["xy"], xy)
 
 
+@pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (21, 6000, 9)])
+def test_smoothing_sweeps_leave_only_moved_vertices_movable(n, T, seed):
+    """S12 propagation: a vertex is evaluated again in the next sweep when a
+    neighbour moved, and sweeps stop when one moves nothing.  After such a
+    call every vertex that did not move has failed an evaluation made after
+    its last neighbour move, so the first round of a fresh call can only move
+    vertices the call moved (a moved vertex's own metric changed, so it may
+    gain again)."""
+    w = inputs.psi_workload(n, T, True, seed)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    p = O.make_params(seed=seed)
+    om.refine(p)
+    om.coarsen(p)
+    om.swap(p)
+    xy0 = om.get_raw()["xy"].copy()
+    st = om.smooth(O.make_params(seed=seed, max_smooth_sweeps=1000))
+    xy1 = om.get_raw()["xy"].copy()
+    moved1 = set(np.nonzero((xy1 != xy0).any(axis=1))[0].tolist())
+    assert st["moves"] > 100
+    om.smooth(O.make_params(seed=seed + 1, max_smooth_sweeps=1, max_rounds=1))
+    moved2 = set(np.nonzero((om.get_raw()["xy"] != xy1).any(axis=1))[0].tolist())
+    assert moved2 and moved2 <= moved1
+
+
 def test_smoothing_never_lowers_ball_min_quality():
     w = inputs.psi_workload(25, 8000, True, 4)
     om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
