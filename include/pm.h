@@ -220,6 +220,14 @@ pm_status pm_fp64_peak(double* gops);
  * counterpart. */
 pm_status pm_selftest_wait_timeout(double limit_ms, int32_t* device_status, double* elapsed_ms);
 
+/* Test support: out[i] = x[i] / 3.0 for i < n, computed the way the quality
+ * functional (Sec. 2.2) forms its means of three terms on the device (one
+ * multiplication and two fused multiply-adds, equal to the IEEE quotient).
+ * x[n] and out[n] are device arrays; runs on `stream` (cudaStream_t, null =
+ * legacy default stream) without synchronising.  PM_ERR_INVALID_ARG for a
+ * null pointer or n < 0.  The paper has no counterpart. */
+pm_status pm_selftest_div3_dev(const double* x, double* out, int64_t n, void* stream);
+
 /* pm_quality_arrays_dev for callers that cannot allocate device memory
  * during the call (a framework that has already reserved the device memory
  * for its own allocator, a latency-bound loop, or a program that allows no

@@ -128,7 +128,6 @@ double orient_c(int i0, int i1, int i2, VD a, VD b, VD c) {
 }
 
 const double QC = 12.0 * 1.7320508075688772;  // 12 sqrt(3)
-const double THIRD = 1.0 / 3.0;                 // the mean of three terms is sum * THIRD
 
 // Length of (q - p) under the fixed metric k.
 double len_under(double k00, double k01, double k11, const VD& p, const VD& q) {
@@ -146,16 +145,16 @@ double quality_c(int i0, int i1, int i2, VD a, VD b, VD c) {
   int ids[3] = {i0, i1, i2};
   VD d[3] = {a, b, c};
   canon(ids, d);
-  double k00 = ((d[0].m00 + d[1].m00) + d[2].m00) * THIRD;
-  double k01 = ((d[0].m01 + d[1].m01) + d[2].m01) * THIRD;
-  double k11 = ((d[0].m11 + d[1].m11) + d[2].m11) * THIRD;
+  double k00 = ((d[0].m00 + d[1].m00) + d[2].m00) / 3.0;
+  double k01 = ((d[0].m01 + d[1].m01) + d[2].m01) / 3.0;
+  double k11 = ((d[0].m11 + d[1].m11) + d[2].m11) / 3.0;
   double l0 = len_under(k00, k01, k11, d[0], d[1]);
   double l1 = len_under(k00, k01, k11, d[1], d[2]);
   double l2 = len_under(k00, k01, k11, d[2], d[0]);
   double P = (l0 + l1) + l2;
   double area = 0.5 * orient3(d[0], d[1], d[2]);
   double AM = std::sqrt(k00 * k11 - k01 * k01) * area;
-  double xx = P * THIRD;
+  double xx = P / 3.0;
   double s = (xx <= 1.0) ? xx : 1.0 / xx;
   double f = s * (2.0 - s);
   double F = (f * f) * f;
@@ -174,9 +173,9 @@ double quality_grad_c(int i0, int i1, int i2, VD a, VD b, VD c, double g[3][5]) 
   if (ids[2] < ids[s]) s = 2;
   canon(ids, d);
   const VD &p0 = d[0], &p1 = d[1], &p2 = d[2];
-  double k00 = ((p0.m00 + p1.m00) + p2.m00) * THIRD;
-  double k01 = ((p0.m01 + p1.m01) + p2.m01) * THIRD;
-  double k11 = ((p0.m11 + p1.m11) + p2.m11) * THIRD;
+  double k00 = ((p0.m00 + p1.m00) + p2.m00) / 3.0;
+  double k01 = ((p0.m01 + p1.m01) + p2.m01) / 3.0;
+  double k11 = ((p0.m11 + p1.m11) + p2.m11) / 3.0;
   double dx[3] = {p1.x - p0.x, p2.x - p1.x, p0.x - p2.x};
   double dy[3] = {p1.y - p0.y, p2.y - p1.y, p0.y - p2.y};
   double l[3];
@@ -188,7 +187,7 @@ double quality_grad_c(int i0, int i1, int i2, VD a, VD b, VD c, double g[3][5]) 
   double area = 0.5 * orient3(p0, p1, p2);
   double sd = std::sqrt(k00 * k11 - k01 * k01);
   double AM = sd * area;
-  double xx = P * THIRD;
+  double xx = P / 3.0;
   bool left = (xx <= 1.0);
   double sv = left ? xx : 1.0 / xx;
   double f = sv * (2.0 - sv);
@@ -204,7 +203,7 @@ double quality_grad_c(int i0, int i1, int i2, VD a, VD b, VD c, double g[3][5]) 
   double gf = (3.0 * (f * f)) * gF;
   double gs = (2.0 - 2.0 * sv) * gf;
   double gxx = left ? gs : -(gs / (xx * xx));
-  gP = gP + gxx * THIRD;
+  gP = gP + gxx / 3.0;
   double gsd = area * gAM;
   double garea = sd * gAM;
   double gdet = gsd / (2.0 * sd);
@@ -229,9 +228,9 @@ double quality_grad_c(int i0, int i1, int i2, VD a, VD b, VD c, double g[3][5]) 
   cg[1][1] = (go * (p0.x - p2.x) + gdy[0]) - gdy[1];
   cg[2][1] = (go * (p1.x - p0.x) + gdy[1]) - gdy[2];
   for (int k = 0; k < 3; ++k) {
-    cg[k][2] = gk00 * THIRD;
-    cg[k][3] = gk01 * THIRD;
-    cg[k][4] = gk11 * THIRD;
+    cg[k][2] = gk00 / 3.0;
+    cg[k][3] = gk01 / 3.0;
+    cg[k][4] = gk11 / 3.0;
   }
   // canonical slot k holds stored vertex (s + k) % 3
   for (int k = 0; k < 3; ++k)

@@ -302,7 +302,23 @@ __device__ __forceinline__ double orient_c(int i0, int i1, int i2, VD a, VD b, V
 }
 
 constexpr double QC = 12.0 * 1.7320508075688772;  // 12 sqrt(3)
-constexpr double THIRD = 1.0 / 3.0;                 // mean of three terms = sum * THIRD
+// x / 3.0, bit for bit the IEEE quotient (round to nearest), in one multiply
+// and two fused multiply-adds instead of the division sequence.  With
+// R = RN(1/3), q = RN(x R) lies within one ulp of x/3; the remainder
+// r = x - 3q is exact in one fma; RN(q + r R) is then the correctly rounded
+// quotient (Markstein's correction theorem: P. Markstein, "Computation of
+// elementary functions on the IBM RISC System/6000 processor", IBM J. Res.
+// Dev. 34(1), 1990; J.-M. Muller et al., Handbook of Floating-Point
+// Arithmetic, ch. 4).  A zero remainder keeps q (so -0 stays -0); a
+// non-finite x (r is NaN) keeps q as well (x/3 = x for infinities and NaN).
+__device__ __forceinline__ double div3(double x) {
+  constexpr double R = 1.0 / 3.0;
+  double q = x * R;
+  double r = __fma_rn(-3.0, q, x);
+  long long rb = __double_as_longlong(r);
+  bool keep = ((unsigned long long)rb << 1) == 0ull || ((rb >> 52) & 0x7ff) == 0x7ff;
+  return keep ? q : __fma_rn(r, R, q);
+}
 
 __device__ __forceinline__ double len_under(double k00, double k01, double k11, const VD& p,
                                             const VD& q) {
@@ -315,16 +331,16 @@ __device__ __forceinline__ double len_under(double k00, double k01, double k11, 
 // Vasilevskii-Lipnikov quality in the element-mean metric, canonical rotation.
 __device__ __forceinline__ double quality_c(int i0, int i1, int i2, VD a, VD b, VD c) {
   canon(i0, i1, i2, a, b, c);
-  double k00 = ((a.m00 + b.m00) + c.m00) * THIRD;
-  double k01 = ((a.m01 + b.m01) + c.m01) * THIRD;
-  double k11 = ((a.m11 + b.m11) + c.m11) * THIRD;
+  double k00 = div3((a.m00 + b.m00) + c.m00);
+  double k01 = div3((a.m01 + b.m01) + c.m01);
+  double k11 = div3((a.m11 + b.m11) + c.m11);
   double l0 = len_under(k00, k01, k11, a, b);
   double l1 = len_under(k00, k01, k11, b, c);
   double l2 = len_under(k00, k01, k11, c, a);
   double P = (l0 + l1) + l2;
   double area = 0.5 * orient3(a, b, c);
   double AM = sqrt(k00 * k11 - k01 * k01) * area;
-  double xx = P * THIRD;
+  double xx = div3(P);
   double s = !dgt(xx, 1.0) ? xx : 1.0 / xx;  // xx <= 1
   double f = s * (2.0 - s);
   double F = (f * f) * f;
@@ -340,9 +356,9 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   if (i1 < i0 && i1 < i2) s = 1;
   else if (i2 < i0 && i2 < i1) s = 2;
   canon(i0, i1, i2, a, b, c);
-  double k00 = ((a.m00 + b.m00) + c.m00) * THIRD;
-  double k01 = ((a.m01 + b.m01) + c.m01) * THIRD;
-  double k11 = ((a.m11 + b.m11) + c.m11) * THIRD;
+  double k00 = div3((a.m00 + b.m00) + c.m00);
+  double k01 = div3((a.m01 + b.m01) + c.m01);
+  double k11 = div3((a.m11 + b.m11) + c.m11);
   double dx[3] = {b.x - a.x, c.x - b.x, a.x - c.x};
   double dy[3] = {b.y - a.y, c.y - b.y, a.y - c.y};
   double l[3];
@@ -355,7 +371,7 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   double area = 0.5 * orient3(a, b, c);
   double sd = sqrt(k00 * k11 - k01 * k01);
   double AM = sd * area;
-  double xx = P * THIRD;
+  double xx = div3(P);
   bool left = (xx <= 1.0);
   double sv = left ? xx : 1.0 / xx;
   double f = sv * (2.0 - sv);
@@ -369,7 +385,7 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   double gf = (3.0 * (f * f)) * gF;
   double gs = (2.0 - 2.0 * sv) * gf;
   double gxx = left ? gs : -(gs / (xx * xx));
-  gP = gP + gxx * THIRD;
+  gP = gP + div3(gxx);
   double gsd = area * gAM;
   double garea = sd * gAM;
   double gdet = gsd / (2.0 * sd);
@@ -394,7 +410,7 @@ __device__ __forceinline__ double quality_grad_c(int i0, int i1, int i2, VD a, V
   cg[0][1] = (go * (c.x - b.x) - gdy[0]) + gdy[2];
   cg[1][1] = (go * (a.x - c.x) + gdy[0]) - gdy[1];
   cg[2][1] = (go * (b.x - a.x) + gdy[1]) - gdy[2];
-  double m0 = gk00 * THIRD, m1 = gk01 * THIRD, m2 = gk11 * THIRD;
+  double m0 = div3(gk00), m1 = div3(gk01), m2 = div3(gk11);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     cg[k][2] = m0;

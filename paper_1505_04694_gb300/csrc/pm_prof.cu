@@ -41,6 +41,14 @@ __global__ void k_fp64_peak(int iters, double seed, double* out) {
   if (t == 12345.678) out[0] = t;  // never true; keeps the chains
 }
 
+// Test support: out[i] = div3(x[i]), the quotient by three the quality
+// functional uses for its means.
+__global__ void k_selftest_div3(const double* x, double* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = div3(x[i]);
+}
+
 }  // namespace
 
 int prof_begin(const char* name, cudaStream_t s) {
@@ -122,6 +130,16 @@ pm_status pm_fp64_peak(double* gops) {
   const double ops = 2.0 * 8.0 * iters * (double)blocks * threads;
   *gops = ops / (best * 1e-3) / 1e9;
   return PM_OK;
+}
+
+pm_status pm_selftest_div3_dev(const double* x, double* out, int64_t n, void* stream) {
+  if (!x || !out || n < 0) return PM_ERR_INVALID_ARG;
+  if (n == 0) return PM_OK;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  PM_LAUNCH(k_selftest_div3, dim3((unsigned)blocks), dim3(256), 0, (cudaStream_t)stream, x, out,
+            (long long)n);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
 }
 
 pm_status pm_profile_read(double* total_ms, int64_t* launches, double* work) {

@@ -30,7 +30,7 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_get_mesh_dev", "pm_get_raw", "pm_adjacency", "pm_quality",
            "pm_quality_arrays_dev", "pm_status_string", "pm_last_error", "pm_kernel_launches",
            "pm_profile_enable", "pm_profile_read", "pm_quality_arrays_noalloc_dev",
-           "pm_fp64_peak", "pm_selftest_wait_timeout"]
+           "pm_fp64_peak", "pm_selftest_wait_timeout", "pm_selftest_div3_dev"]
 
 
 class PmParams(C.Structure):
@@ -103,6 +103,8 @@ def _load():
     L.pm_selftest_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int32),
                                            C.POINTER(C.c_double)]
     L.pm_selftest_wait_timeout.restype = C.c_int
+    L.pm_selftest_div3_dev.argtypes = [vp, vp, C.c_int64, vp]
+    L.pm_selftest_div3_dev.restype = C.c_int
     L.pm_status_string.argtypes = [C.c_int]
     L.pm_status_string.restype = C.c_char_p
     L.pm_last_error.argtypes = []
@@ -397,3 +399,10 @@ def quality_arrays_noalloc_dev(xy, m, tri, qsum, dxy=None, dm=None, stream=0):
         C.c_void_p(dxy.data_ptr()) if dxy is not None else None,
         C.c_void_p(dm.data_ptr()) if dm is not None else None, C.c_void_p(stream)),
         "pm_quality_arrays_noalloc_dev")
+
+
+def selftest_div3_dev(x, out, stream=0):
+    """out = x / 3 element-wise on the device, by the quality functional's own
+    division-by-three routine (float64 CUDA tensors of equal length)."""
+    _check(lib.pm_selftest_div3_dev(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                    x.numel(), C.c_void_p(stream)), "pm_selftest_div3_dev")
