@@ -147,6 +147,54 @@ pm_status pm_opt_smooth(pm_mesh* mesh, const pm_params* params, pm_stats* stats)
 pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params,
                          pm_stats* stats);
 
+/* Batch handles: many independent meshes held by one handle, in one device
+ * store.  Every round of every operator runs over all of them at once: a
+ * round's independent set (Sec. 3.2) is taken over the union of the meshes'
+ * vertex graphs, which share no edge, so each mesh's result is the result of
+ * adapting it alone (its own seed, parameters and round counter).
+ *
+ * pm_batch_create: nmesh meshes concatenated, mesh after mesh.
+ *   nv[nmesh], ne[nmesh]: vertex and element count of each mesh (nv >= 3,
+ *   ne >= 1); xy[2 * sum(nv)], tri[3 * sum(ne)] with vertex ids LOCAL to
+ *   each mesh (0 .. nv[i]-1); corner[sum(nv)] nullable (as pm_mesh_create).
+ *   cap_factor and device as pm_mesh_create; every mesh is checked as there
+ *   (PM_ERR_INVALID_MESH names no mesh).  The handle works with
+ *   pm_set_metric (m[3 * sum(nv)], mesh after mesh), the operators
+ *   (pm_coarsen ... pm_adapt: the same parameters for every mesh) and
+ *   pm_mesh_destroy; pm_get_mesh, pm_get_raw, pm_adjacency and pm_quality
+ *   take one-mesh handles only (PM_ERR_INVALID_ARG).
+ * pm_batch_create_dev: the same with device arrays xy, tri, corner (read on
+ *   `stream`, a cudaStream_t or null for a new stream of the library's own);
+ *   nv and ne stay host arrays. */
+pm_status pm_batch_create(const double* xy, const int32_t* nv, const int32_t* tri,
+                          const int32_t* ne, int32_t nmesh, const uint8_t* corner,
+                          int32_t cap_factor, int device, pm_mesh** out);
+pm_status pm_batch_create_dev(const double* xy, const int32_t* nv, const int32_t* tri,
+                              const int32_t* ne, int32_t nmesh, const uint8_t* corner,
+                              int32_t cap_factor, void* stream, pm_mesh** out);
+
+/* Number of meshes a handle holds (1 for pm_mesh_create handles). */
+pm_status pm_batch_size(const pm_mesh* mesh, int32_t* nmesh);
+
+/* Algorithm 1 (Sec. 2.3) and smoothing on every mesh of the handle, each
+ * with its own parameters params[nmesh]; stats[nmesh] (nullable) receives
+ * each mesh's counters, the same as a pm_adapt call on that mesh alone
+ * would report (ms: the whole call).  A mesh leaves the outer loop after an
+ * iteration that changed nothing or after its max_iter; the call returns
+ * when every mesh has, and max_rounds is taken from params[0]. */
+pm_status pm_batch_adapt(pm_mesh* mesh, const pm_params* params, pm_stats* stats);
+
+/* Compacted output of every mesh, mesh after mesh, as pm_get_mesh gives it
+ * for one mesh: nv[nmesh], ne[nmesh] receive the live counts; xy, tri, m
+ * (each nullable) receive sum(nv) vertices and sum(ne) triangles with vertex
+ * ids local to each mesh.  With all three null only the counts are written.
+ * pm_batch_get_mesh takes host arrays (page-locked ones are filled by direct
+ * DMA), pm_batch_get_mesh_dev device arrays on the handle's stream. */
+pm_status pm_batch_get_mesh(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
+                            double* m);
+pm_status pm_batch_get_mesh_dev(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy,
+                                int32_t* tri, double* m);
+
 /* Copy out the mesh, compacted (live vertices and elements in ascending slot
  * order) with every triangle rotated so its smallest vertex id comes first.
  * Two-call protocol: with null arrays only *nv and *ne are written.
@@ -179,11 +227,14 @@ pm_status pm_quality(pm_mesh* mesh, double* q_sum, double* dxy, double* dm);
 
 /* The same functional on plain device arrays (no mesh handle), for use under
  * automatic differentiation: xy[2*nv], m[3*nv], tri[3*ne] on the current
- * device.  q_sum (1 double), dxy[2*nv], dm[3*nv] are device outputs; dxy and
- * dm may be null for the forward value only.  Runs on `stream`
- * (cudaStream_t, null = legacy default stream) and returns without
- * synchronising.  Temporary device memory is allocated and released in the
- * call.  Gradient rows: each vertex sums its elements in ascending id. */
+ * device (ne may be 0: the sum is 0).  q_sum (1 double), dxy[2*nv], dm[3*nv]
+ * are device outputs; dxy and dm may be null for the forward value only.
+ * Runs on `stream` (cudaStream_t, null = legacy default stream), waits for
+ * it and returns the device status: PM_ERR_INVALID_MESH when a vertex id in
+ * tri lies outside [0, nv), PM_ERR_TIMEOUT when the gradient's scan gave up
+ * a bounded wait; the outputs then hold NaN.  Temporary device memory (one
+ * block) is allocated and released in the call (PM_ERR_OOM when that
+ * fails).  Gradient rows: each vertex sums its elements in ascending id. */
 pm_status pm_quality_arrays_dev(const double* xy, const double* m, int32_t nv,
                                 const int32_t* tri, int32_t ne, double* q_sum, double* dxy,
                                 double* dm, void* stream);
@@ -232,8 +283,8 @@ pm_status pm_selftest_div3_dev(const double* x, double* out, int64_t n, void* st
  * during the call (a framework that has already reserved the device memory
  * for its own allocator, a latency-bound loop, or a program that allows no
  * allocation after start-up).  The paper has no counterpart: this is a
- * service of this library.  Same arguments, results and stream behaviour as
- * pm_quality_arrays_dev, but every temporary lives in one fixed array
+ * service of this library.  Same arguments, results, stream behaviour and
+ * statuses as pm_quality_arrays_dev, but every temporary lives in one fixed array
  * (about 9.6 MB) compiled into the library, which each GPU that loads the
  * library keeps until the process exits; the call allocates and frees
  * nothing.  Limits: ne <= 65536 elements and nv <= 65536 vertices, else

@@ -41,6 +41,13 @@ pm_status fail(pm_status s, const std::string& msg) {
   return s;
 }
 
+// Calls that read or write one mesh's arrays take a one-mesh handle.
+pm_status single_only(const pm_mesh* h, const char* what) {
+  if (h->set.nmesh == 1) return PM_OK;
+  return fail(PM_ERR_INVALID_ARG,
+              std::string(what) + " takes a one-mesh handle (use the pm_batch_ calls)");
+}
+
 pm_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return PM_OK;
   set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -60,13 +67,27 @@ pm_status check_params(const pm_params* p) {
   return PM_OK;
 }
 
-__global__ void k_ingest(Store S, const int* tri, int ne, int nv) {
-  int n = ne > nv ? ne : nv;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (i < ne) S.EN[i] = make_int4(tri[3 * i], tri[3 * i + 1], tri[3 * i + 2], 1);
-    if (i < nv) {
-      S.M[i] = make_double4(1.0, 0.0, 1.0, 0.0);
-      S.vflag[i] = VF_ALIVE;
+// Concatenated inputs into the slots of every mesh: input vertex g of mesh
+// i (offsets in S.tab.pre) goes to slot vbase_i + (g - pre_i), with the
+// identity metric and, when the caller flags it, the corner bit.
+__global__ void k_ingest(Store S, const double* xy, const int* tri, const uint8_t* corner,
+                         int nv, int ne) {
+  const int n = S.nmesh;
+  const int* pv = S.tab.pre;
+  const int* pe = S.tab.pre + n + 1;
+  int top = ne > nv ? ne : nv;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < top; g += gridDim.x * blockDim.x) {
+    if (g < nv) {
+      int mi = seg_of(pv, n, g);
+      int slot = S.tab.vbase[mi] + (g - pv[mi]);
+      S.xy[slot] = make_double2(xy[2 * (size_t)g], xy[2 * (size_t)g + 1]);
+      S.M[slot] = make_double4(1.0, 0.0, 1.0, 0.0);
+      S.vflag[slot] = (uint8_t)(VF_ALIVE | ((corner && corner[g]) ? VF_CORNER : 0));
+    }
+    if (g < ne) {
+      int mi = seg_of(pe, n, g);
+      S.EN[S.tab.ebase[mi] + (g - pe[mi])] =
+          make_int4(tri[3 * (size_t)g], tri[3 * (size_t)g + 1], tri[3 * (size_t)g + 2], 1);
     }
   }
 }
@@ -79,9 +100,15 @@ __global__ void k_metric_check(const double* m, int nv, DevStatus* st) {
   }
 }
 
+// Concatenated metric (mesh after mesh, each in its used-slot order; offsets
+// in S.tab.pre) into the slots.
 __global__ void k_metric_set(Store S, const double* m, int nv) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x)
-    S.M[i] = make_double4(m[3 * i], m[3 * i + 1], m[3 * i + 2], 0.0);
+  const int n = S.nmesh;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nv; g += gridDim.x * blockDim.x) {
+    int mi = seg_of(S.tab.pre, n, g);
+    int slot = S.tab.vbase[mi] + (g - S.tab.pre[mi]);
+    S.M[slot] = make_double4(m[3 * (size_t)g], m[3 * (size_t)g + 1], m[3 * (size_t)g + 2], 0.0);
+  }
 }
 
 int sms_of(int dev) {
@@ -99,57 +126,88 @@ void set_mem_pool_retain(int dev) {
   }
 }
 
-// Shared body of pm_mesh_create / _dev.  Inputs are host or device pointers.
-pm_status create_common(const double* xy, int nv, const int32_t* tri, int ne,
-                        const uint8_t* corner, int cap_factor, int dev, cudaStream_t stream,
-                        bool own_stream, bool host, pm_mesh** out) {
+// Exclusive prefix sums of per-mesh vertex and element counts into the
+// device table (S.tab.pre), for kernels that map a concatenated array onto
+// the meshes' slots.
+cudaError_t upload_prefix(MeshSet& m, const std::vector<int>& nv, const std::vector<int>& ne) {
+  const int n = m.nmesh;
+  std::vector<int> pre(2 * ((size_t)n + 1));
+  for (int i = 0; i < n; ++i) {
+    pre[i + 1] = pre[i] + nv[i];
+    pre[n + 1 + i + 1] = pre[n + 1 + i] + ne[i];
+  }
+  // a copy from pageable memory is staged before the call returns
+  return cudaMemcpyAsync(m.S.tab.pre, pre.data(), pre.size() * sizeof(int),
+                         cudaMemcpyHostToDevice, m.stream);
+}
+
+// Shared body of pm_mesh_create / pm_batch_create and their _dev forms.
+// Inputs are host or device pointers: nmesh meshes concatenated (vertex ids
+// local to each mesh), per-mesh sizes nv[i], ne[i] on the host.
+pm_status create_set(const double* xy, const int32_t* nv, const int32_t* tri, const int32_t* ne,
+                     int nmesh, const uint8_t* corner, int cap_factor, int dev,
+                     cudaStream_t stream, bool own_stream, bool host, pm_mesh** out) {
   pm_mesh* h = new pm_mesh();
   MeshSet& m = h->set;
   m.device = dev;
   m.stream = stream;
   m.own_stream = own_stream;
-  m.nmesh = 1;
+  m.nmesh = nmesh;
   m.num_sms = sms_of(dev);
-  m.nv = {nv};
-  m.ne = {ne};
-  m.seed = {1u};
-  m.L_low = {0.4};
-  m.L_up = {std::sqrt(2.0)};
-  m.q_thresh = {0.7};
-  long long vc = std::max<long long>((long long)nv * cap_factor, (long long)nv + 64);
-  long long ec = std::max<long long>((long long)ne * cap_factor, (long long)ne + 64);
-  if (vc >= (1LL << 30) || ec >= (1LL << 30)) {
-    delete h;
-    return fail(PM_ERR_CAPACITY, "mesh too large for 32-bit slot ids");
-  }
-  cudaError_t e = set_alloc(m, {(int)vc}, {(int)ec}, 16);
-  pm_status s = cuda_status(e, "allocating mesh");
-  int32_t* tri_dev = nullptr;
-  uint8_t* corner_dev = nullptr;
-  if (!s) s = cuda_status(upload_tab(m), "mesh table");
-  if (!s) {
-    cudaMemsetAsync(m.S.tab.active, 0xFF, sizeof(int), m.stream);
-    cudaMemcpyKind k = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    e = cudaMemcpyAsync(m.S.xy, xy, (size_t)nv * 2 * sizeof(double), k, m.stream);
-    if (host) {
-      if (!e) e = cudaMallocAsync(&tri_dev, (size_t)ne * 3 * sizeof(int32_t), m.stream);
-      if (!e) e = cudaMemcpyAsync(tri_dev, tri, (size_t)ne * 3 * sizeof(int32_t), k, m.stream);
-      if (!e && corner) e = cudaMallocAsync(&corner_dev, (size_t)nv, m.stream);
-      if (!e && corner) e = cudaMemcpyAsync(corner_dev, corner, (size_t)nv, k, m.stream);
+  m.nv.assign(nv, nv + nmesh);
+  m.ne.assign(ne, ne + nmesh);
+  m.seed.assign(nmesh, 1u);
+  m.L_low.assign(nmesh, 0.4);
+  m.L_up.assign(nmesh, std::sqrt(2.0));
+  m.q_thresh.assign(nmesh, 0.7);
+  std::vector<int> vcap(nmesh), ecap(nmesh);
+  long long nvt = 0, net = 0;
+  for (int i = 0; i < nmesh; ++i) {
+    long long vc = std::max<long long>((long long)nv[i] * cap_factor, (long long)nv[i] + 64);
+    long long ec = std::max<long long>((long long)ne[i] * cap_factor, (long long)ne[i] + 64);
+    if (vc >= (1LL << 30) || ec >= (1LL << 30)) {
+      delete h;
+      return fail(PM_ERR_CAPACITY, "mesh too large for 32-bit slot ids");
     }
-    s = cuda_status(e, "uploading mesh");
+    vcap[i] = (int)vc;
+    ecap[i] = (int)ec;
+    nvt += nv[i];
+    net += ne[i];
+  }
+  cudaError_t e = set_alloc(m, vcap, ecap, 16);
+  pm_status s = cuda_status(e, "allocating mesh");
+  char* tmp = nullptr;
+  const double* dxy = xy;
+  const int32_t* dtri = tri;
+  const uint8_t* dcorner = corner;
+  if (!s) s = cuda_status(upload_tab(m), "mesh table");
+  if (!s) s = cuda_status(upload_prefix(m, m.nv, m.ne), "mesh offsets");
+  if (!s) {
+    cudaMemsetAsync(m.S.tab.active, 0xFF, nmesh * sizeof(int), m.stream);
+    if (host) {
+      const size_t bxy = (size_t)nvt * 2 * sizeof(double), btri = (size_t)net * 3 * sizeof(int32_t);
+      const size_t bc = corner ? (size_t)nvt : 0;
+      e = cudaMallocAsync((void**)&tmp, bxy + btri + bc + 64, m.stream);
+      if (!e) e = cudaMemcpyAsync(tmp, xy, bxy, cudaMemcpyHostToDevice, m.stream);
+      if (!e) e = cudaMemcpyAsync(tmp + bxy, tri, btri, cudaMemcpyHostToDevice, m.stream);
+      if (!e && corner) e = cudaMemcpyAsync(tmp + bxy + btri, corner, bc, cudaMemcpyHostToDevice,
+                                            m.stream);
+      dxy = (const double*)tmp;
+      dtri = (const int32_t*)(tmp + bxy);
+      dcorner = corner ? (const uint8_t*)(tmp + bxy + btri) : nullptr;
+      s = cuda_status(e, "uploading mesh");
+    }
   }
   if (!s) {
-    const int32_t* t = host ? tri_dev : tri;
-    const uint8_t* c = host ? corner_dev : corner;
-    PM_LAUNCH(k_ingest, grid_for(m, std::max(nv, ne)), BLOCK, 0, m.stream, m.S, t, ne, nv);
+    PM_LAUNCH(k_ingest, grid_for(m, std::max(nvt, net)), BLOCK, 0, m.stream, m.S, dxy, dtri,
+              dcorner, (int)nvt, (int)net);
     int err = validate_mesh(m);
     if (err) s = (pm_status)err;
     if (s == PM_ERR_INVALID_MESH)
       set_last_error("invalid mesh: vertex id out of range, repeated in an element, or an "
                      "element that is not counter-clockwise");
     if (!s) {
-      err = rebuild_adjacency(m, true, c);
+      err = rebuild_adjacency(m, true, corner != nullptr);
       if (err) {
         s = (pm_status)err;
         if (s == PM_ERR_INVALID_MESH)
@@ -158,8 +216,7 @@ pm_status create_common(const double* xy, int nv, const int32_t* tri, int ne,
     }
     if (!s) s = (pm_status)refresh_quality(m);
   }
-  if (tri_dev) cudaFreeAsync(tri_dev, m.stream);
-  if (corner_dev) cudaFreeAsync(corner_dev, m.stream);
+  if (tmp) cudaFreeAsync(tmp, m.stream);
   if (s) {
     set_free(m);
     set_release(m);
@@ -428,7 +485,7 @@ pm_status pm_mesh_create(const double* xy, int32_t nv, const int32_t* tri, int32
   cudaStream_t s;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
     return fail(PM_ERR_CUDA, "creating a stream");
-  return create_common(xy, nv, tri, ne, corner, cap_factor, device, s, true, true, out);
+  return create_set(xy, &nv, tri, &ne, 1, corner, cap_factor, device, s, true, true, out);
 }
 
 pm_status pm_mesh_create_dev(const double* xy, int32_t nv, const int32_t* tri, int32_t ne,
@@ -452,7 +509,7 @@ pm_status pm_mesh_create_dev(const double* xy, int32_t nv, const int32_t* tri, i
       return fail(PM_ERR_CUDA, "creating a stream");
     own = true;
   }
-  return create_common(xy, nv, tri, ne, corner, cap_factor, dev, s, own, false, out);
+  return create_set(xy, &nv, tri, &ne, 1, corner, cap_factor, dev, s, own, false, out);
 }
 
 pm_status pm_mesh_destroy(pm_mesh* h) {
@@ -484,10 +541,12 @@ pm_status pm_set_stream(pm_mesh* h, void* stream) {
 static pm_status set_metric_impl(pm_mesh* h, const double* M, bool host) {
   if (!h || !M) return fail(PM_ERR_INVALID_ARG, "mesh or metric is null");
   MeshSet& m = h->set;
-  int nv = m.nv[0];
+  long long nvl = 0;
+  for (int i = 0; i < m.nmesh; ++i) nvl += m.nv[i];
+  const int nv = (int)nvl;
   if (host) {
     for (int i = 0; i < nv; ++i) {
-      double a = M[3 * i], b = M[3 * i + 1], c = M[3 * i + 2];
+      double a = M[3 * (size_t)i], b = M[3 * (size_t)i + 1], c = M[3 * (size_t)i + 2];
       if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c) || !(a > 0.0) ||
           !(a * c - b * b > 0.0))
         return fail(PM_ERR_INVALID_ARG, "metric must be finite and symmetric positive definite");
@@ -510,8 +569,10 @@ static pm_status set_metric_impl(pm_mesh* h, const double* M, bool host) {
       return fail((pm_status)err, "metric must be finite and symmetric positive definite");
     }
   }
-  PM_LAUNCH(k_metric_set, grid_for(m, nv), BLOCK, 0, m.stream, m.S, src, nv);
+  pm_status s = cuda_status(upload_prefix(m, m.nv, m.ne), "mesh offsets");
+  if (!s) PM_LAUNCH(k_metric_set, grid_for(m, nv), BLOCK, 0, m.stream, m.S, src, nv);
   if (tmp) cudaFreeAsync(tmp, m.stream);
+  if (s) return s;
   return (pm_status)refresh_quality(m);
 }
 
@@ -541,6 +602,7 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params, p
   if (!meshes || n < 1 || !params) return fail(PM_ERR_INVALID_ARG, "need meshes, n >= 1, params");
   for (int i = 0; i < n; ++i) {
     if (!meshes[i]) return fail(PM_ERR_INVALID_ARG, "null mesh in batch");
+    if (pm_status gs = single_only(meshes[i], "pm_adapt_batch")) return gs;
     pm_status s = check_params(params + i);
     if (s) return s;
     if (meshes[i]->set.device != meshes[0]->set.device)
@@ -612,6 +674,7 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params, p
 pm_status pm_get_mesh(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
                       double* M) {
   if (!h || !nv || !ne) return fail(PM_ERR_INVALID_ARG, "mesh, nv and ne are required");
+  if (pm_status gs = single_only(h, "pm_get_mesh")) return gs;
   MeshSet& m = h->set;
   DeviceGuard g(m.device);
   int n1 = 0, n2 = 0;
@@ -650,6 +713,7 @@ pm_status pm_get_mesh(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int32_t*
 pm_status pm_get_mesh_dev(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
                           double* M) {
   if (!h || !nv || !ne) return fail(PM_ERR_INVALID_ARG, "mesh, nv and ne are required");
+  if (pm_status gs = single_only(h, "pm_get_mesh_dev")) return gs;
   MeshSet& m = h->set;
   DeviceGuard g(m.device);
   int n1 = 0, n2 = 0;
@@ -662,6 +726,7 @@ pm_status pm_get_mesh_dev(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int3
 pm_status pm_get_raw(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, double* M, int32_t* tri,
                      uint8_t* valive, uint8_t* talive, uint8_t* vflag) {
   if (!h || !nv || !ne) return fail(PM_ERR_INVALID_ARG, "mesh, nv and ne are required");
+  if (pm_status gs = single_only(h, "pm_get_raw")) return gs;
   MeshSet& m = h->set;
   DeviceGuard g(m.device);
   int n1 = m.nv[0], n2 = m.ne[0];
@@ -705,6 +770,7 @@ pm_status pm_get_raw(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, double* M
 pm_status pm_adjacency(pm_mesh* h, int32_t v, int32_t* nn, int32_t* nnlen, int32_t* ne,
                        int32_t* nelen, int32_t cap) {
   if (!h || !nnlen || !nelen || cap < 0) return fail(PM_ERR_INVALID_ARG, "bad arguments");
+  if (pm_status gs = single_only(h, "pm_adjacency")) return gs;
   MeshSet& m = h->set;
   if (v < 0 || v >= m.nv[0]) return fail(PM_ERR_INVALID_ARG, "vertex slot out of range");
   DeviceGuard g(m.device);
@@ -728,6 +794,7 @@ pm_status pm_adjacency(pm_mesh* h, int32_t v, int32_t* nn, int32_t* nnlen, int32
 
 pm_status pm_quality(pm_mesh* h, double* q_sum, double* dxy, double* dm) {
   if (!h || !q_sum) return fail(PM_ERR_INVALID_ARG, "mesh and q_sum are required");
+  if (pm_status gs = single_only(h, "pm_quality")) return gs;
   MeshSet& m = h->set;
   DeviceGuard g(m.device);
   return (pm_status)quality_mesh(m, q_sum, dxy, dm);
@@ -736,9 +803,152 @@ pm_status pm_quality(pm_mesh* h, double* q_sum, double* dxy, double* dm) {
 pm_status pm_quality_arrays_dev(const double* xy, const double* M, int32_t nv, const int32_t* tri,
                                 int32_t ne, double* q_sum, double* dxy, double* dm,
                                 void* stream) {
-  if (!xy || !M || !tri || !q_sum || nv < 1 || ne < 0)
+  if (!xy || !M || (!tri && ne > 0) || !q_sum || nv < 1 || ne < 0)
     return fail(PM_ERR_INVALID_ARG, "need xy, m, tri, q_sum, nv >= 1, ne >= 0");
   return (pm_status)quality_arrays(xy, M, nv, tri, ne, q_sum, dxy, dm, (cudaStream_t)stream);
+}
+
+// ---- batch handles ---------------------------------------------------------------
+
+static pm_status check_batch_sizes(const int32_t* nv, const int32_t* ne, int32_t nmesh) {
+  long long vt = 0, et = 0;
+  for (int i = 0; i < nmesh; ++i) {
+    if (nv[i] < 3 || ne[i] < 1) return fail(PM_ERR_INVALID_ARG, "every mesh needs nv >= 3, ne >= 1");
+    vt += nv[i];
+    et += ne[i];
+  }
+  if (vt >= (1LL << 30) || et >= (1LL << 30))
+    return fail(PM_ERR_CAPACITY, "batch too large for 32-bit slot ids");
+  return PM_OK;
+}
+
+pm_status pm_batch_create(const double* xy, const int32_t* nv, const int32_t* tri,
+                          const int32_t* ne, int32_t nmesh, const uint8_t* corner,
+                          int32_t cap_factor, int device, pm_mesh** out) {
+  if (!out) return fail(PM_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (!xy || !nv || !tri || !ne || nmesh < 1 || cap_factor < 1)
+    return fail(PM_ERR_INVALID_ARG, "need xy, nv, tri, ne, nmesh >= 1, cap_factor >= 1");
+  if (pm_status s = check_batch_sizes(nv, ne, nmesh)) return s;
+  long long vo = 0, eo = 0;
+  for (int i = 0; i < nmesh; ++i) {
+    for (long long k = 3 * eo; k < 3 * (eo + ne[i]); ++k)
+      if (tri[k] < 0 || tri[k] >= nv[i])
+        return fail(PM_ERR_INVALID_MESH, "vertex id out of range");
+    for (long long k = 2 * vo; k < 2 * (vo + nv[i]); ++k)
+      if (!std::isfinite(xy[k])) return fail(PM_ERR_INVALID_ARG, "non-finite coordinate");
+    vo += nv[i];
+    eo += ne[i];
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(PM_ERR_INVALID_ARG, "no such CUDA device");
+  DeviceGuard g(device);
+  set_mem_pool_retain(device);
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(PM_ERR_CUDA, "creating a stream");
+  return create_set(xy, nv, tri, ne, nmesh, corner, cap_factor, device, s, true, true, out);
+}
+
+pm_status pm_batch_create_dev(const double* xy, const int32_t* nv, const int32_t* tri,
+                              const int32_t* ne, int32_t nmesh, const uint8_t* corner,
+                              int32_t cap_factor, void* stream, pm_mesh** out) {
+  if (!out) return fail(PM_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (!xy || !nv || !tri || !ne || nmesh < 1 || cap_factor < 1)
+    return fail(PM_ERR_INVALID_ARG, "need xy, nv, tri, ne, nmesh >= 1, cap_factor >= 1");
+  if (pm_status s = check_batch_sizes(nv, ne, nmesh)) return s;
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, xy) != cudaSuccess || pa.type != cudaMemoryTypeDevice)
+    return fail(PM_ERR_INVALID_ARG, "xy is not device memory");
+  const int dev = pa.device;
+  DeviceGuard g(dev);
+  set_mem_pool_retain(dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool own = false;
+  if (!s) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(PM_ERR_CUDA, "creating a stream");
+    own = true;
+  }
+  return create_set(xy, nv, tri, ne, nmesh, corner, cap_factor, dev, s, own, false, out);
+}
+
+pm_status pm_batch_size(const pm_mesh* h, int32_t* nmesh) {
+  if (!h || !nmesh) return fail(PM_ERR_INVALID_ARG, "mesh and nmesh are required");
+  *nmesh = h->set.nmesh;
+  return PM_OK;
+}
+
+pm_status pm_batch_adapt(pm_mesh* h, const pm_params* params, pm_stats* stats) {
+  if (!h || !params) return fail(PM_ERR_INVALID_ARG, "mesh and params are required");
+  MeshSet& m = h->set;
+  for (int i = 0; i < m.nmesh; ++i)
+    if (pm_status s = check_params(params + i)) return s;
+  DeviceGuard g(m.device);
+  double t0 = now_ms();
+  pm_status s = begin_call(m, params, 1);
+  if (s) return s;
+  CallStats cs;
+  cs.init(m.nmesh);
+  if ((s = adapt_set(m, params, 1, cs))) return s;
+  int err = sync_status(m);
+  if (err) return (pm_status)err;
+  return fill_stats(m, cs, t0, stats, m.nmesh);
+}
+
+static pm_status batch_get(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
+                           double* M, bool host) {
+  if (!h || !nv || !ne) return fail(PM_ERR_INVALID_ARG, "mesh, nv and ne are required");
+  MeshSet& m = h->set;
+  DeviceGuard g(m.device);
+  if (!xy && !tri && !M) return (pm_status)compact_out_set(m, nullptr, nullptr, nullptr, nv, ne);
+  if (!host) return (pm_status)compact_out_set(m, xy, tri, M, nv, ne);
+  // one compaction into device buffers sized by the used slots, then one
+  // copy of each array's live part
+  long long vb = 0, eb = 0;
+  for (int i = 0; i < m.nmesh; ++i) {
+    vb += m.nv[i];
+    eb += m.ne[i];
+  }
+  char* buf = nullptr;
+  pm_status s = cuda_status(cudaMallocAsync((void**)&buf, (size_t)std::max(vb, 1LL) * 5 * 8 +
+                                                              (size_t)std::max(eb, 1LL) * 12,
+                                            m.stream),
+                            "output buffers");
+  if (s) return s;
+  double* dxy = (double*)buf;
+  double* dm = dxy + 2 * std::max(vb, 1LL);
+  int32_t* dtri = (int32_t*)(dm + 3 * std::max(vb, 1LL));
+  int err = compact_out_set(m, xy ? dxy : nullptr, tri ? dtri : nullptr, M ? dm : nullptr, nv, ne);
+  if (err) s = (pm_status)err;
+  if (!s) {
+    long long tv = 0, te = 0;
+    for (int i = 0; i < m.nmesh; ++i) {
+      tv += nv[i];
+      te += ne[i];
+    }
+    cudaError_t e = cudaSuccess;
+    if (xy) e = cudaMemcpyAsync(xy, dxy, tv * 2 * sizeof(double), cudaMemcpyDeviceToHost, m.stream);
+    if (!e && M) e = cudaMemcpyAsync(M, dm, tv * 3 * sizeof(double), cudaMemcpyDeviceToHost, m.stream);
+    if (!e && tri)
+      e = cudaMemcpyAsync(tri, dtri, te * 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, m.stream);
+    s = cuda_status(e, "copying the output");
+  }
+  cudaFreeAsync(buf, m.stream);
+  err = sync_status(m);
+  return s ? s : (pm_status)err;
+}
+
+pm_status pm_batch_get_mesh(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
+                            double* M) {
+  return batch_get(h, nv, ne, xy, tri, M, true);
+}
+
+pm_status pm_batch_get_mesh_dev(pm_mesh* h, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
+                                double* M) {
+  return batch_get(h, nv, ne, xy, tri, M, false);
 }
 
 }  // extern "C"

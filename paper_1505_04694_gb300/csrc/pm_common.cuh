@@ -38,6 +38,10 @@ struct MeshTab {
   double* L_up;
   double* q_thresh;
   double4* band;                 // (L_low_lo^2, L_low_hi^2, L_up_lo^2, L_up_hi^2)
+  // 2 * (nmesh + 1) ints: exclusive prefix sums over the meshes of a vertex
+  // count and an element count (pre[0..nmesh] vertices, pre[nmesh+1..]
+  // elements); the offsets of each mesh in a concatenated input or output.
+  int* pre;
 };
 
 struct Store {
@@ -111,6 +115,17 @@ __device__ __forceinline__ int mesh_of_eslot(const Store& S, int slot) {
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (__ldg(S.tab.ebase + mid) <= slot) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Segment of position g in a concatenation: the largest i < n with
+// pre[i] <= g (pre: n + 1 ascending exclusive prefix sums).
+__device__ __forceinline__ int seg_of(const int* pre, int n, int g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pre + mid) <= g) lo = mid; else hi = mid - 1;
   }
   return lo;
 }

@@ -116,10 +116,11 @@ void set_release(MeshSet& m);
 cudaError_t upload_tab(MeshSet& m);
 void set_used(MeshSet& m);
 cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap, int W);
-int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev);
+int rebuild_adjacency(MeshSet& m, bool derive_flags, bool corners_given);
 int renumber(MeshSet& m, bool final);
 int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
                 int* ne_out);
+int compact_out_set(MeshSet& m, double* xy, int32_t* tri, double* mt, int* nv_out, int* ne_out);
 int sync_status(MeshSet& m);
 int validate_mesh(MeshSet& m);
 int refresh_quality(MeshSet& m);

@@ -94,6 +94,7 @@ __device__ __forceinline__ bool eslot_used(const Store& S, int slot, int& mi) {
 
 // ---- relayout (growth) ------------------------------------------------------
 
+// Per-slot data of every used vertex slot into its place in the new layout.
 __global__ void k_relayout_v(Store A, Store B) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.vused; s += gridDim.x * blockDim.x) {
     int mi;
@@ -109,14 +110,30 @@ __global__ void k_relayout_v(Store A, Store B) {
     B.evm[ns] = A.evm[s];
     B.evr[ns] = A.evr[s];
     if (A.lid && B.lid) B.lid[ns] = A.lid[s];
-    int wn = A.W < B.W ? A.W : B.W;
-    int a = A.NNlen[s], b = A.NElen[s];
-    B.NNlen[ns] = a;
-    B.NElen[ns] = b;
-    for (int k = 0; k < wn; ++k) {
-      B.NN[(size_t)ns * B.W + k] = A.NN[(size_t)s * A.W + k];
-      B.NE[(size_t)ns * B.W + k] = A.NE[(size_t)s * A.W + k];
-    }
+    B.NNlen[ns] = A.NNlen[s];
+    B.NElen[ns] = A.NElen[s];
+  }
+}
+
+// The rows: thread t copies 16-byte chunk t % (W/4) of row t / (W/4), so a
+// warp moves consecutive chunks (whole rows when W = 16); chunks past the
+// row's length are not copied (nothing reads them).  W of both layouts is a
+// multiple of 4 and the new one is at least the old one.
+__global__ void k_relayout_rows(Store A, Store B) {
+  const int cpr = A.W >> 2;
+  const long long total = (long long)A.vused * cpr;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int s = (int)(t / cpr), c = (int)(t - (long long)s * cpr);
+    int mi;
+    if (!vslot_used(A, s, mi)) continue;
+    int ns = B.tab.vbase[mi] + (s - A.tab.vbase[mi]);
+    if (4 * c < A.NNlen[s])
+      reinterpret_cast<int4*>(B.NN + (size_t)ns * B.W)[c] =
+          reinterpret_cast<const int4*>(A.NN + (size_t)s * A.W)[c];
+    if (4 * c < A.NElen[s])
+      reinterpret_cast<int4*>(B.NE + (size_t)ns * B.W)[c] =
+          reinterpret_cast<const int4*>(A.NE + (size_t)s * A.W)[c];
   }
 }
 
@@ -237,8 +254,8 @@ __device__ __forceinline__ int edge_elements(const Store& S, int slot, int eb, i
 }
 
 // Corners: boundary vertices whose two boundary neighbours are not collinear
-// with them (or the caller's flags).
-__global__ void k_corners(Store S, const uint8_t* corner) {
+// with them, or (given) the caller's flags, already set in vflag by the ingest.
+__global__ void k_corners(Store S, int given) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     int mi;
     if (!vslot_used(S, s, mi)) continue;
@@ -246,8 +263,8 @@ __global__ void k_corners(Store S, const uint8_t* corner) {
     if (!(f & VF_ALIVE)) continue;
     int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi];
     bool c = false;
-    if (corner) {
-      c = corner[s - vb] != 0;
+    if (given) {
+      c = (f & VF_CORNER) != 0;
     } else if (f & VF_BND) {
       const int* nn = S.NN + (size_t)s * S.W;
       int nnl = S.NNlen[s];
@@ -437,6 +454,90 @@ __global__ void k_out_e(Store S, int mesh, const int* vscan, const int* escan, i
   }
 }
 
+// Output offsets of every mesh: exclusive prefix sums over the meshes of the
+// live counts tot[2i] (vertices) and tot[2i+1] (elements) into pre (vertex
+// offsets pre[0..n], element offsets pre[n+1..2n+1]).  One block: each
+// thread sums a contiguous chunk of meshes, thread 0 scans the chunk sums.
+__global__ void k_out_prefix(int n, const int* tot, int* pre) {
+  __shared__ long long part[2][1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (n + T - 1) / T;
+  const int a = t * per, b = min(n, a + per);
+  long long sv = 0, se = 0;
+  for (int i = a; i < b; ++i) {
+    sv += tot[2 * i];
+    se += tot[2 * i + 1];
+  }
+  part[0][t] = sv;
+  part[1][t] = se;
+  __syncthreads();
+  if (t == 0) {
+    long long cv = 0, ce = 0;
+    for (int k = 0; k < T; ++k) {
+      long long x = part[0][k], y = part[1][k];
+      part[0][k] = cv;
+      part[1][k] = ce;
+      cv += x;
+      ce += y;
+    }
+    pre[n] = (int)cv;
+    pre[n + 1 + n] = (int)ce;
+  }
+  __syncthreads();
+  long long cv = part[0][t], ce = part[1][t];
+  for (int i = a; i < b; ++i) {
+    pre[i] = (int)cv;
+    pre[n + 1 + i] = (int)ce;
+    cv += tot[2 * i];
+    ce += tot[2 * i + 1];
+  }
+}
+
+// Compacted output of every mesh of the set, meshes one after the other
+// (offsets in S.tab.pre); vertex ids in the triangles are local to the mesh.
+__global__ void k_out_v_set(Store S, const int* vscan, double* xy, double* mt) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!vslot_used(S, s, mi)) continue;
+    if (!(S.vflag[s] & VF_ALIVE)) continue;
+    int vb = S.tab.vbase[mi];
+    int o = S.tab.pre[mi] + (vscan[s] - vscan[vb]);
+    double2 p = S.xy[s];
+    double4 m = S.M[s];
+    if (xy) {
+      xy[2 * (size_t)o] = p.x;
+      xy[2 * (size_t)o + 1] = p.y;
+    }
+    if (mt) {
+      mt[3 * (size_t)o] = m.x;
+      mt[3 * (size_t)o + 1] = m.y;
+      mt[3 * (size_t)o + 2] = m.z;
+    }
+  }
+}
+
+__global__ void k_out_e_set(Store S, const int* vscan, const int* escan, int32_t* tri) {
+  const int n = S.nmesh;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!eslot_used(S, s, mi)) continue;
+    int4 e = S.EN[s];
+    if (!e.w) continue;
+    int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi];
+    int v0 = vscan[vb];
+    int o = S.tab.pre[n + 1 + mi] + (escan[s] - escan[eb]);
+    int a = vscan[vb + e.x] - v0, b = vscan[vb + e.y] - v0, c = vscan[vb + e.z] - v0;
+    if (b < a && b < c) {
+      int t = a; a = b; b = c; c = t;
+    } else if (c < a && c < b) {
+      int t = c; c = b; b = a; a = t;
+    }
+    tri[3 * (size_t)o] = a;
+    tri[3 * (size_t)o + 1] = b;
+    tri[3 * (size_t)o + 2] = c;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -551,7 +652,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   carve_store(cv, m.B);
   size_t tab_bytes = (size_t)n * (6 * sizeof(int) + 2 * sizeof(uint32_t) + 3 * sizeof(int) +
                                   2 * sizeof(unsigned long long) + 3 * sizeof(double) +
-                                  sizeof(double4)) + 64;
+                                  sizeof(double4)) +
+                     2 * ((size_t)n + 1) * sizeof(int) + 64;
   char* t = nullptr;
   cv.add(&t, tab_bytes);
   Work& w = m.w;
@@ -613,6 +715,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   T.r = (uint32_t*)t; t += n * sizeof(uint32_t);
   T.had = (int*)t; t += 2 * n * sizeof(int);  // two sets: persistent rounds alternate
   T.active = (int*)t; t += n * sizeof(int);
+  T.pre = (int*)t; t += 2 * ((size_t)n + 1) * sizeof(int);
   m.B.tab = T;
   if (!m.st) {
     if ((e = cudaMallocAsync((void**)&m.st, sizeof(DevStatus), m.stream))) return e;
@@ -701,6 +804,8 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
     cudaMemcpyAsync(n2.voffbuf, m.S.voff, nm * sizeof(int), cudaMemcpyDeviceToDevice, m.stream);
   }
   PM_LAUNCH(k_relayout_v, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, n2.S);
+  PM_LAUNCH(k_relayout_rows, grid_for(m, (long long)m.S.vused * (m.S.W / 4)), BLOCK, 0, m.stream,
+            m.S, n2.S);
   PM_LAUNCH(k_relayout_e, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, n2.S);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -765,7 +870,7 @@ int sync_status(MeshSet& m) {
 // Build NN and NE from the element list for every mesh of the set.  With
 // `derive_flags` (creation) also derive boundary and corner flags and check
 // manifoldness.  Grows W (rebuilding) when a row does not fit.
-int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) {
+int rebuild_adjacency(MeshSet& m, bool derive_flags, bool corners_given) {
   for (;;) {
     cudaMemsetAsync(&m.st->overflow, 0, 2 * sizeof(int), m.stream);
     PM_LAUNCH(k_zero_nelen, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S);
@@ -789,7 +894,7 @@ int rebuild_adjacency(MeshSet& m, bool derive_flags, const uint8_t* corner_dev) 
     }
   }
   if (derive_flags) {
-    PM_LAUNCH(k_corners, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, corner_dev);
+    PM_LAUNCH(k_corners, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, corners_given ? 1 : 0);
     return sync_status(m);
   }
   return PM_OK;
@@ -896,6 +1001,35 @@ int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int*
   if (err) return err;
   *nv_out = m.hcounts[2 * mesh];
   *ne_out = m.hcounts[2 * mesh + 1];
+  return PM_OK;
+}
+
+// Compacted, canonically rotated copy of every mesh of the set, one after
+// the other in mesh order, into device buffers (each may be null).  Writes
+// each mesh's live counts into nv_out[nmesh] and ne_out[nmesh].
+int compact_out_set(MeshSet& m, double* xy, int32_t* tri, double* mt, int* nv_out, int* ne_out) {
+  Work& w = m.w;
+  const int n = m.nmesh;
+  scan_alive_vertices(m.S, w.vscan, m.S.vused, m.scan, m.st, m.stream);
+  scan_alive_elements(m.S, w.escan, m.S.eused, m.scan, m.st, m.stream);
+  int* tot = w.counts + CN_NUM;
+  PM_LAUNCH(k_mesh_totals, (n + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan, tot,
+            (int*)nullptr);
+  if (xy || mt || tri) {
+    PM_LAUNCH(k_out_prefix, 1, 1024, 0, m.stream, n, (const int*)tot, m.S.tab.pre);
+    if (xy || mt)
+      PM_LAUNCH(k_out_v_set, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, w.vscan, xy, mt);
+    if (tri)
+      PM_LAUNCH(k_out_e_set, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, w.vscan, w.escan,
+                tri);
+  }
+  cudaMemcpyAsync(m.hcounts, tot, 2 * n * sizeof(int), cudaMemcpyDeviceToHost, m.stream);
+  int err = sync_status(m);
+  if (err) return err;
+  for (int i = 0; i < n; ++i) {
+    nv_out[i] = m.hcounts[2 * i];
+    ne_out[i] = m.hcounts[2 * i + 1];
+  }
   return PM_OK;
 }
 

@@ -73,10 +73,17 @@ __global__ void k_na_clear(int* cnt, int* fill, int nv, DevStatus* st) {
   }
 }
 
-__global__ void k_na_elem(const double* xy, const double* m, const int* tri, int ne, double* qel,
-                          NaGrad* eg) {
+// An element with a vertex id outside [0, nv) records PM_ERR_INVALID_MESH
+// and contributes NaN (nothing is read through a bad id).
+__global__ void k_na_elem(const double* xy, const double* m, const int* tri, int ne, int nv,
+                          double* qel, NaGrad* eg, DevStatus* st) {
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x) {
     int a = tri[3 * K], b = tri[3 * K + 1], c = tri[3 * K + 2];
+    if ((unsigned)a >= (unsigned)nv || (unsigned)b >= (unsigned)nv || (unsigned)c >= (unsigned)nv) {
+      set_err(st, PM_ERR_INVALID_MESH);
+      qel[K] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
     double g[3][5];
     qel[K] = quality_grad_c(a, b, c, na_vd(xy, m, a), na_vd(xy, m, b), na_vd(xy, m, c), g);
     if (eg) {
@@ -88,38 +95,53 @@ __global__ void k_na_elem(const double* xy, const double* m, const int* tri, int
   }
 }
 
-__global__ void k_na_count(const int* tri, int ne, int* cnt) {
-  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x)
-    for (int i = 0; i < 3; ++i) atomicAdd(cnt + tri[3 * K + i], 1);
-}
-
-__global__ void k_na_fill(const int* tri, int ne, const int* off, int* fill, int* col) {
+__global__ void k_na_count(const int* tri, int ne, int nv, int* cnt) {
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x)
     for (int i = 0; i < 3; ++i) {
       int v = tri[3 * K + i];
-      col[off[v] + atomicAdd(fill + v, 1)] = 3 * K + i;
+      if ((unsigned)v < (unsigned)nv) atomicAdd(cnt + v, 1);
+    }
+}
+
+// Nothing is written after a device error (the offsets may be stale from an
+// earlier call) and no entry leaves its vertex's range of the array.
+__global__ void k_na_fill(const int* tri, int ne, int nv, const int* off, int* fill, int* col,
+                          const DevStatus* st) {
+  if (st->err) return;
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x)
+    for (int i = 0; i < 3; ++i) {
+      int v = tri[3 * K + i];
+      if ((unsigned)v >= (unsigned)nv) continue;
+      int p = atomicAdd(fill + v, 1);
+      if (off[v] + p < off[v + 1]) col[off[v] + p] = 3 * K + i;
     }
 }
 
 // Per vertex: sort its corner list (ascending element id) and sum the
-// contributions in that order.
+// contributions in that order.  After a device error every output is NaN.
 __global__ void k_na_gather(const int* off, int* col, const NaGrad* eg, int nv, double* dxy,
-                            double* dm) {
+                            double* dm, const DevStatus* st) {
+  const bool bad = st->err != 0;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
-    int a = off[v], b = off[v + 1];
-    for (int k = a + 1; k < b; ++k) {
-      int x = col[k];
-      int j = k - 1;
-      while (j >= a && col[j] > x) {
-        col[j + 1] = col[j];
-        --j;
-      }
-      col[j + 1] = x;
-    }
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int k = a; k < b; ++k) {
-      const double* g = eg[col[k] / 3].g + 5 * (col[k] % 3);
-      for (int j = 0; j < 5; ++j) acc[j] = acc[j] + g[j];
+    if (bad) {
+      for (int j = 0; j < 5; ++j) acc[j] = nan;
+    } else {
+      int a = off[v], b = off[v + 1];
+      for (int k = a + 1; k < b; ++k) {
+        int x = col[k];
+        int j = k - 1;
+        while (j >= a && col[j] > x) {
+          col[j + 1] = col[j];
+          --j;
+        }
+        col[j + 1] = x;
+      }
+      for (int k = a; k < b; ++k) {
+        const double* g = eg[col[k] / 3].g + 5 * (col[k] % 3);
+        for (int j = 0; j < 5; ++j) acc[j] = acc[j] + g[j];
+      }
     }
     if (dxy) {
       dxy[2 * v] = acc[0];
@@ -173,7 +195,7 @@ using namespace pm;
 extern "C" pm_status pm_quality_arrays_noalloc_dev(const double* xy, const double* M, int32_t nv,
                                                    const int32_t* tri, int32_t ne, double* q_sum,
                                                    double* dxy, double* dm, void* stream) {
-  if (!xy || !M || !tri || !q_sum || nv < 1 || ne < 0) {
+  if (!xy || !M || (!tri && ne > 0) || !q_sum || nv < 1 || ne < 0) {
     set_last_error("need xy, m, tri, q_sum, nv >= 1, ne >= 0");
     return PM_ERR_INVALID_ARG;
   }
@@ -219,23 +241,32 @@ extern "C" pm_status pm_quality_arrays_noalloc_dev(const double* xy, const doubl
   DevStatus* st = (DevStatus*)(base + kOffStatus);
   bool grad = dxy || dm;
   PM_LAUNCH(k_na_clear, na_grid(nv + 1), 128, 0, s, cnt, fill, nv, st);
-  PM_LAUNCH(k_na_elem, na_grid(ne), 128, 0, s, xy, M, tri, ne, qel, grad ? eg : nullptr);
+  PM_LAUNCH(k_na_elem, na_grid(ne), 128, 0, s, xy, M, tri, ne, nv, qel, grad ? eg : nullptr, st);
   PM_LAUNCH(k_na_sum1, kRedBlocks, kRedThreads, 0, s, qel, ne, part);
   PM_LAUNCH(k_na_sum2, 1, kRedBlocks, 0, s, part, q_sum);
   if (grad) {
-    PM_LAUNCH(k_na_count, na_grid(ne), 128, 0, s, tri, ne, cnt);
+    PM_LAUNCH(k_na_count, na_grid(ne), 128, 0, s, tri, ne, nv, cnt);
     {
       // the scan's epoch counter is shared by all calls on this device
       std::lock_guard<std::mutex> lk(g_mu);
       scan_exclusive(cnt, off, nv, *sw, st, s);
     }
-    PM_LAUNCH(k_na_fill, na_grid(ne), 128, 0, s, tri, ne, off, fill, col);
-    PM_LAUNCH(k_na_gather, na_grid(nv), 128, 0, s, off, col, eg, nv, dxy, dm);
+    PM_LAUNCH(k_na_fill, na_grid(ne), 128, 0, s, tri, ne, nv, (const int*)off, fill, col,
+              (const DevStatus*)st);
+    PM_LAUNCH(k_na_gather, na_grid(nv), 128, 0, s, (const int*)off, col, (const NaGrad*)eg, nv,
+              dxy, dm, (const DevStatus*)st);
   }
   cudaError_t e = cudaGetLastError();
+  // the status word of this call (a copy into pageable host memory returns
+  // once the stream has reached it)
+  DevStatus h{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     set_last_error(std::string("CUDA: ") + cudaGetErrorString(e));
     return PM_ERR_CUDA;
   }
-  return PM_OK;
+  if (h.err == PM_ERR_INVALID_MESH) set_last_error("vertex id outside [0, nv) in tri");
+  if (h.err == PM_ERR_TIMEOUT) set_last_error("the gradient's scan gave up waiting");
+  return (pm_status)h.err;
 }

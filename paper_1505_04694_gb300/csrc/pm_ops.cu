@@ -2227,7 +2227,7 @@ void zero_round(MeshSet& m, int nxt) {
 // rebuilt rows unset: rows are rebuilt from the elements and no evaluation
 // made before is reused (every lo_* and the callers' pass start move to now).
 int after_overflow(MeshSet& m) {
-  int err = rebuild_adjacency(m, false, nullptr);
+  int err = rebuild_adjacency(m, false, false);
   m.lo_coarsen = m.lo_swap = m.lo_refine = m.tag;
   return err;
 }
@@ -2505,23 +2505,27 @@ int op_refine(MeshSet& m, int max_rounds) {
       if (err) return err;
     }
     for (int i = 0; i < m.nmesh; ++i) newv[i] = m.hcounts[CN_NUM + i];
+    // A growth moves every mesh of the set, so when one mesh needs room,
+    // every mesh that is splitting gets twice what this round needs (the
+    // next rounds of a refinement pass usually split again).
     long long total = 0;
     bool need_grow = false;
-    std::vector<int> vcap = m.vcap, ecap = m.ecap;
     for (int i = 0; i < m.nmesh; ++i) {
       total += newv[i];
+      if ((long long)m.nv[i] + newv[i] > m.vcap[i] || (long long)m.ne[i] + 2LL * newv[i] > m.ecap[i])
+        need_grow = true;
+    }
+    std::vector<int> vcap = m.vcap, ecap = m.ecap;
+    for (int i = 0; need_grow && i < m.nmesh; ++i) {
+      if (newv[i] == 0) continue;
       long long vneed = (long long)m.nv[i] + newv[i];
       long long eneed = (long long)m.ne[i] + 2LL * newv[i];
-      if (vneed > m.vcap[i]) {
-        vcap[i] = (int)std::min<long long>(std::max<long long>(2LL * m.vcap[i], vneed + vneed / 2),
+      if (2 * vneed > m.vcap[i])
+        vcap[i] = (int)std::min<long long>(std::max<long long>(2LL * m.vcap[i], 2 * vneed),
                                            (1LL << 30));
-        need_grow = true;
-      }
-      if (eneed > m.ecap[i]) {
-        ecap[i] = (int)std::min<long long>(std::max<long long>(2LL * m.ecap[i], eneed + eneed / 2),
+      if (2 * eneed > m.ecap[i])
+        ecap[i] = (int)std::min<long long>(std::max<long long>(2LL * m.ecap[i], 2 * eneed),
                                            (1LL << 30));
-        need_grow = true;
-      }
     }
     if (total == 0) {
       complete = true;

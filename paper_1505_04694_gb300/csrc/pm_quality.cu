@@ -79,10 +79,17 @@ __device__ __forceinline__ VD arr_vd(const double* xy, const double* m, int v) {
   return VD{xy[2 * v], xy[2 * v + 1], m[3 * v], m[3 * v + 1], m[3 * v + 2]};
 }
 
+// An element with a vertex id outside [0, nv) records PM_ERR_INVALID_MESH
+// and contributes NaN (nothing is read through a bad id).
 __global__ void k_elem_qgrad_arr(const double* xy, const double* m, const int* tri, int ne,
-                                 double* qel, EGrad* eg) {
+                                 int nv, double* qel, EGrad* eg, DevStatus* st) {
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x) {
     int a = tri[3 * K], b = tri[3 * K + 1], c = tri[3 * K + 2];
+    if ((unsigned)a >= (unsigned)nv || (unsigned)b >= (unsigned)nv || (unsigned)c >= (unsigned)nv) {
+      set_err(st, PM_ERR_INVALID_MESH);
+      qel[K] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
     double g[3][5];
     double q = quality_grad_c(a, b, c, arr_vd(xy, m, a), arr_vd(xy, m, b), arr_vd(xy, m, c), g);
     qel[K] = q;
@@ -97,44 +104,60 @@ __global__ void k_elem_qgrad_arr(const double* xy, const double* m, const int* t
   }
 }
 
-__global__ void k_corner_count(const int* tri, int ne, int* cnt) {
-  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x) {
-    atomicAdd(cnt + tri[3 * K], 1);
-    atomicAdd(cnt + tri[3 * K + 1], 1);
-    atomicAdd(cnt + tri[3 * K + 2], 1);
-  }
+// Corners per vertex (ids outside [0, nv) are skipped: the element pass has
+// recorded them).
+__global__ void k_corner_count(const int* tri, int ne, int nv, int* cnt) {
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x)
+    for (int i = 0; i < 3; ++i) {
+      int v = tri[3 * K + i];
+      if ((unsigned)v < (unsigned)nv) atomicAdd(cnt + v, 1);
+    }
 }
 
-// Corner list per vertex: entry = 3 * element + corner position.
-__global__ void k_corner_fill(const int* tri, int ne, const int* off, int* fill, int* col) {
+// Corner list per vertex: entry = 3 * element + corner position; nothing is
+// written after a device error (the offsets may be unwritten) and no entry
+// leaves its vertex's range.
+__global__ void k_corner_fill(const int* tri, int ne, int nv, const int* off, int* fill, int* col,
+                              const DevStatus* st) {
+  if (st->err) return;
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < ne; K += gridDim.x * blockDim.x) {
     for (int i = 0; i < 3; ++i) {
       int v = tri[3 * K + i];
+      if ((unsigned)v >= (unsigned)nv) continue;
       int p = atomicAdd(fill + v, 1);
-      col[off[v] + p] = 3 * K + i;
+      if (off[v] + p < off[v + 1]) col[off[v] + p] = 3 * K + i;
     }
   }
 }
 
+// Per vertex: its corners in ascending element id, contributions summed in
+// that order.  After a device error every output entry is NaN.
 __global__ void k_vgather_arr(const int* off, int* col, const EGrad* eg, int nv, double* dxy,
-                              double* dm) {
+                              double* dm, const DevStatus* st) {
+  const bool bad = st->err != 0;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
-    int a = off[v], b = off[v + 1];
-    for (int k = a + 1; k < b; ++k) {  // ascending element id
-      int x = col[k];
-      int j = k - 1;
-      while (j >= a && col[j] > x) {
-        col[j + 1] = col[j];
-        --j;
-      }
-      col[j + 1] = x;
-    }
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int k = a; k < b; ++k) {
-      int x = col[k];
-      const double* g = eg[x / 3].g + 5 * (x % 3);
+    if (bad) {
 #pragma unroll
-      for (int j = 0; j < 5; ++j) acc[j] = acc[j] + g[j];
+      for (int j = 0; j < 5; ++j) acc[j] = nan;
+    } else {
+      int a = off[v], b = off[v + 1];
+      for (int k = a + 1; k < b; ++k) {  // ascending element id
+        int x = col[k];
+        int j = k - 1;
+        while (j >= a && col[j] > x) {
+          col[j + 1] = col[j];
+          --j;
+        }
+        col[j + 1] = x;
+      }
+      for (int k = a; k < b; ++k) {
+        int x = col[k];
+        const double* g = eg[x / 3].g + 5 * (x % 3);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) acc[j] = acc[j] + g[j];
+      }
     }
     if (dxy) {
       dxy[2 * v] = acc[0];
@@ -221,54 +244,73 @@ int quality_mesh(MeshSet& m, double* qsum_host, double* dxy_host, double* dm_hos
   return status ? status : err;
 }
 
-// Quality sum (and gradient) on plain device arrays; stream-ordered, no
-// synchronisation.  Temporary memory comes from the stream-ordered pool.
+// Quality sum (and gradient) on plain device arrays.  Temporaries come from
+// one stream-ordered allocation; the call waits for its stream and returns
+// the device status (PM_ERR_INVALID_MESH for a vertex id outside [0, nv),
+// PM_ERR_TIMEOUT when the scan's bounded wait gave up; the outputs then hold
+// NaN).
 int quality_arrays(const double* xy, const double* mt, int nv, const int* tri, int ne,
                    double* qsum, double* dxy, double* dm, cudaStream_t s) {
-  bool grad = dxy || dm;
-  double *qel = nullptr, *part = nullptr;
-  EGrad* eg = nullptr;
-  int *cnt = nullptr, *off = nullptr, *col = nullptr;
-  cudaError_t e = cudaMallocAsync(&qel, std::max(ne, 1) * sizeof(double), s);
-  if (!e) e = cudaMallocAsync(&part, RED_BLOCKS * sizeof(double), s);
-  if (!e && grad) e = cudaMallocAsync(&eg, std::max(ne, 1) * sizeof(EGrad), s);
-  if (!e && grad) e = cudaMallocAsync(&cnt, (nv + 1) * sizeof(int) * 2, s);
-  if (!e && grad) e = cudaMallocAsync(&off, (nv + 1) * sizeof(int), s);
-  if (!e && grad) e = cudaMallocAsync(&col, std::max(3LL * ne, 1LL) * sizeof(int), s);
-  int status = PM_OK;
-  if (e) {
+  const bool grad = dxy || dm;
+  const int tiles = scan_tiles(nv + 1);
+  auto r256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_qel = r256(std::max(ne, 1) * sizeof(double));
+  const size_t b_part = r256(RED_BLOCKS * sizeof(double));
+  const size_t b_st = r256(sizeof(DevStatus));
+  const size_t b_eg = grad ? r256(std::max(ne, 1) * sizeof(EGrad)) : 0;
+  const size_t b_cnt = grad ? r256(2 * ((size_t)nv + 1) * sizeof(int)) : 0;
+  const size_t b_off = grad ? r256(((size_t)nv + 1) * sizeof(int)) : 0;
+  const size_t b_col = grad ? r256(std::max(3LL * ne, 1LL) * sizeof(int)) : 0;
+  const size_t b_state = grad ? r256((size_t)tiles * sizeof(unsigned long long)) : 0;
+  const size_t b_ticket = grad ? r256(sizeof(int)) : 0;
+  char* base = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&base, b_qel + b_part + b_st + b_eg + b_cnt + b_off +
+                                                     b_col + b_state + b_ticket, s);
+  if (e != cudaSuccess) {
     set_last_error(std::string("quality workspace: ") + cudaGetErrorString(e));
-    status = PM_ERR_OOM;
-  } else {
-    PM_LAUNCH(k_elem_qgrad_arr, gridn(ne), 128, 0, s, xy, mt, tri, ne, qel, eg);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;
+  }
+  char* p = base;
+  double* qel = (double*)p; p += b_qel;
+  double* part = (double*)p; p += b_part;
+  DevStatus* st = (DevStatus*)p; p += b_st;
+  EGrad* eg = grad ? (EGrad*)p : nullptr; p += b_eg;
+  int* cnt = (int*)p; p += b_cnt;
+  int* off = (int*)p; p += b_off;
+  int* col = (int*)p; p += b_col;
+  ScanWork sw;
+  sw.state = (unsigned long long*)p; p += b_state;
+  sw.ticket = (int*)p;
+  sw.tiles_cap = tiles;
+  e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+  if (!e && grad) e = cudaMemsetAsync(cnt, 0, 2 * ((size_t)nv + 1) * sizeof(int), s);
+  if (!e && grad) e = cudaMemsetAsync(sw.state, 0, b_state, s);
+  if (!e) {
+    PM_LAUNCH(k_elem_qgrad_arr, gridn(ne), 128, 0, s, xy, mt, tri, ne, nv, qel, eg, st);
     dsum(qel, ne, part, qsum, s);
     if (grad) {
       int* fill = cnt + (nv + 1);
-      cudaMemsetAsync(cnt, 0, (nv + 1) * sizeof(int) * 2, s);
-      PM_LAUNCH(k_corner_count, gridn(ne), 128, 0, s, tri, ne, cnt);
-      ScanWork sw;
-      cudaMallocAsync(&sw.state, (size_t)scan_tiles(nv + 1) * sizeof(unsigned long long), s);
-      cudaMallocAsync(&sw.ticket, sizeof(int), s);
-      cudaMemsetAsync(sw.state, 0, (size_t)scan_tiles(nv + 1) * sizeof(unsigned long long), s);
-      DevStatus* st = nullptr;
-      cudaMallocAsync(&st, sizeof(DevStatus), s);
-      cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+      PM_LAUNCH(k_corner_count, gridn(ne), 128, 0, s, tri, ne, nv, cnt);
       scan_exclusive(cnt, off, nv, sw, st, s);
-      PM_LAUNCH(k_corner_fill, gridn(ne), 128, 0, s, tri, ne, off, fill, col);
-      PM_LAUNCH(k_vgather_arr, gridn(nv), 128, 0, s, off, col, eg, nv, dxy, dm);
-      cudaFreeAsync(sw.state, s);
-      cudaFreeAsync(sw.ticket, s);
-      cudaFreeAsync(st, s);
+      PM_LAUNCH(k_corner_fill, gridn(ne), 128, 0, s, tri, ne, nv, (const int*)off, fill, col,
+                (const DevStatus*)st);
+      PM_LAUNCH(k_vgather_arr, gridn(nv), 128, 0, s, (const int*)off, col, (const EGrad*)eg, nv,
+                dxy, dm, (const DevStatus*)st);
     }
+    e = cudaGetLastError();
   }
-  for (void* p : {(void*)qel, (void*)part, (void*)eg, (void*)cnt, (void*)off, (void*)col})
-    if (p) cudaFreeAsync(p, s);
-  cudaError_t le = cudaGetLastError();
-  if (le != cudaSuccess && !status) {
-    set_last_error(std::string("CUDA: ") + cudaGetErrorString(le));
-    status = PM_ERR_CUDA;
+  DevStatus h{};
+  if (!e) e = cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(base, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("CUDA: ") + cudaGetErrorString(e));
+    return PM_ERR_CUDA;
   }
-  return status;
+  if (h.err == PM_ERR_INVALID_MESH) set_last_error("vertex id outside [0, nv) in tri");
+  if (h.err == PM_ERR_TIMEOUT) set_last_error("the gradient's scan gave up waiting");
+  return h.err;
 }
 
 }  // namespace pm

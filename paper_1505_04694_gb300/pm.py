@@ -30,7 +30,9 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_get_mesh_dev", "pm_get_raw", "pm_adjacency", "pm_quality",
            "pm_quality_arrays_dev", "pm_status_string", "pm_last_error", "pm_kernel_launches",
            "pm_profile_enable", "pm_profile_read", "pm_quality_arrays_noalloc_dev",
-           "pm_fp64_peak", "pm_selftest_wait_timeout", "pm_selftest_div3_dev"]
+           "pm_fp64_peak", "pm_selftest_wait_timeout", "pm_selftest_div3_dev",
+           "pm_batch_create", "pm_batch_create_dev", "pm_batch_size", "pm_batch_adapt",
+           "pm_batch_get_mesh", "pm_batch_get_mesh_dev"]
 
 
 class PmParams(C.Structure):
@@ -86,6 +88,12 @@ def _load():
         "pm_quality": [vp, dp, dp, dp],
         "pm_quality_arrays_dev": [vp, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, vp],
         "pm_quality_arrays_noalloc_dev": [vp, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, vp],
+        "pm_batch_create": [dp, ip, ip, ip, C.c_int32, up, C.c_int32, C.c_int, mp],
+        "pm_batch_create_dev": [vp, ip, vp, ip, C.c_int32, vp, C.c_int32, vp, mp],
+        "pm_batch_size": [vp, ip],
+        "pm_batch_adapt": [vp, C.POINTER(PmParams), C.POINTER(PmStats)],
+        "pm_batch_get_mesh": [vp, ip, ip, dp, ip, dp],
+        "pm_batch_get_mesh_dev": [vp, ip, ip, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -331,6 +339,113 @@ class Mesh:
         return int(a[0]), int(b[0])
 
 
+class Batch(Mesh):
+    """Many meshes in one handle (pm_batch_*): one store, every round of every
+    operator over all of them at once."""
+
+    @classmethod
+    def from_host(cls, meshes, corner=None, cap_factor=2, device=0):
+        """meshes: list of (xy (nv,2) float64, tri (ne,3) int32 local ids)."""
+        xy = np.concatenate([np.asarray(a, np.float64).reshape(-1, 2) for a, _ in meshes])
+        tri = np.concatenate([np.asarray(t, np.int32).reshape(-1, 3) for _, t in meshes])
+        nv = [np.asarray(a).reshape(-1, 2).shape[0] for a, _ in meshes]
+        ne = [np.asarray(t).reshape(-1, 3).shape[0] for _, t in meshes]
+        return cls.from_arrays(xy, nv, tri, ne, corner, cap_factor, device)
+
+    @classmethod
+    def from_arrays(cls, xy, nv, tri, ne, corner=None, cap_factor=2, device=0):
+        """Meshes already concatenated in host arrays: xy (sum nv, 2) float64,
+        tri (sum ne, 3) int32 local ids, nv / ne per-mesh counts."""
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        nv = np.ascontiguousarray(nv, dtype=np.int32)
+        ne = np.ascontiguousarray(ne, dtype=np.int32)
+        cp = None
+        if corner is not None:
+            corner = np.ascontiguousarray(corner, dtype=np.uint8)
+            cp = _u(corner)
+        out = C.c_void_p()
+        _check(lib.pm_batch_create(_d(xy), _i(nv), _i(tri), _i(ne), nv.shape[0], cp, cap_factor,
+                                   device, C.byref(out)), "pm_batch_create")
+        return cls(out.value)
+
+    @classmethod
+    def from_device(cls, xy, nv, tri, ne, corner=None, cap_factor=2, stream=None):
+        """xy: (sum nv, 2) float64 CUDA tensor; tri: (sum ne, 3) int32 CUDA
+        tensor; nv, ne: host int arrays of per-mesh counts."""
+        nv = np.ascontiguousarray(nv, dtype=np.int32)
+        ne = np.ascontiguousarray(ne, dtype=np.int32)
+        out = C.c_void_p()
+        _check(lib.pm_batch_create_dev(C.c_void_p(xy.data_ptr()), _i(nv),
+                                       C.c_void_p(tri.data_ptr()), _i(ne), nv.shape[0],
+                                       C.c_void_p(corner.data_ptr()) if corner is not None
+                                       else None, cap_factor, C.c_void_p(stream), C.byref(out)),
+               "pm_batch_create_dev")
+        return cls(out.value)
+
+    def count(self):
+        n = np.zeros(1, np.int32)
+        _check(lib.pm_batch_size(self.h, _i(n)), "pm_batch_size")
+        return int(n[0])
+
+    def adapt(self, params):
+        """params: one Params for all meshes or a list (one per mesh)."""
+        n = self.count()
+        if not isinstance(params, (list, tuple)):
+            params = [params] * n
+        arr = (PmParams * n)(*[as_params(p) for p in params])
+        st = (PmStats * n)()
+        _check(lib.pm_batch_adapt(self.h, arr, st), "pm_batch_adapt")
+        return [x.as_dict() for x in st]
+
+    def sizes(self):
+        n = self.count()
+        nv = np.zeros(n, np.int32)
+        ne = np.zeros(n, np.int32)
+        _check(lib.pm_batch_get_mesh(self.h, _i(nv), _i(ne), None, None, None),
+               "pm_batch_get_mesh")
+        return nv, ne
+
+    def get_meshes(self, out=None):
+        """Compacted meshes as a list of (xy, tri, m) host arrays (views of one
+        concatenation; `out` = (xy, tri, m) preallocated C-contiguous arrays
+        with enough rows, for example page-locked views)."""
+        nv, ne = self.sizes()
+        tv, te = int(nv.sum()), int(ne.sum())
+        if out is None:
+            xy, tri, m = np.empty((tv, 2)), np.empty((te, 3), np.int32), np.empty((tv, 3))
+        else:
+            bxy, btri, bm = out
+            for arr, rows, cols, dt in ((bxy, tv, 2, np.float64), (btri, te, 3, np.int32),
+                                        (bm, tv, 3, np.float64)):
+                if (arr.dtype != dt or arr.ndim != 2 or arr.shape[1] != cols
+                        or arr.shape[0] < rows or not arr.flags.c_contiguous):
+                    raise ValueError(f"output array needs shape (>={rows}, {cols}), dtype {dt}, "
+                                     "C order")
+            xy, tri, m = bxy[:tv], btri[:te], bm[:tv]
+        a = np.zeros_like(nv)
+        b = np.zeros_like(ne)
+        _check(lib.pm_batch_get_mesh(self.h, _i(a), _i(b), _d(xy), _i(tri), _d(m)),
+               "pm_batch_get_mesh")
+        ov = np.concatenate([[0], np.cumsum(a)])
+        oe = np.concatenate([[0], np.cumsum(b)])
+        return [(xy[ov[i]:ov[i + 1]], tri[oe[i]:oe[i + 1]], m[ov[i]:ov[i + 1]])
+                for i in range(a.shape[0])]
+
+    def get_mesh_dev(self, xy, tri, m):
+        """Compacted meshes into preallocated CUDA tensors (concatenated);
+        returns the per-mesh counts (nv, ne) as numpy arrays."""
+        n = self.count()
+        a = np.zeros(n, np.int32)
+        b = np.zeros(n, np.int32)
+        _check(lib.pm_batch_get_mesh_dev(self.h, _i(a), _i(b),
+                                         C.c_void_p(xy.data_ptr()) if xy is not None else None,
+                                         C.c_void_p(tri.data_ptr()) if tri is not None else None,
+                                         C.c_void_p(m.data_ptr()) if m is not None else None),
+               "pm_batch_get_mesh_dev")
+        return a, b
+
+
 def adapt_batch(meshes, params):
     """pm_adapt_batch over a list of Mesh objects; params: one or one per mesh."""
     n = len(meshes)
@@ -344,7 +459,8 @@ def adapt_batch(meshes, params):
 
 
 def quality_arrays_dev(xy, m, tri, qsum, dxy=None, dm=None, stream=0):
-    """pm_quality_arrays_dev on CUDA tensors (stream-ordered, no sync)."""
+    """pm_quality_arrays_dev on CUDA tensors (runs on `stream` and waits for it;
+    raises PmError on a device-detected error, the outputs then hold NaN)."""
     _check(lib.pm_quality_arrays_dev(C.c_void_p(xy.data_ptr()), C.c_void_p(m.data_ptr()),
                                      xy.shape[0], C.c_void_p(tri.data_ptr()), tri.shape[0],
                                      C.c_void_p(qsum.data_ptr()),

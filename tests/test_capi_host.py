@@ -70,3 +70,24 @@ def test_out_of_range_ids_rejected_on_host(pm):
 def test_struct_layouts_match_header(pm):
     assert C.sizeof(pm.PmParams) == 3 * 8 + 5 * 4 + 4  # padded to 8
     assert C.sizeof(pm.PmStats) == 5 * 8 + 8 + 8
+
+
+def test_batch_arguments_checked_on_host(pm):
+    import numpy as np
+
+    out = C.c_void_p()
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    nv = np.array([3, 3], np.int32)
+    ne = np.array([1, 1], np.int32)
+    good = np.array([[0, 1, 2], [0, 1, 2]], np.int32)
+    bad = np.array([[0, 1, 2], [0, 1, 3]], np.int32)  # id 3 is outside the second mesh
+    f = pm.lib.pm_batch_create
+    assert f(pm._d(xy), pm._i(nv), pm._i(bad), pm._i(ne), 2, None, 1, 0, C.byref(out)) == 2
+    assert f(pm._d(xy), pm._i(nv), pm._i(good), pm._i(ne), 0, None, 1, 0, C.byref(out)) == 1
+    nv1 = np.array([3, 2], np.int32)
+    assert f(pm._d(xy), pm._i(nv1), pm._i(good), pm._i(ne), 2, None, 1, 0, C.byref(out)) == 1
+    assert f(None, pm._i(nv), pm._i(good), pm._i(ne), 2, None, 1, 0, C.byref(out)) == 1
+    assert pm.lib.pm_batch_adapt(None, None, None) == 1
+    n = C.c_int32()
+    assert pm.lib.pm_batch_size(None, C.byref(n)) == 1
+    assert pm.lib.pm_batch_get_mesh(None, None, None, None, None, None) == 1

@@ -231,6 +231,85 @@ def test_batch_equals_single_runs():
             assert st[k] == so[k], (w.name, k, st[k], so[k])
 
 
+def _small_batch():
+    ws = [inputs.psi_workload(n, T, True, s) for n, T, s in ((9, 400, 31), (17, 3000, 32),
+                                                             (13, 1500, 33))]
+    ws.append(inputs.small_uniform())
+    ws += inputs.batch_workloads(count=6, seed=9, tmin=200, tmax=3000)
+    return ws
+
+
+def test_batch_handle_equals_oracle_mesh_by_mesh():
+    """One pm_batch_create handle for ten meshes (psi-Hessian, uniform and
+    constant anisotropic metrics, each with its own seed): pm_batch_adapt's
+    per-mesh results and counters are those of the oracle adapting each mesh
+    alone (Sec. 3.2: a round's set over the union of disjoint vertex graphs)."""
+    ws = _small_batch()
+    b = pm.Batch.from_host([(w.xy, w.tri) for w in ws], device=0)
+    assert b.count() == len(ws)
+    b.set_metric(np.concatenate([w.m for w in ws]))
+    stats = b.adapt([gp(w.params.seed) for w in ws])
+    got = b.get_meshes()
+    for w, g, st in zip(ws, got, stats):
+        o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+        so = o.adapt(op(w.params.seed))
+        assert_same_mesh(g, o.get_mesh(), w.name)
+        for k in STAT_KEYS:
+            assert st[k] == so[k], (w.name, k, st[k], so[k])
+    # one-mesh calls on a batch handle are refused
+    a, c = np.zeros(1, np.int32), np.zeros(1, np.int32)
+    assert pm.lib.pm_get_mesh(b.h, pm._i(a), pm._i(c), None, None, None) == 1
+
+
+def test_batch_handle_device_arrays():
+    """pm_batch_create_dev + pm_set_metric_dev + pm_batch_get_mesh_dev give the
+    host path's meshes; a second adaptation of the same handle continues from
+    the adapted meshes (the metric re-set in their new numbering)."""
+    torch = pytest.importorskip("torch")
+    ws = _small_batch()
+    dev = torch.device("cuda:0")
+    nv = np.array([w.xy.shape[0] for w in ws], np.int32)
+    ne = np.array([w.tri.shape[0] for w in ws], np.int32)
+    xy = torch.tensor(np.concatenate([w.xy for w in ws]), device=dev)
+    tri = torch.tensor(np.concatenate([w.tri for w in ws]), dtype=torch.int32, device=dev)
+    m = torch.tensor(np.concatenate([w.m for w in ws]), device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    b = pm.Batch.from_device(xy, nv, tri, ne, stream=stream)
+    b.set_metric_dev(m)
+    b.adapt([gp(w.params.seed) for w in ws])
+    cap = 200_000
+    oxy = torch.empty((cap, 2), dtype=torch.float64, device=dev)
+    otri = torch.empty((cap, 3), dtype=torch.int32, device=dev)
+    om = torch.empty((cap, 3), dtype=torch.float64, device=dev)
+    a, c = b.get_mesh_dev(oxy, otri, om)
+    torch.cuda.synchronize(dev)
+    ref = pm.Batch.from_host([(w.xy, w.tri) for w in ws])
+    ref.set_metric(np.concatenate([w.m for w in ws]))
+    ref.adapt([gp(w.params.seed) for w in ws])
+    host = ref.get_meshes()
+    va, vc = 0, 0
+    for i, (hxy, htri, hm) in enumerate(host):
+        assert (a[i], c[i]) == (hxy.shape[0], htri.shape[0])
+        g = (oxy[va:va + a[i]].cpu().numpy(), otri[vc:vc + c[i]].cpu().numpy(),
+             om[va:va + a[i]].cpu().numpy())
+        assert_same_mesh(g, (hxy, htri, hm), ws[i].name)
+        va += a[i]
+        vc += c[i]
+    # both continue with a coarser metric in the adapted numbering, against
+    # the oracle continuing in the same way
+    w0 = ws[1]
+    o = O.OracleMesh(w0.xy, w0.tri).set_metric(w0.m)
+    o.adapt(op(w0.params.seed))
+    ref.set_metric(np.concatenate([mm * 0.5 for _, _, mm in host]))
+    st = ref.adapt([gp(w.params.seed) for w in ws])
+    o.set_metric(o.get_mesh()[2] * 0.5)
+    so = o.adapt(op(w0.params.seed))
+    assert_same_mesh(ref.get_meshes()[1], o.get_mesh(), "re-adapted mesh 1")
+    for k in STAT_KEYS:
+        assert st[1][k] == so[k], (k, st[1][k], so[k])
+    assert so["collapses"] > 0
+
+
 def test_bounded_barrier_wait_times_out_and_device_stays_usable():
     """A grid barrier that no arrival completes gives up after its limit and
     reports PM_ERR_TIMEOUT (6) through the status word; the next call works."""
