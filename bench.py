@@ -1,17 +1,29 @@
-"""Benchmark: adapted elements/s of the full 2D adaptation loop on GB300.
+"""Benchmark: adapted elements/s of the full 2D adaptation loop on GB300,
+batched against one mesh per launch.
 
-One step = one pass of the whole path on the psi-Hessian anisotropic
-workload (257 x 257 jittered grid, 131,072 triangles, metric scaled to about
-2M output triangles; the synthetic benchmark of Sec. 4 at t = 0):
-  mesh ingest + adjacency build (pm_mesh_create_dev), metric upload
-  (pm_set_metric_dev), Algorithm 1 with every operator round, smoothing and
-  renumbering (pm_adapt), compacted output (pm_get_mesh_dev).
-Inputs are resident in HBM when a step's timer starts; the L2 is flushed
-(256 MiB write) between steps, outside the timed region.  value = output
-triangles of all steps of all ranks / max over ranks of the summed step time.
+Default workload (the metric's own): 512 independent unit-square meshes,
+initial sizes log-uniform in 1k..200k triangles (19.1M in all), each with its
+own seeded constant anisotropic metric (rotation U[0, pi), aspect
+log-U[1, 100], size log-U[0.002, 0.05]).  One step adapts all 512:
+  pm_batch_create_dev (ingest + adjacency of every mesh in one store),
+  pm_set_metric_dev, pm_batch_adapt (Algorithm 1 with every operator round of
+  every mesh in the same launches, smoothing, renumbering),
+  pm_batch_get_mesh_dev (compacted output of every mesh).
+Inputs are resident in HBM when a step's timer starts (CUDA events on the
+library's stream); the L2 is flushed (256 MiB write) between steps, outside
+the timed region.  value = output triangles of all steps of all ranks / max
+over ranks of the summed step time.  Beside it: the same 512 meshes adapted
+one mesh per launch sequence (pm_mesh_create_dev, pm_set_metric_dev,
+pm_adapt, pm_get_mesh_dev per mesh), and e2e through the host-pointer calls
+with pinned buffers.
 
---impl reference times the CPU oracle (sequential C++, one core) on a bounded
-sample of the same workload family; see the `cpu_baseline` key.
+Other workloads (--workload): psi2m / psi20m / paper550k (one psi-Hessian
+mesh, Sec. 4's synthetic benchmark at t = 0), grad (quality forward and
+backward, optimisation smoothing), psi_t (time-dependent psi).
+
+--impl reference times the CPU oracle (sequential C++) on the same workload,
+one oracle process per host core, each step a size-stratified quarter of the
+meshes; see the `cpu_baseline` key.
 """
 import argparse
 import json
@@ -27,6 +39,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Adapted elements/s, full 2D adapt loop, 1 GB300; batched vs one-mesh-per-launch"
 WORKLOAD = "psi-Hessian anisotropic adaptation, 257x257 jittered grid (131,072 triangles) -> ~2.1M triangles"
+BATCH_WORKLOAD = ("batch of 512 unit-square meshes, initial sizes log-uniform 1k-200k triangles "
+                  "(19.1M), constant anisotropic metrics (theta U[0,pi), aspect log-U[1,100], "
+                  "h log-U[0.002,0.05]), seed 5")
 # bounded CPU sample of the same workload family (about 10-20 s of oracle work)
 SAMPLE = dict(n=181, target=1.0e6, seed=2)
 
@@ -38,14 +53,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-steps", type=int, default=2,
+                    help="timed steps of the one-mesh-per-launch comparison (batch workload)")
     ap.add_argument("--roofline-kernel", default=None)
     ap.add_argument("--kernel-only", action="store_true",
                     help="device-resident steps only (no e2e pass, no CPU baseline)")
-    ap.add_argument("--workload", default="psi2m",
+    ap.add_argument("--workload", default="batch",
                     choices=["psi2m", "psi20m", "paper550k", "batch", "grad", "psi_t"],
-                    help="psi2m (default, the headline line); psi20m / paper550k: other "
-                         "single-mesh sizes; batch: 512 meshes batched vs one mesh per "
-                         "launch; grad: quality forward+backward and optimisation smoothing; "
+                    help="batch (default, the headline line: 512 meshes batched vs one mesh "
+                         "per launch); psi2m / psi20m / paper550k: one psi-Hessian mesh; "
+                         "grad: quality forward+backward and optimisation smoothing; "
                          "psi_t: time-dependent psi, each step re-adapts the last mesh")
     return ap.parse_args()
 
@@ -185,90 +202,285 @@ def timed(fn, dev):
     return r, time.perf_counter() - t
 
 
+# ---- CPU oracle over the batch (a pool of spawned processes, one per core) ----
+
+_WS = None
+
+
+def _oracle_batch_mesh(i):
+    """Adapt batch mesh i with the oracle; (i, output triangles, seconds)."""
+    global _WS
+    from oracle import oracle as O
+    from paper_1505_04694_gb300 import inputs
+
+    if _WS is None:
+        _WS = inputs.batch_workloads()
+    w = _WS[i]
+    o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    t = time.perf_counter()
+    o.adapt(O.make_params(seed=w.params.seed))
+    dt = time.perf_counter() - t
+    return i, int(o.get_mesh()[1].shape[0]), dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_pool(procs):
+    """A pool of spawned oracle workers, warmed (inputs built, oracle loaded)."""
+    import multiprocessing as mp
+
+    pool = mp.get_context("spawn").Pool(procs)
+    pool.map(_oracle_batch_mesh, [int(i) for i in small_meshes(procs)], chunksize=1)
+    return pool
+
+
+def small_meshes(k):
+    from paper_1505_04694_gb300 import inputs
+
+    sizes = [w.tri.shape[0] for w in inputs.batch_workloads()]
+    return sorted(range(len(sizes)), key=lambda i: sizes[i])[:k]
+
+
+def oracle_batch(pool, idx):
+    """Adapt meshes idx over the pool (largest first); (triangles, wall s)."""
+    from paper_1505_04694_gb300 import inputs
+
+    sizes = {i: w.tri.shape[0] for i, w in enumerate(inputs.batch_workloads())}
+    order = sorted(idx, key=lambda i: -sizes[i])
+    t = time.perf_counter()
+    res = pool.map(_oracle_batch_mesh, order, chunksize=1)
+    return sum(r[1] for r in res), time.perf_counter() - t
+
+
+def stratified(k, parts, idx=None):
+    """Part k (of `parts`) of the batch meshes `idx`, stratified by initial size."""
+    from paper_1505_04694_gb300 import inputs
+
+    ws = inputs.batch_workloads()
+    idx = list(range(len(ws))) if idx is None else list(idx)
+    order = sorted(idx, key=lambda i: ws[i].tri.shape[0])
+    return [i for r, i in enumerate(order) if r % parts == k % parts]
+
+
 def run_batch(args, rank, world, local):
-    """512 independent meshes: one pm_adapt_batch (every round one launch per
-    kernel over all meshes) against 512 pm_adapt calls, same GPU, same inputs.
-    Meshes are created from device-resident inputs inside each timed step;
-    over N ranks the meshes are split by size with no collective."""
+    """The 512-mesh batch: one pm_batch_* sequence per step (every round of
+    every operator over all meshes at once) against the same meshes one
+    mesh per launch sequence, same GPU, same inputs.  Over N ranks the
+    meshes are split by size with no collective in the data path."""
+    import numpy as np
     import torch
 
     from paper_1505_04694_gb300 import inputs, pm, shard
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
     ws = inputs.batch_workloads()
     parts = shard.partition([w.tri.shape[0] for w in ws], world)
-    mine = [ws[i] for i in parts[rank]]
-    dev_in = [(torch.tensor(w.xy, device=dev), torch.tensor(w.tri, dtype=torch.int32, device=dev),
-               torch.tensor(w.m, device=dev)) for w in mine]
+    mine_idx = parts[rank]
+    mine = [ws[i] for i in mine_idx]
+    nv = np.array([w.xy.shape[0] for w in mine], np.int32)
+    ne = np.array([w.tri.shape[0] for w in mine], np.int32)
+    ov = np.concatenate([[0], np.cumsum(nv)])
+    oe = np.concatenate([[0], np.cumsum(ne)])
+    h_xy = np.ascontiguousarray(np.concatenate([w.xy for w in mine]))
+    h_tri = np.ascontiguousarray(np.concatenate([w.tri for w in mine]).astype(np.int32))
+    h_m = np.ascontiguousarray(np.concatenate([w.m for w in mine]))
+    xy_d = torch.tensor(h_xy, device=dev)
+    tri_d = torch.tensor(h_tri, device=dev)
+    m_d = torch.tensor(h_m, device=dev)
     params = [pm.Params(seed=w.params.seed) for w in mine]
-    sp = torch.cuda.current_stream(dev).cuda_stream
+    cap = 40_000_000
+    oxy = torch.empty((cap, 2), dtype=torch.float64, device=dev)
+    otri = torch.empty((cap, 3), dtype=torch.int32, device=dev)
+    om_ = torch.empty((cap, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = oracle_pool(host_cores())  # spawned before any GPU work of this process
 
-    def make():
-        ms = []
-        for (xy, tri, m) in dev_in:
-            g = pm.Mesh.from_device(xy, tri, cap_factor=2, stream=sp)
-            g.set_metric_dev(m)
-            ms.append(g)
-        return ms
+    def step():
+        b = pm.Batch.from_device(xy_d, nv, tri_d, ne, stream=sp)
+        b.set_metric_dev(m_d)
+        b.adapt(params)
+        _, c = b.get_mesh_dev(oxy, otri, om_)
+        b.close()
+        return int(c.sum())
 
-    def finish(ms):
-        n = sum(g.sizes()[1] for g in ms)
-        for g in ms:
+    def step_single():
+        n = 0
+        for i in range(len(mine)):
+            g = pm.Mesh.from_device(xy_d[ov[i]:ov[i + 1]], tri_d[oe[i]:oe[i + 1]], stream=sp)
+            g.set_metric_dev(m_d[ov[i]:ov[i + 1]])
+            g.adapt(params[i])
+            n += g.get_mesh_dev(oxy, otri, om_)[1]
             g.close()
         return n
 
-    def run(batched):
-        ms, t_make = timed(make, dev)
-        if batched:
-            _, t_adapt = timed(lambda: pm.adapt_batch(ms, params), dev)
-        else:
-            _, t_adapt = timed(lambda: [g.adapt(p) for g, p in zip(ms, params)], dev)
-        n, t_out = timed(lambda: finish(ms), dev)
-        return n, t_make, t_adapt, t_out
+    def timed_steps(fn, k):
+        ms, tris = 0.0, 0
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tris += fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        return tris, ms
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
 
     for _ in range(args.warmup):
-        run(True)
-        run(False)
-    acc = {True: [0, 0.0, 0.0, 0.0], False: [0, 0.0, 0.0, 0.0]}
-    for _ in range(args.steps):
-        for b in (True, False):
-            r = run(b)
-            for k in range(4):
-                acc[b][k] += r[k]
-    vals = []
-    for b in (True, False):
-        n, tm, ta, to = acc[b]
-        vals += [float(n), tm + ta + to, ta]
+        step()
+    barrier()
+    kname, cand_ms, fp64_meas = choose_roofline_kernel(args, step, flush, pm)
+    barrier()
+    pm.profile_enable(kname)
+    launches0 = pm.kernel_launches()
+    with ClockSampler(local) as clk:
+        tris, total_ms = timed_steps(step, args.steps)
+    barrier()
+    launches = pm.kernel_launches() - launches0
+    kms, klaunch, kwork = pm.profile_read()
+    pm.profile_enable(None)
+    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    n_local = torch.tensor([float(tris)], dtype=torch.float64, device=dev)
+    # one mesh per launch sequence, the same meshes (fewer timed steps: each
+    # takes seconds)
+    step_single()
+    s_tris, s_ms = timed_steps(step_single, max(1, args.single_steps))
+    s_local = torch.tensor([s_ms, float(s_tris)], dtype=torch.float64, device=dev)
     if world > 1:
         import torch.distributed as dist
 
-        v = torch.tensor(vals, dtype=torch.float64, device=dev)
-        cnt = torch.tensor([vals[0], vals[3]], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-        vals = v.tolist()
-        vals[0], vals[3] = cnt.tolist()
-    nb, tb, tab, ns, ts, tas = vals
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n_local, op=dist.ReduceOp.SUM)
+        tmax = s_local[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(s_local, op=dist.ReduceOp.SUM)
+        s_local[0] = tmax[0]
+    t_max = float(t_local.item())
+    value = float(n_local.item()) / (t_max / 1e3)
+    single_value = float(s_local[1].item()) / (float(s_local[0].item()) / 1e3)
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "elements/s",
+                              "ms_per_step": t_max / args.steps, "gpu_launches": launches,
+                              "one_mesh_per_launch": single_value}))
+        return
+    # end to end through the host-pointer calls, inputs and outputs pinned
+    pin = [torch.from_numpy(a).pin_memory() for a in (h_xy, h_tri, h_m)]
+    p_xy, p_tri, p_m = (t.numpy() for t in pin)
+    out_h = (torch.empty((cap, 2), dtype=torch.float64).pin_memory().numpy(),
+             torch.empty((cap, 3), dtype=torch.int32).pin_memory().numpy(),
+             torch.empty((cap, 3), dtype=torch.float64).pin_memory().numpy())
+    e2e_s, e2e_tris, d2h = 0.0, 0, 0
+    for i in range(1 + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        b = pm.Batch.from_arrays(p_xy, nv, p_tri, ne, device=local)
+        b.set_metric(p_m)
+        b.adapt(params)
+        got = b.get_meshes(out=out_h)
+        b.close()
+        dt = time.perf_counter() - t
+        if i >= 1:
+            e2e_s += dt
+            e2e_tris += sum(g[1].shape[0] for g in got)
+            d2h = sum(g[0].nbytes + g[1].nbytes + g[2].nbytes for g in got)
+    h2d = p_xy.nbytes + p_tri.nbytes + p_m.nbytes
+    peaks, how = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "meshes": len(ws),
+                   "output_triangles_per_step": tris // max(args.steps, 1),
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": f"meshes split over {world} GPUs by size" if world > 1
+                   else "single GPU"},
+        "one_mesh_per_launch": {
+            "value": single_value, "unit": "elements/s",
+            "ms_per_step": float(s_local[0].item()) / max(1, args.single_steps),
+            "steps": max(1, args.single_steps),
+            "batched_speedup": value / single_value,
+            "how": "per mesh: pm_mesh_create_dev, pm_set_metric_dev, pm_adapt, "
+                   "pm_get_mesh_dev; CUDA events around all 512"},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_tris / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "how": "pm_batch_create + pm_set_metric + pm_batch_adapt + pm_batch_get_mesh, "
+                       "inputs and outputs in pinned host buffers, wall clock per step"},
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / max(args.steps, 1),
+        "roofline": dict(roofline(kname, kms, klaunch, kwork, total_ms, peaks, how, fp64_meas,
+                                  False),
+                         chosen_from={k: round(v, 4) for k, v in cand_ms.items()},
+                         chosen_by="largest event time in one untimed step (ms)"),
+    }
+    if pool is not None:
+        ncore = host_cores()
+        model = cpu_model()
+        allm = list(range(len(ws)))
+        ot, osec = oracle_batch(pool, allm)
+        pool.close()
+        one = stratified(0, 16)
+        pool1 = oracle_pool(1)
+        ot1, osec1 = oracle_batch(pool1, one)
+        pool1.close()
+        line["cpu_baseline"] = {
+            "value": ot / osec, "unit": "elements/s", "cores": ncore, "kind": "oracle",
+            "sample": f"all {len(allm)} meshes of the batch, one spawned oracle process per host "
+                      f"core ({ncore} x {model}), largest meshes first; oracle = sequential "
+                      f"C++ -O3 -ffp-contract=off; value = output triangles / wall time",
+            "seconds": osec}
+        line["cpu_baseline_1core"] = {
+            "value": ot1 / osec1, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(one)} of the {len(allm)} meshes (every 16th by initial size) on one "
+                      f"core ({model}), sequential", "seconds": osec1}
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": nb / tb, "unit": "elements/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tb / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": f"batch of {len(ws)} unit-square meshes, log-uniform sizes "
-                                   "1k-200k triangles, constant anisotropic metrics",
-                       "output_triangles_per_step": nb / args.steps,
-                       "timing": "wall clock with device synchronisation; a step creates every "
-                                 "mesh from device-resident inputs, adapts, reads the sizes"},
-            "one_mesh_per_launch": {"value": ns / ts, "unit": "elements/s",
-                                    "ms_per_step": 1e3 * ts / args.steps},
-            "adapt_phase": {"batched_elements_per_s": nb / tab,
-                            "one_mesh_per_launch_elements_per_s": ns / tas,
-                            "batched_ms": 1e3 * tab / args.steps,
-                            "one_mesh_per_launch_ms": 1e3 * tas / args.steps,
-                            "speedup": (nb / tab) / (ns / tas)},
-        }), flush=True)
+        print(json.dumps(line), flush=True)
+
+
+def choose_roofline_kernel(args, step, flush, pm):
+    """The dominant evaluation kernel of a step (most event time in one untimed
+    step each), and the measured FP64 peak."""
+    fp64_meas = None if args.kernel_only else pm.fp64_peak()
+    cand_ms = {}
+    for name in ([args.roofline_kernel] if args.roofline_kernel else ROOFLINE_CANDIDATES):
+        pm.profile_enable(name)
+        flush.zero_()
+        step()
+        cand_ms[name] = pm.profile_read()[0]
+    pm.profile_enable(None)
+    return max(cand_ms, key=cand_ms.get), cand_ms, fp64_meas
 
 
 def run_grad(args, rank, world, local):
@@ -440,7 +652,7 @@ def cpu_baseline_run(samples=1):
 
 
 def sample_desc():
-    return (f"oracle (sequential C++, -O2 -ffp-contract=off) full adapt loop on the same workload "
+    return (f"oracle (sequential C++, -O3 -ffp-contract=off) full adapt loop on the same workload "
             f"family at {SAMPLE['n']}x{SAMPLE['n']} jittered grid, target {SAMPLE['target']:.0e} "
             f"triangles; value = output triangles / wall time")
 
@@ -448,6 +660,41 @@ def sample_desc():
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.workload != "batch":
+        return run_reference_single(args)
+    ncore = host_cores()
+    model = cpu_model()
+    pool = oracle_pool(ncore)
+    for _ in range(args.warmup):
+        oracle_batch(pool, small_meshes(ncore))
+    tri, secs = 0, 0.0
+    for k in range(args.steps):
+        t, dt = oracle_batch(pool, stratified(k, 4))
+        tri += t
+        secs += dt
+    pool.close()
+    v = tri / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "meshes": 512,
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": "single GPU"},
+        "cpu_baseline": {"value": v, "unit": "elements/s", "cores": ncore, "kind": "oracle",
+                         "sample": f"step k adapts a size-stratified quarter of the 512 meshes "
+                                   f"(rank by initial size = k mod 4), one spawned oracle process "
+                                   f"per host core ({ncore} x {model}); warm-up steps adapt the "
+                                   f"{ncore} smallest meshes; oracle = sequential C++ -O3 "
+                                   f"-ffp-contract=off"},
+        "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_single(args):
     for _ in range(args.warmup):
         cpu_baseline_run(1)
     res = cpu_baseline_run(args.steps)
