@@ -320,6 +320,7 @@ enum OpKind { OP_COARSEN, OP_SWAP, OP_REFINE, OP_SMOOTH, OP_OPT, OP_ADAPT };
 // optional optimisation-based smoothing, renumber.
 pm_status adapt_set(MeshSet& m, const pm_params* P, int stride, CallStats& cs) {
   int n = m.nmesh;
+  if (int err = presize(m)) return (pm_status)err;
   int max_iter = 0;
   for (int i = 0; i < n; ++i) max_iter = std::max(max_iter, P[stride ? i : 0].max_iter);
   std::vector<int> active(n, 1);

@@ -117,6 +117,7 @@ cudaError_t upload_tab(MeshSet& m);
 void set_used(MeshSet& m);
 cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap, int W);
 int rebuild_adjacency(MeshSet& m, bool derive_flags, bool corners_given);
+int presize(MeshSet& m);
 int renumber(MeshSet& m, bool final);
 int compact_out(MeshSet& m, int mesh, double* xy, int32_t* tri, double* mt, int* nv_out,
                 int* ne_out);

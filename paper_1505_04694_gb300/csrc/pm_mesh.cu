@@ -7,6 +7,7 @@
 // list here; between rebuilds the operators keep them current through the
 // deferred-update commit (pm_ops.cu).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -49,26 +50,42 @@ void pinned_put(void* p) {
 // One device allocation per store, carved into 256-byte aligned arrays:
 // pools fragmented by many small blocks make each allocation slow, so a mesh
 // set asks for one block instead of one per array.
+// Only the arrays that are read before they are first written (stamps,
+// marks, counters, scan state) are cleared: clearing a whole store of many
+// gigabytes at every growth cost more than the growth itself.
 struct Carver {
-  std::vector<std::pair<void**, size_t>> req;
+  struct Req {
+    void** p;
+    size_t bytes;
+    bool zero;
+  };
+  std::vector<Req> req;
   template <class T>
-  void add(T** p, size_t count) {
+  void add(T** p, size_t count, bool zero = false) {
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    req.push_back({(void**)p, (bytes + 255) & ~size_t(255)});
+    req.push_back({(void**)p, (bytes + 255) & ~size_t(255), zero});
   }
   cudaError_t commit(MeshSet& m) {
     size_t total = 0;
-    for (auto& r : req) total += r.second;
+    for (auto& r : req) total += r.bytes;
     char* base = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&base, total, m.stream);
     if (e != cudaSuccess) return e;
     m.allocs.push_back(base);
-    size_t off = 0;
+    size_t off = 0, zoff = 0, zlen = 0;  // adjacent cleared arrays share one memset
     for (auto& r : req) {
-      *r.first = base + off;
-      off += r.second;
+      *r.p = base + off;
+      if (r.zero && zoff + zlen == off) {
+        zlen += r.bytes;
+      } else if (r.zero) {
+        if (zlen && (e = cudaMemsetAsync(base + zoff, 0, zlen, m.stream))) return e;
+        zoff = off;
+        zlen = r.bytes;
+      }
+      off += r.bytes;
     }
-    return cudaMemsetAsync(base, 0, total, m.stream);
+    if (zlen) e = cudaMemsetAsync(base + zoff, 0, zlen, m.stream);
+    return e;
   }
 };
 
@@ -454,6 +471,26 @@ __global__ void k_out_e(Store S, int mesh, const int* vscan, const int* escan, i
   }
 }
 
+// Element count each mesh's metric asks for, before the factor 4/sqrt(3):
+// the sum over live elements of area * mean sqrt(det M) of its vertices (the
+// number of unit equilateral metric triangles that tile the mesh).  Only
+// sizes storage, so the order of the atomic sums does not matter.
+__global__ void k_estimate(Store S, double* est) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
+    int mi;
+    if (!eslot_used(S, s, mi)) continue;
+    int4 e = S.EN[s];
+    if (!e.w) continue;
+    int vb = S.tab.vbase[mi];
+    VD a = load_vd(S, vb + e.x), b = load_vd(S, vb + e.y), c = load_vd(S, vb + e.z);
+    double area = 0.5 * fabs(orient3(a, b, c));
+    double sd = sqrt(fmax(a.m00 * a.m11 - a.m01 * a.m01, 0.0)) +
+                sqrt(fmax(b.m00 * b.m11 - b.m01 * b.m01, 0.0)) +
+                sqrt(fmax(c.m00 * c.m11 - c.m01 * c.m01, 0.0));
+    atomicAdd(est + mi, area * sd / 3.0);
+  }
+}
+
 // Output offsets of every mesh: exclusive prefix sums over the meshes of the
 // live counts tot[2i] (vertices) and tot[2i+1] (elements) into pre (vertex
 // offsets pre[0..n], element offsets pre[n+1..2n+1]).  One block: each
@@ -608,19 +645,20 @@ static void carve_store(Carver& cv, Store& S) {
   size_t V = S.vslots, E = S.eslots, W = S.W;
   cv.add(&S.xy, V);
   cv.add(&S.M, V);
-  cv.add(&S.vflag, V);
   cv.add(&S.EN, E);
   cv.add(&S.qK, E);
   cv.add(&S.NN, V * W);
-  cv.add(&S.NNlen, V);
   cv.add(&S.NE, V * W);
-  cv.add(&S.NElen, V);
-  cv.add(&S.touch, V);
-  cv.add(&S.ntouch, V);
-  cv.add(&S.evc, V);
-  cv.add(&S.evs, V);
-  cv.add(&S.evm, V);
-  cv.add(&S.evr, V);
+  // cleared: flags, row lengths and stamps
+  cv.add(&S.vflag, V, true);
+  cv.add(&S.NNlen, V, true);
+  cv.add(&S.NElen, V, true);
+  cv.add(&S.touch, V, true);
+  cv.add(&S.ntouch, V, true);
+  cv.add(&S.evc, V, true);
+  cv.add(&S.evs, V, true);
+  cv.add(&S.evm, V, true);
+  cv.add(&S.evr, V, true);
 }
 
 cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vector<int>& ecap,
@@ -655,7 +693,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
                                   sizeof(double4)) +
                      2 * ((size_t)n + 1) * sizeof(int) + 64;
   char* t = nullptr;
-  cv.add(&t, tab_bytes);
+  cv.add(&t, tab_bytes, true);
   Work& w = m.w;
   cv.add(&w.D[0], vs);
   cv.add(&w.D[1], vs);
@@ -668,11 +706,11 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   cv.add(&w.opK2, vs);
   cv.add(&w.mvxy, vs);
   cv.add(&w.mvM, vs);
-  cv.add(&w.dmark, vs);
-  cv.add(&w.amark, vs);
-  cv.add(&w.cmark, vs);
-  cv.add(&w.smark, vs);
-  cv.add(&w.pmark, vs);
+  cv.add(&w.dmark, vs, true);
+  cv.add(&w.amark, vs, true);
+  cv.add(&w.cmark, vs, true);
+  cv.add(&w.smark, vs, true);
+  cv.add(&w.pmark, vs, true);
   cv.add(&w.vcnt, vs + 1);
   cv.add(&w.vscan, vs + 1);
   cv.add(&w.vmask, vs);
@@ -688,12 +726,12 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   cv.add(&w.items2, vs);
   cv.add(&w.cand, (size_t)vs * W);
   cv.add(&w.ncand, vs);
-  cv.add(&w.counts, CN_NUM + 2 * n + 8);
+  cv.add(&w.counts, CN_NUM + 2 * n + 8, true);
   cv.add(&m.lidbuf, vs);
   cv.add(&m.voffbuf, n);
   int tiles = scan_tiles((int)std::max(vs, es) + 1);
-  cv.add(&m.scan.state, tiles);
-  cv.add(&m.scan.ticket, 1);
+  cv.add(&m.scan.state, tiles, true);
+  cv.add(&m.scan.ticket, 1, true);
   m.scan.tiles_cap = tiles;
   if ((e = cv.commit(m))) return e;
   m.tabmem = t;
@@ -1029,6 +1067,47 @@ int compact_out_set(MeshSet& m, double* xy, int32_t* tri, double* mt, int* nv_ou
   for (int i = 0; i < n; ++i) {
     nv_out[i] = m.hcounts[2 * i];
     ne_out[i] = m.hcounts[2 * i + 1];
+  }
+  return PM_OK;
+}
+
+// Capacity for the adaptation ahead, in one growth: while adapting, a mesh
+// holds at most about 2.2 times the larger of its element count and the
+// element count its metric asks for (refinement overshoots before the
+// collapses that follow), so every mesh below 2.5 times the estimate grows
+// now, together, instead of round after round of refinement.
+int presize(MeshSet& m) {
+  const int n = m.nmesh;
+  double* est = m.w.gains;  // scratch: no evaluation is kept across calls
+  cudaMemsetAsync(est, 0, n * sizeof(double), m.stream);
+  PM_LAUNCH(k_estimate, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, est);
+  std::vector<double> h(n);
+  cudaError_t e = cudaMemcpyAsync(h.data(), est, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                  m.stream);
+  if (!e) e = cudaStreamSynchronize(m.stream);
+  if (e) {
+    set_last_error(std::string("estimating sizes: ") + cudaGetErrorString(e));
+    return PM_ERR_CUDA;
+  }
+  std::vector<int> vcap = m.vcap, ecap = m.ecap;
+  bool need = false;
+  long long vt = 0, et = 0;
+  for (int i = 0; i < n; ++i) {
+    const double ne_est = 4.0 / std::sqrt(3.0) * h[i];
+    const double want_e = 2.5 * std::max(ne_est, (double)m.ne[i]);
+    if (std::isfinite(want_e) && want_e > ecap[i] && want_e < (double)(1 << 29)) {
+      ecap[i] = (int)want_e + 64;
+      vcap[i] = std::max(vcap[i], (int)(0.6 * want_e) + 64);
+      need = true;
+    }
+    vt += vcap[i];
+    et += ecap[i];
+  }
+  if (!need || vt >= (1LL << 31) - 4 || et >= (1LL << 31) - 4) return PM_OK;
+  e = grow(m, vcap, ecap, m.S.W);
+  if (e) {
+    set_last_error(std::string("growing mesh storage: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;
   }
   return PM_OK;
 }

@@ -886,28 +886,88 @@ __device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, c
   return gain;
 }
 
+// An edge both of whose end points are evaluated this round is listed from
+// both ends with the same two new elements: in canonical rotation their
+// qualities and orientations, hence the gain, are bitwise equal from either
+// side.  The end point with the smaller id evaluates it and writes the gain
+// into both vertices' slots (the other's slot of the same element pair is
+// found in its sorted element row); the other item does no arithmetic.
+//
+// A warp pays the FP64 issue cost of an instruction once whatever its active
+// lanes, so the items that need arithmetic are first collected in a per-warp
+// queue in shared memory and evaluated 32 at a time (full warps); only the
+// last batch of each warp may be partial.  At most 8 warps per block.
+constexpr int kEdgeQueueWarps = 8;
+
+__device__ __forceinline__ void flip_gain_item(const Store& S, int4 q, double* gains,
+                                               unsigned& ops) {
+  const int v = q.x, k1 = q.y & 0xFF, k2 = (q.y >> 8) & 0xFF, sw = q.w;
+  const bool both = (q.y >> 16) & 1;
+  MeshCtx c;
+  c.mi = q.z;
+  c.vb = S.tab.vbase[c.mi];
+  c.eb = S.tab.ebase[c.mi];
+  const int* ne = ne_row(S, v);
+  int cc, d;
+  const double g = flip_gain(S, c, v - c.vb, ne, k1, k2, &cc, &d, ops);
+  gains[(size_t)v * S.W + k1] = g;
+  if (both) {
+    // from w's side the pair is (K2, K1): w's slot of K2
+    const int K2 = ne[k2];
+    const int* nw = ne_row(S, sw);
+    const int nwl = S.NElen[sw];
+    int kk = 0;
+    while (kk < nwl && nw[kk] < K2) ++kk;
+    if (kk < nwl) gains[(size_t)sw * S.W + kk] = g;
+  }
+}
+
 __device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, const int* nIp,
-                                                double* gains, unsigned long long* work,
+                                                double* gains, int tag, unsigned long long* work,
                                                 bool il = false) {
+  __shared__ int4 sq[kEdgeQueueWarps][64];
   const int n = *nIp;
+  const int lane = threadIdx.x & 31;
+  int4* q = sq[(threadIdx.x >> 5) % kEdgeQueueWarps];
+  int qn = 0;  // the same in every lane of the warp
+  unsigned ops = 0;
   for (int i0 = 0; i0 < n; i0 += gsize()) {
-    int i = i0 + grank(il);
-    unsigned ops = 0;
+    const int i = i0 + grank(il);
+    bool need = false;
+    int4 rec = make_int4(0, 0, 0, 0);
     if (i < n) {
       int2 it = items[i];
       int v = it.x, k1 = it.y & 0xFF, k2 = it.y >> 8;
       MeshCtx c = ctx_of(S, v);
-      int cc, d;
-      gains[(size_t)v * S.W + k1] =
-          flip_gain(S, c, v - c.vb, ne_row(S, v), k1, k2, &cc, &d, ops);
+      const int lv = v - c.vb;
+      const int4 e = S.EN[c.eb + ne_row(S, v)[k1]];
+      const int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
+      const int sw = c.vb + w;
+      const bool both = S.evs[sw] == tag;
+      need = !both || lv < w;
+      rec = make_int4(v, k1 | (k2 << 8) | ((both ? 1 : 0) << 16), c.mi, sw);
     }
-    add_work(work, ops);
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (need) q[qn + __popc(m & ((1u << lane) - 1u))] = rec;
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      const int4 mine = q[lane];
+      __syncwarp();
+      if (lane < qn - 32) q[lane] = q[32 + lane];
+      qn -= 32;
+      __syncwarp();
+      flip_gain_item(S, mine, gains, ops);
+    }
   }
+  if (lane < qn) flip_gain_item(S, q[lane], gains, ops);
+  __syncwarp();
+  add_work(work, ops);
 }
 
-__global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* gains,
+__global__ void k_swap_edge(Store S, const int2* items, const int* nIp, double* gains, int tag,
                             unsigned long long* work) {
-  swap_edge_phase(S, items, nIp, gains, work);
+  swap_edge_phase(S, items, nIp, gains, tag, work);
 }
 
 // Pass 3 (per evaluated vertex): largest strictly positive gain, ties to the
@@ -2081,7 +2141,7 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
                       w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
-      swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains, a.work, true);
+      swap_edge_phase(a.S, w.items, cnt + CN_I, w.gains, tag, a.work, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
       swap_pick_phase(a.S, w.E, cnt + CN_E, w.gains, w.opA, w.opK2, w.C, nC, w.cmark, tag, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
@@ -2454,7 +2514,7 @@ int op_swap(MeshSet& m, int max_rounds) {
               w.C, w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E, w.items,
               w.counts + CN_I, icap, w.gains, m.st);
     PM_LAUNCH(k_swap_edge, grid_for(m, 6LL * m.S.vslots, 16), BLOCK, 0, m.stream, m.S, w.items,
-              w.counts + CN_I, w.gains, prof_work("k_swap_edge"));
+              w.counts + CN_I, w.gains, tag, prof_work("k_swap_edge"));
     PM_LAUNCH(k_swap_pick, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
               w.opK2, w.C, w.counts + CN_C, w.cmark, tag);
     zero_counts(m, CN_CL, 1);
