@@ -440,6 +440,7 @@ def run_batch(args, rank, world, local):
                        "inputs and outputs in pinned host buffers, wall clock per step"},
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / max(args.steps, 1),
+        "tuning": dict(pm.get_tuning(), source=pm.tuning_source()),
         "roofline": dict(roofline(kname, kms, klaunch, kwork, total_ms, peaks, how, fp64_meas,
                                   False),
                          chosen_from={k: round(v, 4) for k, v in cand_ms.items()},

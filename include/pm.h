@@ -296,6 +296,46 @@ pm_status pm_quality_arrays_noalloc_dev(const double* xy, const double* m, int32
                                         const int32_t* tri, int32_t ne, double* q_sum,
                                         double* dxy, double* dm, void* stream);
 
+/* Launch shapes (a service of this library; the paper's counterpart is its
+ * load balancing, Sec. 3.5).  Process-wide; no choice changes any result.
+ *   block[4], blocks_per_sm[4]: per operator (collapse, flip, split,
+ *     smoothing), threads per block (64, 128 or 256) and the cap on blocks
+ *     per SM (1..32) of the one-kernel-per-phase round kernels: together they
+ *     set the worklist chunk each thread walks.
+ *   rounds_limit[3]: per operator (collapse, flip, smoothing), the largest
+ *     list (vertices) whose rounds run inside one persistent launch (0: never;
+ *     at most 2^30).
+ * Defaults: 128 threads, 16 blocks per SM, 131072. */
+typedef struct {
+  int32_t block[4];
+  int32_t blocks_per_sm[4];
+  int32_t rounds_limit[3];
+} pm_tuning;
+
+/* Set the launch shapes (null: the defaults).  PM_ERR_INVALID_ARG for a value
+ * out of range (nothing changes then).  Takes effect at the next operator
+ * call; an explicit setting is never replaced by a tuning cache. */
+pm_status pm_set_tuning(const pm_tuning* t);
+pm_status pm_get_tuning(pm_tuning* t);
+
+/* Load the entry of a tuning cache (JSON written by the package's autotuner)
+ * for GPU model `gpu_name` (null: the current device's name) and this
+ * library build (pm_build_id).  PM_OK when an entry was applied;
+ * PM_ERR_INVALID_ARG when the file is missing or holds no valid entry for
+ * them (the current shapes stay).  Without any call, the first mesh created
+ * in the process applies the first of these caches that holds an entry for
+ * its GPU and build: the file named by the environment variable
+ * PM_TUNING_CACHE, tuning.json beside the library, tuning.json in the
+ * directory above the library's. */
+pm_status pm_tuning_load(const char* path, const char* gpu_name);
+
+/* Where the current shapes come from: "default", "set" or "cache <path>". */
+const char* pm_tuning_source(void);
+
+/* Identity of this library build (a hash of its sources and flags), the key
+ * of tuning cache entries. */
+const char* pm_build_id(void);
+
 const char* pm_status_string(pm_status s);
 
 /* Message of the last error on the calling thread ("" if none). */

@@ -6,6 +6,7 @@ the library must not contract a*b+c so that it matches its definition
 operation for operation.
 """
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -15,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpm.so")
-SOURCES = ["pm_scan.cu", "pm_mesh.cu", "pm_ops.cu", "pm_quality.cu", "pm_capi.cu", "pm_prof.cu", "pm_noalloc.cu"]
+SOURCES = ["pm_scan.cu", "pm_mesh.cu", "pm_ops.cu", "pm_quality.cu", "pm_capi.cu", "pm_prof.cu",
+           "pm_noalloc.cu", "pm_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr",
@@ -36,18 +38,38 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_id(extra=()) -> str:
+    """Hash of every source, header and flag of the library: the key of its
+    tuning cache entries."""
+    h = hashlib.sha256()
+    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "pm.h"), "rb") as fh:
+        h.update(fh.read())
+    h.update(" ".join(ARCH + FLAGS + list(extra)).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(ROOT, "include", "pm.h"))
+    bid = build_id(extra)
+    stamp = os.path.join(OUT_DIR, "build_id")
+    old_id = open(stamp).read().strip() if os.path.exists(stamp) else ""
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         objs.append(o)
-        if force or _stale(o, [s] + headers):
-            jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
+        tune = src == "pm_tune.cu"
+        if force or _stale(o, [s] + headers) or (tune and old_id != bid):
+            defs = [f'-DPM_BUILD_ID="{bid}"'] if tune else []
+            jobs.append([nvcc(), *ARCH, *FLAGS, *extra, *defs, "-c", s, "-o", o])
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         res = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
     for c, r in zip(jobs, res):
@@ -63,6 +85,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if r.returncode:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
         os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(bid + "\n")
     return LIB
 
 

@@ -147,6 +147,7 @@ cudaError_t upload_prefix(MeshSet& m, const std::vector<int>& nv, const std::vec
 pm_status create_set(const double* xy, const int32_t* nv, const int32_t* tri, const int32_t* ne,
                      int nmesh, const uint8_t* corner, int cap_factor, int dev,
                      cudaStream_t stream, bool own_stream, bool host, pm_mesh** out) {
+  tuning_autoload();
   pm_mesh* h = new pm_mesh();
   MeshSet& m = h->set;
   m.device = dev;

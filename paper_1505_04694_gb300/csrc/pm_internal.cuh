@@ -167,6 +167,28 @@ inline void launch(const char* name, K kern, dim3 g, dim3 b, size_t sh, cudaStre
 
 #define PM_LAUNCH(k, g, b, sh, s, ...) ::pm::launch(#k, k, g, b, sh, s, __VA_ARGS__)
 
+// ---- launch shapes (pm_tune.cu) ----
+// Per operator (collapse, flip, split, smoothing): threads per block and the
+// cap on blocks per SM of the one-kernel-per-phase grids; per operator
+// (collapse, flip, smoothing): the largest list whose rounds run in one
+// persistent launch.  No choice changes a result.
+enum TuneOp { TO_COARSEN = 0, TO_SWAP = 1, TO_REFINE = 2, TO_SMOOTH = 3 };
+struct Tuning {
+  int block[4];
+  int blocks_per_sm[4];
+  int rounds_limit[3];
+};
+Tuning tuning();
+void tuning_autoload();
+
+// Blocks of `block` threads for n items, at most per_sm blocks per SM.
+inline int grid_tuned(const MeshSet& m, long long n, int block, int per_sm) {
+  long long want = (n + block - 1) / block;
+  long long cap = (long long)m.num_sms * per_sm;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
 inline int grid_for(const MeshSet& m, long long n, int per_sm = 16) {
   long long want = (n + BLOCK - 1) / BLOCK;
   long long cap = (long long)m.num_sms * per_sm;

@@ -237,6 +237,57 @@ __device__ __forceinline__ void round_done(const Store& S, unsigned* done) {
   if (threadIdx.x == 0) *done = 0;
 }
 
+// ---- tile-parallel evaluation: 8 lanes per vertex, one ball element each ----
+// Sums keep the ascending order of the definition (every lane accumulates the
+// lanes' terms in order through shuffles); minima and all-of votes do not
+// depend on order.  All lanes of a tile end with the same result.
+
+constexpr int TW = 8;
+
+struct Tile {
+  int tl;          // lane within the tile
+  unsigned mask;   // the tile's lanes in the warp
+  int shift;       // bit offset of the tile in a warp ballot
+};
+
+__device__ __forceinline__ Tile tile_of() {
+  int lane = threadIdx.x & 31;
+  Tile t;
+  t.tl = lane & (TW - 1);
+  t.shift = lane & ~(TW - 1);
+  t.mask = 0xFFu << t.shift;
+  return t;
+}
+
+__device__ __forceinline__ double tshfl(const Tile& t, double x, int src) {
+  return __shfl_sync(t.mask, x, src, TW);
+}
+
+__device__ __forceinline__ double tmin(const Tile& t, double x) {
+#pragma unroll
+  for (int o = TW / 2; o > 0; o >>= 1) {
+    double y = __shfl_xor_sync(t.mask, x, o, TW);
+    x = dlt(y, x) ? y : x;
+  }
+  return x;
+}
+
+__device__ __forceinline__ bool tall(const Tile& t, bool p) {
+  return ((__ballot_sync(t.mask, !p) >> t.shift) & 0xFFu) == 0u;
+}
+
+__device__ __forceinline__ int tsum(const Tile& t, int x) {
+  return __reduce_add_sync(t.mask, x);
+}
+
+// Position of tile `tid` and the number of tiles of the grid.  Interleaved
+// (`il`): tile i to block i mod gridDim.x (see grank).
+__device__ __forceinline__ int trank(bool il) {
+  const int tpb = blockDim.x / TW, tib = threadIdx.x / TW;
+  return il ? tib * gridDim.x + blockIdx.x : blockIdx.x * tpb + tib;
+}
+__device__ __forceinline__ int tcount() { return gridDim.x * (blockDim.x / TW); }
+
 // ---- coarsening (Sec. 2.4.1) ---------------------------------------------------
 
 struct CoarsenCtx;
@@ -358,6 +409,109 @@ __device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out, un
   return nc;
 }
 
+// collapse_valid with the lanes of a tile splitting v's ball elements (the
+// element count of the edge and the orientations with v on u) and v's
+// neighbours (the link condition and the new edge lengths): the same
+// conjunction of the same tests.  Every lane returns the tile's answer.
+__device__ bool tile_collapse_valid(const Tile& t, const CoarsenCtx& x, int u, double4 band,
+                                    unsigned& ops) {
+  const double L_up = S_L_up(x);
+  const Store& S = *x.S;
+  int cnt = 0;
+  for (int k = t.tl; k < x.nel; k += TW) {
+    int4 e = S.EN[x.c.eb + x.ne[k]];
+    cnt += (e.x == u || e.y == u || e.z == u) ? 1 : 0;
+  }
+  const bool bedge = tsum(t, cnt) == 1;
+  if (x.bnd && !bedge) return false;
+  const int ws = x.c.vb + u;
+  const int* nnw = nn_row(S, ws);
+  const int nnwl = S.NNlen[ws];
+  int common = 0;
+  for (int k = t.tl; k < x.nnl; k += TW) common += row_has(nnw, nnwl, x.nn[k]) ? 1 : 0;
+  if (tsum(t, common) != (bedge ? 1 : 2)) return false;
+  const VD dw = load_vd(S, ws);
+  bool ok = true;
+  for (int k = t.tl; k < x.nel; k += TW) {
+    int4 e = S.EN[x.c.eb + x.ne[k]];
+    if (e.x == u || e.y == u || e.z == u) continue;
+    int i0 = e.x, i1 = e.y, i2 = e.z;
+    VD d0 = (i0 == x.lv) ? dw : load_vd(S, x.c.vb + i0);
+    VD d1 = (i1 == x.lv) ? dw : load_vd(S, x.c.vb + i1);
+    VD d2 = (i2 == x.lv) ? dw : load_vd(S, x.c.vb + i2);
+    if (i0 == x.lv) i0 = u;
+    if (i1 == x.lv) i1 = u;
+    if (i2 == x.lv) i2 = u;
+    ok &= dgt(orient_c(i0, i1, i2, d0, d1, d2), 0.0);
+    ops += kOpsOrient;
+  }
+  if (!tall(t, ok)) return false;
+  for (int k = t.tl; k < x.nnl; k += TW) {
+    int y = x.nn[k];
+    if (y == u || row_has(nnw, nnwl, y)) continue;
+    ok &= !len_gt(metric_len2(dw, load_vd(S, x.c.vb + y)), band.z, band.w, L_up);
+    ops += kOpsLen2;
+  }
+  return tall(t, ok);
+}
+
+// coarsen_candidates with the lanes of a tile splitting v's neighbours: lane
+// tl holds neighbours tl, tl + 8, ...; each candidate's place in the order by
+// (length, id) is the number of candidates before it (a neighbour of lower
+// index has the lower id: rows are sorted), which is the insertion order of
+// the definition.  Returns the candidate count (every lane).
+__device__ int tile_coarsen_candidates(const Tile& t, const Store& S, int v, MeshCtx c, int* out,
+                                       unsigned& ops) {
+  uint8_t f = S.vflag[v];
+  if (!(f & VF_ALIVE) || (f & VF_CORNER)) return 0;
+  const bool bnd = (f & VF_BND) != 0;
+  const int* nn = nn_row(S, v);
+  const int nnl = S.NNlen[v];
+  const int* ne = ne_row(S, v);
+  const int nel = S.NElen[v];
+  const VD dv = load_vd(S, v);
+  const double L_low = S.tab.L_low[c.mi];
+  const double4 band = S.tab.band[c.mi];
+  constexpr int kPer = MAXW / TW;
+  double L[kPer];
+  bool is[kPer];
+  int mine = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int k = j * TW + t.tl;
+    is[j] = false;
+    L[j] = 0.0;
+    if (k < nnl) {
+      const int u = nn[k];
+      const double L2 = metric_len2(dv, load_vd(S, c.vb + u));
+      ops += kOpsLen2;
+      bool cand = len_lt(L2, band.x, band.y, L_low);
+      if (cand && bnd) cand = count_elems_with(S, ne, nel, c.eb, u) == 1;
+      if (cand) {
+        L[j] = sqrt(L2);
+        ++ops;
+        is[j] = true;
+        ++mine;
+      }
+    }
+  }
+  const int steps = (nnl + TW - 1) / TW;
+  for (int j = 0; j < steps; ++j) {
+    int rank = 0;
+    for (int j2 = 0; j2 < steps; ++j2) {
+#pragma unroll
+      for (int src = 0; src < TW; ++src) {
+        const double Lo = tshfl(t, L[j2], src);
+        const bool co = __shfl_sync(t.mask, is[j2] ? 1 : 0, src, TW) != 0;
+        const int ko = j2 * TW + src, k = j * TW + t.tl;
+        if (co && (dlt(Lo, L[j]) || (dbits(Lo) == dbits(L[j]) && ko < k))) ++rank;
+      }
+    }
+    if (is[j]) out[rank] = nn[j * TW + t.tl];
+  }
+  return tsum(t, mine);
+}
+
 __device__ __forceinline__ CoarsenCtx coarsen_ctx(const Store& S, int v, MeshCtx c) {
   CoarsenCtx x;
   x.S = &S;
@@ -378,36 +532,43 @@ __device__ __forceinline__ CoarsenCtx coarsen_ctx(const Store& S, int v, MeshCtx
 // unchanged earlier result or lists v's sorted candidates; a dense pass then
 // checks every listed vertex's best candidate (one work item each), and a
 // last pass goes through the remaining candidates of the vertices whose best
-// one failed.
+// one failed.  Candidates are listed by an 8-lane tile per vertex (see
+// tile_coarsen_candidates), so the FP64 lengths of the neighbours run side
+// by side.  The tile takes the stamp decision from lane 0 before lane 0
+// overwrites the stamp.
 __device__ __forceinline__ void coarsen_scan_phase(Store S, const int* D, const int* nDp,
                                                    int* target, int* cand, int* ncand, int* C,
                                                    int* nC, int* cmark, int tag, int pass0,
                                                    int2* W0, int* nW0) {
+  const Tile t = tile_of();
   const int n = *nDp;
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += tcount()) {
+    const int i = i0 + trank(false);
     int v = 0;
     bool reuse_cand = false, emit = false;
     if (i < n) {
       v = D[i];
       MeshCtx c = ctx_of(S, v);
-      if (unchanged(S, v, c.vb, S.evc[v], pass0)) {
+      const int et = __shfl_sync(t.mask, S.evc[v], 0, TW);
+      if (unchanged(S, v, c.vb, et, pass0)) {
         reuse_cand = target[v] >= 0;
-        if (reuse_cand) {
+        if (reuse_cand && t.tl == 0) {
           cmark[v] = tag;
           S.tab.had[c.mi] = 1;
         }
       } else {
-        S.evc[v] = tag;
+        if (t.tl == 0) S.evc[v] = tag;
         unsigned ops = 0;
-        int nc = coarsen_candidates(S, v, c, cand + (size_t)v * S.W, ops);
-        ncand[v] = nc;
-        if (nc == 0) target[v] = -1;
+        int nc = tile_coarsen_candidates(t, S, v, c, cand + (size_t)v * S.W, ops);
+        if (t.tl == 0) {
+          ncand[v] = nc;
+          if (nc == 0) target[v] = -1;
+        }
         emit = nc > 0;
       }
     }
-    warp_append(reuse_cand, v, C, nC);
-    warp_append_t(emit, make_int2(v, 0), W0, nW0);
+    warp_append(reuse_cand && t.tl == 0, v, C, nC);
+    warp_append_t(emit && t.tl == 0, make_int2(v, 0), W0, nW0);
   }
 }
 
@@ -417,6 +578,8 @@ __global__ void k_coarsen_scan(Store S, const int* D, const int* nDp, int* targe
   coarsen_scan_phase(S, D, nDp, target, cand, ncand, C, nC, cmark, tag, pass0, W0, nW0);
 }
 
+// The check passes stay one thread per item: a check is a short chain of
+// dependent loads, and eight items per warp left too little in flight.
 __device__ __forceinline__ void coarsen_check_phase(Store S, const int2* Win, const int* nWin,
                                                     int2* Wout, int* nWout, int* target,
                                                     const int* cand, const int* ncand, int* C,
@@ -461,48 +624,51 @@ __global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2*
   coarsen_check_phase(S, Win, nWin, Wout, nWout, target, cand, ncand, C, nC, cmark, tag, last);
 }
 
-// One thread per listed vertex, listing and checking at once (persistent
+// One tile per listed vertex, listing and checking at once (persistent
 // rounds): reuse or re-evaluate, then the candidates in order until one is a
 // valid collapse.  Same results as coarsen_scan_phase and the two check passes.
 __device__ __forceinline__ void coarsen_eval_phase(Store S, const int* D, const int* nDp,
                                                    int* target, int* cand, int* ncand, int* C,
                                                    int* nC, int* cmark, int tag, int pass0,
                                                    unsigned long long* work, bool il = false) {
+  const Tile t = tile_of();
   const int n = *nDp;
-  for (int i0 = 0; i0 < n; i0 += gsize()) {
-    int i = i0 + grank(il);
+  unsigned ops = 0;
+  for (int i0 = 0; i0 < n; i0 += tcount()) {
+    const int i = i0 + trank(il);
     int v = 0;
     bool found = false;
-    unsigned ops = 0;
     if (i < n) {
       v = D[i];
       MeshCtx c = ctx_of(S, v);
-      if (unchanged(S, v, c.vb, S.evc[v], pass0)) {
+      const int et = __shfl_sync(t.mask, S.evc[v], 0, TW);
+      if (unchanged(S, v, c.vb, et, pass0)) {
         found = target[v] >= 0;
       } else {
-        S.evc[v] = tag;
+        if (t.tl == 0) S.evc[v] = tag;
         int* cv = cand + (size_t)v * S.W;
-        int nc = coarsen_candidates(S, v, c, cv, ops);
-        ncand[v] = nc;
+        int nc = tile_coarsen_candidates(t, S, v, c, cv, ops);
+        if (t.tl == 0) ncand[v] = nc;
+        __syncwarp(t.mask);  // the candidates written by every lane
         if (nc > 0) {
           CoarsenCtx x = coarsen_ctx(S, v, c);
           const double4 band = S.tab.band[c.mi];
           for (int k = 0; k < nc && !found; ++k)
-            if (collapse_valid(x, cv[k], band, ops)) {
+            if (tile_collapse_valid(t, x, cv[k], band, ops)) {
               found = true;
-              target[v] = cv[k];
+              if (t.tl == 0) target[v] = cv[k];
             }
         }
-        if (!found) target[v] = -1;
+        if (!found && t.tl == 0) target[v] = -1;
       }
-      if (found) {
+      if (found && t.tl == 0) {
         cmark[v] = tag;
         S.tab.had[c.mi] = 1;
       }
     }
-    warp_append(found, v, C, nC);
-    add_work(work, ops);
+    warp_append(found && t.tl == 0, v, C, nC);
   }
+  add_work(work, ops);
 }
 
 // Apply the collapses of S: elements containing edge (v, w) die, the other
@@ -1239,45 +1405,6 @@ __device__ __forceinline__ void smooth_scan_phase(Store S, const int* D, const i
 __global__ void k_smooth_scan(Store S, const int* D, const int* nDp, double4* mvM, int* C, int* nC,
                               int* cmark, int tag, int pass0, int* E, int* nE) {
   smooth_scan_phase(S, D, nDp, mvM, C, nC, cmark, tag, pass0, E, nE);
-}
-
-// ---- tile-parallel evaluation: 8 lanes per vertex, one ball element each ----
-// Sums keep the ascending order of the definition (every lane accumulates the
-// lanes' terms in order through shuffles); minima and all-of votes do not
-// depend on order.  All lanes of a tile end with the same result.
-
-constexpr int TW = 8;
-
-struct Tile {
-  int tl;          // lane within the tile
-  unsigned mask;   // the tile's lanes in the warp
-  int shift;       // bit offset of the tile in a warp ballot
-};
-
-__device__ __forceinline__ Tile tile_of() {
-  int lane = threadIdx.x & 31;
-  Tile t;
-  t.tl = lane & (TW - 1);
-  t.shift = lane & ~(TW - 1);
-  t.mask = 0xFFu << t.shift;
-  return t;
-}
-
-__device__ __forceinline__ double tshfl(const Tile& t, double x, int src) {
-  return __shfl_sync(t.mask, x, src, TW);
-}
-
-__device__ __forceinline__ double tmin(const Tile& t, double x) {
-#pragma unroll
-  for (int o = TW / 2; o > 0; o >>= 1) {
-    double y = __shfl_xor_sync(t.mask, x, o, TW);
-    x = dlt(y, x) ? y : x;
-  }
-  return x;
-}
-
-__device__ __forceinline__ bool tall(const Tile& t, bool p) {
-  return ((__ballot_sync(t.mask, !p) >> t.shift) & 0xFFu) == 0u;
 }
 
 // Minimum cached quality of v's ball (and, if asked, its sum in ascending
@@ -2298,11 +2425,10 @@ int after_round(MeshSet& m, const RoundIO& io) {
   return PM_OK;
 }
 
-// Persistent rounds take over once a pass's list holds at most this many
-// vertices (and hand back when the next list outgrows it).
-constexpr int kRoundsLimit = 131072;        // collapse passes
-constexpr int kSwapRoundsLimit = 131072;    // flip passes (each vertex lists about six edges)
-constexpr int kSmoothRoundsLimit = 131072;  // smoothing sweeps
+// Persistent rounds take over once a pass's list holds at most
+// Tuning::rounds_limit vertices (and hand back when the next list outgrows
+// it); default 131072 for each operator, measured best of 8k to 1M on the
+// 2M workload.
 constexpr int kRoundsThreads = 256;
 
 // Resident blocks per SM of a persistent round kernel: as many as its
@@ -2349,7 +2475,7 @@ RoundArgs round_args(MeshSet& m, int cur, int pass0, long long max_rounds) {
   a.tag0 = m.tag + 2;
   a.pass0 = pass0;
   a.max_rounds = (int)std::min<long long>(max_rounds, 1 << 30);
-  a.limit = kRoundsLimit;
+  a.limit = tuning().rounds_limit[0];
   a.icap = 0;
   a.ptag = 0;
   a.work = nullptr;
@@ -2410,12 +2536,15 @@ cudaError_t fetch_ops(MeshSet& m, std::vector<unsigned long long>& ops) {
 // round's list leaves out vertices whose last collapse evaluation found
 // nothing and whose inputs have not changed since.
 int op_coarsen(MeshSet& m, int max_rounds) {
+  const Tuning tu = tuning();
+  const int bs = tu.block[TO_COARSEN], bps = tu.blocks_per_sm[TO_COARSEN];
+  const int rlimit = tu.rounds_limit[0];
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vused);
+  const int gv = grid_tuned(m, m.S.vused, bs, bps);
   int pass0 = m.tag;
   const bool persist = rounds_grid(m, 0) > 0;
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evc,
+  PM_LAUNCH(k_init_list, gv, bs, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evc,
             m.lo_coarsen);
   // entries of the list the next round reads; unknown (0) at first: the
   // persistent launch itself hands a long first list back
@@ -2424,8 +2553,9 @@ int op_coarsen(MeshSet& m, int max_rounds) {
   bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds;) {
     if (m.lo_coarsen > pass0) pass0 = m.lo_coarsen;  // rows were rebuilt after an overflow
-    if (persist && nlist >= 0 && nlist <= kRoundsLimit) {
+    if (persist && nlist >= 0 && nlist <= rlimit) {
       RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
+      a.limit = rlimit;
       RoundsOut o;
       int err = run_rounds(m, 0, (const void*)k_coarsen_rounds, "k_coarsen_rounds", a, o);
       if (err) return err;
@@ -2442,23 +2572,23 @@ int op_coarsen(MeshSet& m, int max_rounds) {
     int tag = (m.tag += 2);
     int nxt = 1 - cur;
     zero_round(m, nxt);
-    PM_LAUNCH(k_coarsen_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
+    PM_LAUNCH(k_coarsen_scan, gv, bs, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
               w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, pass0, w.items,
               w.counts + CN_I);
     // one dense wave checking every vertex's best candidate, then the
     // remaining candidates of the vertices whose best one failed
-    PM_LAUNCH(k_coarsen_check, gv, BLOCK, 0, m.stream, m.S, w.items, w.counts + CN_I, w.items2,
+    PM_LAUNCH(k_coarsen_check, gv, bs, 0, m.stream, m.S, w.items, w.counts + CN_I, w.items2,
               w.counts + CN_I2, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 0);
-    PM_LAUNCH(k_coarsen_check, gv, BLOCK, 0, m.stream, m.S, w.items2, w.counts + CN_I2, w.items,
+    PM_LAUNCH(k_coarsen_check, gv, bs, 0, m.stream, m.S, w.items2, w.counts + CN_I2, w.items,
               w.counts + CN_I, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 1);
     zero_counts(m, CN_CL, 1);
-    PM_LAUNCH(k_coarsen_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
+    PM_LAUNCH(k_coarsen_select_apply, gv, bs, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
               w.smark, tag, w.target, w.A, w.counts + CN_A, w.amark, w.D[nxt],
               w.counts + cn_list(nxt), w.dmark, w.clist, w.counts + CN_CL,
               (unsigned*)(w.counts + CN_DONE));
-    PM_LAUNCH(k_coarsen_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target,
+    PM_LAUNCH(k_coarsen_commit, gv, bs, 0, m.stream, m.S, w.A, w.counts + CN_A, w.target,
               w.smark, tag, m.st);
-    PM_LAUNCH(k_refine_quality, gv, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
+    PM_LAUNCH(k_refine_quality, gv, bs, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
     RoundIO io = read_round(m);
     if (io.err) return io.err;
     if (io.nC == 0) {
@@ -2477,23 +2607,26 @@ int op_coarsen(MeshSet& m, int max_rounds) {
 
 // Rounds of flips until no dirty vertex has an improving flip.
 int op_swap(MeshSet& m, int max_rounds) {
+  const Tuning tu = tuning();
+  const int bs = tu.block[TO_SWAP], bps = tu.blocks_per_sm[TO_SWAP];
+  const int rlimit = tu.rounds_limit[1];
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vused);
+  const int gv = grid_tuned(m, m.S.vused, bs, bps);
   int pass0 = m.tag;
   const int icap = m.S.vslots * 6 + 64;
   const bool persist = rounds_grid(m, 1) > 0;
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evs,
+  PM_LAUNCH(k_init_list, gv, bs, 0, m.stream, m.S, 0, w.D[0], w.counts + CN_D0, m.S.evs,
             m.lo_swap);
   int nlist = 0;  // unknown at first (see op_coarsen)
   int cur = 0;
   bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds;) {
     if (m.lo_swap > pass0) pass0 = m.lo_swap;  // rows were rebuilt after an overflow
-    if (persist && nlist >= 0 && nlist <= kSwapRoundsLimit) {
+    if (persist && nlist >= 0 && nlist <= rlimit) {
       RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
       a.icap = icap;
-      a.limit = kSwapRoundsLimit;
+      a.limit = rlimit;
       RoundsOut o;
       int err = run_rounds(m, 1, (const void*)k_swap_rounds, "k_swap_rounds", a, o);
       if (err) return err;
@@ -2510,21 +2643,21 @@ int op_swap(MeshSet& m, int max_rounds) {
     int tag = (m.tag += 2);
     int nxt = 1 - cur;
     zero_round(m, nxt);
-    PM_LAUNCH(k_swap_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur), w.opA,
+    PM_LAUNCH(k_swap_scan, gv, bs, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur), w.opA,
               w.C, w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E, w.items,
               w.counts + CN_I, icap, w.gains, m.st);
-    PM_LAUNCH(k_swap_edge, grid_for(m, 6LL * m.S.vslots, 16), BLOCK, 0, m.stream, m.S, w.items,
+    PM_LAUNCH(k_swap_edge, grid_tuned(m, 6LL * m.S.vslots, bs, bps), bs, 0, m.stream, m.S, w.items,
               w.counts + CN_I, w.gains, tag, prof_work("k_swap_edge"));
-    PM_LAUNCH(k_swap_pick, gv, BLOCK, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
+    PM_LAUNCH(k_swap_pick, gv, bs, 0, m.stream, m.S, w.E, w.counts + CN_E, w.gains, w.opA,
               w.opK2, w.C, w.counts + CN_C, w.cmark, tag);
     zero_counts(m, CN_CL, 1);
-    PM_LAUNCH(k_swap_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
+    PM_LAUNCH(k_swap_select_apply, gv, bs, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
               w.smark, tag, w.opA, w.opK2, w.A, w.counts + CN_A, w.amark, w.D[nxt],
               w.counts + cn_list(nxt), w.dmark, w.clist, w.counts + CN_CL,
               (unsigned*)(w.counts + CN_DONE));
-    PM_LAUNCH(k_swap_commit, gv, BLOCK, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2,
+    PM_LAUNCH(k_swap_commit, gv, bs, 0, m.stream, m.S, w.A, w.counts + CN_A, w.opA, w.opK2,
               w.smark, tag, m.st);
-    PM_LAUNCH(k_refine_quality, gv, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
+    PM_LAUNCH(k_refine_quality, gv, bs, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
     RoundIO io = read_round(m);
     if (io.err) return io.err;
     if (io.nC == 0) {
@@ -2544,15 +2677,17 @@ int op_swap(MeshSet& m, int max_rounds) {
 // Rounds of splits until no edge is longer than L_up.  Capacity is checked
 // (and grown) before any new vertex or element is written.
 int op_refine(MeshSet& m, int max_rounds) {
+  const Tuning tu = tuning();
+  const int bs = tu.block[TO_REFINE], bps = tu.blocks_per_sm[TO_REFINE];
   Work& w = m.w;
   int pass0 = m.tag;
   bool complete = false;
   for (long long nr = 0; max_rounds == 0 || nr < max_rounds; ++nr) {
-    const int gv = grid_for(m, m.S.vused);
-    const int ge = grid_for(m, m.S.eused);
+    const int gv = grid_tuned(m, m.S.vused, bs, bps);
+    const int ge = grid_tuned(m, m.S.eused, bs, bps);
     int tag = (m.tag += 2);
     if (m.lo_refine > pass0) pass0 = m.lo_refine;  // storage was regrown
-    PM_LAUNCH(k_refine_mark, gv, BLOCK, 0, m.stream, m.S, w.vcnt, w.vmask, tag, pass0,
+    PM_LAUNCH(k_refine_mark, gv, bs, 0, m.stream, m.S, w.vcnt, w.vmask, tag, pass0,
               m.lo_refine);
     scan_exclusive(w.vcnt, w.vscan, m.S.vused, m.scan, m.st, m.stream);
     int* tot = w.counts + CN_NUM;
@@ -2603,18 +2738,18 @@ int op_refine(MeshSet& m, int max_rounds) {
     const int stamp = tag + 1;
     const int vend = m.vbase.back() + m.nv.back() + newv.back();  // above every new vertex
     PM_LAUNCH(k_refine_vtotals, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan);
-    PM_LAUNCH(k_refine_newverts, gv, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, stamp, w.opA);
+    PM_LAUNCH(k_refine_newverts, gv, bs, 0, m.stream, m.S, w.vscan, w.vmask, stamp, w.opA);
     zero_counts(m, CN_EL, 2);
-    PM_LAUNCH(k_refine_count, ge, BLOCK, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid,
+    PM_LAUNCH(k_refine_count, ge, bs, 0, m.stream, m.S, w.vscan, w.vmask, w.ecnt, w.emid,
               w.elist, w.counts + CN_EL);
     scan_exclusive(w.ecnt, w.escan, m.S.eused, m.scan, m.st, m.stream);
-    PM_LAUNCH(k_refine_split, ge, BLOCK, 0, m.stream, m.S, w.escan, w.emid, w.elist,
+    PM_LAUNCH(k_refine_split, ge, bs, 0, m.stream, m.S, w.escan, w.emid, w.elist,
               w.counts + CN_EL, w.clist, w.counts + CN_CL, stamp);
-    PM_LAUNCH(k_refine_quality, ge, BLOCK, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
+    PM_LAUNCH(k_refine_quality, ge, bs, 0, m.stream, m.S, w.clist, w.counts + CN_CL, nullptr);
     // rows of the vertices whose elements changed, through the spare buffer
-    PM_LAUNCH(k_refine_rows, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, w.vscan,
+    PM_LAUNCH(k_refine_rows, grid_tuned(m, vend, bs, bps), bs, 0, m.stream, m.S, m.B, vend, w.vscan,
               w.escan, w.opA, stamp, m.st);
-    PM_LAUNCH(k_refine_rows_copy, grid_for(m, vend), BLOCK, 0, m.stream, m.S, m.B, vend, stamp);
+    PM_LAUNCH(k_refine_rows_copy, grid_tuned(m, vend, bs, bps), bs, 0, m.stream, m.S, m.B, vend, stamp);
     PM_LAUNCH(k_refine_sizes, (m.nmesh + 127) / 128, 128, 0, m.stream, m.S, w.vscan, w.escan);
     // the new sizes and the status in one read-back
     int* hsz = m.hcounts + CN_NUM;
@@ -2637,12 +2772,15 @@ int op_refine(MeshSet& m, int max_rounds) {
 
 // Laplacian sweeps, each a sequence of rounds over the sweep's pending set.
 int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
+  const Tuning tu = tuning();
+  const int bs = tu.block[TO_SMOOTH], bps = tu.blocks_per_sm[TO_SMOOTH];
+  const int rlimit = tu.rounds_limit[2];
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vused);
+  const int gv = grid_tuned(m, m.S.vused, bs, bps);
   const int pass0 = m.tag;
   const bool persist = rounds_grid(m, 2) > 0;
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0, nullptr, 0);
+  PM_LAUNCH(k_init_list, gv, bs, 0, m.stream, m.S, 1, w.D[0], w.counts + CN_D0, nullptr, 0);
   int nlist = 0;  // unknown at first (see op_coarsen)
   long long nr = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -2651,10 +2789,10 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
     int cur = 0;
     bool moved = false;
     while (max_rounds == 0 || nr < max_rounds) {
-      if (persist && nlist >= 0 && nlist <= kSmoothRoundsLimit) {
+      if (persist && nlist >= 0 && nlist <= rlimit) {
         RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
         a.ptag = ptag;
-        a.limit = kSmoothRoundsLimit;
+        a.limit = rlimit;
         RoundsOut o;
         int err = run_rounds(m, 2, (const void*)k_smooth_rounds, "k_smooth_rounds", a, o);
         if (err) return err;
@@ -2668,12 +2806,12 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
       int tag = (m.tag += 2);
       int nxt = 1 - cur;
       zero_round(m, nxt);
-      PM_LAUNCH(k_smooth_scan, gv, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
+      PM_LAUNCH(k_smooth_scan, gv, bs, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
                 w.mvM, w.C, w.counts + CN_C, w.cmark, tag, pass0, w.E, w.counts + CN_E);
-      PM_LAUNCH(k_smooth_eval, grid_for(m, (long long)m.S.vused * TW), BLOCK, 0, m.stream, m.S,
+      PM_LAUNCH(k_smooth_eval, grid_tuned(m, (long long)m.S.vused * TW, bs, bps), bs, 0, m.stream, m.S,
                 w.E, w.counts + CN_E, w.mvxy, w.mvM, w.gains, w.C, w.counts + CN_C, w.cmark, tag,
                 prof_work("k_smooth_eval"));
-      PM_LAUNCH(k_smooth_select_apply, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C,
+      PM_LAUNCH(k_smooth_select_apply, gv, bs, 0, m.stream, m.S, w.C, w.counts + CN_C,
                 w.cmark, w.smark, tag, w.D[nxt], w.counts + cn_list(nxt), w.dmark, w.mvxy, w.mvM,
                 w.gains, w.P, w.counts + CN_P, w.pmark, ptag, tag + 1,
                 (unsigned*)(w.counts + CN_DONE));
@@ -2697,17 +2835,19 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
 
 // Rounds of optimisation-based smoothing over all interior vertices.
 int op_opt_smooth(MeshSet& m, int nrounds, int max_rounds) {
+  const Tuning tu = tuning();
+  const int bs = tu.block[TO_SMOOTH], bps = tu.blocks_per_sm[TO_SMOOTH];
   Work& w = m.w;
-  const int gv = grid_for(m, m.S.vused);
+  const int gv = grid_tuned(m, m.S.vused, bs, bps);
   zero_counts(m, 0, CN_NUM);
-  PM_LAUNCH(k_init_list, gv, BLOCK, 0, m.stream, m.S, 1, w.C, w.counts + CN_C, nullptr, 0);
+  PM_LAUNCH(k_init_list, gv, bs, 0, m.stream, m.S, 1, w.C, w.counts + CN_C, nullptr, 0);
   for (int it = 0; it < nrounds && (max_rounds == 0 || it < max_rounds); ++it) {
     int tag = (m.tag += 2);
     zero_counts(m, CN_S, 1);
-    PM_LAUNCH(k_stamp_list, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, tag);
-    PM_LAUNCH(k_select, gv, BLOCK, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
+    PM_LAUNCH(k_stamp_list, gv, bs, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, tag);
+    PM_LAUNCH(k_select, gv, bs, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark, w.smark, tag,
               w.Sl, w.counts + CN_S, nullptr, nullptr, nullptr);
-    PM_LAUNCH(k_opt_apply, grid_for(m, (long long)m.S.vused * TW), BLOCK, 0, m.stream, m.S, w.Sl,
+    PM_LAUNCH(k_opt_apply, grid_tuned(m, (long long)m.S.vused * TW, bs, bps), bs, 0, m.stream, m.S, w.Sl,
               w.counts + CN_S, w.gains, tag + 1);
   }
   return sync_status(m);

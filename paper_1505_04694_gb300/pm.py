@@ -32,7 +32,8 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_profile_enable", "pm_profile_read", "pm_quality_arrays_noalloc_dev",
            "pm_fp64_peak", "pm_selftest_wait_timeout", "pm_selftest_div3_dev",
            "pm_batch_create", "pm_batch_create_dev", "pm_batch_size", "pm_batch_adapt",
-           "pm_batch_get_mesh", "pm_batch_get_mesh_dev"]
+           "pm_batch_get_mesh", "pm_batch_get_mesh_dev", "pm_set_tuning", "pm_get_tuning",
+           "pm_tuning_load", "pm_tuning_source", "pm_build_id"]
 
 
 class PmParams(C.Structure):
@@ -49,6 +50,15 @@ class PmStats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PmTuning(C.Structure):
+    _fields_ = [("block", C.c_int32 * 4), ("blocks_per_sm", C.c_int32 * 4),
+                ("rounds_limit", C.c_int32 * 3)]
+
+    def as_dict(self):
+        return {"block": list(self.block), "blocks_per_sm": list(self.blocks_per_sm),
+                "rounds_limit": list(self.rounds_limit)}
 
 
 class PmError(RuntimeError):
@@ -113,6 +123,16 @@ def _load():
     L.pm_selftest_wait_timeout.restype = C.c_int
     L.pm_selftest_div3_dev.argtypes = [vp, vp, C.c_int64, vp]
     L.pm_selftest_div3_dev.restype = C.c_int
+    L.pm_set_tuning.argtypes = [C.POINTER(PmTuning)]
+    L.pm_set_tuning.restype = C.c_int
+    L.pm_get_tuning.argtypes = [C.POINTER(PmTuning)]
+    L.pm_get_tuning.restype = C.c_int
+    L.pm_tuning_load.argtypes = [C.c_char_p, C.c_char_p]
+    L.pm_tuning_load.restype = C.c_int
+    L.pm_tuning_source.argtypes = []
+    L.pm_tuning_source.restype = C.c_char_p
+    L.pm_build_id.argtypes = []
+    L.pm_build_id.restype = C.c_char_p
     L.pm_status_string.argtypes = [C.c_int]
     L.pm_status_string.restype = C.c_char_p
     L.pm_last_error.argtypes = []
@@ -522,3 +542,33 @@ def selftest_div3_dev(x, out, stream=0):
     division-by-three routine (float64 CUDA tensors of equal length)."""
     _check(lib.pm_selftest_div3_dev(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
                                     x.numel(), C.c_void_p(stream)), "pm_selftest_div3_dev")
+
+
+def set_tuning(t=None):
+    """pm_set_tuning: dict with block[4], blocks_per_sm[4], rounds_limit[3]
+    (None restores the defaults)."""
+    if t is None:
+        _check(lib.pm_set_tuning(None), "pm_set_tuning")
+        return
+    c = PmTuning((C.c_int32 * 4)(*t["block"]), (C.c_int32 * 4)(*t["blocks_per_sm"]),
+                 (C.c_int32 * 3)(*t["rounds_limit"]))
+    _check(lib.pm_set_tuning(C.byref(c)), "pm_set_tuning")
+
+
+def get_tuning():
+    c = PmTuning()
+    _check(lib.pm_get_tuning(C.byref(c)), "pm_get_tuning")
+    return c.as_dict()
+
+
+def load_tuning(path, gpu_name=None):
+    """pm_tuning_load; True when an entry for this GPU and build was applied."""
+    return lib.pm_tuning_load(path.encode(), gpu_name.encode() if gpu_name else None) == PM_OK
+
+
+def tuning_source():
+    return lib.pm_tuning_source().decode()
+
+
+def build_id():
+    return lib.pm_build_id().decode()
