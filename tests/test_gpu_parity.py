@@ -345,75 +345,79 @@ def test_rejects_invalid_input():
 
 # --- full-size workloads ------------------------------------------------------------
 
+_ORACLE_2M = {}
+
+
+def oracle_2m():
+    """The oracle's adaptation of the 2M workload (stats, compacted mesh),
+    computed once for the tests that need it."""
+    if not _ORACLE_2M:
+        w = inputs.anisotropic_2m()
+        o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+        _ORACLE_2M["stats"] = o.adapt(op(w.params.seed))
+        _ORACLE_2M["mesh"] = o.get_mesh()
+    return _ORACLE_2M["stats"], _ORACLE_2M["mesh"]
+
+
 @pytest.mark.slow
 def test_anisotropic_2m_full_adapt_bit_exact():
-    """The benchmark workload at full size (2.1M output triangles)."""
+    """The single-mesh anisotropic workload at full size (2.1M output triangles)."""
     w = inputs.anisotropic_2m()
-    g, o = both(w, w.params.seed)
+    g = pm.Mesh.from_host(w.xy, w.tri, device=0)
+    g.set_metric(w.m)
     sg = g.adapt(gp(w.params.seed))
-    so = o.adapt(op(w.params.seed))
+    so, omesh = oracle_2m()
     gm = g.get_mesh()
-    assert_same_mesh(gm, o.get_mesh(), "anisotropic 2M")
+    assert_same_mesh(gm, omesh, "anisotropic 2M")
     for k in STAT_KEYS:
         assert sg[k] == so[k], (k, sg[k], so[k])
     assert gm[1].shape[0] > 2_000_000
 
 
 @pytest.mark.slow
-def test_anisotropic_20m_first_rounds_bit_exact_and_invariants():
-    """The large workload (1025^2 grid, ~20M output triangles): the first
-    rounds of every operator, started from the seeded input on both sides, are
-    compared slot by slot; the complete GPU adaptation is checked through
-    properties that hold at any size (conformity, orientation, area, boundary)."""
-    from tests import meshcheck as MC
-
+def test_anisotropic_20m_full_adapt_bit_exact():
+    """The large workload at full size (1025^2 grid, 2.1M triangles in, about
+    29M out): the whole adaptation against the oracle's, bit for bit."""
     w = inputs.anisotropic_20m()
     seed = w.params.seed
-    g, o = both(w, seed)
-    for name, rounds in (("refine", 1), ("coarsen", 2), ("swap", 2), ("smooth", 2)):
-        sg = getattr(g, name)(gp(seed, max_rounds=rounds))
-        so = getattr(o, name)(op(seed, max_rounds=rounds))
-        for k in STAT_KEYS:
-            assert sg[k] == so[k], (name, k, sg[k], so[k])
-        assert_same_raw(g.get_raw(), o.get_raw(), name)
-    del o
-    g2 = pm.Mesh.from_host(w.xy, w.tri, device=0)
-    g2.set_metric(w.m)
-    st = g2.adapt(gp(seed))
-    xy, tri, m = g2.get_mesh()
-    assert tri.shape[0] > 15_000_000, tri.shape
-    ok, why = MC.fast_conformity(tri, xy.shape[0])
-    assert ok, why
-    ok, why = MC.unit_square_ok(xy, tri, tol=1e-9)
-    assert ok, why
-    assert st["collapses"] > 0 and st["flips"] > 0 and st["splits"] > 0
+    g = pm.Mesh.from_host(w.xy, w.tri, device=0)
+    g.set_metric(w.m)
+    sg = g.adapt(gp(seed))
+    gmesh = g.get_mesh()
+    g.close()
+    o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    so = o.adapt(op(seed))
+    assert_same_mesh(gmesh, o.get_mesh(), "anisotropic 20M")
+    for k in STAT_KEYS:
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    assert gmesh[1].shape[0] > 20_000_000
 
 
-def test_batch_sample_of_the_512_mesh_recipe_bit_exact():
-    """16 meshes of the batch recipe (those with the smallest expected
-    output), adapted in one pm_adapt_batch, against the oracle mesh by mesh."""
-    import math as _m
+@pytest.mark.slow
+def test_batch_recipe_all_512_meshes_bit_exact():
+    """All 512 meshes of the batch recipe adapted in one pm_batch_adapt,
+    against the oracle adapting each alone (one spawned oracle process per
+    host core)."""
+    import os
+
+    from tests import oracle_pool
 
     ws = inputs.batch_workloads()
-
-    def expected(w):
-        m = w.m[0]
-        return (4 / _m.sqrt(3)) * _m.sqrt(m[0] * m[2] - m[1] ** 2)
-
-    pick = sorted(range(len(ws)), key=lambda i: expected(ws[i]))[:16]
-    meshes, params = [], []
-    for i in pick:
-        g = pm.Mesh.from_host(ws[i].xy, ws[i].tri, device=0)
-        g.set_metric(ws[i].m)
-        meshes.append(g)
-        params.append(gp(ws[i].params.seed))
-    stats = pm.adapt_batch(meshes, params)
-    for i, g, st in zip(pick, meshes, stats):
-        o = O.OracleMesh(ws[i].xy, ws[i].tri).set_metric(ws[i].m)
-        so = o.adapt(op(ws[i].params.seed))
-        assert_same_mesh(g.get_mesh(), o.get_mesh(), ws[i].name)
+    cores = len(os.sched_getaffinity(0))
+    order = sorted(range(len(ws)), key=lambda i: -ws[i].tri.shape[0])  # largest first
+    with oracle_pool.pool(cores) as p:
+        pending = p.map_async(oracle_pool.batch_mesh, order, chunksize=1)
+        b = pm.Batch.from_host([(w.xy, w.tri) for w in ws])
+        b.set_metric(np.concatenate([w.m for w in ws]))
+        stats = b.adapt([gp(w.params.seed) for w in ws])
+        got = b.get_meshes()
+        b.close()
+        res = {r[0]: r[1:] for r in pending.get()}
+    for i, w in enumerate(ws):
+        oxy, otri, om, so = res[i]
+        assert_same_mesh(got[i], (oxy, otri, om), w.name)
         for k in STAT_KEYS:
-            assert st[k] == so[k], (ws[i].name, k, st[k], so[k])
+            assert stats[i][k] == so[k], (w.name, k, stats[i][k], so[k])
 
 
 @pytest.mark.slow
@@ -425,10 +429,7 @@ def test_gradient_workload_reference_fd_and_opt_smoothing():
     torch = pytest.importorskip("torch")
     from paper_1505_04694_gb300.autograd import quality
 
-    w = inputs.anisotropic_2m()
-    o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
-    o.adapt(op(w.params.seed))
-    xy0, tri0, m0 = o.get_mesh()
+    xy0, tri0, m0 = oracle_2m()[1]
     assert xy0.shape[0] > 1_000_000
     o2 = O.OracleMesh(xy0, tri0).set_metric(m0)
     qo, do, mo = o2.quality()
