@@ -42,3 +42,13 @@ def gather_results(local, rank, world, group=None):
     for o in objs:
         merged.update(o)
     return merged
+
+
+def adapt_sharded(items, sizes, rank, world, adapt, group=None):
+    """Adapt this rank's share of `items` (split by `sizes` with partition)
+    through adapt(index, item) -> result, then gather every rank's
+    {index: result} on rank 0 (None on the other ranks).  The data path has
+    no exchange: each rank's meshes are adapted where they live."""
+    parts = partition(sizes, world)
+    local = {i: adapt(i, items[i]) for i in parts[rank]}
+    return gather_results(local, rank, world, group)
