@@ -371,10 +371,13 @@ def run_batch(args, rank, world, local):
     t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     n_local = torch.tensor([float(tris)], dtype=torch.float64, device=dev)
     # one mesh per launch sequence, the same meshes (fewer timed steps: each
-    # takes seconds)
-    step_single()
-    s_tris, s_ms = timed_steps(step_single, max(1, args.single_steps))
-    s_local = torch.tensor([s_ms, float(s_tris)], dtype=torch.float64, device=dev)
+    # takes seconds); left out of --kernel-only runs, whose launch lists hold
+    # the batched steps alone
+    s_local = torch.tensor([1.0, 0.0], dtype=torch.float64, device=dev)
+    if not args.kernel_only:
+        step_single()
+        s_tris, s_ms = timed_steps(step_single, max(1, args.single_steps))
+        s_local = torch.tensor([s_ms, float(s_tris)], dtype=torch.float64, device=dev)
     if world > 1:
         import torch.distributed as dist
 
@@ -390,8 +393,7 @@ def run_batch(args, rank, world, local):
     if args.kernel_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "elements/s",
-                              "ms_per_step": t_max / args.steps, "gpu_launches": launches,
-                              "one_mesh_per_launch": single_value}))
+                              "ms_per_step": t_max / args.steps, "gpu_launches": launches}))
         return
     # end to end through the host-pointer calls, inputs and outputs pinned
     pin = [torch.from_numpy(a).pin_memory() for a in (h_xy, h_tri, h_m)]

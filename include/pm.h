@@ -305,11 +305,19 @@ pm_status pm_quality_arrays_noalloc_dev(const double* xy, const double* m, int32
  *   rounds_limit[3]: per operator (collapse, flip, smoothing), the largest
  *     list (vertices) whose rounds run inside one persistent launch (0: never;
  *     at most 2^30).
- * Defaults: 128 threads, 16 blocks per SM, 131072. */
+ *   rounds_blocks_per_sm[3]: resident blocks per SM of those persistent
+ *     launches (1 or 2; fewer when the kernel's registers allow fewer).
+ *   fuse_limit[2]: flips, smoothing: inside the persistent launch, lists up
+ *     to this size (and at most one per 8-lane tile of the grid) are scanned
+ *     and evaluated in one phase.
+ * Defaults: 128 threads, 16 blocks per SM, 131072, 1 block, fuse_limit
+ * {0, 2^30} (on the 2M workload the one-phase flip evaluation was slower). */
 typedef struct {
   int32_t block[4];
   int32_t blocks_per_sm[4];
   int32_t rounds_limit[3];
+  int32_t rounds_blocks_per_sm[3];
+  int32_t fuse_limit[2];
 } pm_tuning;
 
 /* Set the launch shapes (null: the defaults).  PM_ERR_INVALID_ARG for a value

@@ -1,10 +1,11 @@
 """Autotuner of the library's launch shapes (pm_tuning, include/pm.h).
 
-Per operator the library has three knobs that decide which thread takes
-which worklist item and in which launch, never a result: threads per block
-and blocks per SM of the one-kernel-per-phase round kernels (the worklist
-chunk each thread walks), and the list size below which rounds run inside
-one persistent launch.  This is the GPU side of the paper's load balancing
+Per operator the library has knobs that decide which thread takes which
+worklist item and in which launch, never a result: threads per block and
+blocks per SM of the one-kernel-per-phase round kernels (the worklist chunk
+each thread walks), the list size below which rounds run inside one
+persistent launch, that launch's blocks per SM, and (flips, smoothing) the
+list size up to which its rounds evaluate in one phase.  This is the GPU side of the paper's load balancing
 (Sec. 3.5): instead of work-stealing between threads, the tuner measures
 which shapes keep the SMs busiest on a workload.
 
@@ -31,6 +32,8 @@ CANDIDATES = {
     "block": [64, 128, 256],
     "blocks_per_sm": [4, 8, 16, 32],
     "rounds_limit": [0, 16384, 65536, 131072, 524288],
+    "rounds_blocks_per_sm": [1, 2],
+    "fuse_limit": [0, 1024, 4096, 1 << 30],
 }
 OPERATORS = ("collapse", "flip", "split", "smoothing")
 
@@ -75,7 +78,11 @@ def knobs():
         out.append(("block", op))
         out.append(("blocks_per_sm", op))
         if op != 2:  # refinement has no persistent rounds
-            out.append(("rounds_limit", {0: 0, 1: 1, 3: 2}[op]))
+            r = {0: 0, 1: 1, 3: 2}[op]
+            out.append(("rounds_limit", r))
+            out.append(("rounds_blocks_per_sm", r))
+            if op in (1, 3):  # flips and smoothing have a one-phase evaluation
+                out.append(("fuse_limit", 0 if op == 1 else 1))
     return out
 
 

@@ -215,7 +215,6 @@ pm_status create_set(const double* xy, const int32_t* nv, const int32_t* tri, co
           set_last_error("invalid mesh: overlapping elements, non-manifold or unused vertex");
       }
     }
-    if (!s) s = (pm_status)refresh_quality(m);
   }
   if (tmp) cudaFreeAsync(tmp, m.stream);
   if (s) {
@@ -233,6 +232,7 @@ pm_status create_set(const double* xy, const int32_t* nv, const int32_t* tri, co
 // Per-mesh parameters into the table; round counters and op counts cleared;
 // every mesh active.
 pm_status begin_call(MeshSet& m, const pm_params* P, int stride) {
+  if (int err = ensure_quality(m)) return (pm_status)err;
   for (int i = 0; i < m.nmesh; ++i) {
     const pm_params& p = P[stride ? i : 0];
     m.seed[i] = p.seed;
@@ -645,7 +645,11 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params, p
     }
     st = cuda_status(upload_tab(b), "batch table");
   }
-  for (int i = 0; i < n && !st; ++i) st = copy_region(b, i, meshes[i]->set, 0, b.stream);
+  for (int i = 0; i < n && !st; ++i) {
+    st = (pm_status)ensure_quality(meshes[i]->set);
+    if (!st) st = copy_region(b, i, meshes[i]->set, 0, b.stream);
+  }
+  b.qvalid = true;  // the copied cache of every mesh is current
   CallStats cs;
   cs.init(n);
   if (!st) st = begin_call(b, params, 1);

@@ -104,6 +104,7 @@ struct MeshSet {
   // evaluations with tags at or below these are stale for that operator
   int lo_coarsen = 0, lo_swap = 0, lo_refine = 0;
   int num_sms = 152;
+  bool qvalid = false;         // the element quality cache matches the current metric
   std::vector<void*> allocs;   // device allocations owned by the set
 };
 
@@ -125,6 +126,9 @@ int compact_out_set(MeshSet& m, double* xy, int32_t* tri, double* mt, int* nv_ou
 int sync_status(MeshSet& m);
 int validate_mesh(MeshSet& m);
 int refresh_quality(MeshSet& m);
+// The quality cache of every element, computed now when it is stale (a mesh
+// whose metric was never set gets it at its first operator call).
+int ensure_quality(MeshSet& m);
 cudaError_t refresh_sizes(MeshSet& m);
 
 // ---- operators (pm_ops.cu) ----
@@ -171,12 +175,16 @@ inline void launch(const char* name, K kern, dim3 g, dim3 b, size_t sh, cudaStre
 // Per operator (collapse, flip, split, smoothing): threads per block and the
 // cap on blocks per SM of the one-kernel-per-phase grids; per operator
 // (collapse, flip, smoothing): the largest list whose rounds run in one
-// persistent launch.  No choice changes a result.
+// persistent launch, the blocks per SM of that launch, and (flips,
+// smoothing) the list size up to which its rounds evaluate in one phase.
+// No choice changes a result.
 enum TuneOp { TO_COARSEN = 0, TO_SWAP = 1, TO_REFINE = 2, TO_SMOOTH = 3 };
 struct Tuning {
   int block[4];
   int blocks_per_sm[4];
   int rounds_limit[3];
+  int rounds_blocks_per_sm[3];  // resident blocks per SM of the persistent round kernels
+  int fuse_limit[2];            // flips, smoothing: one-phase evaluation up to this list size
 };
 Tuning tuning();
 void tuning_autoload();

@@ -476,18 +476,32 @@ __global__ void k_out_e(Store S, int mesh, const int* vscan, const int* escan, i
 // number of unit equilateral metric triangles that tile the mesh).  Only
 // sizes storage, so the order of the atomic sums does not matter.
 __global__ void k_estimate(Store S, double* est) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
-    int mi;
-    if (!eslot_used(S, s, mi)) continue;
-    int4 e = S.EN[s];
-    if (!e.w) continue;
-    int vb = S.tab.vbase[mi];
-    VD a = load_vd(S, vb + e.x), b = load_vd(S, vb + e.y), c = load_vd(S, vb + e.z);
-    double area = 0.5 * fabs(orient3(a, b, c));
-    double sd = sqrt(fmax(a.m00 * a.m11 - a.m01 * a.m01, 0.0)) +
-                sqrt(fmax(b.m00 * b.m11 - b.m01 * b.m01, 0.0)) +
-                sqrt(fmax(c.m00 * c.m11 - c.m01 * c.m01, 0.0));
-    atomicAdd(est + mi, area * sd / 3.0);
+  const int lane = threadIdx.x & 31;
+  for (int s0 = blockIdx.x * blockDim.x; s0 < S.eused; s0 += gridDim.x * blockDim.x) {
+    const int s = s0 + (int)threadIdx.x;
+    int mi = -1;
+    double x = 0.0;
+    if (s < S.eused && eslot_used(S, s, mi)) {
+      int4 e = S.EN[s];
+      if (e.w) {
+        int vb = S.tab.vbase[mi];
+        VD a = load_vd(S, vb + e.x), b = load_vd(S, vb + e.y), c = load_vd(S, vb + e.z);
+        double area = 0.5 * fabs(orient3(a, b, c));
+        double sd = sqrt(fmax(a.m00 * a.m11 - a.m01 * a.m01, 0.0)) +
+                    sqrt(fmax(b.m00 * b.m11 - b.m01 * b.m01, 0.0)) +
+                    sqrt(fmax(c.m00 * c.m11 - c.m01 * c.m01, 0.0));
+        x = area * sd / 3.0;
+      }
+    }
+    // a warp whose slots all belong to one mesh (meshes are contiguous runs
+    // of slots) adds its sum with one atomic
+    const int m0 = __shfl_sync(0xffffffffu, mi, 0);
+    if (__all_sync(0xffffffffu, mi == m0) && m0 >= 0) {
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) atomicAdd(est + m0, x);
+    } else if (mi >= 0) {
+      atomicAdd(est + mi, x);
+    }
   }
 }
 
@@ -940,8 +954,11 @@ int rebuild_adjacency(MeshSet& m, bool derive_flags, bool corners_given) {
 
 int refresh_quality(MeshSet& m) {
   PM_LAUNCH(k_qcache_all, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S);
+  m.qvalid = true;
   return sync_status(m);
 }
+
+int ensure_quality(MeshSet& m) { return m.qvalid ? PM_OK : refresh_quality(m); }
 
 int validate_mesh(MeshSet& m) {
   PM_LAUNCH(k_validate_elems, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.st);

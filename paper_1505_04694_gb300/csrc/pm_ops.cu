@@ -1197,6 +1197,116 @@ __global__ void k_swap_pick(Store S, const int* E, const int* nEp, const double*
   swap_pick_phase(S, E, nEp, gains, opA, opK2, C, nC, cmark, tag);
 }
 
+// Passes 1-3 in one, for persistent rounds whose list fits one pass of the
+// grid's tiles: lane j of v's tile takes v's ball elements j, j + 8, ... as
+// K1 of the edge (v, w) that follows v in it, lists the edge by pass 1's rule
+// (interior, one of the pair below q_thresh, the flip duplicates no edge),
+// evaluates its gain (pass 2), and the tile keeps the largest positive gain,
+// ties to the smallest w (pass 3's order: a total order, w differs between
+// v's edges).  Each edge of v is the K1 edge of exactly one ball element, so
+// the candidate edges are those pass 1 lists.  Two barriers fewer per round.
+__device__ __forceinline__ bool flip_better(bool f2, double g2, int w2, bool f, double g, int w) {
+  return f2 && (!f || dgt(g2, g) || (dbits(g2) == dbits(g) && w2 < w));
+}
+
+__device__ __forceinline__ void swap_scan_eval_phase(Store S, const int* D, const int* nDp,
+                                                     int4* opA, int* opK2, int* C, int* nC,
+                                                     int* cmark, int tag, int pass0,
+                                                     unsigned long long* work) {
+  const Tile t = tile_of();
+  const int n = *nDp;
+  unsigned ops = 0;
+  for (int i0 = 0; i0 < n; i0 += tcount()) {
+    const int i = i0 + trank(true);
+    int v = 0;
+    bool cand = false;
+    if (i < n) {
+      v = D[i];
+      MeshCtx c = ctx_of(S, v);
+      const int et = __shfl_sync(t.mask, S.evs[v], 0, TW);
+      if (unchanged(S, v, c.vb, et, pass0)) {
+        cand = opA[v].x >= 0;
+        if (cand && t.tl == 0) {
+          cmark[v] = tag;
+          S.tab.had[c.mi] = 1;
+        }
+      } else if (S.vflag[v] & VF_ALIVE) {
+        if (t.tl == 0) S.evs[v] = tag;
+        const int lv = v - c.vb;
+        const int* ne = ne_row(S, v);
+        const int nel = S.NElen[v];
+        const double qt = S.tab.q_thresh[c.mi];
+        bool found = false;
+        double best = 0.0;
+        int bw = 0, bk1 = -1, bk2 = -1, bc = 0, bd = 0;
+        for (int k = t.tl; k < nel; k += TW) {
+          const int K1 = ne[k];
+          const int4 e = S.EN[c.eb + K1];
+          const int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;   // after v
+          const int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;  // before v
+          int k2 = -1, d = 0;
+          for (int j = 0; j < nel; ++j) {
+            if (j == k) continue;
+            const int4 f = S.EN[c.eb + ne[j]];
+            if (((f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y) == w) {
+              k2 = j;
+              d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+              break;
+            }
+          }
+          if (k2 < 0) continue;  // boundary edge
+          if (!dlt(S.qK[c.eb + K1], qt) && !dlt(S.qK[c.eb + ne[k2]], qt)) continue;
+          if (row_has(nn_row(S, c.vb + d), S.NNlen[c.vb + d], cc)) continue;
+          int c2, d2;
+          const double g = flip_gain(S, c, lv, ne, k, k2, &c2, &d2, ops);
+          if (!dgt(g, 0.0)) continue;
+          if (flip_better(true, g, w, found, best, bw)) {
+            found = true;
+            best = g;
+            bw = w;
+            bk1 = k;
+            bk2 = k2;
+            bc = cc;
+            bd = d;
+          }
+        }
+#pragma unroll
+        for (int o = TW / 2; o > 0; o >>= 1) {
+          const bool f2 = __shfl_xor_sync(t.mask, found ? 1 : 0, o, TW) != 0;
+          const double g2 = __shfl_xor_sync(t.mask, best, o, TW);
+          const int w2 = __shfl_xor_sync(t.mask, bw, o, TW);
+          const int k1b = __shfl_xor_sync(t.mask, bk1, o, TW);
+          const int k2b = __shfl_xor_sync(t.mask, bk2, o, TW);
+          const int cb = __shfl_xor_sync(t.mask, bc, o, TW);
+          const int db = __shfl_xor_sync(t.mask, bd, o, TW);
+          if (flip_better(f2, g2, w2, found, best, bw)) {
+            found = true;
+            best = g2;
+            bw = w2;
+            bk1 = k1b;
+            bk2 = k2b;
+            bc = cb;
+            bd = db;
+          }
+        }
+        if (t.tl == 0) {
+          if (found) {
+            opA[v] = make_int4(bw, bc, bd, ne[bk1]);
+            opK2[v] = ne[bk2];
+            cmark[v] = tag;
+            S.tab.had[c.mi] = 1;
+          } else {
+            opA[v].x = -1;
+          }
+        }
+        cand = found;
+      }
+    }
+    warp_append(cand && t.tl == 0, v, C, nC);
+  }
+  add_work(work, ops);
+}
+
 // The two new elements' qualities are left to a dense pass (their slots join
 // list Q), as for collapses.
 __device__ __forceinline__ void swap_apply_one(const Store& S, bool ok, int v, const int4* opA,
@@ -2139,7 +2249,9 @@ __global__ void k_refine_sizes(Store S, const int* vscan, const int* escan) {
 // evaluates in one phase (coarsen_eval_phase) and takes three barriers;
 // smoothing scans and evaluates in one tile-parallel phase when the list fits
 // one pass of tiles (two barriers), else keeps the scan apart (three); flips
-// keep their scan, item-parallel gains and pick (five).  The launch
+// scan, evaluate and pick in one tile-parallel phase when the list fits one
+// pass of tiles (three barriers), else keep their scan, item-parallel gains
+// and pick (five).  The launch
 // returns when a round finds no candidate (the pass is complete), when the
 // next round's list outgrows `limit`, on a row overflow or an error, or after
 // `max_rounds` rounds.
@@ -2217,6 +2329,7 @@ struct RoundArgs {
   int limit;           // leave when the next list holds more entries
   int icap;            // flips: capacity of the item list
   int ptag;            // smoothing: stamp of the next sweep's list
+  int fuse;            // flips, smoothing: lists up to this size take the one-phase evaluation
   unsigned long long* work;  // counted FP64 work (measurement) or null
 };
 
@@ -2233,8 +2346,10 @@ __device__ __forceinline__ void finish_rounds(const RoundArgs& a, int r, int cur
 }
 
 // Rounds of collapses: [evaluate] B1 [select + apply] B2 [commit] B3; rounds
-// of flips: [scan] B1 [gains] [pick] [select + apply] [commit], five
-// barriers.  Block 0 clears, before B1 of round r: A and the list round r
+// of flips whose list fits one pass of the grid's tiles: [scan + gains +
+// pick] B1 [select + apply] B2 [commit] B3; longer flip lists: [scan] B1
+// [gains] [pick] [select + apply] [commit], five barriers.  Block 0 clears,
+// before B1 of round r: A and the list round r
 // fills (both last read before the last barrier of round r - 1); right after
 // B1: the candidate slot of round r + 1 (last read before the last barrier of
 // round r - 1); flips, after the pick: E and the item count (read by the pick
@@ -2261,9 +2376,16 @@ __device__ __forceinline__ void topo_rounds(const RoundArgs& a) {
       cnt[cn_list(nxt)] = 0;
       cnt[CN_CL] = 0;  // elements whose quality changes
     }
-    if (FLIP) {
-      // flips keep their three passes: the gains are many per vertex, and
-      // item-parallel FP64 beats two barriers saved
+    if (FLIP && ld_volatile(cnt + cn_list(cur)) <= min(a.fuse, tcount())) {
+      // the list fits one pass of tiles: scan, gains and pick in one phase
+      // (the list is complete since the last barrier: every block decides alike)
+      swap_scan_eval_phase(a.S, w.D[cur], cnt + cn_list(cur), w.opA, w.opK2, w.C, nC, w.cmark,
+                           tag, a.pass0, a.work);
+      if (!grid_barrier(a.bar, target, a.st)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) *cand_count(cnt, r + 1) = 0;
+    } else if (FLIP) {
+      // a longer list keeps the three passes: item-parallel FP64 gains beat
+      // two barriers saved
       swap_scan_phase(a.S, w.D[cur], cnt + cn_list(cur), w.opA, w.C, nC, w.cmark, tag, a.pass0,
                       w.E, cnt + CN_E, w.items, cnt + CN_I, a.icap, w.gains, a.st, true);
       if (!grid_barrier(a.bar, target, a.st)) return;
@@ -2343,7 +2465,7 @@ __global__ void __launch_bounds__(256) k_smooth_rounds(RoundArgs a) {
     Store S = a.S;
     S.tab.had = a.S.tab.had + (r & 1) * S.nmesh;
     // the list is complete since B2 of the last round: every block decides alike
-    const bool fused = ld_volatile(cnt + cn_list(cur)) <= tiles;
+    const bool fused = ld_volatile(cnt + cn_list(cur)) <= min(a.fuse, tiles);
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[cn_list(nxt)] = 0;
     if (fused) {
       smooth_scan_eval_phase(S, w.D[cur], cnt + cn_list(cur), w.mvxy, w.mvM, w.gains, w.C, nC,
@@ -2431,37 +2553,37 @@ int after_round(MeshSet& m, const RoundIO& io) {
 // 2M workload.
 constexpr int kRoundsThreads = 256;
 
-// Resident blocks per SM of a persistent round kernel: as many as its
-// registers allow, at most this many.
-constexpr int kRoundsBlocksPerSm = 1;
-
 // Blocks of a cooperative launch of the persistent round kernel `which`
-// (0 collapse, 1 flip, 2 smoothing) on this device: whole SMs' worth, or 0
-// when the device cannot run it cooperatively (rounds stay one kernel per
-// phase).
+// (0 collapse, 1 flip, 2 smoothing) on this device: the tuning's blocks per
+// SM (Tuning::rounds_blocks_per_sm, at most what its registers allow) on
+// every SM, or 0 when the device cannot run it cooperatively (rounds stay one
+// kernel per phase).
 int rounds_grid(MeshSet& m, int which) {
   static std::mutex mu;
-  static int cache[64][3];
+  static int occ[64][3];
   static bool known[64];
-  std::lock_guard<std::mutex> lk(mu);
   const int dev = m.device;
   if (dev < 0 || dev >= 64 || which < 0 || which > 2) return 0;
-  if (!known[dev]) {
-    int coop = 0;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    const void* ks[] = {(const void*)k_coarsen_rounds, (const void*)k_swap_rounds,
-                        (const void*)k_smooth_rounds};
-    for (int k = 0; k < 3; ++k) {
-      int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ks[k], kRoundsThreads, 0) !=
-          cudaSuccess)
-        b = 0;
-      cache[dev][k] = (coop && b >= 1) ? m.num_sms * std::min(b, kRoundsBlocksPerSm) : 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!known[dev]) {
+      int coop = 0;
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+      const void* ks[] = {(const void*)k_coarsen_rounds, (const void*)k_swap_rounds,
+                          (const void*)k_smooth_rounds};
+      for (int k = 0; k < 3; ++k) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ks[k], kRoundsThreads, 0) !=
+            cudaSuccess)
+          b = 0;
+        occ[dev][k] = coop ? b : 0;
+      }
+      cudaGetLastError();
+      known[dev] = true;
     }
-    cudaGetLastError();
-    known[dev] = true;
   }
-  return cache[dev][which];
+  const int b = std::min(occ[dev][which], tuning().rounds_blocks_per_sm[which]);
+  return b >= 1 ? m.num_sms * b : 0;
 }
 
 RoundArgs round_args(MeshSet& m, int cur, int pass0, long long max_rounds) {
@@ -2478,6 +2600,7 @@ RoundArgs round_args(MeshSet& m, int cur, int pass0, long long max_rounds) {
   a.limit = tuning().rounds_limit[0];
   a.icap = 0;
   a.ptag = 0;
+  a.fuse = 0;
   a.work = nullptr;
   return a;
 }
@@ -2627,6 +2750,7 @@ int op_swap(MeshSet& m, int max_rounds) {
       RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
       a.icap = icap;
       a.limit = rlimit;
+      a.fuse = tu.fuse_limit[0];
       RoundsOut o;
       int err = run_rounds(m, 1, (const void*)k_swap_rounds, "k_swap_rounds", a, o);
       if (err) return err;
@@ -2793,6 +2917,7 @@ int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
         RoundArgs a = round_args(m, cur, pass0, max_rounds == 0 ? (1LL << 30) : max_rounds - nr);
         a.ptag = ptag;
         a.limit = rlimit;
+        a.fuse = tu.fuse_limit[1];
         RoundsOut o;
         int err = run_rounds(m, 2, (const void*)k_smooth_rounds, "k_smooth_rounds", a, o);
         if (err) return err;

@@ -13,7 +13,8 @@
 //
 // A tuning cache is a JSON file written by the package's autotuner:
 //   {"format": 1, "entries": {"<GPU name>|<build id>": {"block": [4 ints],
-//    "blocks_per_sm": [4 ints], "rounds_limit": [3 ints], ...}}}
+//    "blocks_per_sm": [4 ints], "rounds_limit": [3 ints],
+//    "rounds_blocks_per_sm": [3 ints], "fuse_limit": [2 ints], ...}}}
 // An entry applies only to the GPU model and the library build it was
 // measured on.
 #include <dlfcn.h>
@@ -34,7 +35,8 @@ namespace pm {
 
 namespace {
 
-constexpr Tuning kDefaults = {{128, 128, 128, 128}, {16, 16, 16, 16}, {131072, 131072, 131072}};
+constexpr Tuning kDefaults = {{128, 128, 128, 128}, {16, 16, 16, 16}, {131072, 131072, 131072},
+                               {1, 1, 1}, {0, 1 << 30}};
 
 std::mutex g_tmu;
 Tuning g_tune = kDefaults;
@@ -46,8 +48,12 @@ bool valid(const Tuning& t) {
     if (t.block[i] != 64 && t.block[i] != 128 && t.block[i] != 256) return false;
     if (t.blocks_per_sm[i] < 1 || t.blocks_per_sm[i] > 32) return false;
   }
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 3; ++i) {
     if (t.rounds_limit[i] < 0 || t.rounds_limit[i] > (1 << 30)) return false;
+    if (t.rounds_blocks_per_sm[i] < 1 || t.rounds_blocks_per_sm[i] > 2) return false;
+  }
+  for (int i = 0; i < 2; ++i)
+    if (t.fuse_limit[i] < 0 || t.fuse_limit[i] > (1 << 30)) return false;
   return true;
 }
 
@@ -115,7 +121,9 @@ pm_status load_locked(const char* path, const char* gpu_name) {
   Tuning t;
   if (o.empty() || !int_array(o, "block", t.block, 4) ||
       !int_array(o, "blocks_per_sm", t.blocks_per_sm, 4) ||
-      !int_array(o, "rounds_limit", t.rounds_limit, 3) || !valid(t))
+      !int_array(o, "rounds_limit", t.rounds_limit, 3) ||
+      !int_array(o, "rounds_blocks_per_sm", t.rounds_blocks_per_sm, 3) ||
+      !int_array(o, "fuse_limit", t.fuse_limit, 2) || !valid(t))
     return PM_ERR_INVALID_ARG;
   g_tune = t;
   g_source = std::string("cache ") + path;
@@ -179,6 +187,8 @@ pm_status pm_set_tuning(const pm_tuning* t) {
   std::memcpy(n.block, t->block, sizeof n.block);
   std::memcpy(n.blocks_per_sm, t->blocks_per_sm, sizeof n.blocks_per_sm);
   std::memcpy(n.rounds_limit, t->rounds_limit, sizeof n.rounds_limit);
+  std::memcpy(n.rounds_blocks_per_sm, t->rounds_blocks_per_sm, sizeof n.rounds_blocks_per_sm);
+  std::memcpy(n.fuse_limit, t->fuse_limit, sizeof n.fuse_limit);
   if (!valid(n)) return PM_ERR_INVALID_ARG;
   g_tune = n;
   g_source = "set";
@@ -191,6 +201,8 @@ pm_status pm_get_tuning(pm_tuning* t) {
   std::memcpy(t->block, g_tune.block, sizeof t->block);
   std::memcpy(t->blocks_per_sm, g_tune.blocks_per_sm, sizeof t->blocks_per_sm);
   std::memcpy(t->rounds_limit, g_tune.rounds_limit, sizeof t->rounds_limit);
+  std::memcpy(t->rounds_blocks_per_sm, g_tune.rounds_blocks_per_sm, sizeof t->rounds_blocks_per_sm);
+  std::memcpy(t->fuse_limit, g_tune.fuse_limit, sizeof t->fuse_limit);
   return PM_OK;
 }
 

@@ -54,11 +54,11 @@ class PmStats(C.Structure):
 
 class PmTuning(C.Structure):
     _fields_ = [("block", C.c_int32 * 4), ("blocks_per_sm", C.c_int32 * 4),
-                ("rounds_limit", C.c_int32 * 3)]
+                ("rounds_limit", C.c_int32 * 3), ("rounds_blocks_per_sm", C.c_int32 * 3),
+                ("fuse_limit", C.c_int32 * 2)]
 
     def as_dict(self):
-        return {"block": list(self.block), "blocks_per_sm": list(self.blocks_per_sm),
-                "rounds_limit": list(self.rounds_limit)}
+        return {k: list(getattr(self, k)) for k, _ in self._fields_}
 
 
 class PmError(RuntimeError):
@@ -550,9 +550,14 @@ def set_tuning(t=None):
     if t is None:
         _check(lib.pm_set_tuning(None), "pm_set_tuning")
         return
-    c = PmTuning((C.c_int32 * 4)(*t["block"]), (C.c_int32 * 4)(*t["blocks_per_sm"]),
-                 (C.c_int32 * 3)(*t["rounds_limit"]))
+    d = dict(get_tuning_defaults(), **t)
+    c = PmTuning(*[(C.c_int32 * len(d[k]))(*d[k]) for k, _ in PmTuning._fields_])
     _check(lib.pm_set_tuning(C.byref(c)), "pm_set_tuning")
+
+
+def get_tuning_defaults():
+    return {"block": [128] * 4, "blocks_per_sm": [16] * 4, "rounds_limit": [131072] * 3,
+            "rounds_blocks_per_sm": [1] * 3, "fuse_limit": [0, 1 << 30]}
 
 
 def get_tuning():

@@ -40,20 +40,23 @@ def test_sweep_covers_every_operator_knob():
     assert {("block", i) for i in range(4)} <= set(ks)
     assert {("blocks_per_sm", i) for i in range(4)} <= set(ks)
     assert {("rounds_limit", i) for i in range(3)} <= set(ks)
+    assert {("rounds_blocks_per_sm", i) for i in range(3)} <= set(ks)
+    assert {("fuse_limit", i) for i in range(2)} <= set(ks)
     t = {"block": [128] * 4, "blocks_per_sm": [16] * 4, "rounds_limit": [131072] * 3}
     n = autotune.with_knob(t, "block", 2, 64)
     assert n["block"] == [128, 128, 64, 128] and t["block"] == [128] * 4
 
 
-def _entry(block, bps, lim):
-    return {"block": block, "blocks_per_sm": bps, "rounds_limit": lim, "ms": 1.0}
+def _entry(block, bps, lim, rbps=(1, 1, 1), fuse=(0, 0)):
+    return {"block": block, "blocks_per_sm": bps, "rounds_limit": lim,
+            "rounds_blocks_per_sm": list(rbps), "fuse_limit": list(fuse), "ms": 1.0}
 
 
 def test_library_loads_only_its_own_entry(pm, tmp_path):
     path = str(tmp_path / "tuning.json")
     bid = pm.build_id()
     assert len(bid) == 16
-    good = _entry([64, 256, 128, 64], [8, 32, 4, 16], [0, 65536, 524288])
+    good = _entry([64, 256, 128, 64], [8, 32, 4, 16], [0, 65536, 524288], (2, 1, 2), (4096, 0))
     autotune.write_entry(path, autotune.cache_key("Fake GPU", bid), good)
     autotune.write_entry(path, autotune.cache_key("Fake GPU", "0" * 16),
                          _entry([256] * 4, [1] * 4, [1] * 3))
@@ -62,7 +65,8 @@ def test_library_loads_only_its_own_entry(pm, tmp_path):
     pm.set_tuning(None)
     assert pm.load_tuning(path, "Fake GPU")
     got = pm.get_tuning()
-    assert got == {k: good[k] for k in ("block", "blocks_per_sm", "rounds_limit")}
+    assert got == {k: good[k] for k in ("block", "blocks_per_sm", "rounds_limit",
+                                        "rounds_blocks_per_sm", "fuse_limit")}
     assert pm.tuning_source().startswith("cache ")
     # another GPU model, an invalid entry, a missing file: nothing changes
     assert not pm.load_tuning(path, "Other GPU")
@@ -80,15 +84,21 @@ def test_library_loads_only_its_own_entry(pm, tmp_path):
 @pytest.mark.gpu
 def test_no_launch_shape_changes_a_result(pm):
     """The same meshes (a psi-Hessian mesh and a small batch) under the
-    defaults, under small blocks with every round one kernel per phase, and
-    under large blocks with every round persistent: bit for bit the same."""
+    defaults, under small blocks with every round one kernel per phase,
+    with every round persistent and one-phase evaluations, and under large
+    blocks with every round persistent on two blocks per SM and no one-phase
+    evaluation: bit for bit the same."""
     from paper_1505_04694_gb300 import inputs
 
     ws = [inputs.psi_workload(25, 8000, True, 22)]
     ws += inputs.batch_workloads(count=6, seed=11, tmin=500, tmax=6000)
     shapes = [None,
-              {"block": [64] * 4, "blocks_per_sm": [2] * 4, "rounds_limit": [0] * 3},
-              {"block": [256] * 4, "blocks_per_sm": [32] * 4, "rounds_limit": [1 << 30] * 3}]
+              {"block": [64] * 4, "blocks_per_sm": [2] * 4, "rounds_limit": [0] * 3,
+               "fuse_limit": [1 << 30] * 2},
+              {"block": [128] * 4, "blocks_per_sm": [8] * 4, "rounds_limit": [1 << 30] * 3,
+               "fuse_limit": [1 << 30] * 2},
+              {"block": [256] * 4, "blocks_per_sm": [32] * 4, "rounds_limit": [1 << 30] * 3,
+               "rounds_blocks_per_sm": [2] * 3, "fuse_limit": [0, 0]}]
     results = []
     for t in shapes:
         pm.set_tuning(t)
