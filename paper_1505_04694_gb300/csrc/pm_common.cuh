@@ -42,6 +42,10 @@ struct MeshTab {
   // count and an element count (pre[0..nmesh] vertices, pre[nmesh+1..]
   // elements); the offsets of each mesh in a concatenated input or output.
   int* pre;
+  // Mesh of every vertex slot and every element slot (sets of more than one
+  // mesh; filled once per layout).
+  int* vmesh;
+  int* emesh;
 };
 
 struct Store {
@@ -98,25 +102,14 @@ __device__ __forceinline__ void set_err(DevStatus* st, int code) {
   atomicCAS(&st->err, 0, code);
 }
 
-// Mesh of a global vertex slot (binary search over the sorted bases).
+// Mesh of a global vertex / element slot: one load from the layout's slot
+// index (a set of one mesh needs none).
 __device__ __forceinline__ int mesh_of_vslot(const Store& S, int slot) {
-  if (S.nmesh == 1) return 0;
-  int lo = 0, hi = S.nmesh - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (__ldg(S.tab.vbase + mid) <= slot) lo = mid; else hi = mid - 1;
-  }
-  return lo;
+  return S.nmesh == 1 ? 0 : __ldg(S.tab.vmesh + slot);
 }
 
 __device__ __forceinline__ int mesh_of_eslot(const Store& S, int slot) {
-  if (S.nmesh == 1) return 0;
-  int lo = 0, hi = S.nmesh - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (__ldg(S.tab.ebase + mid) <= slot) lo = mid; else hi = mid - 1;
-  }
-  return lo;
+  return S.nmesh == 1 ? 0 : __ldg(S.tab.emesh + slot);
 }
 
 // Segment of position g in a concatenation: the largest i < n with

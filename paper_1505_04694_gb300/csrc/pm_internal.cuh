@@ -105,6 +105,7 @@ struct MeshSet {
   int lo_coarsen = 0, lo_swap = 0, lo_refine = 0;
   int num_sms = 152;
   bool qvalid = false;         // the element quality cache matches the current metric
+  bool mesh_index_ok = false;  // S.tab.vmesh / emesh describe the current layout
   std::vector<void*> allocs;   // device allocations owned by the set
 };
 

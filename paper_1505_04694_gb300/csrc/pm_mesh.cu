@@ -109,6 +109,19 @@ __device__ __forceinline__ bool eslot_used(const Store& S, int slot, int& mi) {
   return slot - S.tab.ebase[mi] < S.tab.ne[mi];
 }
 
+// Mesh of every slot of the layout (binary search over the sorted bases),
+// once per allocation.
+__global__ void k_mesh_index(int n, const int* base, int slots, int* out) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += gridDim.x * blockDim.x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (base[mid] <= s) lo = mid; else hi = mid - 1;
+    }
+    out[s] = lo;
+  }
+}
+
 // ---- relayout (growth) ------------------------------------------------------
 
 // Per-slot data of every used vertex slot into its place in the new layout.
@@ -637,6 +650,14 @@ cudaError_t upload_tab(MeshSet& m) {
   if (!e) e = cudaMemcpyAsync(m.S.tab.band, band, n * sizeof(double4), cudaMemcpyHostToDevice,
                               m.stream);
   if (!e && m.upev) e = cudaEventRecord(m.upev, m.stream);
+  if (!e && !m.mesh_index_ok) {
+    PM_LAUNCH(k_mesh_index, grid_for(m, m.S.vslots), BLOCK, 0, m.stream, n,
+              (const int*)m.S.tab.vbase, m.S.vslots, m.S.tab.vmesh);
+    PM_LAUNCH(k_mesh_index, grid_for(m, m.S.eslots), BLOCK, 0, m.stream, n,
+              (const int*)m.S.tab.ebase, m.S.eslots, m.S.tab.emesh);
+    m.mesh_index_ok = true;
+    e = cudaGetLastError();
+  }
   return e;
 }
 
@@ -708,6 +729,12 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
                      2 * ((size_t)n + 1) * sizeof(int) + 64;
   char* t = nullptr;
   cv.add(&t, tab_bytes, true);
+  int* vmesh = nullptr;
+  int* emesh = nullptr;
+  if (n > 1) {
+    cv.add(&vmesh, vs);
+    cv.add(&emesh, es);
+  }
   Work& w = m.w;
   cv.add(&w.D[0], vs);
   cv.add(&w.D[1], vs);
@@ -768,6 +795,9 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   T.had = (int*)t; t += 2 * n * sizeof(int);  // two sets: persistent rounds alternate
   T.active = (int*)t; t += n * sizeof(int);
   T.pre = (int*)t; t += 2 * ((size_t)n + 1) * sizeof(int);
+  T.vmesh = vmesh;
+  T.emesh = emesh;
+  m.mesh_index_ok = n == 1;
   m.B.tab = T;
   if (!m.st) {
     if ((e = cudaMallocAsync((void**)&m.st, sizeof(DevStatus), m.stream))) return e;
