@@ -165,6 +165,43 @@ __device__ __forceinline__ void write_row_bits(unsigned long long bits, const in
   }
 }
 
+// A set of entries of one adjacency row (rows hold at most 128 entries): one
+// bit per entry, in two named words so that it stays in registers.
+struct RowMask {
+  unsigned long long lo = 0ull, hi = 0ull;
+  __device__ __forceinline__ void set(int k) {
+    if (k < 64) lo |= 1ull << k;
+    else hi |= 1ull << (k - 64);
+  }
+  __device__ __forceinline__ bool test(int k) const {
+    return k < 64 ? ((lo >> k) & 1ull) != 0ull : ((hi >> (k - 64)) & 1ull) != 0ull;
+  }
+  __device__ __forceinline__ bool any() const { return (lo | hi) != 0ull; }
+  __device__ __forceinline__ int count() const { return __popcll(lo) + __popcll(hi); }
+  // the lowest entry, removed from the set
+  __device__ __forceinline__ int pop() {
+    if (lo) {
+      int k = __ffsll((long long)lo) - 1;
+      lo &= lo - 1ull;
+      return k;
+    }
+    int k = __ffsll((long long)hi) - 1;
+    hi &= hi - 1ull;
+    return 64 + k;
+  }
+  // entries of the set below entry k
+  __device__ __forceinline__ int below(int k) const {
+    return k < 64 ? __popcll(lo & ((1ull << k) - 1ull))
+                  : __popcll(lo) + __popcll(hi & ((1ull << (k - 64)) - 1ull));
+  }
+};
+
+// Writes vb + row[k] for every entry k of `bits`, from slot `pos` on.
+__device__ __forceinline__ void write_row_bits(RowMask bits, const int* row, int vb, int* list,
+                                               int pos) {
+  while (bits.any()) list[pos++] = vb + row[bits.pop()];
+}
+
 template <class T>
 __device__ __forceinline__ void warp_append_t(bool pred, T val, T* list, int* count) {
   unsigned m = __ballot_sync(0xffffffffu, pred);

@@ -11,7 +11,7 @@
 
 namespace pm {
 
-constexpr int MAXW = 64;          // largest supported adjacency row
+constexpr int MAXW = 128;         // largest supported adjacency row (a vertex's degree)
 constexpr int BLOCK = 128;        // threads per block of the round kernels
 
 struct ScanWork {
@@ -47,7 +47,7 @@ struct Work {
   int* pmark = nullptr;
   int* vcnt = nullptr;             // per-vertex counts (refine / renumber), vslots + 1
   int* vscan = nullptr;            // vslots + 1
-  unsigned long long* vmask = nullptr;  // refine: marked NN entries
+  RowMask* vmask = nullptr;        // refine: marked NN entries
   int* ecnt = nullptr;             // per-element counts, eslots + 1
   int* escan = nullptr;
   int4* emid = nullptr;            // refine: midpoint ids per element edge

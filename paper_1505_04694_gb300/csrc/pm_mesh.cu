@@ -966,7 +966,7 @@ int rebuild_adjacency(MeshSet& m, bool derive_flags, bool corners_given) {
     int W = m.S.W;
     while (W < need) W *= 2;
     if (W > MAXW) {
-      set_last_error("adjacency row longer than the supported maximum of 64 entries");
+      set_last_error("adjacency row longer than the supported maximum of 128 entries");
       return PM_ERR_CAPACITY;
     }
     cudaError_t e = grow_rows(m, W);

@@ -369,46 +369,6 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band, unsigne
   return ok;
 }
 
-// Collapse candidates of v: neighbours with metric length below L_low (a
-// boundary vertex: only along boundary edges), sorted by (length, id) into
-// out[0..n).  Corners and dead vertices have none.
-__device__ int coarsen_candidates(const Store& S, int v, MeshCtx c, int* out, unsigned& ops) {
-  uint8_t f = S.vflag[v];
-  if (!(f & VF_ALIVE) || (f & VF_CORNER)) return 0;
-  const bool bnd = (f & VF_BND) != 0;
-  const int* nn = nn_row(S, v);
-  int nnl = S.NNlen[v];
-  const int* ne = ne_row(S, v);
-  int nel = S.NElen[v];
-  VD dv = load_vd(S, v);
-  const double L_low = S.tab.L_low[c.mi];
-  const double4 band = S.tab.band[c.mi];
-  double cl[MAXW], len2[MAXW];
-  // squared lengths first, four neighbours at a time so that their loads overlap
-#pragma unroll 4
-  for (int k = 0; k < nnl; ++k) len2[k] = metric_len2(dv, load_vd(S, c.vb + nn[k]));
-  ops += kOpsLen2 * nnl;
-  int nc = 0;
-  for (int k = 0; k < nnl; ++k) {
-    int u = nn[k];
-    if (bnd && count_elems_with(S, ne, nel, c.eb, u) != 1) continue;
-    double L2 = len2[k];
-    if (!len_lt(L2, band.x, band.y, L_low)) continue;
-    double L = sqrt(L2);
-    ++ops;
-    int j = nc;  // insertion by (L, u); u ascending already, so ties keep order
-    while (j > 0 && dgt(cl[j - 1], L)) {
-      cl[j] = cl[j - 1];
-      out[j] = out[j - 1];
-      --j;
-    }
-    cl[j] = L;
-    out[j] = u;
-    ++nc;
-  }
-  return nc;
-}
-
 // collapse_valid with the lanes of a tile splitting v's ball elements (the
 // element count of the edge and the orientations with v on u) and v's
 // neighbours (the link condition and the new edge lengths): the same
@@ -455,11 +415,14 @@ __device__ bool tile_collapse_valid(const Tile& t, const CoarsenCtx& x, int u, d
   return tall(t, ok);
 }
 
-// coarsen_candidates with the lanes of a tile splitting v's neighbours: lane
-// tl holds neighbours tl, tl + 8, ...; each candidate's place in the order by
-// (length, id) is the number of candidates before it (a neighbour of lower
-// index has the lower id: rows are sorted), which is the insertion order of
-// the definition.  Returns the candidate count (every lane).
+// Collapse candidates of v: neighbours with metric length below L_low (a
+// boundary vertex: only along boundary edges), sorted by (length, id) into
+// out[0..n); corners and dead vertices have none.  The lanes of a tile split
+// v's neighbours: lane tl holds neighbours tl, tl + 8, ...; each candidate's
+// place in the order is the number of candidates before it (a neighbour of
+// lower index has the lower id: rows are sorted), which is the stable order
+// by length the definition asks for.  Returns the candidate count (every
+// lane).
 __device__ int tile_coarsen_candidates(const Tile& t, const Store& S, int v, MeshCtx c, int* out,
                                        unsigned& ops) {
   uint8_t f = S.vflag[v];
@@ -685,7 +648,7 @@ __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v
     int nnl = 0, mi = 0, vb = 0, eb = 0;
     const int* nn = nullptr;
     const int* ne_v = nullptr;
-    unsigned long long qbits = 0;
+    RowMask qbits;
     if (ok) {
       MeshCtx c = ctx_of(S, v);
       mi = c.mi;
@@ -703,7 +666,7 @@ __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v
           if (e.x == lv) e.x = w;
           if (e.y == lv) e.y = w;
           if (e.z == lv) e.z = w;
-          qbits |= 1ull << k;
+          qbits.set(k);
         }
         *pe = e;
       }
@@ -714,21 +677,17 @@ __device__ __forceinline__ void coarsen_apply_one(const Store& S, bool ok, int v
       eb = c.eb;
     }
     count_op(S, ok, mi);
-    int pq = warp_reserve(__popcll(qbits), nQ);
-    while (qbits) {
-      int k = __ffsll((long long)qbits) - 1;
-      qbits &= qbits - 1ull;
-      Q[pq++] = eb + ne_v[k];
-    }
-    unsigned long long fa = 0, fd = 0;
+    int pq = warp_reserve(qbits.count(), nQ);
+    while (qbits.any()) Q[pq++] = eb + ne_v[qbits.pop()];
+    RowMask fa, fd;
 #pragma unroll 4
     for (int k = 0; k < nnl; ++k) {
       int s = vb + nn[k];
-      if (stamp_first(amark, s, tag)) fa |= 1ull << k;
-      if (stamp_first(dmark, s, tag)) fd |= 1ull << k;
+      if (stamp_first(amark, s, tag)) fa.set(k);
+      if (stamp_first(dmark, s, tag)) fd.set(k);
     }
-    int pa = warp_reserve(__popcll(fa), nA);
-    int pd = warp_reserve(__popcll(fd), nDn);
+    int pa = warp_reserve(fa.count(), nA);
+    int pd = warp_reserve(fd.count(), nDn);
     write_row_bits(fa, nn, vb, A, pa);
     write_row_bits(fd, nn, vb, Dn, pd);
   }
@@ -789,19 +748,19 @@ __device__ __forceinline__ void coarsen_commit_phase(Store S, const int* A, cons
     int nn2 = 0, ne2 = 0;
     bool ok = true;
     // gather the per-entry facts first so that their loads overlap
-    unsigned long long alive = 0, sel = 0;
+    RowMask alive, sel;
 #pragma unroll 4
     for (int k = 0; k < nel; ++k)
-      if (S.EN[c.eb + ne[k]].w) alive |= 1ull << k;
+      if (S.EN[c.eb + ne[k]].w) alive.set(k);
 #pragma unroll 4
     for (int k = 0; k < nnl; ++k)
-      if (smark[c.vb + nn[k]] == tag) sel |= 1ull << k;
+      if (smark[c.vb + nn[k]] == tag) sel.set(k);
     for (int k = 0; k < nel; ++k)
-      if ((alive >> k) & 1ull) ok &= sorted_insert(eb, ne2, MAXW, ne[k]);
+      if (alive.test(k)) ok &= sorted_insert(eb, ne2, MAXW, ne[k]);
     for (int k = 0; k < nnl; ++k) {
       int x = nn[k];
       int xs = c.vb + x;
-      if (!((sel >> k) & 1ull)) {
+      if (!sel.test(k)) {
         ok &= sorted_insert(nb, nn2, MAXW, x);
         continue;
       }
@@ -900,10 +859,10 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
     const double qt = eval ? S.tab.q_thresh[c.mi] : 0.0;
     // An edge (v, w) qualifies only when one of its two elements has quality
     // below q_thresh, so the pairs are found from v's poor elements alone.
-    unsigned long long poor = 0;
+    RowMask poor;
     for (int k = 0; k < nel; ++k) {
       gains[(size_t)v * S.W + k] = -1.0;
-      if (dlt(S.qK[c.eb + ne[k]], qt)) poor |= 1ull << k;
+      if (dlt(S.qK[c.eb + ne[k]], qt)) poor.set(k);
     }
     if (__all_sync(0xffffffffu, nel <= kBallFast)) {
       // the ball's vertices after and before v, gathered once into registers
@@ -918,13 +877,12 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
         }
       }
       for (;;) {
-        bool any = poor != 0ull;
+        bool any = poor.any();
         if (!__any_sync(0xffffffffu, any)) break;
         bool emit1 = false, emit2 = false;
         int a1 = 0, a2 = 0;
         if (any) {
-          int kb = __ffsll((long long)poor) - 1;
-          poor &= poor - 1ull;
+          int kb = poor.pop();
           int w = -1, cc = -1;
 #pragma unroll
           for (int k = 0; k < kBallFast; ++k)
@@ -960,14 +918,13 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
       continue;
     }
     for (;;) {
-      bool any = poor != 0ull;
+      bool any = poor.any();
       if (!__any_sync(0xffffffffu, any)) break;
       // pair (K1 = kb, K2): K2 holds the directed edge w -> v
       bool emit1 = false, emit2 = false;
       int a1 = 0, a2 = 0;
       if (any) {
-        int kb = __ffsll((long long)poor) - 1;
-        poor &= poor - 1ull;
+        int kb = poor.pop();
         int4 e = S.EN[c.eb + ne[kb]];
         int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;   // after v
         int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;  // before v
@@ -1415,13 +1372,13 @@ __device__ __forceinline__ void swap_commit_phase(Store S, const int* A, const i
     for (int k = 0; k < nel; ++k) eb[k] = ne[k];
     int nn2 = nnl, ne2 = nel;
     bool ok = true;
-    unsigned long long sel = 0;
+    RowMask sel;
 #pragma unroll 4
     for (int k = 0; k < nnl; ++k)
-      if (smark[c.vb + nn[k]] == tag) sel |= 1ull << k;
+      if (smark[c.vb + nn[k]] == tag) sel.set(k);
     const bool self = smark[u] == tag;
     for (int k = -1; k < nnl; ++k) {
-      if (k < 0 ? !self : !((sel >> k) & 1ull)) continue;
+      if (k < 0 ? !self : !sel.test(k)) continue;
       int x = (k < 0) ? lu : nn[k];
       int xs = c.vb + x;
       int4 op = opA[xs];
@@ -1799,14 +1756,14 @@ __device__ __forceinline__ void smooth_apply_one(const Store& S, bool ok, int v,
       stamp_neighbours(S, nn, nnl, vb, stamp);
     }
     count_op(S, ok, mi);
-    unsigned long long take = 0;
+    RowMask take;
 #pragma unroll 4
     for (int k = 0; k < nnl; ++k) {
       int s = vb + nn[k];
       uint8_t f = S.vflag[s];
-      if ((f & VF_ALIVE) && !(f & VF_BND) && stamp_first(pmark, s, ptag)) take |= 1ull << k;
+      if ((f & VF_ALIVE) && !(f & VF_BND) && stamp_first(pmark, s, ptag)) take.set(k);
     }
-    int pp = warp_reserve(__popcll(take), nP);
+    int pp = warp_reserve(take.count(), nP);
     write_row_bits(take, nn, vb, P, pp);
   }
 }
@@ -1957,26 +1914,25 @@ __global__ void k_stamp_list(Store S, const int* L, const int* nLp, int* cmark, 
 
 // ---- refinement (Sec. 2.4.2) -----------------------------------------------------
 
-// Mark edges (a, b), a < b, longer than L_up: bit k of vmask[a] for NN entry k.
+// Mark edges (a, b), a < b, longer than L_up: entry k of vmask[a] for NN entry k.
 // A vertex unchanged since it was marked earlier in this pass keeps its mask;
 // one unchanged since the end of an earlier complete pass has none.  The mask
 // reads a's own row and the positions and metrics of a and its neighbours;
 // inside one call vertices keep their positions and metrics until the
 // operator loop ends (smoothing runs after it), so a's own stamp tells
 // whether anything the mask read has changed: every change of a's row stamps a.
-__global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int tag, int pass0,
-                              int lo) {
+__global__ void k_refine_mark(Store S, int* cnt, RowMask* mask, int tag, int pass0, int lo) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
     int mi = mesh_of_vslot(S, s);
     int vb = S.tab.vbase[mi];
-    unsigned long long m = 0;
+    RowMask m;
     bool live = s - vb < S.tab.nv[mi] && S.tab.active[mi] && (S.vflag[s] & VF_ALIVE);
     const int et = live ? S.evr[s] : 0;
     const bool same = live && S.touch[s] <= et;
     if (same && et > pass0) {
       m = mask[s];  // kept as it is
     } else if (same && et > lo) {
-      mask[s] = 0;
+      mask[s] = RowMask();
     } else if (live) {
       S.evr[s] = tag;
       int la = s - vb;
@@ -1991,12 +1947,12 @@ __global__ void k_refine_mark(Store S, int* cnt, unsigned long long* mask, int t
       while (k0 < nnl && nn[k0] <= la) ++k0;
 #pragma unroll 4
       for (int k = k0; k < nnl; ++k)
-        if (len_gt(metric_len2(da, load_vd(S, vb + nn[k])), band.z, band.w, L_up)) m |= 1ull << k;
+        if (len_gt(metric_len2(da, load_vd(S, vb + nn[k])), band.z, band.w, L_up)) m.set(k);
       mask[s] = m;
     } else {
-      mask[s] = 0;
+      mask[s] = RowMask();
     }
-    cnt[s] = __popcll(m);
+    cnt[s] = m.count();
   }
 }
 
@@ -2021,21 +1977,21 @@ __global__ void k_refine_vtotals(Store S, const int* vscan) {
 }
 
 __device__ __forceinline__ int mid_id(const Store& S, int vb, int nv, const int* vscan,
-                                      const unsigned long long* mask, int p, int q) {
+                                      const RowMask* mask, int p, int q) {
   int a = p < q ? p : q, b = p < q ? q : p;
-  unsigned long long m = mask[vb + a];
-  if (!m) return -1;
+  const RowMask m = mask[vb + a];
+  if (!m.any()) return -1;
   int k = row_find(nn_row(S, vb + a), S.NNlen[vb + a], b);
-  if (k < 0 || !((m >> k) & 1ull)) return -1;
-  int rank = __popcll(m & ((1ull << k) - 1ull));
+  if (k < 0 || !m.test(k)) return -1;
+  int rank = m.below(k);
   return nv + (vscan[vb + a] - vscan[vb]) + rank;
 }
 
-__global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long long* mask,
-                                  int stamp, int4* owner) {
+__global__ void k_refine_newverts(Store S, const int* vscan, const RowMask* mask, int stamp,
+                                  int4* owner) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
-    unsigned long long m = mask[s];
-    if (!m) continue;
+    RowMask m = mask[s];
+    if (!m.any()) continue;
     int mi = mesh_of_vslot(S, s);
     int vb = S.tab.vbase[mi], eb = S.tab.ebase[mi], nv = S.tab.nv[mi];
     const int* nn = nn_row(S, s);
@@ -2044,10 +2000,8 @@ __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long
     int base = nv + (vscan[s] - vscan[vb]);
     int rank = 0;
     VD da = load_vd(S, s);
-    while (m) {
-      int k = __ffsll((long long)m) - 1;
-      m &= m - 1;
-      int b = nn[k];
+    while (m.any()) {
+      int b = nn[m.pop()];
       VD db = load_vd(S, vb + b);
       int slot = vb + base + rank;
       ++rank;
@@ -2066,8 +2020,8 @@ __global__ void k_refine_newverts(Store S, const int* vscan, const unsigned long
 
 // Extra children per live element (0..3); an element that splits gets the
 // midpoint ids of its edges and joins the split list.
-__global__ void k_refine_count(Store S, const int* vscan, const unsigned long long* mask,
-                               int* ecnt, int4* emid, int* elist, int* nel) {
+__global__ void k_refine_count(Store S, const int* vscan, const RowMask* mask, int* ecnt,
+                               int4* emid, int* elist, int* nel) {
   for (int i0 = blockIdx.x * blockDim.x; i0 < S.eused; i0 += gridDim.x * blockDim.x) {
     int s = i0 + threadIdx.x;
     int extra = 0;

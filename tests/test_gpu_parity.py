@@ -310,6 +310,43 @@ def test_batch_handle_device_arrays():
     assert so["collapses"] > 0
 
 
+def _wheel(nb):
+    """The unit square as a wheel: a centre vertex joined to nb vertices spaced
+    evenly along the boundary (the four corners among them), so the centre's
+    degree is nb."""
+    per_side = nb // 4
+    pts = []
+    for side in range(4):
+        for k in range(per_side):
+            t = k / per_side
+            pts.append([(t, 0.0), (1.0, t), (1.0 - t, 1.0), (0.0, 1.0 - t)][side])
+    xy = np.array([[0.5, 0.5]] + pts)
+    tri = np.array([[0, 1 + i, 1 + (i + 1) % nb] for i in range(nb)], np.int32)
+    return xy, tri
+
+
+def test_vertex_of_degree_84_adapts_bit_exact():
+    """Rows longer than 64 entries: a wheel whose centre has 84 neighbours,
+    adapted in full against the oracle (which has no row limit)."""
+    xy, tri = _wheel(84)
+    m = inputs.uniform_metric(xy.shape[0], 0.05)
+    g = pm.Mesh.from_host(xy, tri, device=0)
+    assert g.adjacency(0)[0].shape[0] == 84
+    g.set_metric(m)
+    o = O.OracleMesh(xy, tri).set_metric(m)
+    sg = g.adapt(gp(17))
+    so = o.adapt(op(17))
+    assert_same_mesh(g.get_mesh(), o.get_mesh(), "wheel of 84")
+    for k in STAT_KEYS:
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    assert sg["splits"] > 0 and sg["collapses"] + sg["flips"] > 0
+    # beyond the supported row length (128 entries) the mesh is refused
+    xy2, tri2 = _wheel(140)
+    with pytest.raises(pm.PmError) as e:
+        pm.Mesh.from_host(xy2, tri2, device=0)
+    assert e.value.status == 4
+
+
 def test_bounded_barrier_wait_times_out_and_device_stays_usable():
     """A grid barrier that no arrival completes gives up after its limit and
     reports PM_ERR_TIMEOUT (6) through the status word; the next call works."""
