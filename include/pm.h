@@ -279,6 +279,15 @@ pm_status pm_selftest_wait_timeout(double limit_ms, int32_t* device_status, doub
  * null pointer or n < 0.  The paper has no counterpart. */
 pm_status pm_selftest_div3_dev(const double* x, double* out, int64_t n, void* stream);
 
+/* Test support: out[i] = the exact orientation sign (-1, 0, +1) of the points
+ * (px, py), (qx, qy), (rx, ry) = pts[6i .. 6i+5], the predicate behind every
+ * validity decision of the operators (an element counter-clockwise, a point
+ * in the closed element, a corner; Sec. 2.4): the sign of the determinant of
+ * the doubles' exact values.  pts[6n] and out[n] are device arrays; runs on
+ * `stream` without synchronising.  PM_ERR_INVALID_ARG for a null pointer or
+ * n < 0. */
+pm_status pm_selftest_orient_dev(const double* pts, int32_t* out, int64_t n, void* stream);
+
 /* pm_quality_arrays_dev for callers that cannot allocate device memory
  * during the call (a framework that has already reserved the device memory
  * for its own allocator, a latency-bound loop, or a program that allows no

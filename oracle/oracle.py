@@ -61,6 +61,8 @@ def lib():
         L.or_tri_quality_grad.restype = C.c_double
         L.or_edge_length.argtypes = [dp, dp, dp, dp]
         L.or_edge_length.restype = C.c_double
+        L.or_orient_sign.argtypes = [dp]
+        L.or_orient_sign.restype = C.c_int32
         L.or_fmix32.argtypes = [C.c_uint32]
         L.or_fmix32.restype = C.c_uint32
         L.or_prio.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
@@ -257,3 +259,9 @@ def fmix32(h):
 
 def prio(v, seed, r):
     return int(lib().or_prio(v & 0xFFFFFFFF, seed & 0xFFFFFFFF, r & 0xFFFFFFFF))
+
+
+def orient_sign(p, q, r):
+    """Exact sign of the orientation of points p, q, r (the oracle's predicate)."""
+    pts = np.ascontiguousarray([p[0], p[1], q[0], q[1], r[0], r[1]], dtype=np.float64)
+    return int(lib().or_orient_sign(_d(pts)))

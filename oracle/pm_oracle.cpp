@@ -105,8 +105,10 @@ double orient3(const VD& p, const VD& q, const VD& r) {
 }
 
 // Canonical rotation of a triangle: the smallest vertex id goes first, the
-// cyclic order is kept.  All orientation and quality values are taken in this
-// rotation so that they do not depend on how a triangle happens to be stored.
+// cyclic order is kept.  Orientation values (areas, barycentric weights) and
+// qualities are taken in this rotation so that they do not depend on how a
+// triangle happens to be stored; orientation signs are exact (below) and so
+// independent of the rotation anyway.
 void canon(int ids[3], VD d[3]) {
   int s = 0;
   if (ids[1] < ids[s]) s = 1;
@@ -120,11 +122,84 @@ void canon(int ids[3], VD d[3]) {
   }
 }
 
-double orient_c(int i0, int i1, int i2, VD a, VD b, VD c) {
-  int ids[3] = {i0, i1, i2};
-  VD d[3] = {a, b, c};
-  canon(ids, d);
-  return orient3(d[0], d[1], d[2]);
+// ---------------------------------------------------------------------------
+// Exact orientation sign (reading S3 with robust predicates).  Every validity
+// decision (an element counter-clockwise, a point in the closed element, a
+// corner) takes the sign of
+//   det = (q.x - p.x)(r.y - p.y) - (q.y - p.y)(r.x - p.x)
+// of the real numbers the doubles stand for, so it does not depend on the
+// rounding of the formula or on the rotation it is evaluated in.
+//   - Filter: when |det| computed in floating point exceeds 8 eps (|t1| +
+//     |t2|), eps = 2^-53, its sign is the exact one (a bound on the rounding
+//     error of this form is (3 + 16 eps) eps (|t1| + |t2|): J. R. Shewchuk,
+//     "Adaptive precision floating-point arithmetic and fast robust
+//     geometric predicates", 1997).
+//   - Otherwise det is summed exactly: each difference is a two-term
+//     expansion (its rounded value and rounding error), each of the eight
+//     partial products is exact as a product and its error (fma), and the
+//     sixteen terms are grown into a non-overlapping expansion by exact
+//     two-sums; the sign of such an expansion is that of its largest term.
+// Exact as long as no product or error underflows or overflows (coordinates
+// zero or of magnitude between 1e-140 and 1e140).  Parity: pinned against
+// rational arithmetic.
+void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  double bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
+}
+
+void two_diff(double a, double b, double& s, double& e) {
+  s = a - b;
+  double bv = a - s;
+  e = (a - (s + bv)) + (bv - b);
+}
+
+// Adds b to the non-overlapping expansion e[0..n) (increasing magnitude),
+// dropping zero terms; returns the new length.
+int grow_expansion(double* e, int n, double b) {
+  double q = b;
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    double sum, err;
+    two_sum(q, e[i], sum, err);
+    if (err != 0.0) e[m++] = err;
+    q = sum;
+  }
+  if (q != 0.0) e[m++] = q;
+  return m;
+}
+
+int orient_exact(const VD& p, const VD& q, const VD& r) {
+  double a[2], b[2], c[2], d[2];  // {rounded difference, its error}
+  two_diff(q.x, p.x, a[0], a[1]);
+  two_diff(r.y, p.y, b[0], b[1]);
+  two_diff(q.y, p.y, c[0], c[1]);
+  two_diff(r.x, p.x, d[0], d[1]);
+  double e[32];
+  int n = 0;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      double pr = a[i] * b[j];
+      n = grow_expansion(e, n, pr);
+      n = grow_expansion(e, n, std::fma(a[i], b[j], -pr));
+      double ps = c[i] * d[j];
+      n = grow_expansion(e, n, -ps);
+      n = grow_expansion(e, n, -std::fma(c[i], d[j], -ps));
+    }
+  if (n == 0) return 0;
+  return e[n - 1] > 0.0 ? 1 : -1;
+}
+
+const double ORIENT_FILTER = 8.0 * 1.1102230246251565e-16;  // 8 eps
+
+int orient_sign(const VD& p, const VD& q, const VD& r) {
+  double t1 = (q.x - p.x) * (r.y - p.y);
+  double t2 = (q.y - p.y) * (r.x - p.x);
+  double det = t1 - t2;
+  double bound = ORIENT_FILTER * (std::fabs(t1) + std::fabs(t2));
+  if (det > bound) return 1;
+  if (-det > bound) return -1;
+  return orient_exact(p, q, r);
 }
 
 const double QC = 12.0 * 1.7320508075688772;  // 12 sqrt(3)
@@ -383,7 +458,7 @@ bool collapse_valid(const OMesh& m, int v, int w, const Params& P) {
       id[i] = (t[i] == v) ? w : t[i];
       d[i] = (t[i] == v) ? dw : m.vd(t[i]);
     }
-    if (!(orient_c(id[0], id[1], id[2], d[0], d[1], d[2]) > 0.0)) return false;
+    if (orient_sign(d[0], d[1], d[2]) <= 0) return false;
   }
   for (int x : m.NN[v]) {
     if (x == w || sorted_has(m.NN[w], x)) continue;
@@ -469,8 +544,8 @@ bool flip_candidate(const OMesh& m, int v, int w, const Params& P, SwapOp& op) {
   double qold = (q1 < q2) ? q1 : q2;
   if (!(qold < P.q_thresh)) return false;
   VD dv = m.vd(v), dw = m.vd(w), dc = m.vd(c), dd = m.vd(d);
-  if (!(orient_c(v, d, c, dv, dd, dc) > 0.0)) return false;
-  if (!(orient_c(d, w, c, dd, dw, dc) > 0.0)) return false;
+  if (orient_sign(dv, dd, dc) <= 0) return false;
+  if (orient_sign(dd, dw, dc) <= 0) return false;
   double n1 = quality_c(v, d, c, dv, dd, dc);
   double n2 = quality_c(d, w, c, dd, dw, dc);
   double qnew = (n1 < n2) ? n1 : n2;
@@ -545,14 +620,15 @@ bool interpolate_in_ball(const OMesh& m, int v, double X, double Y, Move& mv) {
     VD d[3] = {m.vd(t[0]), m.vd(t[1]), m.vd(t[2])};
     canon(ids, d);
     // X lies in the closed element when all three sub-triangles (X replacing
-    // one vertex) are counter-clockwise or flat; its barycentric
-    // coordinates are then the sub-triangle orientations over the element's
-    // own orientation.
-    double o = orient3(d[0], d[1], d[2]);
-    double s0 = orient3(px, d[1], d[2]);
-    double s1 = orient3(d[0], px, d[2]);
-    double s2 = orient3(d[0], d[1], px);
-    if (s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0) {
+    // one vertex) are counter-clockwise or flat (exact signs); its
+    // barycentric coordinates are then the sub-triangle orientations over
+    // the element's own orientation.
+    if (orient_sign(px, d[1], d[2]) >= 0 && orient_sign(d[0], px, d[2]) >= 0 &&
+        orient_sign(d[0], d[1], px) >= 0) {
+      double o = orient3(d[0], d[1], d[2]);
+      double s0 = orient3(px, d[1], d[2]);
+      double s1 = orient3(d[0], px, d[2]);
+      double s2 = orient3(d[0], d[1], px);
       double l0 = s0 / o, l1 = s1 / o, l2 = s2 / o;
       mv.x = X;
       mv.y = Y;
@@ -576,7 +652,7 @@ bool ball_after_move(const OMesh& m, int v, const Move& mv, double& qmin, double
     const auto& t = m.tri[K];
     VD d[3];
     for (int i = 0; i < 3; ++i) d[i] = (t[i] == v) ? nv : m.vd(t[i]);
-    if (!(orient_c(t[0], t[1], t[2], d[0], d[1], d[2]) > 0.0)) return false;
+    if (orient_sign(d[0], d[1], d[2]) <= 0) return false;
     double q = quality_c(t[0], t[1], t[2], d[0], d[1], d[2]);
     if (first || q < qmin) qmin = q;
     first = false;
@@ -1066,7 +1142,7 @@ int check_invariants(const OMesh& m) {
       out[t[i]].push_back(t[(i + 1) % 3]);
     }
     VD d0 = m.vd(t[0]), d1 = m.vd(t[1]), d2 = m.vd(t[2]);
-    if (!(orient_c(t[0], t[1], t[2], d0, d1, d2) > 0.0)) return 16;
+    if (orient_sign(d0, d1, d2) <= 0) return 16;
   }
   for (int v = 0; v < m.nv(); ++v) {
     std::vector<int> o = out[v];
@@ -1127,6 +1203,14 @@ double now_ms() {
 // ---------------------------------------------------------------------------
 
 extern "C" {
+
+// Exact orientation sign of (p, q, r), pts = {px, py, qx, qy, rx, ry}.
+int32_t or_orient_sign(const double* pts) {
+  VD p{pts[0], pts[1], 0.0, 0.0, 0.0}, q{pts[2], pts[3], 0.0, 0.0, 0.0},
+      r{pts[4], pts[5], 0.0, 0.0, 0.0};
+  return orient_sign(p, q, r);
+}
+
 
 typedef struct OMesh or_mesh;
 
@@ -1191,7 +1275,7 @@ or_mesh* or_create(const double* xy, int32_t nv, const int32_t* tri, int32_t ne,
       continue;
     }
     int lo = bn[0] < bn[1] ? bn[0] : bn[1], hi = bn[0] < bn[1] ? bn[1] : bn[0];
-    m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) != 0.0 ? 1 : 0;
+    m->vcorner[v] = orient_sign(m->vd(lo), m->vd(v), m->vd(hi)) != 0 ? 1 : 0;
   }
   m->euler0 = euler_characteristic(*m);
   int inv = check_invariants(*m);

@@ -274,6 +274,14 @@ __device__ __forceinline__ VD load_vd(const Store& S, int slot) {
   return VD{p.x, p.y, m.x, m.y, m.z};
 }
 
+// The position alone, read again through L2 (ld.global.cg, never merged
+// with an earlier load): for rarely taken branches that need coordinates the
+// hot path no longer holds in registers.
+__device__ __forceinline__ VD load_xy_again(const Store& S, int slot) {
+  const double2 p = __ldcg(&S.xy[slot]);
+  return VD{p.x, p.y, 0.0, 0.0, 0.0};
+}
+
 // Metric length of edge (a,b) under the mean of the end-point metrics.
 __device__ __forceinline__ double metric_len(const VD& a, const VD& b) {
   double e00 = 0.5 * (a.m00 + b.m00);
@@ -330,7 +338,9 @@ __device__ __forceinline__ double orient3(const VD& p, const VD& q, const VD& r)
   return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);
 }
 
-// Rotate (i0,i1,i2) so that the smallest id comes first (cyclic order kept).
+// Rotate (i0,i1,i2) so that the smallest id comes first (cyclic order kept):
+// orientation values (areas, barycentric weights) and qualities are taken in
+// this rotation, so they do not depend on how an element is stored.
 __device__ __forceinline__ void canon(int& i0, int& i1, int& i2, VD& a, VD& b, VD& c) {
   if (i1 < i0 && i1 < i2) {
     int t = i0; i0 = i1; i1 = i2; i2 = t;
@@ -341,9 +351,138 @@ __device__ __forceinline__ void canon(int& i0, int& i1, int& i2, VD& a, VD& b, V
   }
 }
 
-__device__ __forceinline__ double orient_c(int i0, int i1, int i2, VD a, VD b, VD c) {
-  canon(i0, i1, i2, a, b, c);
-  return orient3(a, b, c);
+// ---------------------------------------------------------------------------
+// Exact orientation sign.  Every validity decision (an element
+// counter-clockwise, a point in the closed element, a corner) takes the sign
+// of det = (q.x - p.x)(r.y - p.y) - (q.y - p.y)(r.x - p.x) of the real
+// numbers the doubles stand for, so it depends neither on rounding nor on the
+// rotation the triangle is taken in.  A floating-point filter decides when
+// |det| clearly exceeds 8 eps (|t1| + |t2|) (eps = 2^-53; the rounding error
+// of this form is at most (3 + 16 eps) eps (|t1| + |t2|): J. R. Shewchuk,
+// "Adaptive precision floating-point arithmetic and fast robust geometric
+// predicates", 1997); otherwise det is summed exactly.  Exact while no product or error
+// underflows or overflows (coordinates zero or of magnitude 1e-140..1e140).
+// ---------------------------------------------------------------------------
+
+// a + b = s + e exactly (Knuth's two-sum; round to nearest, no contraction)
+__device__ __forceinline__ void exact_add(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
+}
+
+// det as an exact sum: each difference is its rounded value plus its error
+// (two-sum of a and -b), each of the eight partial products is its rounded
+// value plus its error (fused multiply-add), and the sixteen terms are added
+// one by one into a list of non-overlapping parts of increasing magnitude
+// (each addition a chain of two-sums, zero parts dropped); the sign of the
+// sum is the sign of its largest part.  Rarely taken, kept out of line.
+static __device__ __noinline__ int orient_sign_exact(double px, double py, double qx, double qy,
+                                              double rx, double ry) {
+  double a[2], b[2], c[2], d[2];
+  exact_add(qx, -px, a[0], a[1]);
+  exact_add(ry, -py, b[0], b[1]);
+  exact_add(qy, -py, c[0], c[1]);
+  exact_add(rx, -px, d[0], d[1]);
+  double part[32];
+  int n = 0;
+  for (int k = 0; k < 16; ++k) {
+    const int i = (k >> 2) & 1, j = (k >> 1) & 1;
+    const bool second = k & 1;  // the product's error rather than its value
+    const bool cd = k >= 8;     // the subtracted product c * d
+    const double x = cd ? c[i] : a[i], y = cd ? d[j] : b[j];
+    const double pr = x * y;
+    double term = second ? __fma_rn(x, y, -pr) : pr;
+    if (cd) term = -term;
+    double q = term;
+    int m = 0;
+    for (int u = 0; u < n; ++u) {
+      double sum, err;
+      exact_add(q, part[u], sum, err);
+      if (err != 0.0) part[m++] = err;
+      q = sum;
+    }
+    if (q != 0.0) part[m++] = q;
+    n = m;
+  }
+  if (n == 0) return 0;
+  return part[n - 1] > 0.0 ? 1 : -1;
+}
+
+// Sign of a double on its bit pattern (-0 and +0 give 0): integer ALUs.
+__device__ __forceinline__ int dsign(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b << 1) == 0ull ? 0 : ((b >> 63) ? -1 : 1);
+}
+
+// Sign of a * b - c * d for exact doubles a, b, c, d: each product is its
+// rounded value plus its error (fused multiply-add), so the difference is
+// the exact sum p1 + e1 - p2 - e2.  (e1, p1) is already a non-overlapping
+// pair of increasing magnitude; -e2 and then -p2 are added by chains of
+// two-sums, leaving four non-overlapping parts (zeros allowed among them)
+// whose largest non-zero part carries the sign.  All in registers.
+__device__ __forceinline__ int sign_of_product_difference(double a, double b, double c, double d) {
+  const double p1 = a * b, e1 = __fma_rn(a, b, -p1);
+  const double p2 = c * d, e2 = __fma_rn(c, d, -p2);
+  double s, h0, h1, h2, h3;
+  exact_add(-e2, e1, s, h0);
+  exact_add(s, p1, h2, h1);
+  exact_add(-p2, h0, s, h0);
+  exact_add(s, h1, s, h1);
+  exact_add(s, h2, h3, h2);
+  const int s3 = dsign(h3), s2 = dsign(h2), s1 = dsign(h1);
+  return s3 != 0 ? s3 : (s2 != 0 ? s2 : (s1 != 0 ? s1 : dsign(h0)));
+}
+
+// Error of the rounded difference s = RN(a - b): a - b = s + e exactly.
+// Dekker's fast two-sum on the operand of larger magnitude first (chosen on
+// the bit patterns): two FP64 operations instead of the six of Knuth's form.
+__device__ __forceinline__ double diff_error(double a, double b, double s) {
+  const bool abig = ((unsigned long long)__double_as_longlong(a) << 1) >=
+                    ((unsigned long long)__double_as_longlong(b) << 1);
+  const double x = abig ? a : -b, y = abig ? -b : a;
+  return y - (s - x);
+}
+
+// Biased exponent field of a double (0 for zero and subnormals).
+__device__ __forceinline__ int dexp(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFull);
+}
+
+// The filter: +1 or -1 when the rounded determinant decides the sign, 0 when
+// it cannot (then orient_resolve gives the exact sign).  Decided when det is
+// normal and its exponent is at least max(exponent(t1), exponent(t2)) - 48:
+// then |det| >= 2^(e_det - 1023) >= 2^(e_max - 1071) > 2^-50 * 2 max(|t1|, |t2|)
+// >= 8 eps (|t1| + |t2|), beyond the rounding error bound.  Only the seven
+// FP64 operations of det itself; the test and the sign use integer ALUs.
+__device__ __forceinline__ int orient_filter(const VD& p, const VD& q, const VD& r) {
+  const double t1 = (q.x - p.x) * (r.y - p.y);
+  const double t2 = (q.y - p.y) * (r.x - p.x);
+  const double det = t1 - t2;
+  const int ed = dexp(det);
+  if (ed > 0 && ed + 48 >= max(dexp(t1), dexp(t2))) return __double_as_longlong(det) < 0 ? -1 : 1;
+  return 0;
+}
+
+// Exact sign where the filter cannot decide: when the four coordinate
+// differences are exact (their two-sum errors zero, the usual case for nearly
+// or exactly collinear points close together) the exact sign of the
+// two-product difference above, else the full sixteen-term sum.
+__device__ __forceinline__ int orient_resolve(const VD& p, const VD& q, const VD& r) {
+  const double ax = q.x - p.x, by = r.y - p.y, ay = q.y - p.y, bx = r.x - p.x;
+  const unsigned long long tails =
+      (unsigned long long)(__double_as_longlong(diff_error(q.x, p.x, ax)) |
+                           __double_as_longlong(diff_error(r.y, p.y, by)) |
+                           __double_as_longlong(diff_error(q.y, p.y, ay)) |
+                           __double_as_longlong(diff_error(r.x, p.x, bx)));
+  if ((tails << 1) == 0ull) return sign_of_product_difference(ax, by, ay, bx);
+  return orient_sign_exact(p.x, p.y, q.x, q.y, r.x, r.y);
+}
+
+// Sign of the exact determinant (-1, 0, +1).
+__device__ __forceinline__ int orient_sign(const VD& p, const VD& q, const VD& r) {
+  const int f = orient_filter(p, q, r);
+  return f != 0 ? f : orient_resolve(p, q, r);
 }
 
 constexpr double QC = 12.0 * 1.7320508075688772;  // 12 sqrt(3)

@@ -308,7 +308,7 @@ __global__ void k_corners(Store S, int given) {
       } else {
         int lo = bn[0] < bn[1] ? bn[0] : bn[1];
         int hi = bn[0] < bn[1] ? bn[1] : bn[0];
-        c = orient3(load_vd(S, vb + lo), load_vd(S, s), load_vd(S, vb + hi)) != 0.0;
+        c = orient_sign(load_vd(S, vb + lo), load_vd(S, s), load_vd(S, vb + hi)) != 0;
       }
     }
     S.vflag[s] = (uint8_t)((f & ~VF_CORNER) | (c ? VF_CORNER : 0));
@@ -328,8 +328,7 @@ __global__ void k_validate_elems(Store S, DevStatus* st) {
       set_err(st, PM_ERR_INVALID_MESH);
       continue;
     }
-    if (!(orient_c(e.x, e.y, e.z, load_vd(S, vb + e.x), load_vd(S, vb + e.y),
-                   load_vd(S, vb + e.z)) > 0.0))
+    if (orient_sign(load_vd(S, vb + e.x), load_vd(S, vb + e.y), load_vd(S, vb + e.z)) <= 0)
       set_err(st, PM_ERR_INVALID_MESH);
   }
 }

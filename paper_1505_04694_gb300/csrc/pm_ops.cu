@@ -344,14 +344,10 @@ __device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band, unsigne
       if (k >= x.nel) break;
       int4 e = S.EN[x.c.eb + x.ne[k]];
       if (e.x == u || e.y == u || e.z == u) continue;
-      int i0 = e.x, i1 = e.y, i2 = e.z;
-      VD d0 = (i0 == x.lv) ? dw : load_vd(S, x.c.vb + i0);
-      VD d1 = (i1 == x.lv) ? dw : load_vd(S, x.c.vb + i1);
-      VD d2 = (i2 == x.lv) ? dw : load_vd(S, x.c.vb + i2);
-      if (i0 == x.lv) i0 = u;
-      if (i1 == x.lv) i1 = u;
-      if (i2 == x.lv) i2 = u;
-      ok &= dgt(orient_c(i0, i1, i2, d0, d1, d2), 0.0);
+      VD d0 = (e.x == x.lv) ? dw : load_vd(S, x.c.vb + e.x);
+      VD d1 = (e.y == x.lv) ? dw : load_vd(S, x.c.vb + e.y);
+      VD d2 = (e.z == x.lv) ? dw : load_vd(S, x.c.vb + e.z);
+      ok &= orient_sign(d0, d1, d2) > 0;
       ops += kOpsOrient;
     }
   }
@@ -395,14 +391,10 @@ __device__ bool tile_collapse_valid(const Tile& t, const CoarsenCtx& x, int u, d
   for (int k = t.tl; k < x.nel; k += TW) {
     int4 e = S.EN[x.c.eb + x.ne[k]];
     if (e.x == u || e.y == u || e.z == u) continue;
-    int i0 = e.x, i1 = e.y, i2 = e.z;
-    VD d0 = (i0 == x.lv) ? dw : load_vd(S, x.c.vb + i0);
-    VD d1 = (i1 == x.lv) ? dw : load_vd(S, x.c.vb + i1);
-    VD d2 = (i2 == x.lv) ? dw : load_vd(S, x.c.vb + i2);
-    if (i0 == x.lv) i0 = u;
-    if (i1 == x.lv) i1 = u;
-    if (i2 == x.lv) i2 = u;
-    ok &= dgt(orient_c(i0, i1, i2, d0, d1, d2), 0.0);
+    VD d0 = (e.x == x.lv) ? dw : load_vd(S, x.c.vb + e.x);
+    VD d1 = (e.y == x.lv) ? dw : load_vd(S, x.c.vb + e.y);
+    VD d2 = (e.z == x.lv) ? dw : load_vd(S, x.c.vb + e.z);
+    ok &= orient_sign(d0, d1, d2) > 0;
     ops += kOpsOrient;
   }
   if (!tall(t, ok)) return false;
@@ -988,25 +980,34 @@ __device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, c
   double qold = dlt(q1, q2) ? q1 : q2;
   VD dv = load_vd(S, c.vb + lv), dw = load_vd(S, c.vb + w), dc = load_vd(S, c.vb + cc),
      dd = load_vd(S, c.vb + d);
-  double gain = -1.0;
-  bool o1 = dgt(orient_c(lv, d, cc, dv, dd, dc), 0.0);
+  // The gain is -1 unless all four hold: (v, d, c) and (d, w, c)
+  // counter-clockwise, n1 > qold, n2 > qold.  A conjunction may be decided in
+  // any order: the orientation filters first (a decided negative sign ends
+  // it), then the qualities, and only then the exact sign of an orientation
+  // the filter left open (nearly or exactly collinear points, whose element
+  // has quality near zero and so has almost always failed by then).  Every
+  // test is still made before a gain is returned, so the result is the one
+  // of the order orientations-then-qualities whatever the values.
+  const int s1 = orient_filter(dv, dd, dc);
   ops += kOpsOrient;
-  if (o1 && dgt(orient_c(d, w, cc, dd, dw, dc), 0.0)) {
-    ops += kOpsOrient + kOpsQuality;
-    // gain = min(n1, n2) - qold > 0 exactly when both exceed qold
-    double n1 = quality_c(lv, d, cc, dv, dd, dc);
-    if (dgt(n1, qold)) {
-      ops += kOpsQuality;
-      double n2 = quality_c(d, w, cc, dd, dw, dc);
-      if (dgt(n2, qold)) {
-        gain = (dlt(n1, n2) ? n1 : n2) - qold;
-        ops += 1;
-      }
-    }
-  } else if (o1) {
-    ops += kOpsOrient;
+  if (s1 < 0) return -1.0;
+  const int s2 = orient_filter(dd, dw, dc);
+  ops += kOpsOrient;
+  if (s2 < 0) return -1.0;
+  ops += kOpsQuality;
+  const double n1 = quality_c(lv, d, cc, dv, dd, dc);
+  if (!dgt(n1, qold)) return -1.0;
+  ops += kOpsQuality;
+  const double n2 = quality_c(d, w, cc, dd, dw, dc);
+  if (!dgt(n2, qold)) return -1.0;
+  if (s1 == 0 || s2 == 0) {
+    const VD pv = load_xy_again(S, c.vb + lv), pw = load_xy_again(S, c.vb + w),
+             pc = load_xy_again(S, c.vb + cc), pd = load_xy_again(S, c.vb + d);
+    if (s1 == 0 && orient_resolve(pv, pd, pc) <= 0) return -1.0;
+    if (s2 == 0 && orient_resolve(pd, pw, pc) <= 0) return -1.0;
   }
-  return gain;
+  ops += 1;
+  return (dlt(n1, n2) ? n1 : n2) - qold;
 }
 
 // An edge both of whose end points are evaluated this round is listed from
@@ -1510,11 +1511,22 @@ __device__ bool tile_interpolate(const Tile& t, const Store& S, MeshCtx c, const
       b = load_vd(S, c.vb + i1);
       d = load_vd(S, c.vb + i2);
       canon(i0, i1, i2, a, b, d);
-      o = orient3(a, b, d);
-      s0 = orient3(px, b, d);
-      s1 = orient3(a, px, d);
-      s2 = orient3(a, b, px);
-      inside = dge0(s0) && dge0(s1) && dge0(s2);
+      // filters first; a lane with a sign left open (X on or near an edge
+      // line) resolves it exactly below, all such lanes in one pass per sign
+      int f0 = orient_filter(px, b, d), f1 = orient_filter(a, px, d), f2 = orient_filter(a, b, px);
+      while ((f0 | f1 | f2) >= 0 && (f0 == 0 || f1 == 0 || f2 == 0)) {
+        const int j = f0 == 0 ? 0 : (f1 == 0 ? 1 : 2);
+        const int r = orient_resolve(j == 0 ? px : a, j == 1 ? px : b, j == 2 ? px : d);
+        const int fr = r == 0 ? 2 : r;  // decided: an exact zero counts as inside
+        if (j == 0) f0 = fr; else if (j == 1) f1 = fr; else f2 = fr;
+      }
+      inside = f0 > 0 && f1 > 0 && f2 > 0;
+      if (inside) {
+        o = orient3(a, b, d);
+        s0 = orient3(px, b, d);
+        s1 = orient3(a, px, d);
+        s2 = orient3(a, b, px);
+      }
     }
     unsigned bal = (__ballot_sync(t.mask, inside) >> t.shift) & 0xFFu;
     if (bal) {
@@ -1550,7 +1562,7 @@ __device__ bool tile_ball_after_move(const Tile& t, const Store& S, MeshCtx c, i
       VD a = (e.x == lv) ? nvd : load_vd(S, c.vb + e.x);
       VD b = (e.y == lv) ? nvd : load_vd(S, c.vb + e.y);
       VD d = (e.z == lv) ? nvd : load_vd(S, c.vb + e.z);
-      if (dgt(orient_c(e.x, e.y, e.z, a, b, d), 0.0)) {
+      if (orient_sign(a, b, d) > 0) {
         q = quality_c(e.x, e.y, e.z, a, b, d);
         if (strict ? !dgt(q, floor) : dlt(q, floor)) ok = false;
         if (qout) qout[k] = q;

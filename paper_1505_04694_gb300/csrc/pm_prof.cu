@@ -49,6 +49,17 @@ __global__ void k_selftest_div3(const double* x, double* out, long long n) {
     out[i] = div3(x[i]);
 }
 
+// Test support: out[i] = exact orientation sign of points pts[6i .. 6i+5]
+// = (px, py, qx, qy, rx, ry), the predicate every validity decision uses.
+__global__ void k_selftest_orient(const double* pts, int* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double* t = pts + 6 * i;
+    VD p{t[0], t[1], 0.0, 0.0, 0.0}, q{t[2], t[3], 0.0, 0.0, 0.0}, r{t[4], t[5], 0.0, 0.0, 0.0};
+    out[i] = orient_sign(p, q, r);
+  }
+}
+
 }  // namespace
 
 int prof_begin(const char* name, cudaStream_t s) {
@@ -139,6 +150,16 @@ pm_status pm_selftest_div3_dev(const double* x, double* out, int64_t n, void* st
   if (blocks > 152 * 16) blocks = 152 * 16;
   PM_LAUNCH(k_selftest_div3, dim3((unsigned)blocks), dim3(256), 0, (cudaStream_t)stream, x, out,
             (long long)n);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+}
+
+pm_status pm_selftest_orient_dev(const double* pts, int32_t* out, int64_t n, void* stream) {
+  if (!pts || !out || n < 0) return PM_ERR_INVALID_ARG;
+  if (n == 0) return PM_OK;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  PM_LAUNCH(k_selftest_orient, dim3((unsigned)blocks), dim3(256), 0, (cudaStream_t)stream, pts,
+            out, (long long)n);
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
 }
 

@@ -33,7 +33,7 @@ EXPORTS = ["pm_mesh_create", "pm_mesh_create_dev", "pm_mesh_destroy", "pm_set_st
            "pm_fp64_peak", "pm_selftest_wait_timeout", "pm_selftest_div3_dev",
            "pm_batch_create", "pm_batch_create_dev", "pm_batch_size", "pm_batch_adapt",
            "pm_batch_get_mesh", "pm_batch_get_mesh_dev", "pm_set_tuning", "pm_get_tuning",
-           "pm_tuning_load", "pm_tuning_source", "pm_build_id"]
+           "pm_tuning_load", "pm_tuning_source", "pm_build_id", "pm_selftest_orient_dev"]
 
 
 class PmParams(C.Structure):
@@ -123,6 +123,8 @@ def _load():
     L.pm_selftest_wait_timeout.restype = C.c_int
     L.pm_selftest_div3_dev.argtypes = [vp, vp, C.c_int64, vp]
     L.pm_selftest_div3_dev.restype = C.c_int
+    L.pm_selftest_orient_dev.argtypes = [vp, vp, C.c_int64, vp]
+    L.pm_selftest_orient_dev.restype = C.c_int
     L.pm_set_tuning.argtypes = [C.POINTER(PmTuning)]
     L.pm_set_tuning.restype = C.c_int
     L.pm_get_tuning.argtypes = [C.POINTER(PmTuning)]
@@ -577,3 +579,10 @@ def tuning_source():
 
 def build_id():
     return lib.pm_build_id().decode()
+
+
+def selftest_orient_dev(pts, out, stream=0):
+    """out[i] = exact orientation sign of pts[i] = (px, py, qx, qy, rx, ry) on the
+    device (pts: (n, 6) float64 CUDA tensor, out: (n,) int32 CUDA tensor)."""
+    _check(lib.pm_selftest_orient_dev(C.c_void_p(pts.data_ptr()), C.c_void_p(out.data_ptr()),
+                                      pts.shape[0], C.c_void_p(stream)), "pm_selftest_orient_dev")

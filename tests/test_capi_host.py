@@ -54,6 +54,7 @@ def test_argument_checks_need_no_device(pm):
         assert pm.lib.pm_selftest_wait_timeout(bad, C.byref(st32), C.byref(ms)) == 1
     assert pm.lib.pm_selftest_div3_dev(None, None, 4, None) == 1
     assert pm.lib.pm_selftest_div3_dev(C.c_void_p(16), C.c_void_p(32), -1, None) == 1
+    assert pm.lib.pm_selftest_orient_dev(None, None, 4, None) == 1
 
 
 def test_out_of_range_ids_rejected_on_host(pm):

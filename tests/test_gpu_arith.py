@@ -1,4 +1,5 @@
-"""Device arithmetic against IEEE binary64 on the host.
+"""Device arithmetic against IEEE binary64 on the host, and the device's
+exact orientation sign against the oracle's and rational arithmetic.
 
 The quality functional (Sec. 2.2) takes means of three terms: the oracle
 divides by 3.0; the library forms the same quotient by Markstein's
@@ -60,3 +61,28 @@ def test_division_by_three_is_the_ieee_quotient():
     # third of all doubles: the sample does tell the two apart
     approx = x[~nan] * (1.0 / 3.0)
     assert np.count_nonzero(approx.view(np.uint64) != want[~nan].view(np.uint64)) > 1_000_000
+
+
+def test_orientation_sign_is_exact_on_the_device():
+    """The device predicate behind every validity decision gives the sign of
+    the exact determinant (rational arithmetic) and the oracle's sign, on
+    nearly collinear triples (some far from the origin, where the rounded
+    formula is often wrong), general and exactly collinear ones."""
+    from oracle import oracle as O
+    from tests.test_oracle_pins import _exact_orient, _orient_cases
+
+    cases = _orient_cases(3000, 91)
+    pts = np.array([[*p, *q, *r] for p, q, r in cases], dtype=np.float64)
+    dev = torch.device("cuda:0")
+    pd = torch.from_numpy(pts).to(dev)
+    od = torch.empty(pts.shape[0], dtype=torch.int32, device=dev)
+    pm.selftest_orient_dev(pd, od)
+    torch.cuda.synchronize(dev)
+    got = od.cpu().numpy()
+    wrong = 0
+    for i, (p, q, r) in enumerate(cases):
+        e = _exact_orient(p, q, r)
+        assert got[i] == e == O.orient_sign(p, q, r), (i, got[i], e)
+        naive = float((q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0]))
+        wrong += int((naive > 0) - (naive < 0) != e)
+    assert wrong > 50

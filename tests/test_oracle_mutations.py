@@ -28,6 +28,18 @@ PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 
 # (what, text in the oracle, planted text, pins that must fail)
 MUTATIONS = [
+    ("orientation sign: the rounded formula decides every case",
+     "const double ORIENT_FILTER = 8.0 * 1.1102230246251565e-16;  // 8 eps",
+     "const double ORIENT_FILTER = 0.0;  // 8 eps",
+     "orient_sign_exact"),
+    ("orientation sign: product errors left out of the exact sum",
+     "      n = grow_expansion(e, n, std::fma(a[i], b[j], -pr));",
+     "      n = grow_expansion(e, n, 0.0);",
+     "orient_sign_exact"),
+    ("orientation sign: difference errors left out of the exact sum",
+     "  two_diff(q.x, p.x, a[0], a[1]);",
+     "  two_diff(q.x, p.x, a[0], a[1]);\n  a[1] = 0.0;",
+     "orient_sign_exact"),
     ("metric length: off-diagonal term not doubled",
      "double L2 = ((e00 * dx) * dx + ((2.0 * e01) * dx) * dy) + (e11 * dy) * dy;",
      "double L2 = ((e00 * dx) * dx + (e01 * dx) * dy) + (e11 * dy) * dy;",
@@ -141,8 +153,8 @@ MUTATIONS = [
      "    double X = m.x[v] + alpha * gy;",
      "step_rule"),
     ("boundary: corner test inverted",
-     "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) != 0.0 ? 1 : 0;",
-     "m->vcorner[v] = orient3(m->vd(lo), m->vd(v), m->vd(hi)) == 0.0 ? 1 : 0;",
+     "m->vcorner[v] = orient_sign(m->vd(lo), m->vd(v), m->vd(hi)) != 0 ? 1 : 0;",
+     "m->vcorner[v] = orient_sign(m->vd(lo), m->vd(v), m->vd(hi)) == 0 ? 1 : 0;",
      "collapse_rule_brute_force"),
 ]
 

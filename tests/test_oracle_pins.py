@@ -875,3 +875,54 @@ def test_psi_metric_hits_target_estimate():
     assert abs(n / 1.0e5 - 1) < 1e-6
     det = w.m[:, 0] * w.m[:, 2] - w.m[:, 1] ** 2
     assert (w.m[:, 0] > 0).all() and (det > 0).all()
+
+
+# --- exact orientation signs (reading S3 with robust predicates) -------------
+
+def _exact_orient(p, q, r):
+    from fractions import Fraction as F
+
+    px, py, qx, qy, rx, ry = (F(float(v)) for v in (*p, *q, *r))
+    d = (qx - px) * (ry - py) - (qy - py) * (rx - px)
+    return (d > 0) - (d < 0)
+
+
+def _orient_cases(n, seed):
+    """Nearly collinear triples (r on the line through p and q, rounded, then a
+    few units in the last place off it), some far from the origin where the
+    differences themselves round; general triples; exactly collinear ones."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        scale = 10.0 ** float(rng.integers(-3, 3))
+        offset = (10.0 ** float(rng.integers(0, 9))) * rng.uniform(-1, 1, 2) * rng.integers(0, 2)
+        p = rng.uniform(-1, 1, 2) * scale + offset
+        q = rng.uniform(-1, 1, 2) * scale + offset
+        r = p + rng.uniform(-2, 2) * (q - p)
+        for k in range(2):
+            for _ in range(int(rng.integers(0, 3))):
+                r[k] = np.nextafter(r[k], np.inf if rng.integers(0, 2) else -np.inf)
+        out.append((p, q, r))
+    for _ in range(n // 4):
+        out.append(tuple(rng.uniform(-1, 1, (3, 2))))
+    out += [((0.0, 0.0), (1.0, 1.0), (2.0, 2.0)), ((0.1, 0.3), (0.2, 0.3), (0.7, 0.3)),
+            ((0.25, 0.5), (0.25, 0.75), (0.25, 0.125)), ((1.0, 2.0), (1.0, 2.0), (3.0, 5.0))]
+    return out
+
+
+def test_orient_sign_exact():
+    """The oracle's orientation sign equals the sign of the exact determinant
+    of the doubles (rational arithmetic), is invariant under rotation and
+    flips under a swap; the sample holds many triples whose rounded formula
+    gives the wrong sign, and exactly collinear ones (sign 0)."""
+    wrong, zeros = 0, 0
+    for p, q, r in _orient_cases(3000, 77):
+        e = _exact_orient(p, q, r)
+        assert O.orient_sign(p, q, r) == e, (p, q, r)
+        assert O.orient_sign(q, r, p) == e and O.orient_sign(r, p, q) == e
+        assert O.orient_sign(q, p, r) == -e
+        naive = float((q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0]))
+        wrong += int((naive > 0) - (naive < 0) != e)
+        zeros += e == 0
+    assert wrong > 50, wrong
+    assert zeros >= 4, zeros
