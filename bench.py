@@ -150,7 +150,7 @@ def measured_peaks():
 # (+ - * / sqrt, one each) along the paths the kernel took, counted by the
 # kernel while profiled.
 ROOFLINE_CANDIDATES = ("k_swap_rounds", "k_smooth_rounds", "k_coarsen_rounds", "k_smooth_eval",
-                       "k_swap_edge")
+                       "k_coarsen_check", "k_swap_edge")
 FP64_RESULTS_PER_CYCLE = 304
 
 

@@ -307,62 +307,29 @@ struct CoarsenCtx {
 
 __device__ __forceinline__ double S_L_up(const CoarsenCtx& x) { return x.S->tab.L_up[x.c.mi]; }
 
-// Validity of collapsing v onto local neighbour u: link condition, all
-// remaining ball elements counter-clockwise, no new edge longer than L_up.
-__device__ bool collapse_valid(const CoarsenCtx& x, int u, double4 band, unsigned& ops) {
-  const double L_up = S_L_up(x);
-  const Store& S = *x.S;
-  bool bedge = count_elems_with(S, x.ne, x.nel, x.c.eb, u) == 1;
+// The integer part of the validity of collapsing v onto local neighbour u:
+// the link condition (|NN(v) & NN(u)| = 2 for an interior edge, 1 for a
+// boundary edge; a boundary vertex only along a boundary edge).
+__device__ bool collapse_link(const Store& S, const CoarsenCtx& x, int u) {
+  const bool bedge = count_elems_with(S, x.ne, x.nel, x.c.eb, u) == 1;
   if (x.bnd && !bedge) return false;
-  int ws = x.c.vb + u;
+  const int ws = x.c.vb + u;
   const int* nnw = nn_row(S, ws);
-  int nnwl = S.NNlen[ws];
-  int common = 0;
-  {
-    int a = 0, b = 0;
-    while (a < x.nnl && b < nnwl) {
-      int p = x.nn[a], q = nnw[b];
-      if (p == q) {
-        ++common;
-        ++a;
-        ++b;
-      } else if (p < q) {
-        ++a;
-      } else {
-        ++b;
-      }
+  const int nnwl = S.NNlen[ws];
+  int common = 0, a = 0, b = 0;
+  while (a < x.nnl && b < nnwl) {
+    const int p = x.nn[a], q = nnw[b];
+    if (p == q) {
+      ++common;
+      ++a;
+      ++b;
+    } else if (p < q) {
+      ++a;
+    } else {
+      ++b;
     }
   }
-  if (common != (bedge ? 1 : 2)) return false;
-  VD dw = load_vd(S, ws);
-  // every test below is evaluated (no early exit inside a group of four) so
-  // that the loads of a group overlap
-  bool ok = true;
-  for (int k0 = 0; k0 < x.nel && ok; k0 += 4) {
-#pragma unroll
-    for (int k = k0; k < k0 + 4; ++k) {
-      if (k >= x.nel) break;
-      int4 e = S.EN[x.c.eb + x.ne[k]];
-      if (e.x == u || e.y == u || e.z == u) continue;
-      VD d0 = (e.x == x.lv) ? dw : load_vd(S, x.c.vb + e.x);
-      VD d1 = (e.y == x.lv) ? dw : load_vd(S, x.c.vb + e.y);
-      VD d2 = (e.z == x.lv) ? dw : load_vd(S, x.c.vb + e.z);
-      ok &= orient_sign(d0, d1, d2) > 0;
-      ops += kOpsOrient;
-    }
-  }
-  if (!ok) return false;
-  for (int k0 = 0; k0 < x.nnl && ok; k0 += 4) {
-#pragma unroll
-    for (int k = k0; k < k0 + 4; ++k) {
-      if (k >= x.nnl) break;
-      int y = x.nn[k];
-      if (y == u || row_has(nnw, nnwl, y)) continue;
-      ok &= !len_gt(metric_len2(dw, load_vd(S, x.c.vb + y)), band.z, band.w, L_up);
-      ops += kOpsLen2;
-    }
-  }
-  return ok;
+  return common == (bedge ? 1 : 2);
 }
 
 // collapse_valid with the lanes of a tile splitting v's ball elements (the
@@ -535,33 +502,153 @@ __global__ void k_coarsen_scan(Store S, const int* D, const int* nDp, int* targe
 
 // The check passes stay one thread per item: a check is a short chain of
 // dependent loads, and eight items per warp left too little in flight.
+// The check passes, one work item (v, k) per thread: is collapsing v onto
+// its k-th candidate valid (in the last pass: the first valid one from k on)?
+// Validity is the conjunction of the link condition and, for the collapse
+// with v on u, every remaining ball element counter-clockwise and no new edge
+// longer than L_up (collapse_valid below, tile form).  Balls differ in size
+// and most tests need no arithmetic (elements containing u, neighbours
+// shared with u), so the FP64 tests of a warp's items are queued in shared
+// memory per warp, orientations and lengths apart, and evaluated 32 at a
+// time: full warps on the FP64 pipe instead of the lanes whose own loop is
+// still running.  Any failed test clears the owner's flag; the conjunction
+// does not depend on the order of its tests.
+constexpr int kCheckWarps = 8;
+
+struct CheckQueues {
+  int4* qo;  // orientations: (owner lane, element's local vertex ids)
+  int2* ql;  // lengths: (owner lane, neighbour's local id)
+  int* ok;   // per lane of the warp: its item's conjunction so far
+};
+
+// Evaluate the first `cnt` (<= 32) queued orientations; all lanes call.
+__device__ __forceinline__ void check_orient_chunk(const Store& S, const CheckQueues& Q, int cnt,
+                                                   int vb, int lv, int ws, unsigned& ops) {
+  const int lane = threadIdx.x & 31;
+  const int4 r = lane < cnt ? Q.qo[lane] : make_int4(lane, 0, 0, 0);
+  const int o_vb = __shfl_sync(0xffffffffu, vb, r.x);
+  const int o_lv = __shfl_sync(0xffffffffu, lv, r.x);
+  const int o_ws = __shfl_sync(0xffffffffu, ws, r.x);
+  if (lane < cnt) {
+    const VD dw = load_vd(S, o_ws);
+    const VD d0 = (r.y == o_lv) ? dw : load_vd(S, o_vb + r.y);
+    const VD d1 = (r.z == o_lv) ? dw : load_vd(S, o_vb + r.z);
+    const VD d2 = (r.w == o_lv) ? dw : load_vd(S, o_vb + r.w);
+    if (orient_sign(d0, d1, d2) <= 0) Q.ok[r.x] = 0;
+    ops += kOpsOrient;
+  }
+}
+
+// Evaluate the first `cnt` (<= 32) queued new-edge lengths; all lanes call.
+__device__ __forceinline__ void check_len_chunk(const Store& S, const CheckQueues& Q, int cnt,
+                                                int vb, int ws, int mi, unsigned& ops) {
+  const int lane = threadIdx.x & 31;
+  const int2 r = lane < cnt ? Q.ql[lane] : make_int2(lane, 0);
+  const int o_vb = __shfl_sync(0xffffffffu, vb, r.x);
+  const int o_ws = __shfl_sync(0xffffffffu, ws, r.x);
+  const int o_mi = __shfl_sync(0xffffffffu, mi, r.x);
+  if (lane < cnt) {
+    const double4 band = S.tab.band[o_mi];
+    const double L_up = S.tab.L_up[o_mi];
+    if (len_gt(metric_len2(load_vd(S, o_ws), load_vd(S, o_vb + r.y)), band.z, band.w, L_up))
+      Q.ok[r.x] = 0;
+    ops += kOpsLen2;
+  }
+}
+
 __device__ __forceinline__ void coarsen_check_phase(Store S, const int2* Win, const int* nWin,
                                                     int2* Wout, int* nWout, int* target,
                                                     const int* cand, const int* ncand, int* C,
-                                                    int* nC, int* cmark, int tag, int last) {
+                                                    int* nC, int* cmark, int tag, int last,
+                                                    unsigned long long* work) {
+  __shared__ int4 sqo[kCheckWarps][64];
+  __shared__ int2 sql[kCheckWarps][64];
+  __shared__ int sok[kCheckWarps][32];
+  const int lane = threadIdx.x & 31, wq = (threadIdx.x >> 5) % kCheckWarps;
+  CheckQueues Q{sqo[wq], sql[wq], sok[wq]};
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned ops = 0;
   const int n = *nWin;
   for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    int i = i0 + threadIdx.x;
-    int v = 0;
-    bool found = false, next = false;
-    int k = 0;
-    if (i < n) {
-      int2 it = Win[i];
+    const int i = i0 + threadIdx.x;
+    int v = 0, k = 0, nc = 0;
+    bool found = false, done = i >= n;
+    CoarsenCtx x{};
+    const int* cv = nullptr;
+    if (!done) {
+      const int2 it = Win[i];
       v = it.x;
       k = it.y;
-      MeshCtx c = ctx_of(S, v);
-      CoarsenCtx x = coarsen_ctx(S, v, c);
-      const double4 band = S.tab.band[c.mi];
-      const int* cv = cand + (size_t)v * S.W;
-      int nc = ncand[v];
-      unsigned ops = 0;
-      found = collapse_valid(x, cv[k], band, ops);
-      if (last)
-        while (!found && ++k < nc) found = collapse_valid(x, cv[k], band, ops);
+      x = coarsen_ctx(S, v, ctx_of(S, v));
+      cv = cand + (size_t)v * S.W;
+      nc = ncand[v];
+    }
+    // one candidate per lane and turn; the last pass moves on to the next
+    // candidate of each lane whose candidate failed
+    while (__ballot_sync(0xffffffffu, !done)) {
+      const int u = done ? 0 : cv[k];
+      const bool link = !done && collapse_link(S, x, u);
+      const int ws = x.c.vb + u;
+      const int* nnw = link ? nn_row(S, ws) : nullptr;
+      const int nnwl = link ? S.NNlen[ws] : 0;
+      Q.ok[lane] = link ? 1 : 0;
+      const int T = link ? x.nel + x.nnl : 0;
+      const int Tmax = __reduce_max_sync(0xffffffffu, T);
+      int no = 0, nl = 0;  // queue lengths, the same in every lane
+      __syncwarp();
+      for (int t = 0; t < Tmax; ++t) {
+        bool po = false, pl = false;
+        int4 ro = make_int4(lane, 0, 0, 0);
+        int2 rl = make_int2(lane, 0);
+        if (t < T) {
+          if (t < x.nel) {
+            const int4 e = S.EN[x.c.eb + x.ne[t]];
+            po = e.x != u && e.y != u && e.z != u;
+            ro = make_int4(lane, e.x, e.y, e.z);
+          } else {
+            const int y = x.nn[t - x.nel];
+            pl = y != u && !row_has(nnw, nnwl, y);
+            rl = make_int2(lane, y);
+          }
+        }
+        const unsigned mo = __ballot_sync(0xffffffffu, po);
+        const unsigned ml = __ballot_sync(0xffffffffu, pl);
+        if (po) Q.qo[no + __popc(mo & lt)] = ro;
+        if (pl) Q.ql[nl + __popc(ml & lt)] = rl;
+        no += __popc(mo);
+        nl += __popc(ml);
+        __syncwarp();
+        if (no >= 32) {
+          check_orient_chunk(S, Q, 32, x.c.vb, x.lv, ws, ops);
+          __syncwarp();
+          if (lane < no - 32) Q.qo[lane] = Q.qo[32 + lane];
+          no -= 32;
+          __syncwarp();
+        }
+        if (nl >= 32) {
+          check_len_chunk(S, Q, 32, x.c.vb, ws, x.c.mi, ops);
+          __syncwarp();
+          if (lane < nl - 32) Q.ql[lane] = Q.ql[32 + lane];
+          nl -= 32;
+          __syncwarp();
+        }
+      }
+      if (no > 0) check_orient_chunk(S, Q, no, x.c.vb, x.lv, ws, ops);
+      if (nl > 0) check_len_chunk(S, Q, nl, x.c.vb, ws, x.c.mi, ops);
+      __syncwarp();
+      if (!done) {
+        found = Q.ok[lane] != 0;
+        if (found || !last || k + 1 >= nc) done = true;
+        else ++k;
+      }
+      __syncwarp();
+    }
+    bool next = false;
+    if (i < n) {
       if (found) {
         target[v] = cv[k];
         cmark[v] = tag;
-        S.tab.had[c.mi] = 1;
+        S.tab.had[x.c.mi] = 1;
       } else if (!last && k + 1 < nc) {
         next = true;
       } else {
@@ -571,12 +658,14 @@ __device__ __forceinline__ void coarsen_check_phase(Store S, const int2* Win, co
     warp_append(found, v, C, nC);
     if (!last) warp_append_t(next, make_int2(v, k + 1), Wout, nWout);
   }
+  add_work(work, ops);
 }
 
 __global__ void k_coarsen_check(Store S, const int2* Win, const int* nWin, int2* Wout, int* nWout,
                                 int* target, const int* cand, const int* ncand, int* C, int* nC,
-                                int* cmark, int tag, int last) {
-  coarsen_check_phase(S, Win, nWin, Wout, nWout, target, cand, ncand, C, nC, cmark, tag, last);
+                                int* cmark, int tag, int last, unsigned long long* work) {
+  coarsen_check_phase(S, Win, nWin, Wout, nWout, target, cand, ncand, C, nC, cmark, tag, last,
+                      work);
 }
 
 // One tile per listed vertex, listing and checking at once (persistent
@@ -2667,9 +2756,11 @@ int op_coarsen(MeshSet& m, int max_rounds) {
     // one dense wave checking every vertex's best candidate, then the
     // remaining candidates of the vertices whose best one failed
     PM_LAUNCH(k_coarsen_check, gv, bs, 0, m.stream, m.S, w.items, w.counts + CN_I, w.items2,
-              w.counts + CN_I2, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 0);
+              w.counts + CN_I2, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 0,
+              prof_work("k_coarsen_check"));
     PM_LAUNCH(k_coarsen_check, gv, bs, 0, m.stream, m.S, w.items2, w.counts + CN_I2, w.items,
-              w.counts + CN_I, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 1);
+              w.counts + CN_I, w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, 1,
+              prof_work("k_coarsen_check"));
     zero_counts(m, CN_CL, 1);
     PM_LAUNCH(k_coarsen_select_apply, gv, bs, 0, m.stream, m.S, w.C, w.counts + CN_C, w.cmark,
               w.smark, tag, w.target, w.A, w.counts + CN_A, w.amark, w.D[nxt],
