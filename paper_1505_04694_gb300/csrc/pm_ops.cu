@@ -1107,42 +1107,186 @@ __device__ __forceinline__ double flip_gain(const Store& S, MeshCtx c, int lv, c
 // found in its sorted element row); the other item does no arithmetic.
 //
 // A warp pays the FP64 issue cost of an instruction once whatever its active
-// lanes, so the items that need arithmetic are first collected in a per-warp
-// queue in shared memory and evaluated 32 at a time (full warps); only the
-// last batch of each warp may be partial.  At most 8 warps per block.
+// lanes, so the items that need arithmetic are collected in per-warp queues
+// in shared memory and evaluated 32 at a time (full warps).  The tests of a
+// gain end early (a decided negative orientation, a quality not above the
+// old minimum), so each stage has its own queue: orientations, first
+// quality, second quality and gain; an item that passes a stage joins the
+// next stage's queue.  Only the last batch of each queue may be partial.
+// At most 8 warps per block.
 constexpr int kEdgeQueueWarps = 8;
 
-__device__ __forceinline__ void flip_gain_item(const Store& S, int4 q, double* gains,
-                                               unsigned& ops) {
-  const int v = q.x, k1 = q.y & 0xFF, k2 = (q.y >> 8) & 0xFF, sw = q.w;
-  const bool both = (q.y >> 16) & 1;
+// Queued item q = (v, k1 | k2 << 8 | both << 16 | open << 17, mesh, slot of
+// w): the flip of edge (v, w) between v's ball elements k1 and k2.
+struct FlipGeom {
   MeshCtx c;
-  c.mi = q.z;
-  c.vb = S.tab.vbase[c.mi];
-  c.eb = S.tab.ebase[c.mi];
-  const int* ne = ne_row(S, v);
-  int cc, d;
-  const double g = flip_gain(S, c, v - c.vb, ne, k1, k2, &cc, &d, ops);
-  gains[(size_t)v * S.W + k1] = g;
-  if (both) {
+  int lv, w, cc, d, K1, K2;
+};
+
+__device__ __forceinline__ FlipGeom flip_geom(const Store& S, int4 q) {
+  FlipGeom g;
+  g.c.mi = q.z;
+  g.c.vb = S.tab.vbase[q.z];
+  g.c.eb = S.tab.ebase[q.z];
+  g.lv = q.x - g.c.vb;
+  const int* ne = ne_row(S, q.x);
+  g.K1 = ne[q.y & 0xFF];
+  g.K2 = ne[(q.y >> 8) & 0xFF];
+  const int4 e = S.EN[g.c.eb + g.K1];
+  const int4 f = S.EN[g.c.eb + g.K2];
+  g.w = (e.x == g.lv) ? e.y : (e.y == g.lv) ? e.z : e.x;
+  g.cc = (e.x == g.lv) ? e.z : (e.y == g.lv) ? e.x : e.y;
+  g.d = (f.x == g.lv) ? f.y : (f.y == g.lv) ? f.z : f.x;
+  return g;
+}
+
+__device__ __forceinline__ double flip_qold(const Store& S, const FlipGeom& g) {
+  const double q1 = S.qK[g.c.eb + g.K1], q2 = S.qK[g.c.eb + g.K2];
+  return dlt(q1, q2) ? q1 : q2;
+}
+
+// The tests of flip_gain in the same order, one stage per queue: A the two
+// orientation filters (0: failed, else 1 | the open signs << 1), B the first
+// new quality, C the second, the open signs exactly, the gain.
+__device__ __forceinline__ int flip_stage_a(const Store& S, int4 q, unsigned& ops) {
+  const FlipGeom g = flip_geom(S, q);
+  const VD dv = load_vd(S, g.c.vb + g.lv), dw = load_vd(S, g.c.vb + g.w),
+           dc = load_vd(S, g.c.vb + g.cc), dd = load_vd(S, g.c.vb + g.d);
+  const int s1 = orient_filter(dv, dd, dc);
+  ops += kOpsOrient;
+  if (s1 < 0) return 0;
+  const int s2 = orient_filter(dd, dw, dc);
+  ops += kOpsOrient;
+  if (s2 < 0) return 0;
+  return 1 | (s1 == 0 ? 2 : 0) | (s2 == 0 ? 4 : 0);
+}
+
+__device__ __forceinline__ bool flip_stage_b(const Store& S, int4 q, double& n1, unsigned& ops) {
+  const FlipGeom g = flip_geom(S, q);
+  const VD dv = load_vd(S, g.c.vb + g.lv), dc = load_vd(S, g.c.vb + g.cc),
+           dd = load_vd(S, g.c.vb + g.d);
+  n1 = quality_c(g.lv, g.d, g.cc, dv, dd, dc);
+  ops += kOpsQuality;
+  return dgt(n1, flip_qold(S, g));
+}
+
+__device__ __forceinline__ double flip_stage_c(const Store& S, int4 q, double n1, unsigned& ops) {
+  const FlipGeom g = flip_geom(S, q);
+  const double qold = flip_qold(S, g);
+  const VD dw = load_vd(S, g.c.vb + g.w), dc = load_vd(S, g.c.vb + g.cc),
+           dd = load_vd(S, g.c.vb + g.d);
+  const double n2 = quality_c(g.d, g.w, g.cc, dd, dw, dc);
+  ops += kOpsQuality;
+  if (!dgt(n2, qold)) return -1.0;
+  const int open = (q.y >> 18) & 3;
+  if (open) {
+    const VD pv = load_xy_again(S, g.c.vb + g.lv), pw = load_xy_again(S, g.c.vb + g.w),
+             pc = load_xy_again(S, g.c.vb + g.cc), pd = load_xy_again(S, g.c.vb + g.d);
+    if ((open & 1) && orient_resolve(pv, pd, pc) <= 0) return -1.0;
+    if ((open & 2) && orient_resolve(pd, pw, pc) <= 0) return -1.0;
+  }
+  ops += 1;
+  return (dlt(n1, n2) ? n1 : n2) - qold;
+}
+
+// The gain of item q into v's slot and, when w evaluates the same edge this
+// round, into w's slot of the same element pair.
+__device__ __forceinline__ void flip_store_gain(const Store& S, int4 q, double g, double* gains) {
+  const int v = q.x;
+  gains[(size_t)v * S.W + (q.y & 0xFF)] = g;
+  if ((q.y >> 16) & 1) {
     // from w's side the pair is (K2, K1): w's slot of K2
-    const int K2 = ne[k2];
-    const int* nw = ne_row(S, sw);
-    const int nwl = S.NElen[sw];
+    const int K2 = ne_row(S, v)[(q.y >> 8) & 0xFF];
+    const int* nw = ne_row(S, q.w);
+    const int nwl = S.NElen[q.w];
     int kk = 0;
     while (kk < nwl && nw[kk] < K2) ++kk;
-    if (kk < nwl) gains[(size_t)sw * S.W + kk] = g;
+    if (kk < nwl) gains[(size_t)q.w * S.W + kk] = g;
   }
+}
+
+// Per-warp stage queues (shared memory), each holding fewer than 32 entries
+// between calls; the counts are the same in every lane.  All lanes call.
+struct FlipQueues {
+  int4 *a, *b, *c;
+  double* n1;
+  int na, nb, nc;
+};
+
+__device__ __forceinline__ void flip_run_c(const Store& S, FlipQueues& Q, int cnt, double* gains,
+                                           unsigned& ops) {
+  const int lane = threadIdx.x & 31;
+  if (lane < cnt) {
+    const int4 q = Q.c[lane];
+    flip_store_gain(S, q, flip_stage_c(S, q, Q.n1[lane], ops), gains);
+  }
+  __syncwarp();
+  if (lane < Q.nc - cnt) {
+    Q.c[lane] = Q.c[cnt + lane];
+    Q.n1[lane] = Q.n1[cnt + lane];
+  }
+  Q.nc -= cnt;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void flip_run_b(const Store& S, FlipQueues& Q, int cnt, double* gains,
+                                           unsigned& ops) {
+  const int lane = threadIdx.x & 31;
+  bool pass = false;
+  int4 q = make_int4(0, 0, 0, 0);
+  double n1 = 0.0;
+  if (lane < cnt) {
+    q = Q.b[lane];
+    pass = flip_stage_b(S, q, n1, ops);
+    if (!pass) flip_store_gain(S, q, -1.0, gains);
+  }
+  __syncwarp();
+  if (lane < Q.nb - cnt) Q.b[lane] = Q.b[cnt + lane];
+  Q.nb -= cnt;
+  const unsigned m = __ballot_sync(0xffffffffu, pass);
+  if (pass) {
+    const int at = Q.nc + __popc(m & ((1u << lane) - 1u));
+    Q.c[at] = q;
+    Q.n1[at] = n1;
+  }
+  Q.nc += __popc(m);
+  __syncwarp();
+  if (Q.nc >= 32) flip_run_c(S, Q, 32, gains, ops);
+}
+
+__device__ __forceinline__ void flip_run_a(const Store& S, FlipQueues& Q, int cnt, double* gains,
+                                           unsigned& ops) {
+  const int lane = threadIdx.x & 31;
+  bool pass = false;
+  int4 q = make_int4(0, 0, 0, 0);
+  if (lane < cnt) {
+    q = Q.a[lane];
+    const int r = flip_stage_a(S, q, ops);
+    pass = r != 0;
+    if (pass) q.y |= (r >> 1) << 18;
+    else flip_store_gain(S, q, -1.0, gains);
+  }
+  __syncwarp();
+  if (lane < Q.na - cnt) Q.a[lane] = Q.a[cnt + lane];
+  Q.na -= cnt;
+  const unsigned m = __ballot_sync(0xffffffffu, pass);
+  if (pass) Q.b[Q.nb + __popc(m & ((1u << lane) - 1u))] = q;
+  Q.nb += __popc(m);
+  __syncwarp();
+  if (Q.nb >= 32) flip_run_b(S, Q, 32, gains, ops);
 }
 
 __device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, const int* nIp,
                                                 double* gains, int tag, unsigned long long* work,
                                                 bool il = false) {
-  __shared__ int4 sq[kEdgeQueueWarps][64];
+  __shared__ int4 sqa[kEdgeQueueWarps][64];
+  __shared__ int4 sqb[kEdgeQueueWarps][64];
+  __shared__ int4 sqc[kEdgeQueueWarps][64];
+  __shared__ double sn1[kEdgeQueueWarps][64];
   const int n = *nIp;
   const int lane = threadIdx.x & 31;
-  int4* q = sq[(threadIdx.x >> 5) % kEdgeQueueWarps];
-  int qn = 0;  // the same in every lane of the warp
+  const int wq = (threadIdx.x >> 5) % kEdgeQueueWarps;
+  FlipQueues Q{sqa[wq], sqb[wq], sqc[wq], sn1[wq], 0, 0, 0};
   unsigned ops = 0;
   for (int i0 = 0; i0 < n; i0 += gsize()) {
     const int i = i0 + grank(il);
@@ -1161,20 +1305,14 @@ __device__ __forceinline__ void swap_edge_phase(Store S, const int2* items, cons
       rec = make_int4(v, k1 | (k2 << 8) | ((both ? 1 : 0) << 16), c.mi, sw);
     }
     const unsigned m = __ballot_sync(0xffffffffu, need);
-    if (need) q[qn + __popc(m & ((1u << lane) - 1u))] = rec;
-    qn += __popc(m);
+    if (need) Q.a[Q.na + __popc(m & ((1u << lane) - 1u))] = rec;
+    Q.na += __popc(m);
     __syncwarp();
-    if (qn >= 32) {
-      const int4 mine = q[lane];
-      __syncwarp();
-      if (lane < qn - 32) q[lane] = q[32 + lane];
-      qn -= 32;
-      __syncwarp();
-      flip_gain_item(S, mine, gains, ops);
-    }
+    if (Q.na >= 32) flip_run_a(S, Q, 32, gains, ops);
   }
-  if (lane < qn) flip_gain_item(S, q[lane], gains, ops);
-  __syncwarp();
+  if (Q.na > 0) flip_run_a(S, Q, Q.na, gains, ops);
+  if (Q.nb > 0) flip_run_b(S, Q, Q.nb, gains, ops);
+  if (Q.nc > 0) flip_run_c(S, Q, Q.nc, gains, ops);
   add_work(work, ops);
 }
 
