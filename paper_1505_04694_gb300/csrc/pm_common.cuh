@@ -220,22 +220,29 @@ __device__ __forceinline__ bool stamp_first(int* stamp, int slot, int tag) {
   return atomicExch(stamp + slot, tag) != tag;
 }
 
-__device__ __forceinline__ bool row_has(const int* row, int len, int val) {
-  for (int k = 0; k < len; ++k) {
-    int x = row[k];
-    if (x == val) return true;
-    if (x > val) return false;
+// Position of val in the first len entries of an adjacency row, or -1.  A
+// row starts on a 64-byte boundary (arrays are 256-byte aligned and the row
+// width is a power of two of at least 16), so it is read in 16-byte chunks
+// whose loads do not wait on one another (no exit that depends on a loaded
+// value): one memory round trip for a row of up to 16 entries instead of a
+// chain of dependent loads.  Chunks never pass the row's end (len <= width,
+// a multiple of 4); entries at len and beyond are not compared.
+__device__ __forceinline__ int row_find(const int* row, int len, int val) {
+  const int4* r4 = reinterpret_cast<const int4*>(row);
+  int at = -1;
+#pragma unroll 4
+  for (int k = 0; k < len; k += 4) {
+    const int4 q = r4[k >> 2];
+    at = (q.w == val && k + 3 < len) ? k + 3 : at;
+    at = (q.z == val && k + 2 < len) ? k + 2 : at;
+    at = (q.y == val && k + 1 < len) ? k + 1 : at;
+    at = (q.x == val) ? k : at;
   }
-  return false;
+  return at;
 }
 
-__device__ __forceinline__ int row_find(const int* row, int len, int val) {
-  for (int k = 0; k < len; ++k) {
-    int x = row[k];
-    if (x == val) return k;
-    if (x > val) return -1;
-  }
-  return -1;
+__device__ __forceinline__ bool row_has(const int* row, int len, int val) {
+  return row_find(row, len, val) >= 0;
 }
 
 // Insert into a sorted small buffer without duplicates; returns false when

@@ -998,6 +998,14 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
       }
       continue;
     }
+    // larger balls: the same vertices gathered once (independent loads) into
+    // per-thread local arrays, which stay in L1 while they are searched
+    int nxa[MAXW], pva[MAXW];
+    for (int k = 0; k < nel; ++k) {
+      const int4 f = S.EN[c.eb + ne[k]];
+      nxa[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+      pva[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
+    }
     for (;;) {
       bool any = poor.any();
       if (!__any_sync(0xffffffffu, any)) break;
@@ -1005,24 +1013,20 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
       bool emit1 = false, emit2 = false;
       int a1 = 0, a2 = 0;
       if (any) {
-        int kb = poor.pop();
-        int4 e = S.EN[c.eb + ne[kb]];
-        int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;   // after v
-        int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;  // before v
+        const int kb = poor.pop();
+        const int w = nxa[kb];   // after v
+        const int cc = pva[kb];  // before v
         int k2 = -1, k1 = -1;
         int d2 = 0, c1 = 0;
-        for (int k = 0; k < nel && (k2 < 0 || k1 < 0); ++k) {
+        for (int k = 0; k < nel && (k2 < 0 || k1 < 0); ++k) {  // the first match wins
           if (k == kb) continue;
-          int4 f = S.EN[c.eb + ne[k]];
-          int nx = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
-          int pv = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
-          if (k2 < 0 && pv == w) {
+          if (k2 < 0 && pva[k] == w) {
             k2 = k;
-            d2 = nx;
+            d2 = nxa[k];
           }
-          if (k1 < 0 && nx == cc) {
+          if (k1 < 0 && nxa[k] == cc) {
             k1 = k;
-            c1 = pv;
+            c1 = pva[k];
           }
         }
         if (k2 >= 0) {
