@@ -940,11 +940,19 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
     const double qt = eval ? S.tab.q_thresh[c.mi] : 0.0;
     // An edge (v, w) qualifies only when one of its two elements has quality
     // below q_thresh, so the pairs are found from v's poor elements alone.
+    // Each poor element kb = (v, w, c) gives the pair (kb, k2), k2 the
+    // element (v, d, w) after it around v, and the pair (k1, kb), k1 the
+    // element before it, when k1 is not poor itself (else that pair is found
+    // from k1).  Whether the flipped edge (c, d) already exists is left to
+    // the gain evaluation (gain -1): the scan reads no adjacency row, so its
+    // loop over the poor elements is register arithmetic.  Items are counted
+    // first, reserved with one atomic per warp, then written.
     RowMask poor;
     for (int k = 0; k < nel; ++k) {
       gains[(size_t)v * S.W + k] = -1.0;
       if (dlt(S.qK[c.eb + ne[k]], qt)) poor.set(k);
     }
+    const RowMask poor0 = poor;
     if (__all_sync(0xffffffffu, nel <= kBallFast)) {
       // the ball's vertices after and before v, gathered once into registers
       int nx[kBallFast], pv[kBallFast];
@@ -957,13 +965,13 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
           pv[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
         }
       }
-      for (;;) {
-        bool any = poor.any();
-        if (!__any_sync(0xffffffffu, any)) break;
-        bool emit1 = false, emit2 = false;
-        int a1 = 0, a2 = 0;
-        if (any) {
-          int kb = poor.pop();
+      // pass 0 counts the items, pass 1 writes them
+      int at = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        RowMask pm = poor0;
+        int cnt = 0;
+        while (pm.any()) {
+          const int kb = pm.pop();
           int w = -1, cc = -1;
 #pragma unroll
           for (int k = 0; k < kBallFast; ++k)
@@ -971,30 +979,31 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
               w = nx[k];
               cc = pv[k];
             }
-          int k2 = -1, k1 = -1, d2 = 0, c1 = 0;
+          int k2 = -1, k1 = -1;
 #pragma unroll
           for (int k = kBallFast - 1; k >= 0; --k) {  // the first match wins
             if (k == kb || k >= nel) continue;
-            if (pv[k] == w) {
-              k2 = k;
-              d2 = nx[k];
-            }
-            if (nx[k] == cc) {
-              k1 = k;
-              c1 = pv[k];
-            }
+            if (pv[k] == w) k2 = k;
+            if (nx[k] == cc) k1 = k;
           }
           if (k2 >= 0) {
-            emit1 = !row_has(nn_row(S, c.vb + d2), S.NNlen[c.vb + d2], cc);
-            a1 = kb | (k2 << 8);
+            if (pass == 1) {
+              if (at < icap) items[at] = make_int2(v, kb | (k2 << 8));
+              else set_err(st, PM_ERR_CAPACITY);
+              ++at;
+            }
+            ++cnt;
           }
-          if (k1 >= 0 && !dlt(S.qK[c.eb + ne[k1]], qt)) {
-            emit2 = !row_has(nn_row(S, c.vb + w), S.NNlen[c.vb + w], c1);
-            a2 = k1 | (kb << 8);
+          if (k1 >= 0 && !poor0.test(k1)) {
+            if (pass == 1) {
+              if (at < icap) items[at] = make_int2(v, k1 | (kb << 8));
+              else set_err(st, PM_ERR_CAPACITY);
+              ++at;
+            }
+            ++cnt;
           }
         }
-        append_item(emit1, make_int2(v, a1), items, nI, icap, st);
-        append_item(emit2, make_int2(v, a2), items, nI, icap, st);
+        if (pass == 0) at = warp_reserve(cnt, nI);
       }
       continue;
     }
@@ -1006,42 +1015,38 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
       nxa[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
       pva[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
     }
-    for (;;) {
-      bool any = poor.any();
-      if (!__any_sync(0xffffffffu, any)) break;
-      // pair (K1 = kb, K2): K2 holds the directed edge w -> v
-      bool emit1 = false, emit2 = false;
-      int a1 = 0, a2 = 0;
-      if (any) {
-        const int kb = poor.pop();
+    int at = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      RowMask pm = poor0;
+      int cnt = 0;
+      while (pm.any()) {
+        const int kb = pm.pop();
         const int w = nxa[kb];   // after v
         const int cc = pva[kb];  // before v
         int k2 = -1, k1 = -1;
-        int d2 = 0, c1 = 0;
         for (int k = 0; k < nel && (k2 < 0 || k1 < 0); ++k) {  // the first match wins
           if (k == kb) continue;
-          if (k2 < 0 && pva[k] == w) {
-            k2 = k;
-            d2 = nxa[k];
-          }
-          if (k1 < 0 && nxa[k] == cc) {
-            k1 = k;
-            c1 = pva[k];
-          }
+          if (k2 < 0 && pva[k] == w) k2 = k;
+          if (k1 < 0 && nxa[k] == cc) k1 = k;
         }
         if (k2 >= 0) {
-          emit1 = !row_has(nn_row(S, c.vb + d2), S.NNlen[c.vb + d2], cc);
-          a1 = kb | (k2 << 8);
+          if (pass == 1) {
+            if (at < icap) items[at] = make_int2(v, kb | (k2 << 8));
+            else set_err(st, PM_ERR_CAPACITY);
+            ++at;
+          }
+          ++cnt;
         }
-        // pair (K1 = k1, K2 = kb) when K1 is not poor itself (else it is
-        // listed from K1's side): w' = cc, c' = c1, d' = w
-        if (k1 >= 0 && !dlt(S.qK[c.eb + ne[k1]], qt)) {
-          emit2 = !row_has(nn_row(S, c.vb + w), S.NNlen[c.vb + w], c1);
-          a2 = k1 | (kb << 8);
+        if (k1 >= 0 && !poor0.test(k1)) {
+          if (pass == 1) {
+            if (at < icap) items[at] = make_int2(v, k1 | (kb << 8));
+            else set_err(st, PM_ERR_CAPACITY);
+            ++at;
+          }
+          ++cnt;
         }
       }
-      append_item(emit1, make_int2(v, a1), items, nI, icap, st);
-      append_item(emit2, make_int2(v, a2), items, nI, icap, st);
+      if (pass == 0) at = warp_reserve(cnt, nI);
     }
   }
 }
@@ -1154,6 +1159,8 @@ __device__ __forceinline__ double flip_qold(const Store& S, const FlipGeom& g) {
 // new quality, C the second, the open signs exactly, the gain.
 __device__ __forceinline__ int flip_stage_a(const Store& S, int4 q, unsigned& ops) {
   const FlipGeom g = flip_geom(S, q);
+  // the flipped edge (c, d) must not exist already
+  if (row_has(nn_row(S, g.c.vb + g.d), S.NNlen[g.c.vb + g.d], g.cc)) return 0;
   const VD dv = load_vd(S, g.c.vb + g.lv), dw = load_vd(S, g.c.vb + g.w),
            dc = load_vd(S, g.c.vb + g.cc), dd = load_vd(S, g.c.vb + g.d);
   const int s1 = orient_filter(dv, dd, dc);
