@@ -245,6 +245,21 @@ __device__ __forceinline__ bool row_has(const int* row, int len, int val) {
   return row_find(row, len, val) >= 0;
 }
 
+// Copies the first len entries of an adjacency row into out (capacity: the
+// row width or more) in 16-byte chunks whose loads do not wait on one
+// another; entries of the last chunk past len are copied too and ignored.
+__device__ __forceinline__ void load_row(const int* row, int len, int* out) {
+  const int4* r4 = reinterpret_cast<const int4*>(row);
+#pragma unroll 4
+  for (int k = 0; k < len; k += 4) {
+    const int4 q = r4[k >> 2];
+    out[k] = q.x;
+    out[k + 1] = q.y;
+    out[k + 2] = q.z;
+    out[k + 3] = q.w;
+  }
+}
+
 // Insert into a sorted small buffer without duplicates; returns false when
 // the buffer is full.
 __device__ __forceinline__ bool sorted_insert(int* buf, int& n, int cap, int val) {

@@ -850,16 +850,21 @@ __device__ __forceinline__ void coarsen_commit_phase(Store S, const int* A, cons
         ok &= sorted_insert(nb, nn2, MAXW, t);
         continue;
       }
-      const int* nnx = nn_row(S, xs);
-      int nnxl = S.NNlen[xs];
+      // the collapsed neighbour's rows, read in chunks; its elements'
+      // liveness gathered before the merge so that those loads overlap
+      int rb[MAXW];
+      const int nnxl = S.NNlen[xs];
+      load_row(nn_row(S, xs), nnxl, rb);
       for (int j = 0; j < nnxl; ++j)
-        if (nnx[j] != lu) ok &= sorted_insert(nb, nn2, MAXW, nnx[j]);
-      const int* nex = ne_row(S, xs);
-      int nexl = S.NElen[xs];
-      for (int j = 0; j < nexl; ++j) {
-        int K = nex[j];
-        if (S.EN[c.eb + K].w) ok &= sorted_insert(eb, ne2, MAXW, K);
-      }
+        if (rb[j] != lu) ok &= sorted_insert(nb, nn2, MAXW, rb[j]);
+      const int nexl = S.NElen[xs];
+      load_row(ne_row(S, xs), nexl, rb);
+      RowMask live;
+#pragma unroll 4
+      for (int j = 0; j < nexl; ++j)
+        if (S.EN[c.eb + rb[j]].w) live.set(j);
+      for (int j = 0; j < nexl; ++j)
+        if (live.test(j)) ok &= sorted_insert(eb, ne2, MAXW, rb[j]);
     }
     if (!ok || nn2 > S.W || ne2 > S.W) {
       atomicExch(&st->overflow, 1);
@@ -947,22 +952,22 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
     // the gain evaluation (gain -1): the scan reads no adjacency row, so its
     // loop over the poor elements is register arithmetic.  Items are counted
     // first, reserved with one atomic per warp, then written.
-    RowMask poor;
-    for (int k = 0; k < nel; ++k) {
-      gains[(size_t)v * S.W + k] = -1.0;
-      if (dlt(S.qK[c.eb + ne[k]], qt)) poor.set(k);
-    }
-    const RowMask poor0 = poor;
     if (__all_sync(0xffffffffu, nel <= kBallFast)) {
-      // the ball's vertices after and before v, gathered once into registers
+      // the ball's vertices after and before v and its poor elements,
+      // gathered once into registers (unrolled: the loads of all elements
+      // are in flight together)
       int nx[kBallFast], pv[kBallFast];
+      RowMask poor0;
 #pragma unroll
       for (int k = 0; k < kBallFast; ++k) {
         nx[k] = pv[k] = -1;
         if (k < nel) {
-          int4 f = S.EN[c.eb + ne[k]];
+          const int K = ne[k];
+          const int4 f = S.EN[c.eb + K];
           nx[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
           pv[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
+          if (dlt(S.qK[c.eb + K], qt)) poor0.set(k);
+          gains[(size_t)v * S.W + k] = -1.0;
         }
       }
       // pass 0 counts the items, pass 1 writes them
@@ -1010,10 +1015,14 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
     // larger balls: the same vertices gathered once (independent loads) into
     // per-thread local arrays, which stay in L1 while they are searched
     int nxa[MAXW], pva[MAXW];
+    RowMask poor0;
     for (int k = 0; k < nel; ++k) {
-      const int4 f = S.EN[c.eb + ne[k]];
+      const int K = ne[k];
+      const int4 f = S.EN[c.eb + K];
       nxa[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
       pva[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
+      if (dlt(S.qK[c.eb + K], qt)) poor0.set(k);
+      gains[(size_t)v * S.W + k] = -1.0;
     }
     int at = 0;
     for (int pass = 0; pass < 2; ++pass) {
@@ -1350,38 +1359,91 @@ __device__ __forceinline__ void swap_pick_phase(Store S, const int* E, const int
       int nel = S.NElen[v];
       double best = 0.0;
       int bw = 0, bk = -1;
-      for (int k = 0; k < nel; ++k) {
-        double g = gains[(size_t)v * S.W + k];
-        if (!dgt(g, 0.0)) continue;
-        int4 e = S.EN[c.eb + ne[k]];
-        int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
-        if (!found || dgt(g, best) || (dbits(g) == dbits(best) && w < bw)) {
-          found = true;
-          best = g;
-          bw = w;
-          bk = k;
-        }
-      }
-      if (found) {
-        int4 e = S.EN[c.eb + ne[bk]];
-        int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;
-        int k2 = -1;
-        for (int k = 0; k < nel; ++k) {
-          int4 f = S.EN[c.eb + ne[k]];
-          int pv = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
-          if (pv == bw) {
-            k2 = k;
-            break;
+      if (nel <= kBallFast) {
+        // gains, elements and the vertices after and before v gathered in
+        // one unrolled pass (all loads in flight together), then decided in
+        // registers
+        int nx[kBallFast], pv[kBallFast], K[kBallFast];
+        double g[kBallFast];
+#pragma unroll
+        for (int k = 0; k < kBallFast; ++k) {
+          nx[k] = pv[k] = K[k] = -1;
+          g[k] = -1.0;
+          if (k < nel) {
+            K[k] = ne[k];
+            g[k] = gains[(size_t)v * S.W + k];
+            const int4 f = S.EN[c.eb + K[k]];
+            nx[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+            pv[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
           }
         }
-        int4 f = S.EN[c.eb + ne[k2]];
-        int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
-        opA[v] = make_int4(bw, cc, d, ne[bk]);
-        opK2[v] = ne[k2];
-        cmark[v] = tag;
-        S.tab.had[c.mi] = 1;
+        int bc = 0;
+#pragma unroll
+        for (int k = 0; k < kBallFast; ++k) {
+          if (k < nel && dgt(g[k], 0.0) &&
+              (!found || dgt(g[k], best) || (dbits(g[k]) == dbits(best) && nx[k] < bw))) {
+            found = true;
+            best = g[k];
+            bw = nx[k];
+            bk = k;
+            bc = pv[k];
+          }
+        }
+        if (found) {
+          int k2 = -1;
+#pragma unroll
+          for (int k = kBallFast - 1; k >= 0; --k)  // the first match wins
+            if (k < nel && pv[k] == bw) k2 = k;
+          int K1 = -1, K2 = -1, d = -1;
+#pragma unroll
+          for (int k = 0; k < kBallFast; ++k) {
+            if (k == bk) K1 = K[k];
+            if (k == k2) {
+              K2 = K[k];
+              d = nx[k];
+            }
+          }
+          opA[v] = make_int4(bw, bc, d, K1);
+          opK2[v] = K2;
+          cmark[v] = tag;
+          S.tab.had[c.mi] = 1;
+        } else {
+          opA[v].x = -1;
+        }
       } else {
-        opA[v].x = -1;
+        for (int k = 0; k < nel; ++k) {
+          double g = gains[(size_t)v * S.W + k];
+          if (!dgt(g, 0.0)) continue;
+          int4 e = S.EN[c.eb + ne[k]];
+          int w = (e.x == lv) ? e.y : (e.y == lv) ? e.z : e.x;
+          if (!found || dgt(g, best) || (dbits(g) == dbits(best) && w < bw)) {
+            found = true;
+            best = g;
+            bw = w;
+            bk = k;
+          }
+        }
+        if (found) {
+          int4 e = S.EN[c.eb + ne[bk]];
+          int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;
+          int k2 = -1;
+          for (int k = 0; k < nel; ++k) {
+            int4 f = S.EN[c.eb + ne[k]];
+            int pv = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
+            if (pv == bw) {
+              k2 = k;
+              break;
+            }
+          }
+          int4 f = S.EN[c.eb + ne[k2]];
+          int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
+          opA[v] = make_int4(bw, cc, d, ne[bk]);
+          opK2[v] = ne[k2];
+          cmark[v] = tag;
+          S.tab.had[c.mi] = 1;
+        } else {
+          opA[v].x = -1;
+        }
       }
     }
     warp_append(found, v, C, nC);
@@ -1607,8 +1669,8 @@ __device__ __forceinline__ void swap_commit_phase(Store S, const int* A, const i
     int* ne = S.NE + (size_t)u * S.W;
     int nnl = S.NNlen[u], nel = S.NElen[u];
     int nb[MAXW], eb[MAXW];
-    for (int k = 0; k < nnl; ++k) nb[k] = nn[k];
-    for (int k = 0; k < nel; ++k) eb[k] = ne[k];
+    load_row(nn, nnl, nb);
+    load_row(ne, nel, eb);
     int nn2 = nnl, ne2 = nel;
     bool ok = true;
     RowMask sel;
