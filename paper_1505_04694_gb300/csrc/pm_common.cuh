@@ -245,6 +245,17 @@ __device__ __forceinline__ bool row_has(const int* row, int len, int val) {
   return row_find(row, len, val) >= 0;
 }
 
+// Position of val in a sorted array a[0..len) (binary search), or -1.
+__device__ __forceinline__ int sorted_pos(const int* a, int len, int val) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < val) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < len && a[lo] == val) ? lo : -1;
+}
+
 // Copies the first len entries of an adjacency row into out (capacity: the
 // row width or more) in 16-byte chunks whose loads do not wait on one
 // another; entries of the last chunk past len are copied too and ignored.

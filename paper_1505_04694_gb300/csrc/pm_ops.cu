@@ -1013,9 +1013,17 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
       continue;
     }
     // larger balls: the same vertices gathered once (independent loads) into
-    // per-thread local arrays, which stay in L1 while they are searched
-    int nxa[MAXW], pva[MAXW];
+    // per-thread local arrays, which stay in L1.  Each neighbour of v is the
+    // vertex after v in exactly one ball element and the vertex before v in
+    // exactly one, so the partner elements are indexed by the neighbour's
+    // position in v's sorted row (binary search): O(nel log nel) per vertex
+    // instead of a search of the ball per poor element, which let one
+    // high-degree vertex hold up a whole round.
+    int nxa[MAXW], pva[MAXW], nnr[MAXW], byp[MAXW], byn[MAXW];
     RowMask poor0;
+    const int nnl = S.NNlen[v];
+    load_row(nn_row(S, v), nnl, nnr);
+#pragma unroll 8
     for (int k = 0; k < nel; ++k) {
       const int K = ne[k];
       const int4 f = S.EN[c.eb + K];
@@ -1024,20 +1032,24 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
       if (dlt(S.qK[c.eb + K], qt)) poor0.set(k);
       gains[(size_t)v * S.W + k] = -1.0;
     }
+    for (int j = 0; j < nnl; ++j) byp[j] = byn[j] = -1;
+    for (int k = nel - 1; k >= 0; --k) {  // the first match wins
+      const int jp = sorted_pos(nnr, nnl, pva[k]), jn = sorted_pos(nnr, nnl, nxa[k]);
+      if (jp >= 0) byp[jp] = k;
+      if (jn >= 0) byn[jn] = k;
+    }
     int at = 0;
     for (int pass = 0; pass < 2; ++pass) {
       RowMask pm = poor0;
       int cnt = 0;
       while (pm.any()) {
         const int kb = pm.pop();
-        const int w = nxa[kb];   // after v
-        const int cc = pva[kb];  // before v
-        int k2 = -1, k1 = -1;
-        for (int k = 0; k < nel && (k2 < 0 || k1 < 0); ++k) {  // the first match wins
-          if (k == kb) continue;
-          if (k2 < 0 && pva[k] == w) k2 = k;
-          if (k1 < 0 && nxa[k] == cc) k1 = k;
-        }
+        const int jw = sorted_pos(nnr, nnl, nxa[kb]);  // w, after v
+        const int jc = sorted_pos(nnr, nnl, pva[kb]);  // c, before v
+        int k2 = jw >= 0 ? byp[jw] : -1;
+        int k1 = jc >= 0 ? byn[jc] : -1;
+        if (k2 == kb) k2 = -1;
+        if (k1 == kb) k1 = -1;
         if (k2 >= 0) {
           if (pass == 1) {
             if (at < icap) items[at] = make_int2(v, kb | (k2 << 8));
@@ -1411,6 +1423,7 @@ __device__ __forceinline__ void swap_pick_phase(Store S, const int* E, const int
           opA[v].x = -1;
         }
       } else {
+#pragma unroll 8
         for (int k = 0; k < nel; ++k) {
           double g = gains[(size_t)v * S.W + k];
           if (!dgt(g, 0.0)) continue;
@@ -1427,13 +1440,11 @@ __device__ __forceinline__ void swap_pick_phase(Store S, const int* E, const int
           int4 e = S.EN[c.eb + ne[bk]];
           int cc = (e.x == lv) ? e.z : (e.y == lv) ? e.x : e.y;
           int k2 = -1;
-          for (int k = 0; k < nel; ++k) {
+#pragma unroll 8
+          for (int k = nel - 1; k >= 0; --k) {  // the first match wins
             int4 f = S.EN[c.eb + ne[k]];
             int pv = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
-            if (pv == bw) {
-              k2 = k;
-              break;
-            }
+            if (pv == bw) k2 = k;
           }
           int4 f = S.EN[c.eb + ne[k2]];
           int d = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
