@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--single-steps", type=int, default=2,
                     help="timed steps of the one-mesh-per-launch comparison (batch workload)")
     ap.add_argument("--roofline-kernel", default=None)
+    ap.add_argument("--batch-every", type=int, default=1,
+                    help="batch workload: every n-th mesh by initial size (a sub-batch for "
+                         "profiling captures; 1 = the 512-mesh batch)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="device-resident steps only (no e2e pass, no CPU baseline)")
     ap.add_argument("--workload", default="batch",
@@ -154,15 +157,14 @@ ROOFLINE_CANDIDATES = ("k_swap_rounds", "k_smooth_rounds", "k_coarsen_rounds", "
 FP64_RESULTS_PER_CYCLE = 304
 
 
-def roofline(kname, kms, klaunch, kwork, total_ms, peaks, how, fp64_meas=None, psi2m=True):
+def roofline(kname, kms, klaunch, kwork, total_ms, peaks, how, fp64_meas=None, workload=None):
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = FP64_RESULTS_PER_CYCLE * mhz * 1e6 / 1e9  # G FP64 ops/s
     out = {"kernel": kname, "bound": "alu", "unit": "GFLOP/s (FP64 ops)",
            "peak": peak, "peak_source": f"derived: {FP64_RESULTS_PER_CYCLE} FP64 results/cycle x "
                                         f"{mhz:.0f} MHz (sm_max_mhz {how})",
            "achieved": None, "frac": None,
-           # the committed capture covers the 2M workload only
-           "traffic": traffic_of(kname) if psi2m else None,
+           "traffic": traffic_of(kname, workload) if workload else None,
            "kernel_ms_per_step_share": (kms / total_ms) if total_ms else None,
            "launches": klaunch, "kernel_ms": kms, "fp64_ops": kwork}
     if fp64_meas:
@@ -178,15 +180,16 @@ def roofline(kname, kms, klaunch, kwork, total_ms, peaks, how, fp64_meas=None, p
     return out
 
 
-def traffic_of(kname):
-    """DRAM bytes per launch of the kernel from the committed ncu summary
-    (profiles/traffic.txt: one "kernel bytes_per_launch" pair per line)."""
+def traffic_of(kname, workload):
+    """DRAM bytes per launch of the kernel on this workload from the committed
+    ncu summary (profiles/traffic.txt: "kernel workload bytes_per_launch" per
+    line), or None when no capture of the current kernel exists."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
             for line in f:
                 parts = line.split("#", 1)[0].split()
-                if len(parts) >= 2 and parts[0] == kname:
-                    return float(parts[1])
+                if len(parts) >= 3 and parts[0] == kname and parts[1] == workload:
+                    return float(parts[2])
     except OSError:
         pass
     return None
@@ -293,6 +296,10 @@ def run_batch(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     ws = inputs.batch_workloads()
+    if args.batch_every > 1:
+        order = sorted(range(len(ws)), key=lambda i: ws[i].tri.shape[0])
+        ws = [ws[i] for i in order[::args.batch_every]]
+    batch_key = f"batch{len(ws)}"
     parts = shard.partition([w.tri.shape[0] for w in ws], world)
     mine_idx = parts[rank]
     mine = [ws[i] for i in mine_idx]
@@ -313,7 +320,7 @@ def run_batch(args, rank, world, local):
     om_ = torch.empty((cap, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     pool = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.batch_every == 1:
         pool = oracle_pool(host_cores())  # spawned before any GPU work of this process
 
     def step():
@@ -423,7 +430,9 @@ def run_batch(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "meshes": len(ws),
+        "config": {"workload": BATCH_WORKLOAD if len(ws) == 512 else
+                   f"{len(ws)} of the 512 meshes (every {args.batch_every}-th by initial size) of "
+                   + BATCH_WORKLOAD, "meshes": len(ws),
                    "output_triangles_per_step": tris // max(args.steps, 1),
                    "l2": "flushed between steps (256 MiB write, untimed)",
                    "parallelism": f"meshes split over {world} GPUs by size" if world > 1
@@ -434,7 +443,7 @@ def run_batch(args, rank, world, local):
             "steps": max(1, args.single_steps),
             "batched_speedup": value / single_value,
             "how": "per mesh: pm_mesh_create_dev, pm_set_metric_dev, pm_adapt, "
-                   "pm_get_mesh_dev; CUDA events around all 512"},
+                   f"pm_get_mesh_dev; CUDA events around all {len(ws)}"},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_tris / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
@@ -444,7 +453,7 @@ def run_batch(args, rank, world, local):
         "gpu_launches_per_step": launches / max(args.steps, 1),
         "tuning": dict(pm.get_tuning(), source=pm.tuning_source()),
         "roofline": dict(roofline(kname, kms, klaunch, kwork, total_ms, peaks, how, fp64_meas,
-                                  False),
+                                  batch_key),
                          chosen_from={k: round(v, 4) for k, v in cand_ms.items()},
                          chosen_by="largest event time in one untimed step (ms)"),
     }
@@ -871,7 +880,7 @@ def main():
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / max(args.steps, 1),
         "roofline": dict(roofline(kname, kms, klaunch, kwork, total_ms, peaks, how, fp64_meas,
-                                  args.workload == "psi2m"),
+                                  args.workload),
                          chosen_from={k: round(v, 4) for k, v in cand_ms.items()},
                          chosen_by="largest event time in one untimed step (ms)"),
     }

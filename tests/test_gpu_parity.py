@@ -414,7 +414,8 @@ def test_anisotropic_2m_full_adapt_bit_exact():
 @pytest.mark.slow
 def test_anisotropic_20m_full_adapt_bit_exact():
     """The large workload at full size (1025^2 grid, 2.1M triangles in, about
-    29M out): the whole adaptation against the oracle's, bit for bit."""
+    20M out, within the 10% the size reading allows): the whole adaptation
+    against the oracle's, bit for bit."""
     w = inputs.anisotropic_20m()
     seed = w.params.seed
     g = pm.Mesh.from_host(w.xy, w.tri, device=0)
@@ -427,7 +428,7 @@ def test_anisotropic_20m_full_adapt_bit_exact():
     assert_same_mesh(gmesh, o.get_mesh(), "anisotropic 20M")
     for k in STAT_KEYS:
         assert sg[k] == so[k], (k, sg[k], so[k])
-    assert gmesh[1].shape[0] > 20_000_000
+    assert 18_000_000 <= gmesh[1].shape[0] <= 22_000_000
 
 
 @pytest.mark.slow
