@@ -907,6 +907,79 @@ __device__ __forceinline__ void append_item(bool pred, int2 val, int2* list, int
   }
 }
 
+// A vertex whose ball holds more than kBallFast elements, listed by the whole
+// warp (all lanes call): lane l gathers elements l, l + 32, ... into the
+// warp's shared arrays and then finds the partner elements of its own poor
+// elements there; the same pairs, in the same order per poor element, as the
+// register path below.  One such vertex used to hold up its round: one thread
+// walked its whole ball for every poor element.
+constexpr int kScanWarps = 8;
+
+__device__ __forceinline__ void swap_scan_heavy(const Store& S, int v, int* sx, int* sp,
+                                                int2* items, int* nI, int icap, double* gains,
+                                                DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const MeshCtx c = ctx_of(S, v);
+  const int lv = v - c.vb;
+  const int* ne = ne_row(S, v);
+  const int nel = S.NElen[v];
+  const double qt = S.tab.q_thresh[c.mi];
+  unsigned pw[MAXW / 32];
+#pragma unroll
+  for (int j = 0; j < MAXW / 32; ++j) {
+    const int k = 32 * j + lane;
+    bool poor = false;
+    if (k < nel) {
+      const int K = ne[k];
+      const int4 f = S.EN[c.eb + K];
+      sx[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;  // after v
+      sp[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;  // before v
+      poor = dlt(S.qK[c.eb + K], qt);
+      gains[(size_t)v * S.W + k] = -1.0;
+    }
+    pw[j] = __ballot_sync(0xffffffffu, poor);
+  }
+  __syncwarp();
+  int at = 0;
+  for (int pass = 0; pass < 2; ++pass) {  // count, reserve, write
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < MAXW / 32; ++j) {
+      const int kb = 32 * j + lane;
+      if (kb >= nel || !((pw[j] >> lane) & 1u)) continue;
+      const int w = sx[kb], cc = sp[kb];
+      int k2 = -1, k1 = -1;
+      for (int k = 0; k < nel && (k2 < 0 || k1 < 0); ++k) {  // the first match wins
+        if (k == kb) continue;
+        if (k2 < 0 && sp[k] == w) k2 = k;
+        if (k1 < 0 && sx[k] == cc) k1 = k;
+      }
+      if (k2 >= 0) {
+        if (pass == 1) {
+          if (at < icap) items[at] = make_int2(v, kb | (k2 << 8));
+          else set_err(st, PM_ERR_CAPACITY);
+          ++at;
+        }
+        ++cnt;
+      }
+      bool k1poor = false;
+#pragma unroll
+      for (int jj = 0; jj < MAXW / 32; ++jj)
+        if (k1 >= 0 && (k1 >> 5) == jj) k1poor = (pw[jj] >> (k1 & 31)) & 1u;
+      if (k1 >= 0 && !k1poor) {
+        if (pass == 1) {
+          if (at < icap) items[at] = make_int2(v, k1 | (kb << 8));
+          else set_err(st, PM_ERR_CAPACITY);
+          ++at;
+        }
+        ++cnt;
+      }
+    }
+    if (pass == 0) at = warp_reserve(cnt, nI);
+  }
+  __syncwarp();  // the shared arrays serve the next heavy vertex
+}
+
 // Flip evaluation in three passes so that the FP64 work runs on full warps.
 // Pass 1 (per dirty vertex): reuse an unchanged earlier result, or list the
 // vertex's interior edges whose two elements' cached minimum quality is below
@@ -916,6 +989,8 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
                                                 int tag, int pass0, int* E, int* nE, int2* items,
                                                 int* nI, int icap, double* gains, DevStatus* st,
                                                 bool il = false) {
+  __shared__ int s_hx[kScanWarps][MAXW], s_hp[kScanWarps][MAXW];
+  const int wq = (threadIdx.x >> 5) % kScanWarps;
   const int n = *nDp;
   for (int i0 = 0; i0 < n; i0 += gsize()) {
     int i = i0 + grank(il);
@@ -952,7 +1027,11 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
     // the gain evaluation (gain -1): the scan reads no adjacency row, so its
     // loop over the poor elements is register arithmetic.  Items are counted
     // first, reserved with one atomic per warp, then written.
-    if (__all_sync(0xffffffffu, nel <= kBallFast)) {
+    // balls above kBallFast elements are listed by the whole warp after the
+    // register path, which the other lanes take
+    const bool heavy = nel > kBallFast;
+    const int nfast = heavy ? 0 : nel;
+    {
       // the ball's vertices after and before v and its poor elements,
       // gathered once into registers (unrolled: the loads of all elements
       // are in flight together)
@@ -961,7 +1040,7 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
 #pragma unroll
       for (int k = 0; k < kBallFast; ++k) {
         nx[k] = pv[k] = -1;
-        if (k < nel) {
+        if (k < nfast) {
           const int K = ne[k];
           const int4 f = S.EN[c.eb + K];
           nx[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
@@ -987,7 +1066,7 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
           int k2 = -1, k1 = -1;
 #pragma unroll
           for (int k = kBallFast - 1; k >= 0; --k) {  // the first match wins
-            if (k == kb || k >= nel) continue;
+            if (k == kb || k >= nfast) continue;
             if (pv[k] == w) k2 = k;
             if (nx[k] == cc) k1 = k;
           }
@@ -1010,64 +1089,10 @@ __device__ __forceinline__ void swap_scan_phase(Store S, const int* D, const int
         }
         if (pass == 0) at = warp_reserve(cnt, nI);
       }
-      continue;
     }
-    // larger balls: the same vertices gathered once (independent loads) into
-    // per-thread local arrays, which stay in L1.  Each neighbour of v is the
-    // vertex after v in exactly one ball element and the vertex before v in
-    // exactly one, so the partner elements are indexed by the neighbour's
-    // position in v's sorted row (binary search): O(nel log nel) per vertex
-    // instead of a search of the ball per poor element, which let one
-    // high-degree vertex hold up a whole round.
-    int nxa[MAXW], pva[MAXW], nnr[MAXW], byp[MAXW], byn[MAXW];
-    RowMask poor0;
-    const int nnl = S.NNlen[v];
-    load_row(nn_row(S, v), nnl, nnr);
-#pragma unroll 8
-    for (int k = 0; k < nel; ++k) {
-      const int K = ne[k];
-      const int4 f = S.EN[c.eb + K];
-      nxa[k] = (f.x == lv) ? f.y : (f.y == lv) ? f.z : f.x;
-      pva[k] = (f.x == lv) ? f.z : (f.y == lv) ? f.x : f.y;
-      if (dlt(S.qK[c.eb + K], qt)) poor0.set(k);
-      gains[(size_t)v * S.W + k] = -1.0;
-    }
-    for (int j = 0; j < nnl; ++j) byp[j] = byn[j] = -1;
-    for (int k = nel - 1; k >= 0; --k) {  // the first match wins
-      const int jp = sorted_pos(nnr, nnl, pva[k]), jn = sorted_pos(nnr, nnl, nxa[k]);
-      if (jp >= 0) byp[jp] = k;
-      if (jn >= 0) byn[jn] = k;
-    }
-    int at = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-      RowMask pm = poor0;
-      int cnt = 0;
-      while (pm.any()) {
-        const int kb = pm.pop();
-        const int jw = sorted_pos(nnr, nnl, nxa[kb]);  // w, after v
-        const int jc = sorted_pos(nnr, nnl, pva[kb]);  // c, before v
-        int k2 = jw >= 0 ? byp[jw] : -1;
-        int k1 = jc >= 0 ? byn[jc] : -1;
-        if (k2 == kb) k2 = -1;
-        if (k1 == kb) k1 = -1;
-        if (k2 >= 0) {
-          if (pass == 1) {
-            if (at < icap) items[at] = make_int2(v, kb | (k2 << 8));
-            else set_err(st, PM_ERR_CAPACITY);
-            ++at;
-          }
-          ++cnt;
-        }
-        if (k1 >= 0 && !poor0.test(k1)) {
-          if (pass == 1) {
-            if (at < icap) items[at] = make_int2(v, k1 | (kb << 8));
-            else set_err(st, PM_ERR_CAPACITY);
-            ++at;
-          }
-          ++cnt;
-        }
-      }
-      if (pass == 0) at = warp_reserve(cnt, nI);
+    for (unsigned hb = __ballot_sync(0xffffffffu, heavy); hb; hb &= hb - 1u) {
+      const int hv = __shfl_sync(0xffffffffu, v, __ffs(hb) - 1);
+      swap_scan_heavy(S, hv, s_hx[wq], s_hp[wq], items, nI, icap, gains, st);
     }
   }
 }
