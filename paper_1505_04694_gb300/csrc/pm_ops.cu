@@ -108,6 +108,10 @@ __device__ __forceinline__ bool unchanged(const Store& S, int v, int vb, int et,
 // quality 77, a square root or a division 1.
 constexpr unsigned kOpsLen2 = 17, kOpsOrient = 8, kOpsQuality = 77;
 
+// Warps per block that own a per-warp shared-memory queue or array in the
+// scan phases (blocks hold at most 256 threads).
+constexpr int kScanWarps = 8;
+
 __device__ __forceinline__ void add_work(unsigned long long* work, unsigned ops) {
   if (!work) return;
   unsigned tot = __reduce_add_sync(0xffffffffu, ops);
@@ -458,50 +462,124 @@ __device__ __forceinline__ CoarsenCtx coarsen_ctx(const Store& S, int v, MeshCtx
 // tile_coarsen_candidates), so the FP64 lengths of the neighbours run side
 // by side.  The tile takes the stamp decision from lane 0 before lane 0
 // overwrites the stamp.
+// Pass 1 of the large rounds, one dirty vertex per thread: reuse an unchanged
+// earlier result, or list v's collapse candidates.  The metric lengths of all
+// the warp's vertices' edges are the FP64 work; they are evaluated 32 at a
+// time from a per-warp queue (full warps on the FP64 pipe, where a tile per
+// vertex kept about 19 of 32 lanes busy), each candidate's length stored in
+// a scratch row and its bit in a per-lane mask; then each thread places its
+// own candidates by rank in the (length, id) order, as tile_coarsen_candidates
+// does in the persistent rounds.
+__device__ __forceinline__ void coarsen_len_chunk(const Store& S, const int2* q, int cnt, int v,
+                                                  MeshCtx c, unsigned long long (*cm)[2],
+                                                  double* Lbuf) {
+  const int lane = threadIdx.x & 31;
+  const int2 r = lane < cnt ? q[lane] : make_int2(lane, 0);
+  const int ov = __shfl_sync(0xffffffffu, v, r.x);
+  const int ovb = __shfl_sync(0xffffffffu, c.vb, r.x);
+  const int oeb = __shfl_sync(0xffffffffu, c.eb, r.x);
+  const int omi = __shfl_sync(0xffffffffu, c.mi, r.x);
+  if (lane < cnt) {
+    const int u = nn_row(S, ov)[r.y];
+    const double L2 = metric_len2(load_vd(S, ov), load_vd(S, ovb + u));
+    const double4 band = S.tab.band[omi];
+    bool is = len_lt(L2, band.x, band.y, S.tab.L_low[omi]);
+    // a boundary vertex collapses only along a boundary edge
+    if (is && (S.vflag[ov] & VF_BND)) is = count_elems_with(S, ne_row(S, ov), S.NElen[ov], oeb, u) == 1;
+    if (is) {
+      Lbuf[(size_t)ov * S.W + r.y] = sqrt(L2);
+      atomicOr(&cm[r.x][r.y >> 6], 1ull << (r.y & 63));
+    }
+  }
+}
+
 __device__ __forceinline__ void coarsen_scan_phase(Store S, const int* D, const int* nDp,
                                                    int* target, int* cand, int* ncand, int* C,
                                                    int* nC, int* cmark, int tag, int pass0,
-                                                   int2* W0, int* nW0) {
-  const Tile t = tile_of();
+                                                   int2* W0, int* nW0, double* Lbuf) {
+  __shared__ int2 sq[kScanWarps][64];
+  __shared__ unsigned long long scm[kScanWarps][32][2];
+  const int lane = threadIdx.x & 31, wq = (threadIdx.x >> 5) % kScanWarps;
+  const unsigned lt = (1u << lane) - 1u;
   const int n = *nDp;
-  for (int i0 = 0; i0 < n; i0 += tcount()) {
-    const int i = i0 + trank(false);
-    int v = 0;
-    bool reuse_cand = false, emit = false;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    int v = 0, nnl = 0;
+    bool reuse_cand = false, eval = false;
+    MeshCtx c{0, 0, 0};
     if (i < n) {
       v = D[i];
-      MeshCtx c = ctx_of(S, v);
-      const int et = __shfl_sync(t.mask, S.evc[v], 0, TW);
-      if (unchanged(S, v, c.vb, et, pass0)) {
+      c = ctx_of(S, v);
+      if (unchanged(S, v, c.vb, S.evc[v], pass0)) {
         reuse_cand = target[v] >= 0;
-        if (reuse_cand && t.tl == 0) {
+        if (reuse_cand) {
           cmark[v] = tag;
           S.tab.had[c.mi] = 1;
         }
       } else {
-        if (t.tl == 0) S.evc[v] = tag;
-        unsigned ops = 0;
-        int nc = tile_coarsen_candidates(t, S, v, c, cand + (size_t)v * S.W, ops);
-        if (t.tl == 0) {
-          ncand[v] = nc;
-          if (nc == 0) target[v] = -1;
-        }
-        emit = nc > 0;
+        S.evc[v] = tag;
+        eval = true;
+        const uint8_t f = S.vflag[v];
+        // corners and dead vertices have no candidates
+        if ((f & VF_ALIVE) && !(f & VF_CORNER)) nnl = S.NNlen[v];
       }
     }
-    warp_append(reuse_cand && t.tl == 0, v, C, nC);
-    warp_append_t(emit && t.tl == 0, make_int2(v, 0), W0, nW0);
+    scm[wq][lane][0] = scm[wq][lane][1] = 0ull;
+    __syncwarp();
+    const int tmax = __reduce_max_sync(0xffffffffu, nnl);
+    int qn = 0;  // the same in every lane
+    for (int t = 0; t < tmax; ++t) {
+      const bool p = t < nnl;
+      const unsigned m = __ballot_sync(0xffffffffu, p);
+      if (p) sq[wq][qn + __popc(m & lt)] = make_int2(lane, t);
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        coarsen_len_chunk(S, sq[wq], 32, v, c, scm[wq], Lbuf);
+        __syncwarp();
+        if (lane < qn - 32) sq[wq][lane] = sq[wq][32 + lane];
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+    if (qn > 0) coarsen_len_chunk(S, sq[wq], qn, v, c, scm[wq], Lbuf);
+    __syncwarp();
+    int nc = 0;
+    if (eval) {
+      RowMask cm;
+      cm.lo = scm[wq][lane][0];
+      cm.hi = scm[wq][lane][1];
+      nc = cm.count();
+      const int* nn = nn_row(S, v);
+      const double* L = Lbuf + (size_t)v * S.W;
+      int* out = cand + (size_t)v * S.W;
+      RowMask a = cm;
+      while (a.any()) {
+        const int k = a.pop();
+        const double Lk = L[k];
+        int rank = 0;
+        RowMask b = cm;
+        while (b.any()) {
+          const int k2 = b.pop();
+          const double Lo = L[k2];
+          if (dlt(Lo, Lk) || (dbits(Lo) == dbits(Lk) && k2 < k)) ++rank;
+        }
+        out[rank] = nn[k];
+      }
+      ncand[v] = nc;
+      if (nc == 0) target[v] = -1;
+    }
+    warp_append(reuse_cand, v, C, nC);
+    warp_append_t(eval && nc > 0, make_int2(v, 0), W0, nW0);
   }
 }
 
 __global__ void k_coarsen_scan(Store S, const int* D, const int* nDp, int* target, int* cand,
                                int* ncand, int* C, int* nC, int* cmark, int tag, int pass0,
-                               int2* W0, int* nW0) {
-  coarsen_scan_phase(S, D, nDp, target, cand, ncand, C, nC, cmark, tag, pass0, W0, nW0);
+                               int2* W0, int* nW0, double* Lbuf) {
+  coarsen_scan_phase(S, D, nDp, target, cand, ncand, C, nC, cmark, tag, pass0, W0, nW0, Lbuf);
 }
 
-// The check passes stay one thread per item: a check is a short chain of
-// dependent loads, and eight items per warp left too little in flight.
 // The check passes, one work item (v, k) per thread: is collapsing v onto
 // its k-th candidate valid (in the last pass: the first valid one from k on)?
 // Validity is the conjunction of the link condition and, for the collapse
@@ -913,7 +991,6 @@ __device__ __forceinline__ void append_item(bool pred, int2 val, int2* list, int
 // elements there; the same pairs, in the same order per poor element, as the
 // register path below.  One such vertex used to hold up its round: one thread
 // walked its whole ball for every poor element.
-constexpr int kScanWarps = 8;
 
 __device__ __forceinline__ void swap_scan_heavy(const Store& S, int v, int* sx, int* sp,
                                                 int2* items, int* nI, int icap, double* gains,
@@ -2999,7 +3076,7 @@ int op_coarsen(MeshSet& m, int max_rounds) {
     zero_round(m, nxt);
     PM_LAUNCH(k_coarsen_scan, gv, bs, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
               w.target, w.cand, w.ncand, w.C, w.counts + CN_C, w.cmark, tag, pass0, w.items,
-              w.counts + CN_I);
+              w.counts + CN_I, w.gains);
     // one dense wave checking every vertex's best candidate, then the
     // remaining candidates of the vertices whose best one failed
     PM_LAUNCH(k_coarsen_check, gv, bs, 0, m.stream, m.S, w.items, w.counts + CN_I, w.items2,
