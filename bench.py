@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--single-steps", type=int, default=2,
                     help="timed steps of the one-mesh-per-launch comparison (batch workload)")
     ap.add_argument("--roofline-kernel", default=None)
+    ap.add_argument("--select", default="hash", choices=["hash", "colour"],
+                    help="how a round's independent set is formed: hash-priority local maxima "
+                         "(default) or colour classes (the vertex graph coloured per pass)")
     ap.add_argument("--batch-every", type=int, default=1,
                     help="batch workload: every n-th mesh by initial size (a sub-batch for "
                          "profiling captures; 1 = the 512-mesh batch)")
@@ -313,7 +316,8 @@ def run_batch(args, rank, world, local):
     xy_d = torch.tensor(h_xy, device=dev)
     tri_d = torch.tensor(h_tri, device=dev)
     m_d = torch.tensor(h_m, device=dev)
-    params = [pm.Params(seed=w.params.seed) for w in mine]
+    sel = pm.SELECT_COLOUR if args.select == "colour" else pm.SELECT_HASH
+    params = [pm.Params(seed=w.params.seed, select=sel) for w in mine]
     cap = 40_000_000
     oxy = torch.empty((cap, 2), dtype=torch.float64, device=dev)
     otri = torch.empty((cap, 3), dtype=torch.int32, device=dev)
@@ -323,10 +327,13 @@ def run_batch(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.batch_every == 1:
         pool = oracle_pool(host_cores())  # spawned before any GPU work of this process
 
+    last = {"rounds": 0}
+
     def step():
         b = pm.Batch.from_device(xy_d, nv, tri_d, ne, stream=sp)
         b.set_metric_dev(m_d)
-        b.adapt(params)
+        st = b.adapt(params)
+        last["rounds"] = sum(x["rounds"] for x in st)
         _, c = b.get_mesh_dev(oxy, otri, om_)
         b.close()
         return int(c.sum())
@@ -400,7 +407,9 @@ def run_batch(args, rank, world, local):
     if args.kernel_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "elements/s",
-                              "ms_per_step": t_max / args.steps, "gpu_launches": launches}))
+                              "ms_per_step": t_max / args.steps, "gpu_launches": launches,
+                              "select": args.select, "rounds_per_step": last["rounds"],
+                              "output_triangles_per_step": tris // max(args.steps, 1)}))
         return
     # end to end through the host-pointer calls, inputs and outputs pinned
     pin = [torch.from_numpy(a).pin_memory() for a in (h_xy, h_tri, h_m)]
@@ -435,6 +444,7 @@ def run_batch(args, rank, world, local):
                    + BATCH_WORKLOAD, "meshes": len(ws),
                    "output_triangles_per_step": tris // max(args.steps, 1),
                    "l2": "flushed between steps (256 MiB write, untimed)",
+                   "independent_sets": args.select, "rounds_per_step": last["rounds"],
                    "parallelism": f"meshes split over {world} GPUs by size" if world > 1
                    else "single GPU"},
         "one_mesh_per_launch": {

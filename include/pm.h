@@ -66,13 +66,23 @@ typedef enum {
  *   seed             seed of the independent-set priorities.
  *   opt_smooth_rounds  rounds of optimisation-based smoothing run after the
  *                    Laplacian sweeps (0 = none).
- *   max_rounds       cap on the rounds of one operator call (0 = none). */
+ *   max_rounds       cap on the rounds of one operator call (0 = none).
+ *   select           how a round's independent set is formed (Sec. 3.2):
+ *                    PM_SELECT_HASH (0), the candidates whose hash priority
+ *                    beats every candidate neighbour's; PM_SELECT_COLOUR (1),
+ *                    the vertex graph coloured at the start of every
+ *                    collapse, flip and smoothing pass and round r taking
+ *                    the candidates of colour r mod (number of colours), with
+ *                    the same priority rule among neighbours of that colour.
+ *                    Optimisation smoothing always uses PM_SELECT_HASH. */
+enum { PM_SELECT_HASH = 0, PM_SELECT_COLOUR = 1 };
 typedef struct {
   double L_low, L_up, q_thresh;
   int32_t max_iter, max_smooth_sweeps;
   uint32_t seed;
   int32_t opt_smooth_rounds;
   int32_t max_rounds;
+  int32_t select;
 } pm_params;
 
 /* Counters of one call: rounds executed (every round that formed a

@@ -17,7 +17,7 @@ class OrParams(C.Structure):
     _fields_ = [("L_low", C.c_double), ("L_up", C.c_double), ("q_thresh", C.c_double),
                 ("max_iter", C.c_int32), ("max_smooth_sweeps", C.c_int32),
                 ("seed", C.c_uint32), ("opt_smooth_rounds", C.c_int32),
-                ("max_rounds", C.c_int32)]
+                ("max_rounds", C.c_int32), ("select_mode", C.c_int32)]
 
 
 class OrStats(C.Structure):
@@ -68,6 +68,8 @@ def lib():
         L.or_prio.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_prio.restype = C.c_uint32
         L.or_independent_set.argtypes = [P, up, C.c_uint32, C.c_uint32, up]
+        L.or_colour.argtypes = [P, C.c_uint32, C.c_uint32, ip]
+        L.or_colour.restype = C.c_int32
         L.or_coarsen_target.argtypes = [P, C.c_int32, C.POINTER(OrParams)]
         L.or_coarsen_target.restype = C.c_int32
         L.or_swap_target.argtypes = [P, C.c_int32, C.POINTER(OrParams), ip]
@@ -92,9 +94,9 @@ def _u(a):
 
 
 def make_params(L_low=0.4, L_up=2.0 ** 0.5, q_thresh=0.7, max_iter=10, max_smooth_sweeps=10,
-                seed=1, opt_smooth_rounds=0, max_rounds=0):
+                seed=1, opt_smooth_rounds=0, max_rounds=0, select_mode=0):
     return OrParams(L_low, L_up, q_thresh, max_iter, max_smooth_sweeps, seed & 0xFFFFFFFF,
-                    opt_smooth_rounds, max_rounds)
+                    opt_smooth_rounds, max_rounds, select_mode)
 
 
 class OracleError(RuntimeError):
@@ -222,6 +224,16 @@ class OracleMesh:
         out = np.zeros(cand.shape[0], np.uint8)
         lib().or_independent_set(self.h, _u(cand), seed & 0xFFFFFFFF, r & 0xFFFFFFFF, _u(out))
         return out
+
+    def colour(self, seed, r):
+        """(colour of every vertex slot, -1 when dead; number of colours) as a
+        pass whose first round counter is r colours the vertex graph."""
+        nv = np.zeros(1, np.int32)
+        ne = np.zeros(1, np.int32)
+        lib().or_get_raw(self.h, _i(nv), _i(ne), None, None, None, None, None, None)
+        col = np.zeros(int(nv[0]), np.int32)
+        n = int(lib().or_colour(self.h, seed & 0xFFFFFFFF, r & 0xFFFFFFFF, _i(col)))
+        return col, n
 
     def coarsen_target(self, v, p):
         return int(lib().or_coarsen_target(self.h, v, C.byref(p)))

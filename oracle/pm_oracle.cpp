@@ -50,7 +50,8 @@ struct Params {
   int32_t max_iter, max_smooth_sweeps;
   uint32_t seed;
   int32_t opt_smooth_rounds;
-  int32_t max_rounds;  // cap on rounds per operator call; 0 = none
+  int32_t max_rounds;   // cap on rounds per operator call; 0 = none
+  int32_t select_mode;  // 0: hash-priority sets; 1: colour classes (Sec. 3.2)
 };
 
 struct Stats {
@@ -71,6 +72,8 @@ struct OMesh {
   std::vector<uint8_t> talive;
   std::vector<std::vector<int>> NN, NE;  // sorted sets
   uint32_t r = 0;                        // round counter of the current call
+  std::vector<int> col;                  // colour of each vertex (colour-class sets)
+  int ncol = 1;                          // colours in use
   bool check_seq = false;                // round-equals-sequential self check
   int seq_fail = 0;
   int64_t euler0 = 1;                    // V - E + F at creation (1 for a disk)
@@ -336,14 +339,20 @@ uint32_t prio(uint32_t v, uint32_t seed, uint32_t r) {
 }
 
 // S = { v in C : prio(v) > prio(u) for every u in NN(v) that is also in C }.
+// With colour classes (by_colour): only the candidates of class m.r mod
+// ncol compete, and among them the same rule (a collapse or flip may have
+// joined two vertices of one class since the colouring).
 std::vector<int> independent_set(const OMesh& m, const std::vector<uint8_t>& inC,
-                                 const std::vector<int>& C, uint32_t seed) {
+                                 const std::vector<int>& C, uint32_t seed,
+                                 bool by_colour = false) {
   std::vector<int> S;
+  const int cls = by_colour ? (int)(m.r % (uint32_t)m.ncol) : -1;
   for (int v : C) {
+    if (by_colour && m.col[v] != cls) continue;
     uint32_t pv = prio((uint32_t)v, seed, m.r);
     bool best = true;
     for (int u : m.NN[v]) {
-      if (inC[u] && prio((uint32_t)u, seed, m.r) > pv) {
+      if (inC[u] && (!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) > pv) {
         best = false;
         break;
       }
@@ -351,6 +360,53 @@ std::vector<int> independent_set(const OMesh& m, const std::vector<uint8_t>& inC
     if (best) S.push_back(v);
   }
   return S;
+}
+
+// ---------------------------------------------------------------------------
+// Colouring of the vertex graph (Sec. 3.2: independent sets as colour
+// classes, re-coloured after the topology changes; here once per operator
+// pass).  Speculative rounds on a snapshot: every uncoloured live vertex
+// proposes the smallest colour that no coloured neighbour holds; of two
+// uncoloured neighbours proposing the same colour the one of lower priority
+// (prio with the pass's first round counter) withdraws; every other
+// proposal is kept.  The vertex of highest priority among the uncoloured
+// always keeps its proposal, so the rounds end.  Parity: pinned by the
+// colouring's properness, completeness and the smallest-free-colour rule
+// checked by brute force.
+// ---------------------------------------------------------------------------
+
+void colour_vertices(OMesh& m, uint32_t seed) {
+  const int nv = m.nv();
+  const uint32_t rc = m.r;
+  m.col.assign(nv, -1);
+  std::vector<int> prop(nv, -1);
+  for (;;) {
+    bool open = false;
+    for (int v = 0; v < nv; ++v) {
+      if (!m.valive[v] || m.col[v] >= 0) continue;
+      open = true;
+      std::vector<uint8_t> used(m.NN[v].size() + 1, 0);
+      for (int u : m.NN[v])
+        if (m.col[u] >= 0 && m.col[u] < (int)used.size()) used[m.col[u]] = 1;
+      int c = 0;
+      while (used[c]) ++c;
+      prop[v] = c;
+    }
+    if (!open) break;
+    std::vector<int> next = m.col;
+    for (int v = 0; v < nv; ++v) {
+      if (!m.valive[v] || m.col[v] >= 0) continue;
+      bool keep = true;
+      const uint32_t pv = prio((uint32_t)v, seed, rc);
+      for (int u : m.NN[v])
+        if (m.col[u] < 0 && prop[u] == prop[v] && prio((uint32_t)u, seed, rc) > pv) keep = false;
+      if (keep) next[v] = prop[v];
+    }
+    m.col.swap(next);
+  }
+  m.ncol = 1;
+  for (int v = 0; v < nv; ++v)
+    if (m.valive[v] && m.col[v] + 1 > m.ncol) m.ncol = m.col[v] + 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -781,6 +837,8 @@ int64_t op_coarsen(OMesh& m, const Params& P, Stats& st) {
   for (int v = 0; v < nv; ++v) dirty[v] = m.valive[v];
   std::vector<int> target(nv, -1);
   int64_t ops = 0, rounds = 0;
+  const bool by_colour = P.select_mode == 1;
+  if (by_colour) colour_vertices(m, P.seed);
   while (!round_cap(P, rounds)) {
     std::vector<int> C;
     for (int v = 0; v < nv; ++v) {
@@ -795,7 +853,7 @@ int64_t op_coarsen(OMesh& m, const Params& P, Stats& st) {
       }
     }
     if (C.empty()) break;
-    std::vector<int> S = independent_set(m, inC, C, P.seed);
+    std::vector<int> S = independent_set(m, inC, C, P.seed, by_colour);
     m.r += 1;
     ++rounds;
     OMesh before;
@@ -832,6 +890,8 @@ int64_t op_swap(OMesh& m, const Params& P, Stats& st) {
   for (int v = 0; v < nv; ++v) dirty[v] = m.valive[v];
   std::vector<SwapOp> ops_of(nv);
   int64_t ops = 0, rounds = 0;
+  const bool by_colour = P.select_mode == 1;
+  if (by_colour) colour_vertices(m, P.seed);
   while (!round_cap(P, rounds)) {
     std::vector<int> C;
     for (int v = 0; v < nv; ++v) {
@@ -845,7 +905,7 @@ int64_t op_swap(OMesh& m, const Params& P, Stats& st) {
       }
     }
     if (C.empty()) break;
-    std::vector<int> S = independent_set(m, inC, C, P.seed);
+    std::vector<int> S = independent_set(m, inC, C, P.seed, by_colour);
     m.r += 1;
     ++rounds;
     OMesh before;
@@ -989,6 +1049,9 @@ int64_t op_smooth_laplace(OMesh& m, const Params& P, Stats& st) {
   for (int v = 0; v < nv; ++v) pending[v] = m.valive[v] && !m.vbnd[v];
   std::vector<Move> mv(nv);
   int64_t moves = 0, rounds = 0;
+  // smoothing changes no topology: one colouring serves every sweep
+  const bool by_colour = P.select_mode == 1;
+  if (by_colour) colour_vertices(m, P.seed);
   for (int sweep = 0; sweep < P.max_smooth_sweeps; ++sweep) {
     int64_t moved_sweep = 0;
     std::fill(next.begin(), next.end(), 0);
@@ -1005,7 +1068,7 @@ int64_t op_smooth_laplace(OMesh& m, const Params& P, Stats& st) {
         }
       }
       if (C.empty()) break;
-      std::vector<int> S = independent_set(m, inC, C, P.seed);
+      std::vector<int> S = independent_set(m, inC, C, P.seed, by_colour);
       m.r += 1;
       ++rounds;
       OMesh before;
@@ -1495,6 +1558,17 @@ int32_t or_independent_set(or_mesh* m, const uint8_t* cand, uint32_t seed, uint3
   std::memset(inS, 0, (size_t)m->nv());
   for (int v : S) inS[v] = 1;
   return OK;
+}
+
+// Colours of the vertex graph as a pass with round counter r colours it
+// (-1 for dead slots); returns the number of colours.
+int32_t or_colour(or_mesh* m, uint32_t seed, uint32_t r, int32_t* col) {
+  const uint32_t keep = m->r;
+  m->r = r;
+  colour_vertices(*m, seed);
+  m->r = keep;
+  for (int v = 0; v < m->nv(); ++v) col[v] = m->col[v];
+  return m->ncol;
 }
 
 int32_t or_coarsen_target(or_mesh* m, int32_t v, const Params* P) { return coarsen_target(*m, v, *P); }

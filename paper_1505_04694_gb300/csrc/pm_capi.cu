@@ -64,6 +64,8 @@ pm_status check_params(const pm_params* p) {
   if (p->max_iter < 0 || p->max_smooth_sweeps < 0 || p->opt_smooth_rounds < 0 ||
       p->max_rounds < 0)
     return fail(PM_ERR_INVALID_ARG, "iteration, sweep and round limits must be >= 0");
+  if (p->select != PM_SELECT_HASH && p->select != PM_SELECT_COLOUR)
+    return fail(PM_ERR_INVALID_ARG, "select must be PM_SELECT_HASH or PM_SELECT_COLOUR");
   return PM_OK;
 }
 
@@ -161,6 +163,7 @@ pm_status create_set(const double* xy, const int32_t* nv, const int32_t* tri, co
   m.L_low.assign(nmesh, 0.4);
   m.L_up.assign(nmesh, std::sqrt(2.0));
   m.q_thresh.assign(nmesh, 0.7);
+  m.select.assign(nmesh, 0);
   std::vector<int> vcap(nmesh), ecap(nmesh);
   long long nvt = 0, net = 0;
   for (int i = 0; i < nmesh; ++i) {
@@ -239,6 +242,7 @@ pm_status begin_call(MeshSet& m, const pm_params* P, int stride) {
     m.L_low[i] = p.L_low;
     m.L_up[i] = p.L_up;
     m.q_thresh[i] = p.q_thresh;
+    m.select[i] = p.select;
   }
   pm_status s = cuda_status(upload_tab(m), "mesh table");
   if (s) return s;
@@ -627,6 +631,7 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params, p
   b.L_low.resize(n);
   b.L_up.resize(n);
   b.q_thresh.resize(n);
+  b.select.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     MeshSet& s = meshes[i]->set;
     W = std::max(W, s.S.W);
@@ -642,6 +647,7 @@ pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params, p
       b.L_low[i] = params[i].L_low;
       b.L_up[i] = params[i].L_up;
       b.q_thresh[i] = params[i].q_thresh;
+      b.select[i] = params[i].select;
     }
     st = cuda_status(upload_tab(b), "batch table");
   }

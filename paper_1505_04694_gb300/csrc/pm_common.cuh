@@ -46,6 +46,9 @@ struct MeshTab {
   // mesh; filled once per layout).
   int* vmesh;
   int* emesh;
+  int* select;  // PM_SELECT_* of each mesh
+  int* ncol;    // colours of each mesh's current colouring (colour-class sets)
+  int* col;     // colour of every vertex slot (colour-class sets; -1: none)
 };
 
 struct Store {

@@ -60,6 +60,8 @@ struct Work {
   int* cand = nullptr;             // collapse candidates of each vertex by (length, id), vslots * W
   int* ncand = nullptr;
   int* counts = nullptr;           // device counters (see CountIdx)
+  int* cprop = nullptr;            // colouring: proposed colour per vertex slot
+  int* cstamp = nullptr;           // colouring: round in which the slot was uncoloured
 };
 
 // The per-round counters sit between the two dirty-list counts so that one
@@ -85,6 +87,7 @@ struct MeshSet {
   std::vector<int> vbase, vcap, ebase, ecap, nv, ne;
   std::vector<uint32_t> seed;
   std::vector<double> L_low, L_up, q_thresh;
+  std::vector<int> select;  // PM_SELECT_* per mesh
   Store S{};          // device arrays (S.tab points into tabmem)
   Store B{};          // second buffer set for renumbering
   Work w{};

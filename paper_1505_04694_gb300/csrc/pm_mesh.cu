@@ -21,9 +21,9 @@ namespace {
 // process: page-locking is slow and gets slower after many allocate/free
 // cycles, so slots of one arena are handed out and recycled instead.
 constexpr size_t kPinnedSlot = 16384;
-// staging per mesh of upload_tab: band (double4), L_low/L_up/q_thresh, six
+// staging per mesh of upload_tab: band (double4), L_low/L_up/q_thresh, seven
 // ints, the seed
-constexpr size_t kTabUploadBytes = sizeof(double4) + 3 * sizeof(double) + 6 * sizeof(int) +
+constexpr size_t kTabUploadBytes = sizeof(double4) + 3 * sizeof(double) + 7 * sizeof(int) +
                                    sizeof(uint32_t);
 constexpr size_t kPinnedBlock = 64 * kPinnedSlot;
 std::mutex g_pin_mu;
@@ -623,7 +623,7 @@ cudaError_t upload_tab(MeshSet& m) {
   double4* band = (double4*)m.hup;
   double* dbl = (double*)(band + n);
   int* ints = (int*)(dbl + 3 * n);
-  uint32_t* seed = (uint32_t*)(ints + 6 * n);
+  uint32_t* seed = (uint32_t*)(ints + 7 * n);
   for (int i = 0; i < n; ++i) {
     ints[i] = m.vbase[i];
     ints[n + i] = m.vcap[i];
@@ -631,6 +631,7 @@ cudaError_t upload_tab(MeshSet& m) {
     ints[3 * n + i] = m.ecap[i];
     ints[4 * n + i] = m.nv[i];
     ints[5 * n + i] = m.ne[i];
+    ints[6 * n + i] = m.select.empty() ? 0 : m.select[i];
     seed[i] = m.seed[i];
     dbl[i] = m.L_low[i];
     dbl[n + i] = m.L_up[i];
@@ -640,7 +641,7 @@ cudaError_t upload_tab(MeshSet& m) {
     double blo = b * (1.0 - 1e-9), bhi = b * (1.0 + 1e-9);
     band[i] = make_double4(alo * alo, ahi * ahi, blo * blo, bhi * bhi);
   }
-  cudaError_t e = cudaMemcpyAsync(m.S.tab.vbase, ints, 6 * n * sizeof(int), cudaMemcpyHostToDevice,
+  cudaError_t e = cudaMemcpyAsync(m.S.tab.vbase, ints, 7 * n * sizeof(int), cudaMemcpyHostToDevice,
                                   m.stream);
   if (!e) e = cudaMemcpyAsync(m.S.tab.seed, seed, n * sizeof(uint32_t), cudaMemcpyHostToDevice,
                               m.stream);
@@ -722,7 +723,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   Carver cv;
   carve_store(cv, S);
   carve_store(cv, m.B);
-  size_t tab_bytes = (size_t)n * (6 * sizeof(int) + 2 * sizeof(uint32_t) + 3 * sizeof(int) +
+  size_t tab_bytes = (size_t)n * (8 * sizeof(int) + 2 * sizeof(uint32_t) + 3 * sizeof(int) +
                                   2 * sizeof(unsigned long long) + 3 * sizeof(double) +
                                   sizeof(double4)) +
                      2 * ((size_t)n + 1) * sizeof(int) + 64;
@@ -734,6 +735,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
     cv.add(&vmesh, vs);
     cv.add(&emesh, es);
   }
+  int* col = nullptr;
+  cv.add(&col, vs);
   Work& w = m.w;
   cv.add(&w.D[0], vs);
   cv.add(&w.D[1], vs);
@@ -767,6 +770,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   cv.add(&w.cand, (size_t)vs * W);
   cv.add(&w.ncand, vs);
   cv.add(&w.counts, CN_NUM + 2 * n + 8, true);
+  cv.add(&w.cprop, vs);
+  cv.add(&w.cstamp, vs, true);
   cv.add(&m.lidbuf, vs);
   cv.add(&m.voffbuf, n);
   int tiles = scan_tiles((int)std::max(vs, es) + 1);
@@ -789,6 +794,8 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   T.ecap = (int*)t; t += n * sizeof(int);
   T.nv = (int*)t; t += n * sizeof(int);
   T.ne = (int*)t; t += n * sizeof(int);
+  T.select = (int*)t; t += n * sizeof(int);
+  T.ncol = (int*)t; t += n * sizeof(int);
   T.seed = (uint32_t*)t; t += n * sizeof(uint32_t);
   T.r = (uint32_t*)t; t += n * sizeof(uint32_t);
   T.had = (int*)t; t += 2 * n * sizeof(int);  // two sets: persistent rounds alternate
@@ -796,6 +803,7 @@ cudaError_t set_alloc(MeshSet& m, const std::vector<int>& vcap, const std::vecto
   T.pre = (int*)t; t += 2 * ((size_t)n + 1) * sizeof(int);
   T.vmesh = vmesh;
   T.emesh = emesh;
+  T.col = col;
   m.mesh_index_ok = n == 1;
   m.B.tab = T;
   if (!m.st) {
@@ -856,6 +864,7 @@ cudaError_t grow(MeshSet& m, const std::vector<int>& vcap, const std::vector<int
   n2.L_low = m.L_low;
   n2.L_up = m.L_up;
   n2.q_thresh = m.q_thresh;
+  n2.select = m.select;
   n2.st = m.st;
   n2.hst = m.hst;
   n2.hcounts = m.hcounts;

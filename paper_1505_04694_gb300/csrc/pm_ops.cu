@@ -205,6 +205,10 @@ __global__ void k_select(Store S, const int* C, const int* nCp, const int* cmark
 __device__ __forceinline__ bool local_max(const Store& S, int v, const int* cmark, int tag) {
   MeshCtx c = ctx_of(S, v);
   uint32_t seed = S.tab.seed[c.mi], r = S.tab.r[c.mi];
+  // colour-class sets: only the candidates of colour r mod ncol compete
+  const bool by_colour = S.tab.select[c.mi] == PM_SELECT_COLOUR;
+  const int cls = by_colour ? (int)(r % (uint32_t)S.tab.ncol[c.mi]) : 0;
+  if (by_colour && S.tab.col[v] != cls) return false;
   uint32_t pv = prio(vid_of(S, v, c.vb), seed, r);
   const int* nn = nn_row(S, v);
   int nnl = S.NNlen[v];
@@ -214,10 +218,90 @@ __device__ __forceinline__ bool local_max(const Store& S, int v, const int* cmar
     int u = c.vb + nn[k];
     int cu = cmark[u];
     uint32_t iu = vid_of(S, u, c.vb);
-    win &= !(cu == tag && prio(iu, seed, r) > pv);
+    win &= !(cu == tag && (!by_colour || S.tab.col[u] == cls) && prio(iu, seed, r) > pv);
   }
   return win;
 }
+
+// ---- colouring of the vertex graph (Sec. 3.2, colour-class sets) --------------
+// Speculative rounds on a snapshot, the same as the oracle's: every uncoloured
+// live vertex of a mesh in colour mode proposes the smallest colour no
+// coloured neighbour holds; of two uncoloured neighbours proposing the same
+// colour the one of lower priority (prio with the mesh's round counter at the
+// start of the pass) withdraws; the others keep their proposals.  The
+// proposals of a round are stamped with the round, so the resolve pass reads
+// only stamps and proposals while it writes colours.
+__global__ void k_colour_init(Store S, int* U, int* nU) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nmesh; i += gridDim.x * blockDim.x)
+    S.tab.ncol[i] = 1;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < S.vused; i0 += gridDim.x * blockDim.x) {
+    const int s = i0 + threadIdx.x;
+    bool take = false;
+    if (s < S.vused) {
+      S.tab.col[s] = -1;
+      const int mi = mesh_of_vslot(S, s);
+      take = s - S.tab.vbase[mi] < S.tab.nv[mi] && S.tab.active[mi] &&
+             S.tab.select[mi] == PM_SELECT_COLOUR && (S.vflag[s] & VF_ALIVE);
+    }
+    warp_append(take, s, U, nU);
+  }
+}
+
+__global__ void k_colour_propose(Store S, const int* U, const int* nUp, int* prop, int* stamp,
+                                 int rt) {
+  const int n = *nUp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int v = U[i];
+    const int vb = S.tab.vbase[mesh_of_vslot(S, v)];
+    const int* nn = nn_row(S, v);
+    const int nnl = S.NNlen[v];
+    RowMask used;  // colours 0..127 held by coloured neighbours
+#pragma unroll 4
+    for (int k = 0; k < nnl; ++k) {
+      const int c = S.tab.col[vb + nn[k]];
+      if (c >= 0 && c < MAXW) used.set(c);
+    }
+    int c = 0;
+    if (~used.lo) c = __ffsll((long long)~used.lo) - 1;
+    else if (~used.hi) c = 64 + __ffsll((long long)~used.hi) - 1;
+    else c = MAXW;  // a vertex of degree MAXW whose neighbours hold 0..MAXW-1
+    prop[v] = c;
+    stamp[v] = rt;
+  }
+}
+
+__global__ void k_colour_resolve(Store S, const int* U, const int* nUp, const int* prop,
+                                 const int* stamp, int rt, int* Un, int* nUn) {
+  const int n = *nUp;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    bool again = false;
+    int v = 0;
+    if (i < n) {
+      v = U[i];
+      const int mi = mesh_of_vslot(S, v);
+      const int vb = S.tab.vbase[mi];
+      const uint32_t seed = S.tab.seed[mi], r = S.tab.r[mi];
+      const uint32_t pv = prio(vid_of(S, v, vb), seed, r);
+      const int pc = prop[v];
+      const int* nn = nn_row(S, v);
+      const int nnl = S.NNlen[v];
+      bool keep = true;
+#pragma unroll 4
+      for (int k = 0; k < nnl; ++k) {
+        const int u = vb + nn[k];
+        keep &= !(stamp[u] == rt && prop[u] == pc && prio(vid_of(S, u, vb), seed, r) > pv);
+      }
+      if (keep) {
+        S.tab.col[v] = pc;
+        atomicMax(S.tab.ncol + mi, pc + 1);
+      }
+      again = !keep;
+    }
+    warp_append(again, v, Un, nUn);
+  }
+}
+
 
 // End of a fused select-and-apply launch: the last block to finish advances
 // the round counter of every mesh that formed candidates (every block has
@@ -2904,6 +2988,36 @@ void zero_counts(MeshSet& m, int first, int num) {
   cudaMemsetAsync(m.w.counts + first, 0, num * sizeof(int), m.stream);
 }
 
+// Colours every active mesh whose parameters ask for colour-class sets, at
+// the start of a collapse, flip or smoothing pass: speculative rounds until
+// no vertex is left uncoloured (each round keeps at least the proposal of
+// the highest priority; the cap is far beyond any mesh's rounds).
+int colour_set(MeshSet& m) {
+  bool any = false;
+  for (int x : m.select) any |= x == PM_SELECT_COLOUR;
+  if (!any) return PM_OK;
+  Work& w = m.w;
+  const int g = grid_for(m, m.S.vused);
+  zero_counts(m, CN_D0, 1);
+  PM_LAUNCH(k_colour_init, g, BLOCK, 0, m.stream, m.S, w.D[0], w.counts + CN_D0);
+  int cur = 0;
+  for (int it = 0; it < (1 << 20); ++it) {
+    const int nxt = 1 - cur;
+    const int rt = (m.tag += 2);
+    zero_counts(m, cn_list(nxt), 1);
+    PM_LAUNCH(k_colour_propose, g, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
+              w.cprop, w.cstamp, rt);
+    PM_LAUNCH(k_colour_resolve, g, BLOCK, 0, m.stream, m.S, w.D[cur], w.counts + cn_list(cur),
+              w.cprop, w.cstamp, rt, w.D[nxt], w.counts + cn_list(nxt));
+    RoundIO io = read_round(m);
+    if (io.err) return io.err;
+    if (m.hcounts[cn_list(nxt)] == 0) return PM_OK;
+    cur = nxt;
+  }
+  set_last_error("colouring did not finish");
+  return PM_ERR_INVALID_MESH;
+}
+
 // The counters of a new round (C, S, A, E, I, I2) and of the list it fills
 // (D[nxt]); the list it reads keeps its count.
 void zero_round(MeshSet& m, int nxt) {
@@ -3038,6 +3152,7 @@ cudaError_t fetch_ops(MeshSet& m, std::vector<unsigned long long>& ops) {
 // round's list leaves out vertices whose last collapse evaluation found
 // nothing and whose inputs have not changed since.
 int op_coarsen(MeshSet& m, int max_rounds) {
+  if (int err = colour_set(m)) return err;
   const Tuning tu = tuning();
   const int bs = tu.block[TO_COARSEN], bps = tu.blocks_per_sm[TO_COARSEN];
   const int rlimit = tu.rounds_limit[0];
@@ -3111,6 +3226,7 @@ int op_coarsen(MeshSet& m, int max_rounds) {
 
 // Rounds of flips until no dirty vertex has an improving flip.
 int op_swap(MeshSet& m, int max_rounds) {
+  if (int err = colour_set(m)) return err;
   const Tuning tu = tuning();
   const int bs = tu.block[TO_SWAP], bps = tu.blocks_per_sm[TO_SWAP];
   const int rlimit = tu.rounds_limit[1];
@@ -3277,6 +3393,8 @@ int op_refine(MeshSet& m, int max_rounds) {
 
 // Laplacian sweeps, each a sequence of rounds over the sweep's pending set.
 int op_smooth(MeshSet& m, int max_sweeps, int max_rounds) {
+  // smoothing changes no topology: one colouring serves every sweep
+  if (int err = colour_set(m)) return err;
   const Tuning tu = tuning();
   const int bs = tu.block[TO_SMOOTH], bps = tu.blocks_per_sm[TO_SMOOTH];
   const int rlimit = tu.rounds_limit[2];

@@ -206,6 +206,7 @@ class Params:
     seed: int = 1
     opt_smooth_rounds: int = 0
     max_rounds: int = 0
+    select: int = 0
 
 
 @dataclass

@@ -40,7 +40,10 @@ class PmParams(C.Structure):
     _fields_ = [("L_low", C.c_double), ("L_up", C.c_double), ("q_thresh", C.c_double),
                 ("max_iter", C.c_int32), ("max_smooth_sweeps", C.c_int32),
                 ("seed", C.c_uint32), ("opt_smooth_rounds", C.c_int32),
-                ("max_rounds", C.c_int32)]
+                ("max_rounds", C.c_int32), ("select", C.c_int32)]
+
+
+SELECT_HASH, SELECT_COLOUR = 0, 1
 
 
 class PmStats(C.Structure):
@@ -173,11 +176,12 @@ class Params:
     seed: int = 1
     opt_smooth_rounds: int = 0
     max_rounds: int = 0
+    select: int = SELECT_HASH  # SELECT_COLOUR: colour-class sets (Sec. 3.2)
 
     def c(self) -> PmParams:
         return PmParams(self.L_low, self.L_up, self.q_thresh, self.max_iter,
                         self.max_smooth_sweeps, self.seed & 0xFFFFFFFF, self.opt_smooth_rounds,
-                        self.max_rounds)
+                        self.max_rounds, self.select)
 
 
 def as_params(p) -> PmParams:

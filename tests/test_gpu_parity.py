@@ -261,6 +261,47 @@ def test_batch_handle_equals_oracle_mesh_by_mesh():
     assert pm.lib.pm_get_mesh(b.h, pm._i(a), pm._i(c), None, None, None) == 1
 
 
+@pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (65, 100000, 2)])
+def test_colour_class_adapt_bit_exact(n, T, seed):
+    """Colour-class sets (pm_params.select = PM_SELECT_COLOUR): the vertex
+    graph coloured at the start of every collapse, flip and smoothing pass,
+    one class per round.  Mesh and counters equal the oracle's in the same
+    mode, on a mesh that runs in persistent rounds and on one whose first
+    rounds take the one-kernel-per-phase path."""
+    w = inputs.psi_workload(n, T, True, seed)
+    g = pm.Mesh.from_host(w.xy, w.tri, device=0)
+    g.set_metric(w.m)
+    sg = g.adapt(gp(seed, select=pm.SELECT_COLOUR))
+    gm = g.get_mesh()
+    g.close()
+    o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    so = o.adapt(op(seed, select_mode=1))
+    assert_same_mesh(gm, o.get_mesh(), f"colour classes {n}")
+    for k in STAT_KEYS:
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    # the same mesh with hash-priority sets takes other rounds
+    oh = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    assert oh.adapt(op(seed))["rounds"] != so["rounds"]
+
+
+def test_colour_class_batch_mixed_modes_bit_exact():
+    """A batch in which every other mesh uses colour-class sets: each mesh's
+    result and counters equal the oracle's in its own mode."""
+    ws = _small_batch()
+    modes = [i % 2 for i in range(len(ws))]
+    b = pm.Batch.from_host([(w.xy, w.tri) for w in ws], device=0)
+    b.set_metric(np.concatenate([w.m for w in ws]))
+    stats = b.adapt([gp(w.params.seed, select=md) for w, md in zip(ws, modes)])
+    got = b.get_meshes()
+    b.close()
+    for w, g, st, md in zip(ws, got, stats, modes):
+        o = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+        so = o.adapt(op(w.params.seed, select_mode=md))
+        assert_same_mesh(g, o.get_mesh(), f"{w.name} mode {md}")
+        for k in STAT_KEYS:
+            assert st[k] == so[k], (w.name, md, k, st[k], so[k])
+
+
 def test_batch_handle_device_arrays():
     """pm_batch_create_dev + pm_set_metric_dev + pm_batch_get_mesh_dev give the
     host path's meshes; a second adaptation of the same handle continues from
@@ -377,6 +418,9 @@ def test_rejects_invalid_input():
     assert e.value.status == 1
     with pytest.raises(pm.PmError) as e:
         g.adapt(pm.Params(L_low=2.0, L_up=1.0))
+    assert e.value.status == 1
+    with pytest.raises(pm.PmError) as e:
+        g.adapt(pm.Params(select=2))
     assert e.value.status == 1
 
 

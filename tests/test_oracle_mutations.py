@@ -28,6 +28,14 @@ PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 
 # (what, text in the oracle, planted text, pins that must fail)
 MUTATIONS = [
+    ("colouring: the lower priority keeps its proposal",
+     "        if (m.col[u] < 0 && prop[u] == prop[v] && prio((uint32_t)u, seed, rc) > pv) keep = false;",
+     "        if (m.col[u] < 0 && prop[u] == prop[v] && prio((uint32_t)u, seed, rc) < pv) keep = false;",
+     "colouring_proper_complete_smallest_free"),
+    ("colouring: proposals ignore coloured neighbours",
+     "        if (m.col[u] >= 0 && m.col[u] < (int)used.size()) used[m.col[u]] = 1;",
+     "        if (m.col[u] >= 0 && m.col[u] < 0) used[m.col[u]] = 1;",
+     "colouring_proper_complete_smallest_free"),
     ("orientation sign: the rounded formula decides every case",
      "const double ORIENT_FILTER = 8.0 * 1.1102230246251565e-16;  // 8 eps",
      "const double ORIENT_FILTER = 0.0;  // 8 eps",
@@ -61,8 +69,8 @@ MUTATIONS = [
      "  uint32_t sr = seed + 0x9E3779B9u * (r + 1u);",
      "round_zero"),
     ("independent set: non-candidate neighbours compete",
-     "if (inC[u] && prio((uint32_t)u, seed, m.r) > pv) {",
-     "if (prio((uint32_t)u, seed, m.r) > pv) {",
+     "if (inC[u] && (!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) > pv) {",
+     "if ((!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) > pv) {",
      "independent_set_brute_force"),
     ("collapse: boundary edges need two common neighbours",
      "if (common != (bedge ? 1 : 2)) return false;",

@@ -926,3 +926,65 @@ def test_orient_sign_exact():
         zeros += e == 0
     assert wrong > 50, wrong
     assert zeros >= 4, zeros
+
+
+# --- colouring and colour-class sets (Sec. 3.2) --------------------------------
+
+@pytest.mark.parametrize("n,T,seed", [(9, 300, 7), (17, 3000, 8)])
+def test_colouring_proper_complete_smallest_free(n, T, seed):
+    """The colouring of the vertex graph is proper and complete, every colour
+    below a vertex's own is held by one of its neighbours (each vertex takes
+    the smallest colour its neighbours coloured before it leave free, and
+    those keep their colours), and the local maxima of the priority take
+    colour 0 (in the first round every vertex proposes 0 and exactly the
+    local maxima keep it)."""
+    w = inputs.psi_workload(n, T, True, seed)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    nv = w.xy.shape[0]
+    NN, _ = MC.adjacency([tuple(int(a) for a in t) for t in w.tri], nv)
+    rng = np.random.default_rng(seed)
+    for _ in range(4):
+        s, r = int(rng.integers(0, 2 ** 32)), int(rng.integers(0, 1000))
+        col, ncol = om.colour(s, r)
+        assert (col >= 0).all() and ncol == col.max() + 1
+        pr = [O.prio(v, s, r) for v in range(nv)]
+        for v in range(nv):
+            assert all(col[u] != col[v] for u in NN[v])
+            assert set(range(col[v])) <= {int(col[u]) for u in NN[v]}
+            if all(pr[u] < pr[v] for u in NN[v]):
+                assert col[v] == 0
+        assert ncol <= max(len(a) for a in NN) + 1
+        col2, _ = om.colour(s, r)
+        assert np.array_equal(col, col2)
+
+
+def test_colour_class_first_round_collapses_colour_zero_candidates():
+    """With colour-class sets the first round of a collapse call takes class
+    r mod ncol = 0; a proper class is independent, so every candidate of
+    colour 0 collapses and no other vertex does."""
+    w = inputs.psi_workload(17, 1000, True, 3)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    nv = w.xy.shape[0]
+    seed = 4242
+    p = O.make_params(seed=seed, select_mode=1)
+    col, _ = om.colour(seed, 0)
+    cand = {v for v in range(nv) if om.coarsen_target(v, p) >= 0}
+    S = {v for v in cand if col[v] == 0}
+    assert len(S) >= 5
+    st = om.coarsen(O.make_params(seed=seed, max_rounds=1, select_mode=1))
+    assert st["collapses"] == len(S)
+    assert set(np.nonzero(om.get_raw()["valive"] == 0)[0].tolist()) == S
+
+
+@pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (25, 8000, 22)])
+def test_colour_class_adaptation_round_equals_sequential(n, T, seed):
+    w = inputs.psi_workload(n, T, True, seed)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    om.set_check_sequential(True)
+    st = om.adapt(O.make_params(seed=seed, select_mode=1))
+    assert not om.seq_failed()
+    assert om.check() == 0
+    xy, tri, m = om.get_mesh()
+    ok, why = MC.unit_square_ok(xy, tri)
+    assert ok, why
+    assert st["collapses"] > 0 and st["flips"] > 0 and st["moves"] > 0
