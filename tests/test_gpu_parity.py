@@ -302,6 +302,58 @@ def test_colour_class_batch_mixed_modes_bit_exact():
             assert st[k] == so[k], (w.name, md, k, st[k], so[k])
 
 
+def _edge_case_meshes():
+    """Small and degenerate inputs: one triangle (three corners), two
+    triangles, a strip of slivers 1e-7 high (orientation determinants of
+    order 1e-9, where the exact sign stages decide), and a grid whose metric
+    it already satisfies (nothing to do)."""
+    out = []
+    one = (np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), np.array([[0, 1, 2]], np.int32))
+    out.append(("one triangle", one[0], one[1], inputs.uniform_metric(3, 0.3)))
+    xy, tri = inputs.grid_mesh(2)
+    out.append(("two triangles", xy, tri, inputs.uniform_metric(4, 0.4)))
+    xy, tri = inputs.grid_mesh(17)
+    xs = xy.copy()
+    xs[:, 1] *= 1e-7
+    out.append(("sliver strip", xs, tri, inputs.uniform_metric(xs.shape[0], 0.05)))
+    xy, tri = inputs.grid_mesh(9)
+    out.append(("already adapted", xy, tri, inputs.uniform_metric(xy.shape[0], 0.13)))
+    return out
+
+
+@pytest.mark.parametrize("select", [0, 1])
+def test_edge_cases_alone_and_in_a_ragged_batch(select):
+    """Each edge case adapted alone and inside one batch with a regular mesh
+    (sizes 1 to 3,000 triangles): mesh and counters equal the oracle's."""
+    cases = _edge_case_meshes()
+    w = inputs.psi_workload(17, 3000, True, 5)
+    cases.append(("psi", w.xy, w.tri, w.m))
+    want = []
+    for name, xy, tri, m in cases:
+        o = O.OracleMesh(xy, tri).set_metric(m)
+        so = o.adapt(op(7, select_mode=select))
+        want.append((name, o.get_mesh(), so))
+        g = pm.Mesh.from_host(xy, tri, device=0)
+        g.set_metric(m)
+        sg = g.adapt(gp(7, select=select))
+        assert_same_mesh(g.get_mesh(), o.get_mesh(), name)
+        g.close()
+        for k in STAT_KEYS:
+            assert sg[k] == so[k], (name, k, sg[k], so[k])
+    by = {name: so for name, _, so in want}
+    assert by["already adapted"]["collapses"] == by["already adapted"]["splits"] == 0
+    assert by["already adapted"]["converged"] == 1
+    b = pm.Batch.from_host([(xy, tri) for _, xy, tri, _ in cases], device=0)
+    b.set_metric(np.concatenate([m for _, _, _, m in cases]))
+    stats = b.adapt([gp(7, select=select)] * len(cases))
+    got = b.get_meshes()
+    b.close()
+    for (name, om, so), g, st in zip(want, got, stats):
+        assert_same_mesh(g, om, f"{name} in the batch")
+        for k in STAT_KEYS:
+            assert st[k] == so[k], (name, k, st[k], so[k])
+
+
 def test_batch_handle_device_arrays():
     """pm_batch_create_dev + pm_set_metric_dev + pm_batch_get_mesh_dev give the
     host path's meshes; a second adaptation of the same handle continues from
