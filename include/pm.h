@@ -103,9 +103,12 @@ typedef struct {
  *   mesh grows beyond it by itself when refinement needs room).
  * The metric starts as the identity; set it with pm_set_metric.
  * Builds the adjacency (Sec. 3.1: NN vertex-vertex and NE vertex-element
- * lists, kept as sorted sets) and checks the mesh: PM_ERR_INVALID_MESH when a
- * triangle is not counter-clockwise, an edge is used twice in the same
- * direction, a vertex is not manifold, or a vertex is not used. */
+ * lists, kept as sorted sets) and checks the mesh on the device, after the
+ * upload and before any adjacency is built: PM_ERR_INVALID_ARG for a
+ * non-finite coordinate; PM_ERR_INVALID_MESH when a vertex id lies outside
+ * [0, nv) or repeats in a triangle, a triangle is not counter-clockwise, an
+ * edge is used twice in the same direction, a vertex is not manifold, or a
+ * vertex is not used. */
 pm_status pm_mesh_create(const double* xy, int32_t nv, const int32_t* tri, int32_t ne,
                          const uint8_t* corner, int32_t cap_factor, int device,
                          pm_mesh** out);

@@ -315,6 +315,16 @@ __global__ void k_corners(Store S, int given) {
   }
 }
 
+// Every used vertex slot holds finite coordinates (PM_ERR_INVALID_ARG).
+__global__ void k_validate_coords(Store S, DevStatus* st) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.vused; s += gridDim.x * blockDim.x) {
+    const int mi = mesh_of_vslot(S, s);
+    if (s - S.tab.vbase[mi] >= S.tab.nv[mi]) continue;
+    const double2 p = S.xy[s];
+    if (!isfinite(p.x) || !isfinite(p.y)) set_err(st, PM_ERR_INVALID_ARG);
+  }
+}
+
 // Ids in range, distinct, and every element counter-clockwise (canonical).
 __global__ void k_validate_elems(Store S, DevStatus* st) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.eused; s += gridDim.x * blockDim.x) {
@@ -999,6 +1009,9 @@ int refresh_quality(MeshSet& m) {
 int ensure_quality(MeshSet& m) { return m.qvalid ? PM_OK : refresh_quality(m); }
 
 int validate_mesh(MeshSet& m) {
+  PM_LAUNCH(k_validate_coords, grid_for(m, m.S.vused), BLOCK, 0, m.stream, m.S, m.st);
+  int err = sync_status(m);
+  if (err) return err;  // orientations of non-finite points mean nothing
   PM_LAUNCH(k_validate_elems, grid_for(m, m.S.eused), BLOCK, 0, m.stream, m.S, m.st);
   return sync_status(m);
 }

@@ -57,19 +57,24 @@ def test_argument_checks_need_no_device(pm):
     assert pm.lib.pm_selftest_orient_dev(None, None, 4, None) == 1
 
 
-def test_out_of_range_ids_rejected_on_host(pm):
+def test_create_arguments_checked_on_host(pm):
+    """Pointer and size arguments are refused before any device work (vertex
+    ids and coordinates are checked on the device after the upload, which
+    the GPU tests cover)."""
     import numpy as np
 
     xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
-    tri = np.array([[0, 1, 7]], np.int32)
+    tri = np.array([[0, 1, 2]], np.int32)
     out = C.c_void_p()
-    s = pm.lib.pm_mesh_create(pm._d(xy), 3, pm._i(tri), 1, None, 1, 0, C.byref(out))
-    # the id check runs before the device is touched
-    assert s == 2
+    assert pm.lib.pm_mesh_create(None, 3, pm._i(tri), 1, None, 1, 0, C.byref(out)) == 1
+    assert pm.lib.pm_mesh_create(pm._d(xy), 2, pm._i(tri), 1, None, 1, 0, C.byref(out)) == 1
+    assert pm.lib.pm_mesh_create(pm._d(xy), 3, pm._i(tri), 0, None, 1, 0, C.byref(out)) == 1
+    assert pm.lib.pm_mesh_create(pm._d(xy), 3, pm._i(tri), 1, None, 0, 0, C.byref(out)) == 1
+    assert not out.value
 
 
 def test_struct_layouts_match_header(pm):
-    assert C.sizeof(pm.PmParams) == 3 * 8 + 5 * 4 + 4  # padded to 8
+    assert C.sizeof(pm.PmParams) == 3 * 8 + 6 * 4
     assert C.sizeof(pm.PmStats) == 5 * 8 + 8 + 8
 
 
@@ -81,9 +86,8 @@ def test_batch_arguments_checked_on_host(pm):
     nv = np.array([3, 3], np.int32)
     ne = np.array([1, 1], np.int32)
     good = np.array([[0, 1, 2], [0, 1, 2]], np.int32)
-    bad = np.array([[0, 1, 2], [0, 1, 3]], np.int32)  # id 3 is outside the second mesh
+    # (an id outside its mesh is found on the device after the upload: GPU test)
     f = pm.lib.pm_batch_create
-    assert f(pm._d(xy), pm._i(nv), pm._i(bad), pm._i(ne), 2, None, 1, 0, C.byref(out)) == 2
     assert f(pm._d(xy), pm._i(nv), pm._i(good), pm._i(ne), 0, None, 1, 0, C.byref(out)) == 1
     nv1 = np.array([3, 2], np.int32)
     assert f(pm._d(xy), pm._i(nv1), pm._i(good), pm._i(ne), 2, None, 1, 0, C.byref(out)) == 1

@@ -462,6 +462,24 @@ def test_rejects_invalid_input():
     with pytest.raises(pm.PmError) as e:
         pm.Mesh.from_host(xy, bad, device=0)
     assert e.value.status == 2
+    # a vertex id out of range, alone and as the second mesh of a batch
+    # (checked on the device before any adjacency is built)
+    bad = tri.copy()
+    bad[5, 1] = xy.shape[0] + 7
+    with pytest.raises(pm.PmError) as e:
+        pm.Mesh.from_host(xy, bad, device=0)
+    assert e.value.status == 2
+    with pytest.raises(pm.PmError) as e:
+        pm.Batch.from_host([(xy, tri), (xy, bad)], device=0)
+    assert e.value.status == 2
+    # a non-finite coordinate
+    nan = xy.copy()
+    nan[6, 0] = np.nan
+    for make in (lambda: pm.Mesh.from_host(nan, tri, device=0),
+                 lambda: pm.Batch.from_host([(xy, tri), (nan, tri)], device=0)):
+        with pytest.raises(pm.PmError) as e:
+            make()
+        assert e.value.status == 1
     g = pm.Mesh.from_host(xy, tri, device=0)
     m = inputs.uniform_metric(xy.shape[0], 0.1)
     m[4, 2] = -1.0
