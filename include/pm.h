@@ -213,7 +213,7 @@ pm_status pm_batch_get_mesh_dev(pm_mesh* mesh, int32_t* nv, int32_t* ne, double*
  * Two-call protocol: with null arrays only *nv and *ne are written.
  * xy[2*nv], tri[3*ne], m[3*nv] may each be null.  Host arrays in page-locked
  * memory (cudaHostAlloc / pinned) are filled by direct DMA; pageable ones go
- * through the driver's staging copy, several times slower. */
+ * through the CUDA driver's staging copy, several times slower. */
 pm_status pm_get_mesh(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
                       double* m);
 pm_status pm_get_mesh_dev(pm_mesh* mesh, int32_t* nv, int32_t* ne, double* xy, int32_t* tri,
