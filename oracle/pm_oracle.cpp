@@ -16,8 +16,14 @@
 //  * Sec. 2.4: the four kernels (collapse, split + templates, flip, smoothing)
 //    and propagation (operators sweep until nothing changes).
 //  * Sec. 3.2: every operator runs in rounds; each round processes one
-//    independent set of the vertex graph.  Here the set is the local maxima of
-//    a hash priority among the round's candidates.
+//    independent set of the vertex graph.  By default the set is the local
+//    maxima of a hash priority among the round's candidates; with
+//    select_mode 1 the vertex graph is coloured at the start of each
+//    collapse, flip and smoothing pass and round r takes the candidates of
+//    colour r mod (number of colours), the paper's own scheme.
+//  * Sec. 2.4 validity tests (an element counter-clockwise, a point in the
+//    closed element, a corner): the sign of the exact orientation
+//    determinant (a floating-point filter, else an exact expansion).
 //  * Sec. 3.3: deferred update.  While a round applies its operations, every
 //    adjacency change is queued as a record addressed to the vertex whose list
 //    changes; the queue is committed only after the whole set was processed.
