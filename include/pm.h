@@ -28,9 +28,12 @@
  *   - The library owns all device state of a mesh (released by
  *     pm_mesh_destroy).  A handle is not thread-safe; different handles may be
  *     used from different threads.
- *   - Every call returns a pm_status.  Invalid arguments are rejected before
- *     any device work.  Errors detected on the device (capacity, timeout)
- *     come back through a status word; pm_last_error() gives a message.
+ *   - Every call returns a pm_status.  Invalid pointers, sizes and parameters
+ *     are rejected before any device work; the contents of input arrays
+ *     (vertex ids, coordinates, metric) are checked on the device after their
+ *     upload and before the mesh is built or adapted.  Errors detected on the
+ *     device (invalid contents, capacity, timeout) come back through a status
+ *     word; pm_last_error() gives a message.
  */
 #ifndef PM_H
 #define PM_H
