@@ -158,7 +158,7 @@ pm_status pm_opt_smooth(pm_mesh* mesh, const pm_params* params, pm_stats* stats)
 
 /* Adapt n meshes together (each with its own parameters and seed): every
  * round of every operator is one launch per kernel over all meshes'
- * worklists.  Results are identical to n separate pm_adapt calls.
+ * worklists, and a run of small rounds one persistent launch.  Results are identical to n separate pm_adapt calls.
  * stats[n] may be null.  All meshes must live on the same device. */
 pm_status pm_adapt_batch(pm_mesh** meshes, int32_t n, const pm_params* params,
                          pm_stats* stats);
