@@ -36,6 +36,14 @@ MUTATIONS = [
      "        if (m.col[u] >= 0 && m.col[u] < (int)used.size()) used[m.col[u]] = 1;",
      "        if (m.col[u] >= 0 && m.col[u] < 0) used[m.col[u]] = 1;",
      "colouring_proper_complete_smallest_free"),
+    ("colour classes: a round takes the next class",
+     "  const int cls = by_colour ? (int)(m.r % (uint32_t)m.ncol) : -1;",
+     "  const int cls = by_colour ? (int)((m.r + 1u) % (uint32_t)m.ncol) : -1;",
+     "colour_class_first_round"),
+    ("colour classes: candidates of every class compete",
+     "    if (by_colour && m.col[v] != cls) continue;",
+     "    if (false && by_colour && m.col[v] != cls) continue;",
+     "colour_class_first_round"),
     ("orientation sign: the rounded formula decides every case",
      "const double ORIENT_FILTER = 8.0 * 1.1102230246251565e-16;  // 8 eps",
      "const double ORIENT_FILTER = 0.0;  // 8 eps",
