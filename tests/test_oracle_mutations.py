@@ -11,7 +11,9 @@ the orientation test rejects it first) and dropping the second orientation
 test of a flip (an inverted element has negative quality, so the gain test
 rejects it).  Nor is leaving a flip's two opposite vertices unmarked: a flip
 they would enable is found from its other end, and on the test meshes every
-pass still ends with nothing left to do.
+pass still ends with nothing left to do.  Nor is dropping one of the two
+tests that keep a boundary vertex on boundary edges: the candidate list and
+the collapse validity test each enforce it.
 """
 import os
 import subprocess
@@ -68,6 +70,14 @@ MUTATIONS = [
      "double f = s * (2.0 - s);",
      "double f = s * (2.0 - s * s);",
      "quality_right_isosceles"),
+    ("quality: determinant of the element metric with the wrong sign",
+     "  double AM = std::sqrt(k00 * k11 - k01 * k01) * area;\n  double xx = P / 3.0;",
+     "  double AM = std::sqrt(k00 * k11 + k01 * k01) * area;\n  double xx = P / 3.0;",
+     "quality_affine_invariance"),
+    ("quality: ideal perimeter taken as two",
+     "  double AM = std::sqrt(k00 * k11 - k01 * k01) * area;\n  double xx = P / 3.0;",
+     "  double AM = std::sqrt(k00 * k11 - k01 * k01) * area;\n  double xx = P / 2.0;",
+     "quality_equilateral_unit"),
     ("hash priority: wrong multiplier",
      "h *= 0x85ebca6bu;",
      "h *= 0x85ebca6du;",
@@ -83,6 +93,10 @@ MUTATIONS = [
     ("collapse: boundary edges need two common neighbours",
      "if (common != (bedge ? 1 : 2)) return false;",
      "if (common != (bedge ? 2 : 2)) return false;",
+     "collapse_rule_brute_force"),
+    ("collapse: candidates tried longest first",
+     "  std::sort(cand.begin(), cand.end());\n  for (const auto& c : cand)",
+     "  std::sort(cand.rbegin(), cand.rend());\n  for (const auto& c : cand)",
      "collapse_rule_brute_force"),
     ("collapse: new-edge bound relaxed",
      "if (metric_len(dw, m.vd(x)) > P.L_up) return false;",
@@ -100,6 +114,18 @@ MUTATIONS = [
      "    if (!found || op.gain > best.gain) {",
      "    if (!found || op.gain < best.gain) {",
      "flip_rule_brute_force"),
+    ("flip: the second new element clockwise",
+     "  m.tri[op.K2] = {op.d, op.w, op.c};",
+     "  m.tri[op.K2] = {op.w, op.d, op.c};",
+     "operators_keep_invariants_round_by_round"),
+    ("flip: the new edge missing from one end's row",
+     "  recs.push_back({op.d, NN_ADD, op.c});\n",
+     "",
+     "operators_keep_invariants_round_by_round"),
+    ("collapse: the surviving end keeps the removed vertex in its row",
+     "  recs.push_back({w, NN_DEL, v});\n  m.valive[v] = 0;",
+     "  m.valive[v] = 0;",
+     "operators_keep_invariants_round_by_round"),
     ("refinement: the longer diagonal",
      "if (d1 <= d2) {",
      "if (d1 > d2) {",
@@ -124,6 +150,10 @@ MUTATIONS = [
      "  return qmin > qold;\n}",
      "  return qmin >= qold;\n}",
      "strict_gain"),
+    ("refinement: the midpoint of a boundary edge is not a boundary vertex",
+     "      m.vbnd.push_back(edge_elements(m, a, b) == 1 ? 1 : 0);",
+     "      m.vbnd.push_back(0);",
+     "round_equals_sequential_and_invariants"),
     ("refinement: a midpoint takes one end's metric",
      "      m.m00.push_back(0.5 * (da.m00 + db.m00));",
      "      m.m00.push_back(0.5 * (da.m00 + da.m00));",
