@@ -73,14 +73,17 @@ def parse():
     return ap.parse_args()
 
 
-def dist_init(n):
+def dist_init(n, host_only=False):
+    """Rank, world size and local rank from the launcher's environment; a
+    process group when several ranks run (gloo for the oracle arm, whose
+    ranks hold no GPU work)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl" if n > 1 else "gloo")
+        dist.init_process_group("nccl" if n > 1 and not host_only else "gloo")
     return rank, world, local
 
 
@@ -738,7 +741,7 @@ def run_reference_single(args):
 
 def main():
     args = parse()
-    rank, world, local = dist_init(args.gpus)
+    rank, world, local = dist_init(args.gpus, host_only=args.impl == "reference")
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
