@@ -126,6 +126,18 @@ MUTATIONS = [
      "  recs.push_back({w, NN_DEL, v});\n  m.valive[v] = 0;",
      "  m.valive[v] = 0;",
      "operators_keep_invariants_round_by_round"),
+    ("refinement: the centre child of a three-split clockwise",
+     "      emit(K, false, m0, m1, m2);",
+     "      emit(K, false, m0, m2, m1);",
+     "operators_keep_invariants_round_by_round"),
+    ("refinement: a one-split child on the wrong end",
+     "      emit(K, false, mm, b, o);",
+     "      emit(K, false, mm, a, o);",
+     "operators_keep_invariants_round_by_round"),
+    ("refinement: a midpoint's x from one end",
+     "      m.x.push_back(0.5 * (da.x + db.x));",
+     "      m.x.push_back(0.5 * (da.x + da.x));",
+     "operators_keep_invariants_round_by_round"),
     ("refinement: the longer diagonal",
      "if (d1 <= d2) {",
      "if (d1 > d2) {",
@@ -193,6 +205,18 @@ MUTATIONS = [
     ("optimisation smoothing: first step doubled",
      "  double alpha = (0.1 * lmin) / gn;",
      "  double alpha = (0.2 * lmin) / gn;",
+     "step_rule"),
+    ("optimisation smoothing: a step kept without a rising quality sum",
+     "      if (ball_after_move(m, v, cand, qmin, qsum) && qmin >= qmin_old && qsum > qsum_old) {",
+     "      if (ball_after_move(m, v, cand, qmin, qsum) && qmin >= qmin_old) {",
+     "step_rule"),
+    ("optimisation smoothing: a step kept that lowers the minimum quality",
+     "      if (ball_after_move(m, v, cand, qmin, qsum) && qmin >= qmin_old && qsum > qsum_old) {",
+     "      if (ball_after_move(m, v, cand, qmin, qsum) && qsum > qsum_old) {",
+     "step_rule"),
+    ("optimisation smoothing: seven step sizes tried",
+     "  for (int k = 0; k < 6; ++k) {\n    double X = m.x[v] + alpha * gx;",
+     "  for (int k = 0; k < 7; ++k) {\n    double X = m.x[v] + alpha * gx;",
      "step_rule"),
     ("optimisation smoothing: step along a swapped gradient component",
      "    double X = m.x[v] + alpha * gx;",
