@@ -19,6 +19,7 @@ import os
 import subprocess
 import sys
 import textwrap
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -238,32 +239,53 @@ CHILD = textwrap.dedent("""
 """)
 
 
-def run_pins(tmp_path, src, sel):
-    """Compile `src` as the oracle and run the pins `sel` against it in a
-    child process; returns pytest's exit status and output."""
-    path = tmp_path / "pm_oracle.cpp"
-    path.write_text(src)
-    lib = tmp_path / "liboracle.so"
-    subprocess.check_call(["g++", *FLAGS, str(path), "-o", str(lib)])
+def read_source():
+    with open(SRC) as f:
+        return f.read()
+
+
+@pytest.fixture(scope="module")
+def libs(tmp_path_factory):
+    """The unchanged oracle and every mutant whose site occurs once, compiled
+    with the oracle's own flags, all at once (one g++ per core); maps a
+    mutation's name (None: unchanged) to its library."""
+    src = read_source()
+    d = tmp_path_factory.mktemp("mutants")
+    jobs = {None: src}
+    for what, old, new, _ in MUTATIONS:
+        if src.count(old) == 1:
+            jobs[what] = src.replace(old, new)
+    out = {}
+    for i, (what, text) in enumerate(jobs.items()):
+        (d / f"m{i}.cpp").write_text(text)
+        out[what] = d / f"m{i}.so"
+
+    def compile_one(i):
+        subprocess.check_call(["g++", *FLAGS, str(d / f"m{i}.cpp"), "-o", str(d / f"m{i}.so")])
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        list(ex.map(compile_one, range(len(jobs))))
+    return out
+
+
+def run_pins(lib, sel):
+    """Run the pins `sel` against the oracle library `lib` in a child
+    process; returns pytest's exit status and output."""
     code = CHILD.format(root=ROOT, lib=str(lib), pins=PINS, sel=sel)
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
                        timeout=600)
     return r.returncode, r.stdout
 
 
-def test_selected_pins_pass_on_the_unchanged_oracle(tmp_path):
-    with open(SRC) as f:
-        src = f.read()
+def test_selected_pins_pass_on_the_unchanged_oracle(libs):
     sel = " or ".join(sorted({m[3] for m in MUTATIONS}))
-    status, out = run_pins(tmp_path, src, sel)
+    status, out = run_pins(libs[None], sel)
     assert status == 0, out[-3000:]
 
 
 @pytest.mark.parametrize("what,old,new,sel", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(tmp_path, what, old, new, sel):
-    with open(SRC) as f:
-        src = f.read()
-    assert src.count(old) == 1, f"{what}: the planted site must occur once"
-    status, out = run_pins(tmp_path, src.replace(old, new), sel)
+def test_pins_catch_planted_mistake(libs, what, old, new, sel):
+    assert read_source().count(old) == 1, f"{what}: the planted site must occur once"
+    status, out = run_pins(libs[what], sel)
     # pytest's exit status 1: tests ran and some failed (5 would mean none ran)
     assert status == 1, f"{what}: pins {sel!r} did not fail\n{out[-3000:]}"
