@@ -91,6 +91,18 @@ MUTATIONS = [
      "if (inC[u] && (!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) > pv) {",
      "if ((!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) > pv) {",
      "independent_set_brute_force"),
+    ("independent set: the lower priority wins",
+     "if (inC[u] && (!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) > pv) {",
+     "if (inC[u] && (!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) < pv) {",
+     "independent_set_brute_force"),
+    ("collapse: candidates below twice L_low",
+     "    if (L < P.L_low) cand.push_back({L, w});",
+     "    if (L < 2.0 * P.L_low) cand.push_back({L, w});",
+     "collapse_rule_brute_force"),
+    ("refinement: edges split above half of L_up",
+     "      if (!(metric_len(m.vd(a), m.vd(b)) > P.L_up)) continue;",
+     "      if (!(metric_len(m.vd(a), m.vd(b)) > 0.5 * P.L_up)) continue;",
+     "small_uniform_exact_result"),
     ("collapse: boundary edges need two common neighbours",
      "if (common != (bedge ? 1 : 2)) return false;",
      "if (common != (bedge ? 2 : 2)) return false;",

@@ -450,11 +450,14 @@ def brute_collapse_valid(xy, tris, corner, v, w, L_up, elen):
     return True
 
 
-# L_up = 1.3 makes rule (iii) (no new edge longer than L_up) decide cases too
-@pytest.mark.parametrize("L_up", [2.5, 1.3])
-def test_collapse_rule_brute_force(L_up):
+# L_up = 1.3 makes rule (iii) (no new edge longer than L_up) decide cases too;
+# L_low = 0.5 makes the candidate bound decide cases: vertices with no valid
+# collapse below L_low but a valid one below 2 L_low (counted)
+@pytest.mark.parametrize("L_low,L_up", [(1.0, 2.5), (1.0, 1.3), (0.5, 2.5)])
+def test_collapse_rule_brute_force(L_low, L_up):
     checked = 0
     by_iii = 0  # candidates rejected by rule (iii) alone
+    by_low = 0  # vertices whose only valid collapses lie in [L_low, 2 L_low)
     for xy, tri, m in tiny_meshes():
         om = O.OracleMesh(xy, tri).set_metric(m)
         tris = [tuple(int(a) for a in t) for t in tri]
@@ -463,19 +466,21 @@ def test_collapse_rule_brute_force(L_up):
         NN, _ = MC.adjacency(tris, xy.shape[0])
         bedges = MC.boundary_edges(tris)
         bverts = {a for e in bedges for a in e}
-        p = O.make_params(L_low=1.0, L_up=L_up)
+        p = O.make_params(L_low=L_low, L_up=L_up)
 
         def elen(a, b):
             return O.edge_length(xy[a], m[a], xy[b], m[b])
 
         for v in range(xy.shape[0]):
-            cands = []
+            cands, near = [], []
             for w in sorted(NN[v]):
                 if v in bverts and not ((v, w) in bedges or (w, v) in bedges):
                     continue
                 L = elen(v, w)
                 if L < p.L_low:
                     cands.append((L, w))
+                elif L < 2.0 * p.L_low:
+                    near.append(w)
             cands.sort()
             expect = -1
             if not corner[v]:
@@ -484,11 +489,16 @@ def test_collapse_rule_brute_force(L_up):
                         expect = w
                         break
                     by_iii += brute_collapse_valid(xy, tris, corner, v, w, math.inf, elen)
+                if expect < 0:
+                    by_low += any(brute_collapse_valid(xy, tris, corner, v, w, p.L_up, elen)
+                                  for w in near)
             assert om.coarsen_target(v, p) == expect, (v, cands)
             checked += len(cands)
     assert checked > 50
     if L_up < 2.0:
         assert by_iii > 5
+    if L_low < 1.0:
+        assert by_low > 5, by_low
 
 
 # q_thresh = 1 lists every edge; on these meshes the improving flips have old
