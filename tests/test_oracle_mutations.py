@@ -13,7 +13,9 @@ rejects it).  Nor is leaving a flip's two opposite vertices unmarked: a flip
 they would enable is found from its other end, and on the test meshes every
 pass still ends with nothing left to do.  Nor is dropping one of the two
 tests that keep a boundary vertex on boundary edges: the candidate list and
-the collapse validity test each enforce it.
+the collapse validity test each enforce it.  Nor is allowing a zero-area
+element after a smoothing move: its quality is 0, so the move has no strict
+gain.
 """
 import os
 import subprocess
@@ -103,6 +105,14 @@ MUTATIONS = [
      "      if (!(metric_len(m.vd(a), m.vd(b)) > P.L_up)) continue;",
      "      if (!(metric_len(m.vd(a), m.vd(b)) > 0.5 * P.L_up)) continue;",
      "small_uniform_exact_result"),
+    ("collapse: a degenerate element allowed",
+     "    if (orient_sign(d[0], d[1], d[2]) <= 0) return false;\n  }\n  for (int x : m.NN[v]) {",
+     "    if (orient_sign(d[0], d[1], d[2]) < 0) return false;\n  }\n  for (int x : m.NN[v]) {",
+     "collapse_rule_brute_force"),
+    ("smoothing: candidates up to twice the quality threshold",
+     "  if (!(qold < P.q_thresh)) return false;\n  double a00 = 0.0",
+     "  if (!(qold < 2.0 * P.q_thresh)) return false;\n  double a00 = 0.0",
+     "below_the_quality_threshold"),
     ("collapse: boundary edges need two common neighbours",
      "if (common != (bedge ? 1 : 2)) return false;",
      "if (common != (bedge ? 2 : 2)) return false;",

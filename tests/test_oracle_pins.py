@@ -421,7 +421,34 @@ def tiny_meshes():
     return out
 
 
-def brute_collapse_valid(xy, tris, corner, v, w, L_up, elen):
+def grid_random_diagonals(n, seed):
+    """Unjittered n x n grid of the unit square (n - 1 a power of two, so the
+    coordinates are exact), each square cut along a random diagonal, with
+    random anisotropic metrics as in tiny_meshes: many exactly collinear
+    vertex triples, so some collapses would leave a zero-area element."""
+    rng = np.random.default_rng(seed)
+    g = np.arange(n) / (n - 1)
+    xy = np.array([[x, y] for y in g for x in g])
+    tri = []
+    for j in range(n - 1):
+        for i in range(n - 1):
+            a, b, c, d = j * n + i, j * n + i + 1, (j + 1) * n + i + 1, (j + 1) * n + i
+            tri += [(a, b, c), (a, c, d)] if rng.random() < 0.5 else [(a, b, d), (b, c, d)]
+    m = []
+    for _ in range(xy.shape[0]):
+        th = rng.uniform(0, math.pi)
+        h1 = (1.0 / (n - 1)) * rng.uniform(1.0, 4.0)
+        h2 = h1 * rng.uniform(1.0, 3.0)
+        c_, s_ = math.cos(th), math.sin(th)
+        a_, b_ = 1 / h1 ** 2, 1 / h2 ** 2
+        m.append([a_ * c_ * c_ + b_ * s_ * s_, (a_ - b_) * c_ * s_, a_ * s_ * s_ + b_ * c_ * c_])
+    return xy, np.array(tri, dtype=np.int32), np.array(m)
+
+
+def brute_collapse_valid(xy, tris, corner, v, w, L_up, elen, flat_ok=False):
+    """Collapse of v onto w checked on the triangulation it would leave, in
+    exact arithmetic; flat_ok accepts elements of zero area (for counting the
+    cases where that requirement decides)."""
     NN, NE = MC.adjacency(tris, xy.shape[0])
     bedges = MC.boundary_edges(tris)
     bverts = {a for e in bedges for a in e}
@@ -435,7 +462,12 @@ def brute_collapse_valid(xy, tris, corner, v, w, L_up, elen):
         if v in t and w in t:
             continue
         new.append(tuple(w if a == v else a for a in t))
-    ok, _ = MC.valid_triangulation(xy, new)
+    if flat_ok:
+        if any(MC.exact_orient(xy[t[0]], xy[t[1]], xy[t[2]]) < 0 for t in new):
+            return False
+        ok, _ = MC.valid_triangulation(xy, new, exact=False)
+    else:
+        ok, _ = MC.valid_triangulation(xy, new)
     if not ok:
         return False
     if MC.total_area_exact(xy, new) != MC.total_area_exact(xy, tris):
@@ -452,13 +484,19 @@ def brute_collapse_valid(xy, tris, corner, v, w, L_up, elen):
 
 # L_up = 1.3 makes rule (iii) (no new edge longer than L_up) decide cases too;
 # L_low = 0.5 makes the candidate bound decide cases: vertices with no valid
-# collapse below L_low but a valid one below 2 L_low (counted)
+# collapse below L_low but a valid one below 2 L_low (counted); with the first
+# bounds, unjittered grids make rule (ii)'s strict orientation decide cases:
+# vertices whose target would change if a zero-area element were allowed
+# (counted)
 @pytest.mark.parametrize("L_low,L_up", [(1.0, 2.5), (1.0, 1.3), (0.5, 2.5)])
 def test_collapse_rule_brute_force(L_low, L_up):
     checked = 0
     by_iii = 0  # candidates rejected by rule (iii) alone
     by_low = 0  # vertices whose only valid collapses lie in [L_low, 2 L_low)
-    for xy, tri, m in tiny_meshes():
+    by_flat = 0  # vertices whose target a zero-area element would change
+    grids = L_low == 1.0 and L_up == 2.5  # the unjittered grids: once
+    meshes = tiny_meshes() + ([grid_random_diagonals(9, s) for s in range(41, 47)] if grids else [])
+    for xy, tri, m in meshes:
         om = O.OracleMesh(xy, tri).set_metric(m)
         tris = [tuple(int(a) for a in t) for t in tri]
         raw = om.get_raw()
@@ -492,9 +530,14 @@ def test_collapse_rule_brute_force(L_low, L_up):
                 if expect < 0:
                     by_low += any(brute_collapse_valid(xy, tris, corner, v, w, p.L_up, elen)
                                   for w in near)
+                flat = next((w for L, w in cands if brute_collapse_valid(
+                    xy, tris, corner, v, w, p.L_up, elen, flat_ok=True)), -1)
+                by_flat += flat != expect
             assert om.coarsen_target(v, p) == expect, (v, cands)
             checked += len(cands)
     assert checked > 50
+    if grids:
+        assert by_flat > 5, by_flat
     if L_up < 2.0:
         assert by_iii > 5
     if L_low < 1.0:
@@ -748,6 +791,33 @@ def test_smoothing_sweeps_leave_only_moved_vertices_movable(n, T, seed):
     om.smooth(O.make_params(seed=seed + 1, max_smooth_sweeps=1, max_rounds=1))
     moved2 = set(np.nonzero((om.get_raw()["xy"] != xy1).any(axis=1))[0].tolist())
     assert moved2 and moved2 <= moved1
+
+
+def test_smoothing_candidates_lie_below_the_quality_threshold():
+    """S12 and S14: only a vertex whose ball holds an element of quality below
+    q_thresh is smoothed.  A round at q_thresh = 0.5 moves no vertex whose
+    ball minimum was at least 0.5; the same round at q_thresh = 1.01 moves
+    some of them, so the threshold decides cases (counted)."""
+    w = inputs.psi_workload(25, 8000, True, 4)
+    counts = {}
+    for thresh in (0.5, 1.01):
+        om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+        p = O.make_params(seed=4)
+        om.refine(p)
+        om.swap(p)
+        raw0 = om.get_raw()
+        q = om.quality_elems()
+        qmin = np.full(raw0["xy"].shape[0], np.inf)
+        for t, alive, qk in zip(raw0["tri"], raw0["talive"], q):
+            if alive:
+                for a in t:
+                    qmin[a] = min(qmin[a], qk)
+        om.smooth(O.make_params(seed=4, q_thresh=thresh, max_smooth_sweeps=1, max_rounds=1))
+        moved = np.nonzero((om.get_raw()["xy"] != raw0["xy"]).any(axis=1))[0]
+        assert moved.size > 0
+        counts[thresh] = int((qmin[moved] >= 0.5).sum())
+    assert counts[0.5] == 0
+    assert counts[1.01] > 5, counts
 
 
 def test_smoothing_never_lowers_ball_min_quality():
