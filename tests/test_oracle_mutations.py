@@ -133,6 +133,10 @@ MUTATIONS = [
      "double qold = (q1 < q2) ? q1 : q2;\n  if (!(qold < P.q_thresh)) return false;",
      "double qold = (q1 < q2) ? q1 : q2;\n  if (!(qold < 2.0 * P.q_thresh)) return false;",
      "flip_rule_brute_force"),
+    ("flip: a flip without gain taken",
+     "  if (!(gain > 0.0)) return false;",
+     "  if (!(gain >= 0.0)) return false;",
+     "flip_needs_a_strict_gain"),
     ("flip: the smallest gain wins",
      "    if (!found || op.gain > best.gain) {",
      "    if (!found || op.gain < best.gain) {",

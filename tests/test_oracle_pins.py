@@ -544,6 +544,21 @@ def test_collapse_rule_brute_force(L_low, L_up):
         assert by_low > 5, by_low
 
 
+def test_flip_needs_a_strict_gain():
+    """Sec. 2.4.3: an edge is flipped only when the flip raises the minimum
+    quality.  On unjittered grids under a uniform metric every element is a
+    right isosceles triangle and a flip of a square's diagonal gives two
+    congruent ones (gain zero, up to the summation order of the perimeter):
+    with every edge listed, no flip is made."""
+    for n, seed in ((5, 41), (9, 42), (17, 43)):
+        xy, tri, _ = grid_random_diagonals(n, seed)
+        m = np.tile([float((n - 1) ** 2), 0.0, float((n - 1) ** 2)], (xy.shape[0], 1))
+        om = O.OracleMesh(xy, tri).set_metric(m)
+        st = om.swap(O.make_params(q_thresh=1.01, max_rounds=500))
+        assert st["flips"] == 0, (n, st)
+        np.testing.assert_array_equal(om.get_raw()["tri"], tri)
+
+
 # q_thresh = 1 lists every edge; on these meshes the improving flips have old
 # qualities from 0.03 to 0.67 (median 0.14), so 0.15 lets the threshold decide
 @pytest.mark.parametrize("q_thresh", [1.0, 0.15])
