@@ -213,6 +213,14 @@ MUTATIONS = [
      "    int64_t n = refine_round(m, P, st);\n    if (n == 0) break;",
      "    int64_t n = refine_round(m, P, st);\n    if (n == 0 || rounds == 3) break;",
      "no_edge_too_long"),
+    ("Algorithm 1: refinement first",
+     "    int64_t n = op_coarsen(*m, *P, local);\n    n += op_swap(*m, *P, local);\n    n += op_refine(*m, *P, local);",
+     "    int64_t n = op_refine(*m, *P, local);\n    n += op_coarsen(*m, *P, local);\n    n += op_swap(*m, *P, local);",
+     "algorithm_1"),
+    ("Algorithm 1: no renumbering between iterations",
+     "    renumber(*m);\n    if (n == 0) {\n      local.converged = 1;",
+     "    if (n == 0) {\n      local.converged = 1;",
+     "algorithm_1"),
     ("Algorithm 1: stops after one iteration",
      "    if (n == 0) {\n      local.converged = 1;",
      "    if (n >= 0) {\n      local.converged = 1;",

@@ -670,6 +670,44 @@ def test_round_equals_sequential_and_invariants(n, T, seed):
     assert st["collapses"] > 0 and st["flips"] > 0 and st["splits"] > 0 and st["moves"] > 0
 
 
+@pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (25, 8000, 22)])
+def test_adapt_is_algorithm_1(n, T, seed):
+    """Algorithm 1 (Sec. 2.3) written out with the single-operator calls:
+    repeat {coarsen; swap; refine} (renumbering after each iteration) until
+    an iteration changes nothing or max_iter, then smooth.  Each call starts
+    its round counter at 0, and seed_r = seed + 0x9E3779B9 r, so a call given
+    seed + 0x9E3779B9 r0 continues a counter that stood at r0.  The mesh and
+    the counters equal those of one adapt call."""
+    w = inputs.psi_workload(n, T, True, seed)
+    a = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    sa = a.adapt(O.make_params(seed=seed))
+    b = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    r0 = 0
+    tot = dict(collapses=0, flips=0, splits=0, moves=0)
+    iters = 0
+
+    def run(op, key):
+        nonlocal r0
+        st = op(O.make_params(seed=(seed + 0x9E3779B9 * r0) & 0xFFFFFFFF))
+        r0 += st["rounds"]
+        tot[key] += st[key]
+        return st[key]
+
+    for _ in range(O.make_params().max_iter):
+        iters += 1
+        changed = run(b.coarsen, "collapses") + run(b.swap, "flips") + run(b.refine, "splits")
+        b.renumber()
+        if changed == 0:
+            break
+    run(b.smooth, "moves")
+    assert iters >= 2
+    for x, y in zip(a.get_mesh(), b.get_mesh()):
+        assert x.shape == y.shape and np.array_equal(x.view(np.uint8), y.view(np.uint8))
+    for k, v in tot.items():
+        assert sa[k] == v, (k, sa[k], v)
+    assert sa["rounds"] == r0
+
+
 def test_operators_keep_invariants_round_by_round():
     w = inputs.psi_workload(21, 6000, True, 9)
     om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
