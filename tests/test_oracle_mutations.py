@@ -221,6 +221,14 @@ MUTATIONS = [
      "    renumber(*m);\n    if (n == 0) {\n      local.converged = 1;",
      "    if (n == 0) {\n      local.converged = 1;",
      "algorithm_1"),
+    ("independent set: seeds of later rounds by exclusive or",
+     "  uint32_t sr = seed + 0x9E3779B9u * r;",
+     "  uint32_t sr = seed ^ (0x9E3779B9u * r);",
+     "algorithm_1"),
+    ("smoothing: the plain centroid as the target",
+     "    double w00 = 0.5 * (m.m00[v] + m.m00[j]);\n    double w01 = 0.5 * (m.m01[v] + m.m01[j]);\n    double w11 = 0.5 * (m.m11[v] + m.m11[j]);",
+     "    double w00 = 1.0;\n    double w01 = 0.0;\n    double w11 = 1.0;",
+     "smoothing"),
     ("Algorithm 1: stops after one iteration",
      "    if (n == 0) {\n      local.converged = 1;",
      "    if (n >= 0) {\n      local.converged = 1;",
