@@ -67,7 +67,7 @@ def lib():
         L.or_fmix32.restype = C.c_uint32
         L.or_prio.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_prio.restype = C.c_uint32
-        L.or_independent_set.argtypes = [P, up, C.c_uint32, C.c_uint32, up]
+        L.or_independent_set.argtypes = [P, up, C.c_uint32, C.c_uint32, C.c_int32, up]
         L.or_colour.argtypes = [P, C.c_uint32, C.c_uint32, ip]
         L.or_colour.restype = C.c_int32
         L.or_coarsen_target.argtypes = [P, C.c_int32, C.POINTER(OrParams)]
@@ -219,10 +219,13 @@ class OracleMesh:
         lib().or_quality(self.h, _d(qs), _d(dxy), _d(dm))
         return float(qs[0]), dxy, dm
 
-    def independent_set(self, cand, seed, r):
+    def independent_set(self, cand, seed, r, by_colour=False):
+        """0/1 per vertex slot: the round-r set of the candidates `cand`
+        (by_colour: colour classes of the mesh's last colouring)."""
         cand = np.ascontiguousarray(cand, dtype=np.uint8)
         out = np.zeros(cand.shape[0], np.uint8)
-        lib().or_independent_set(self.h, _u(cand), seed & 0xFFFFFFFF, r & 0xFFFFFFFF, _u(out))
+        lib().or_independent_set(self.h, _u(cand), seed & 0xFFFFFFFF, r & 0xFFFFFFFF,
+                                 1 if by_colour else 0, _u(out))
         return out
 
     def colour(self, seed, r):

@@ -1551,15 +1551,18 @@ uint32_t or_fmix32(uint32_t h) { return fmix32(h); }
 uint32_t or_prio(uint32_t v, uint32_t seed, uint32_t r) { return prio(v, seed, r); }
 
 // Independent set of the given candidate flags on the current vertex graph,
-// with round counter r.  Writes 0/1 per vertex slot.
-int32_t or_independent_set(or_mesh* m, const uint8_t* cand, uint32_t seed, uint32_t r, uint8_t* inS) {
+// with round counter r (by_colour: among the candidates of colour r mod the
+// number of colours, from the mesh's last colouring).  Writes 0/1 per vertex
+// slot.
+int32_t or_independent_set(or_mesh* m, const uint8_t* cand, uint32_t seed, uint32_t r,
+                           int32_t by_colour, uint8_t* inS) {
   std::vector<uint8_t> inC(cand, cand + m->nv());
   std::vector<int> C;
   for (int v = 0; v < m->nv(); ++v)
     if (inC[v] && m->valive[v]) C.push_back(v);
   uint32_t keep = m->r;
   m->r = r;
-  std::vector<int> S = independent_set(*m, inC, C, seed);
+  std::vector<int> S = independent_set(*m, inC, C, seed, by_colour != 0);
   m->r = keep;
   std::memset(inS, 0, (size_t)m->nv());
   for (int v : S) inS[v] = 1;

@@ -49,6 +49,10 @@ MUTATIONS = [
      "    if (by_colour && m.col[v] != cls) continue;",
      "    if (false && by_colour && m.col[v] != cls) continue;",
      "colour_class_first_round"),
+    ("colour classes: neighbours of other classes compete",
+     "if (inC[u] && (!by_colour || m.col[u] == cls) && prio((uint32_t)u, seed, m.r) > pv) {",
+     "if (inC[u] && prio((uint32_t)u, seed, m.r) > pv) {",
+     "colour_class_round_takes_the_whole_class"),
     ("orientation sign: the rounded formula decides every case",
      "const double ORIENT_FILTER = 8.0 * 1.1102230246251565e-16;  // 8 eps",
      "const double ORIENT_FILTER = 0.0;  // 8 eps",

@@ -1109,6 +1109,28 @@ def test_colour_class_first_round_collapses_colour_zero_candidates():
     assert set(np.nonzero(om.get_raw()["valive"] == 0)[0].tolist()) == S
 
 
+def test_colour_class_round_takes_the_whole_class():
+    """Sec. 3.2: the classes of a proper colouring are independent sets, so
+    the round with counter r takes every candidate of colour r mod ncol and
+    nothing else, whatever their priorities against candidates of other
+    classes (which the hash rule alone would make lose: counted)."""
+    w = inputs.psi_workload(17, 1000, True, 3)
+    om = O.OracleMesh(w.xy, w.tri).set_metric(w.m)
+    seed = 4242
+    col, ncol = om.colour(seed, 0)
+    assert ncol >= 3
+    rng = np.random.default_rng(0)
+    lose = 0
+    for r in range(2 * ncol):
+        cand = (rng.random(col.shape[0]) < 0.7).astype(np.uint8)
+        cand[col < 0] = 0
+        S = om.independent_set(cand, seed, r, by_colour=True).astype(bool)
+        expect = (cand == 1) & (col == r % ncol)
+        assert np.array_equal(S, expect), r
+        lose += int((expect & ~om.independent_set(cand, seed, r).astype(bool)).sum())
+    assert lose > 10, lose
+
+
 @pytest.mark.parametrize("n,T,seed", [(17, 3000, 21), (25, 8000, 22)])
 def test_colour_class_adaptation_round_equals_sequential(n, T, seed):
     w = inputs.psi_workload(n, T, True, seed)
