@@ -69,6 +69,14 @@ MUTATIONS = [
      "double L2 = ((e00 * dx) * dx + ((2.0 * e01) * dx) * dy) + (e11 * dy) * dy;",
      "double L2 = ((e00 * dx) * dx + (e01 * dx) * dy) + (e11 * dy) * dy;",
      "rotated_anisotropic"),
+    ("metric length: the edge metric from one end only",
+     "  double e00 = 0.5 * (a.m00 + b.m00);\n  double e01 = 0.5 * (a.m01 + b.m01);\n  double e11 = 0.5 * (a.m11 + b.m11);\n  double dx = b.x - a.x;",
+     "  double e00 = a.m00;\n  double e01 = a.m01;\n  double e11 = a.m11;\n  double dx = b.x - a.x;",
+     "edge_length"),
+    ("quality: the shape factor without the reciprocal above the ideal perimeter",
+     "  double s = (xx <= 1.0) ? xx : 1.0 / xx;",
+     "  double s = xx;",
+     "quality_right_isosceles"),
     ("orientation: wrong vertex in the second product",
      "return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);",
      "return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - q.x);",
