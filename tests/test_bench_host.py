@@ -68,7 +68,7 @@ def test_oracle_arm_prints_one_json_line():
                         "d2h_bytes_per_step": 0}
 
 
-def test_oracle_arm_under_two_ranks_prints_once():
+def test_oracle_arm_under_two_ranks_prints_once(tmp_path):
     """Launched with two ranks, rank 0 alone runs the oracle arm and prints
     its line; the other rank exits 0 without work."""
     import socket
@@ -79,7 +79,8 @@ def test_oracle_arm_under_two_ranks_prints_once():
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
                         "--nproc-per-node", "2", "--master-addr", "127.0.0.1", "--master-port",
                         str(port), "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
-                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=900,
+                       env=dict(os.environ, TMPDIR=str(tmp_path)))
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
     assert len(lines) == 1, r.stdout[-2000:]
